@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput of the free-space Poisson solve: grid points per second per solve (N^3 / solve
+time) on the 4-anisotropic-Gaussian workload (box [-10, 10]^3, N = 256, padded 512^3),
+FP32 split-precision path, with the FP64 path, the per-pass HBM roofline, an end-to-end
+figure through the C-ABI on host buffers, and the FP64 CPU oracle as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one solve (all five passes).  Inputs are resident in HBM before the timed
+region; L2 (129 MB) is flushed by a 512 MB write between steps; each step is timed with
+CUDA events on the launching stream.  With --gpus N > 1 (torchrun, one rank per GPU)
+every rank solves its own density and rank 0 prints the aggregate (weak scaling; no
+data-path collective, the solves are independent).  --impl reference times the oracle
+(plain FP64 CPU implementation of the same discretisation) on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, L_BOX, TOL32, TOL64 = 256, 10.0, 1e-6, 1e-12
+METRIC = "grid pts/s per solve (N^3/s) FP32 vs FP64 at stated rel-L2 err; % HBM roofline"
+UNIT = "pts/s"
+PASSES = ["x_forward", "y_forward", "z_fwd_symbol_inv", "y_inverse", "x_inverse"]
+KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_inverse"]
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; a
+# source change makes the figure stale and it is reported as null.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fft_core.cuh", "passes.cuh"):
+        with open(os.path.join(ROOT, "paper_1612_01799_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def pass_bytes(N, s):
+    """Algorithmic DRAM bytes of each pass (each operand read or written once), s = bytes
+    per real value.  Complex workspace rows hold the N+1 Hermitian x frequencies."""
+    K = N + 1
+    c = 2 * s
+    return [N ** 3 * s + N * N * K * c,                 # x forward: rho in, w1 out
+            N * N * K * c + 2 * N * N * K * c,          # y forward: w1 in, w2 out
+            2 * (2 * N * N * K * c) + K ** 3 * s,       # z fused: w2 in, w3 out, symbol octant
+            2 * N * N * K * c + N * N * K * c,          # y inverse: w3 in, w1 out
+            N * N * K * c + N ** 3 * s]                 # x inverse: w1 in, u out
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_baseline(N, steps=1):
+    """The oracle as it stands on the host cores: setup once (untimed, as for the GPU plan),
+    then `steps` full solves of the same workload.  Returns (pts/s, cores, seconds)."""
+    from oracle import gtensor, solver as osolver
+    from paper_1612_01799_gb300 import densities as D
+    w = D.config_aniso4(N=N)
+    rho = w.sample()
+    plan = gtensor.make_plan(N, w.L, TOL32)
+    G = gtensor.symbol(plan)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        osolver.solve(rho, w.L, TOL32, plan=plan, G=G)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+    return steps * N ** 3 / dt, cores, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import gtensor, solver as osolver
+    from paper_1612_01799_gb300 import densities as D
+    N = args.N
+    w = D.config_aniso4(N=N)
+    rho = w.sample()
+    plan = gtensor.make_plan(N, w.L, TOL32)
+    G = gtensor.symbol(plan)
+    for _ in range(args.warmup):
+        osolver.solve(rho, w.L, TOL32, plan=plan, G=G)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        osolver.solve(rho, w.L, TOL32, plan=plan, G=G)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = N ** 3 / (ms / 1e3)
+    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+    sample = ("one full FP64 oracle solve per step of the N=%d workload (scipy FFT of the "
+              "padded %d^3 grid, symbol product, inverse FFT, crop); setup untimed" % (N, 2 * N))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(N, "f64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(N, dtype):
+    return {"workload": "aniso4_N%d: 4 anisotropic normalised Gaussians (seed 2), box [-10,10]^3, "
+                        "N=%d per axis, padded %d^3" % (N, N, 2 * N),
+            "N": N, "L": L_BOX, "tol": TOL32 if dtype == "f32" else TOL64, "dtype": dtype,
+            "l2": "flushed between steps (512 MB write)", "parallelism": "independent solves per GPU"}
+
+
+def time_solves(torch, plan, rho_t, out_t, steps, warmup, flush):
+    """Per-step event times (ms) of whole solves, and per-pass times from the same steps."""
+    for _ in range(warmup):
+        plan.solve_timed(rho_t, out_t)
+    torch.cuda.synchronize()
+    totals, passes = [], []
+    for _ in range(steps):
+        flush.zero_()
+        ms = plan.solve_timed(rho_t, out_t)  # events on the launching stream, synchronised
+        passes.append(ms)
+        totals.append(sum(ms))
+    return totals, passes
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1612_01799_gb300 import Plan, build
+    from paper_1612_01799_gb300 import densities as D
+    build.build()
+    N = args.N
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # Each rank solves its own density of the same family (weak scaling).
+    wl = D.config_aniso4(N=N, seed=2 + rank)
+    rho64 = wl.sample()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    results = {}
+    for dtype in ("f32", "f64"):
+        tol = TOL32 if dtype == "f32" else TOL64
+        plan = Plan(N, L_BOX, tol, dtype)
+        rho_t = torch.from_numpy(rho64.astype(plan.np_dtype)).to(dev)
+        out_t = torch.empty_like(rho_t)
+        steps = args.steps if dtype == "f32" else max(3, args.steps // 4)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev.index) if dtype == "f32" else None
+        if sampler:
+            sampler.__enter__()
+        totals, passes = time_solves(torch, plan, rho_t, out_t, steps, args.warmup, flush)
+        if sampler:
+            sampler.__exit__(None, None, None)
+        torch.cuda.synchronize()
+        ms = statistics.mean(totals)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
+        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps,
+                          "clocks": sampler.summary() if sampler else None, "plan": plan,
+                          "rho": rho_t, "out": out_t}
+
+    # End to end through the C-ABI on pinned host buffers (H2D + solve + D2H each step).
+    p32 = results["f32"]["plan"]
+    host_in = torch.from_numpy(rho64.astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        p32.solve_host(host_in, host_out)
+    t0 = time.perf_counter()
+    e2e_steps = args.steps
+    for _ in range(e2e_steps):
+        p32.solve_host(host_in, host_out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        peak, peak_kind = load_peaks()
+        r32 = results["f32"]
+        bytes32 = pass_bytes(N, 4)
+        dom = max(range(5), key=lambda i: r32["per_pass"][i])
+        gbs = [bytes32[i] / (r32["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
+        src_hash = kernel_source_hash()
+        traffic = NCU_TRAFFIC.get((src_hash, KERNEL_NAMES[dom], N))
+        r64 = results["f64"]
+        bytes64 = pass_bytes(N, 8)
+        gbs64 = [bytes64[i] / (r64["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
+        line = {
+            "metric": METRIC, "value": world * N ** 3 / (r32["ms"] * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(N, "f32"),
+            "roofline": {"bound": "hbm", "achieved": gbs[dom], "peak": peak, "unit": "GB/s",
+                         "frac": gbs[dom] / peak, "traffic": traffic,
+                         "kernel": KERNEL_NAMES[dom], "algorithmic_bytes": bytes32[dom],
+                         "peak_source": peak_kind},
+            "passes": [{"pass": PASSES[i], "kernel": KERNEL_NAMES[i], "ms": r32["per_pass"][i],
+                        "GB_s": gbs[i], "frac": gbs[i] / peak} for i in range(5)],
+            "f64": {"value": world * N ** 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
+                    "steps": r64["steps"],
+                    "passes": [{"pass": PASSES[i], "ms": r64["per_pass"][i], "GB_s": gbs64[i],
+                                "frac": gbs64[i] / peak} for i in range(5)]},
+            "e2e": {"value": world * N ** 3 / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": N ** 3 * 4, "d2h_bytes_per_step": N ** 3 * 4},
+            "gpu_launches": 5 * r32["steps"],
+            "clocks": r32["clocks"],
+        }
+        if not args.no_cpu_baseline and world == 1:
+            v, cores, dt = cpu_oracle_baseline(N, steps=args.cpu_steps)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": "%d full FP64 oracle solve(s) of the same N=%d workload "
+                                              "(setup untimed), %.1f s" % (args.cpu_steps, N, dt)}
+        print(json.dumps(line), flush=True)
+    for r in results.values():
+        r["plan"].close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,142 @@
+/*
+ * gspoisson: free-space Poisson solver on the GPU (Gaussian-sum FFT convolution).
+ *
+ * Solves -Laplace(u) = rho in R^3 with u -> 0 at infinity as u = U * rho,
+ * U(x) = 1/(4 pi |x|) (Exl, arXiv:1612.01799, Sec. 1, eqs. problem1 and conv), for a
+ * density sampled on the cube [-L, L]^3 with N cell-centred points per axis,
+ * x_i = -L + (i + 1/2) * 2L/N.
+ *
+ * Method (Sec. 2): after scaling the box by lambda = L to [-1, 1]^3,
+ *   u = lambda^2 (I_1 + I_delta),
+ * where I_1 is the convolution with the Gaussian-sum kernel
+ *   U_GS(y) = sum_j w_j exp(-tau_j^2 |y|^2)   (sinc quadrature, eq. approx)
+ * done with zero padding to (2N)^3 and the FFT, with the symbol (the G-tensor)
+ *   G_k = sum_j w_j prod_q A_j(k_q),  A_j(k) = 2 int_0^2 exp(-tau_j^2 t^2) cos(pi k t/2) dt,
+ * and I_delta = C0 rho + C2 Laplace(rho) is the Taylor near-zone correction inside the
+ * delta-ball (Sec. 2, last paragraph).  The correction enters the padded symbol as
+ * C0 - C2 |kappa|^2 with kappa = pi k / 2, so one solve is
+ *   u = lambda^2 Re IFFT_(2N)^3 [ G_tot . FFT_(2N)^3 (pad(rho)) ] cropped to N^3.
+ * delta follows the Sec. 3 heuristic: min_q (b_q - a_q)/(50 n_q), at least 1e-3.
+ * Setup (plan creation) is separate from the solve and a plan is reused for many
+ * solves (Sec. 3 and Sec. 4: the solver object is set up once per geometry).
+ *
+ * Conventions for every call:
+ *   - Return value: POISSON_OK (0) or a negative POISSON_ERR_* code; no call aborts
+ *     the process or traps the device.  poisson_strerror() names a code.
+ *   - Arrays: N^3 values, x fastest: index i + N*(j + N*k) for point (x_i, y_j, z_k).
+ *   - Streams are cudaStream_t values passed as void*; NULL is the legacy default stream.
+ *   - Device pointers must be device (or managed) memory of the plan's device.
+ *   - A plan may be used by one stream at a time: its workspace is shared by its solves.
+ */
+#ifndef GSPOISSON_POISSON_H
+#define GSPOISSON_POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct poisson_plan_s *poisson_plan;
+
+/* Arithmetic of the solve.  POISSON_F32: FP32 data, FFT butterflies and symbol table;
+ * twiddles and the symbol are computed in FP64 and rounded once.  POISSON_F64: FP64
+ * throughout. */
+typedef enum { POISSON_F32 = 0, POISSON_F64 = 1 } poisson_dtype;
+
+enum {
+    POISSON_OK = 0,
+    POISSON_ERR_ARG = -1,         /* invalid argument (null pointer, N, L, tol, dtype) */
+    POISSON_ERR_ALLOC = -2,       /* device or host allocation failed */
+    POISSON_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    POISSON_ERR_UNSUPPORTED = -4, /* N not in the supported set */
+    POISSON_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    POISSON_ERR_NUMERIC = -6      /* plan setup could not reach the requested accuracy */
+};
+
+/*
+ * Create a plan: the setup phase of Sec. 3 (delta, the Gaussian sum, the per-axis
+ * G-tensor factors by quadrature, C0 and C2, the symbol table, FFT twiddles) and the
+ * device workspace for solves.  Runs on the current CUDA device, synchronously.
+ *   out   [out] receives the plan; *out is set to NULL on failure.
+ *   N     points per axis: even, 4 <= N <= 1024, from poisson_supported_n().
+ *   L     half-width of the cube [-L, L]^3, L > 0 and L < 25 N (the Sec. 3 condition
+ *         lambda <= 25 min_q n_q that keeps delta inside the scaled box).
+ *   tol   requested accuracy of the Gaussian sum: eps = clamp(tol/10, 1e-14, 1e-7) is
+ *         the maximum relative error of U_GS on [delta, 2 sqrt(3)] (Sec. 2 and 3).
+ *   dtype POISSON_F32 or POISSON_F64.
+ * The plan owns its device memory; poisson_plan_destroy() frees it.
+ */
+int poisson_plan_create(poisson_plan *out, int N, double L, double tol, int dtype);
+
+/* Free a plan and its device memory.  NULL is accepted.  The caller must make sure no
+ * solve on the plan is still running (synchronise its stream first). */
+int poisson_plan_destroy(poisson_plan p);
+
+/*
+ * One solve (Sec. 2/3: I_1 by the padded FFT with the symbol, plus the near-zone
+ * correction folded into the symbol), entirely on the device and stream ordered:
+ * no host synchronisation and no host<->device traffic.
+ *   rho_d  device pointer to N^3 values of the plan's dtype (input density).
+ *   u_d    device pointer to N^3 values of the plan's dtype (output potential); may
+ *          equal rho_d.
+ *   stream cudaStream_t as void*.
+ * The caller owns both buffers.  Launch errors are reported; errors of kernels still
+ * running are reported by the next synchronising call.
+ */
+int poisson_solve(poisson_plan p, const void *rho_d, void *u_d, void *stream);
+
+/*
+ * The same solve on host buffers: copies rho_h to the device, solves, copies u back
+ * and synchronises the stream before returning.  rho_h, u_h: host pointers to N^3
+ * values of the plan's dtype (pinned memory gives full copy bandwidth).  Uses the
+ * plan's own device staging buffers.
+ */
+int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream);
+
+/*
+ * Solves of several independent densities, possibly of different N, in stream order.
+ * plans[i], rho_d[i], u_d[i] as for poisson_solve; all plans on the current device.
+ * count >= 0.  A plan must not appear twice in one call (its workspace is shared).
+ */
+int poisson_solve_batched(int count, const poisson_plan *plans, const void *const *rho_d,
+                          void *const *u_d, void *stream);
+
+/*
+ * Per-pass device times of one solve, in milliseconds, measured with CUDA events
+ * recorded on `stream` around each of the five passes (x forward, y forward, z
+ * forward + symbol + z inverse, y inverse, x inverse).  ms[5] receives them.  The call
+ * synchronises the stream.  Same arguments and aliasing rules as poisson_solve.
+ */
+int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d, void *stream, float *ms);
+
+/*
+ * Facts of a plan, for checks and reports.  Any output pointer may be NULL.
+ *   delta       near-zone radius in scaled coordinates (Sec. 3 heuristic).
+ *   eps         Gaussian-sum accuracy actually requested.
+ *   n_terms     S + 1, the number of Gaussian-sum terms.
+ *   c0, c2      near-zone constants of I_delta = C0 rho + C2 Laplace(rho).
+ *   ws_bytes    device workspace of one solve.
+ *   table_bytes device bytes of the symbol table and twiddles.
+ */
+int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, double *c0,
+                      double *c2, size_t *ws_bytes, size_t *table_bytes);
+
+/* Copy the Gaussian sum of a plan: tau[j], w[j] for j < min(cap, n_terms). */
+int poisson_plan_gauss_sum(poisson_plan p, double *tau, double *w, int cap);
+
+/* Copy the per-axis G-tensor factors A_j(k), k = 0..N, row-major (n_terms x (N+1)),
+ * into a[cap] (cap in doubles). */
+int poisson_plan_axis_table(poisson_plan p, double *a, size_t cap);
+
+/* 1 if N is supported (even, 4..1024, with a compiled FFT plan for N and 2N), else 0. */
+int poisson_supported_n(int N);
+
+/* Human-readable name of a return code. */
+const char *poisson_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSPOISSON_POISSON_H */

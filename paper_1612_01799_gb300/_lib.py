@@ -1,0 +1,62 @@
+"""ctypes binding of libgspoisson.so: signatures of include/poisson.h, nothing more."""
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgspoisson.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "poisson.h")
+
+F32, F64 = 0, 1
+OK = 0
+ERRORS = {-1: "POISSON_ERR_ARG", -2: "POISSON_ERR_ALLOC", -3: "POISSON_ERR_CUDA",
+          -4: "POISSON_ERR_UNSUPPORTED", -5: "POISSON_ERR_TIMEOUT", -6: "POISSON_ERR_NUMERIC"}
+
+_lock = threading.Lock()
+_lib = None
+
+c_int, c_double, c_size_t, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+P = ctypes.POINTER
+
+SIGNATURES = {
+    "poisson_plan_create": (c_int, [P(c_void_p), c_int, c_double, c_double, c_int]),
+    "poisson_plan_destroy": (c_int, [c_void_p]),
+    "poisson_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "poisson_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "poisson_solve_batched": (c_int, [c_int, P(c_void_p), P(c_void_p), P(c_void_p), c_void_p]),
+    "poisson_solve_timed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(ctypes.c_float)]),
+    "poisson_plan_info": (c_int, [c_void_p, P(c_double), P(c_double), P(c_int), P(c_double),
+                                  P(c_double), P(c_size_t), P(c_size_t)]),
+    "poisson_plan_gauss_sum": (c_int, [c_void_p, P(c_double), P(c_double), c_int]),
+    "poisson_plan_axis_table": (c_int, [c_void_p, P(c_double), c_size_t]),
+    "poisson_supported_n": (c_int, [c_int]),
+    "poisson_strerror": (ctypes.c_char_p, [c_int]),
+}
+
+
+class PoissonError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "unknown"), code))
+
+
+def load():
+    """Load the in-tree library.  There is no fallback: without it nothing can run."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libgspoisson.so is not built (%s); run "
+                                  "paper_1612_01799_gb300.build.build() first" % LIB_PATH)
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(rc, what):
+    if rc != OK:
+        raise PoissonError(rc, what)

@@ -1,0 +1,160 @@
+"""Python front of the C-ABI.  Argument marshalling only: every step of a solve runs in
+the CUDA kernels of libgspoisson.so.  torch supplies device memory and streams."""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+DTYPES = {"f32": _lib.F32, "f64": _lib.F64}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def supported_n(N):
+    return bool(_lib.load().poisson_supported_n(int(N)))
+
+
+class Plan:
+    """A solve plan for the cube [-L, L]^3 with N cell-centred points per axis
+    (setup phase: Gaussian sum, G-tensor factors, near-zone constants, symbol table)."""
+
+    def __init__(self, N, L, tol, dtype="f32"):
+        if dtype not in DTYPES:
+            raise ValueError("dtype must be 'f32' or 'f64'")
+        self.N, self.L, self.tol, self.dtype = int(N), float(L), float(tol), dtype
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.poisson_plan_create(ctypes.byref(self._h), self.N, self.L, self.tol,
+                                                 DTYPES[dtype]), "poisson_plan_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def torch_dtype(self):
+        torch = _torch()
+        return torch.float32 if self.dtype == "f32" else torch.float64
+
+    @property
+    def np_dtype(self):
+        return np.float32 if self.dtype == "f32" else np.float64
+
+    def _check_tensor(self, t, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if t.dtype != self.torch_dtype or t.numel() != self.N ** 3 or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor of N^3 = %d values"
+                             % (name, self.torch_dtype, self.N ** 3))
+
+    def solve(self, rho, out=None, stream=None):
+        """u = U * rho on the device; rho, out: contiguous CUDA tensors of N^3 values."""
+        self._check_tensor(rho, "rho")
+        if out is None:
+            out = _torch().empty_like(rho)
+        self._check_tensor(out, "out")
+        _lib.check(self._lib.poisson_solve(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+                   "poisson_solve")
+        return out
+
+    def solve_host(self, rho, out=None, stream=None):
+        """The same solve on host memory (numpy array or CPU tensor; pinned is fastest)."""
+        torch = _torch()
+        if isinstance(rho, np.ndarray):
+            rho = np.ascontiguousarray(rho, dtype=self.np_dtype)
+            if rho.size != self.N ** 3:
+                raise ValueError("rho must hold N^3 values")
+            if out is None:
+                out = np.empty_like(rho)
+            pin, pout = rho.ctypes.data, out.ctypes.data
+        else:
+            if rho.is_cuda or rho.dtype != self.torch_dtype or rho.numel() != self.N ** 3:
+                raise ValueError("rho must be a CPU tensor of N^3 values of the plan's dtype")
+            rho = rho.contiguous()
+            if out is None:
+                out = torch.empty_like(rho)
+            pin, pout = rho.data_ptr(), out.data_ptr()
+        _lib.check(self._lib.poisson_solve_host(self._h, ctypes.c_void_p(pin), ctypes.c_void_p(pout),
+                                                _stream_handle(stream)), "poisson_solve_host")
+        return out
+
+    def solve_timed(self, rho, out, stream=None):
+        """Solve and return the five per-pass device times (ms) from CUDA events."""
+        self._check_tensor(rho, "rho")
+        self._check_tensor(out, "out")
+        ms = (ctypes.c_float * 5)()
+        _lib.check(self._lib.poisson_solve_timed(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr()),
+                                                 _stream_handle(stream), ms), "poisson_solve_timed")
+        return list(ms)
+
+    def info(self):
+        d, e, c0, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int()
+        ws, tb = ctypes.c_size_t(), ctypes.c_size_t()
+        _lib.check(self._lib.poisson_plan_info(self._h, ctypes.byref(d), ctypes.byref(e), ctypes.byref(n),
+                                               ctypes.byref(c0), ctypes.byref(c2), ctypes.byref(ws),
+                                               ctypes.byref(tb)), "poisson_plan_info")
+        return {"delta": d.value, "eps": e.value, "n_terms": n.value, "C0": c0.value, "C2": c2.value,
+                "ws_bytes": ws.value, "table_bytes": tb.value}
+
+    def gauss_sum(self):
+        n = self.info()["n_terms"]
+        tau, w = np.empty(n), np.empty(n)
+        _lib.check(self._lib.poisson_plan_gauss_sum(
+            self._h, tau.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n), "poisson_plan_gauss_sum")
+        return tau, w
+
+    def axis_table(self):
+        n = self.info()["n_terms"]
+        a = np.empty((n, self.N + 1))
+        _lib.check(self._lib.poisson_plan_axis_table(
+            self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size), "poisson_plan_axis_table")
+        return a
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.poisson_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def solve_batched(plans, rhos, outs, stream=None):
+    """Independent solves (uneven N allowed) through poisson_solve_batched."""
+    n = len(plans)
+    if not (len(rhos) == len(outs) == n):
+        raise ValueError("plans, rhos and outs must have the same length")
+    for p, r, o in zip(plans, rhos, outs):
+        p._check_tensor(r, "rho")
+        p._check_tensor(o, "out")
+    H = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    R = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    lib = _lib.load()
+    _lib.check(lib.poisson_solve_batched(n, H, R, O, _stream_handle(stream)), "poisson_solve_batched")
+    return outs

@@ -1,0 +1,72 @@
+"""Build the CUDA library libgspoisson.so in-tree for sm_103a.
+
+Each translation unit is compiled by nvcc in its own process (in parallel), then linked
+into paper_1612_01799_gb300/libgspoisson.so.  Objects go to _build/ at the repo root.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+OUT = os.path.join(PKG, "libgspoisson.so")
+BUILD = os.path.join(ROOT, "_build")
+SOURCES = ["capi.cpp", "setup.cpp", "passes_f32.cu", "passes_f64.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc():
+    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cand):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libgspoisson")
+    return cand
+
+
+def _deps(src):
+    """Sources and headers whose change forces a rebuild of src."""
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    return [os.path.join(CSRC, src), os.path.join(ROOT, "include", "poisson.h")] + hdrs
+
+
+def _stale(target, deps):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force=False, verbose=False, extra_flags=()):
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH + list(extra_flags)
+    jobs = []
+    for src in SOURCES:
+        obj = os.path.join(BUILD, src + ".o")
+        if force or _stale(obj, _deps(src)):
+            cmd = [nvcc] + flags + ["-I", os.path.join(ROOT, "include"), "-c",
+                                    os.path.join(CSRC, src), "-o", obj]
+            jobs.append(cmd)
+    objs = [os.path.join(BUILD, s + ".o") for s in SOURCES]
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        if verbose:
+            sys.stderr.write(r.stderr)
+
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            list(ex.map(run, jobs))
+    if force or jobs or _stale(OUT, objs):
+        tmp = OUT + ".%d.tmp" % os.getpid()
+        run([nvcc, "-shared"] + ARCH + ["-o", tmp] + objs)
+        os.replace(tmp, OUT)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,267 @@
+// C-ABI of the solver (include/poisson.h): plan creation (setup phase), solves, facts.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/poisson.h"
+#include "setup.h"
+#include "solver.h"
+
+namespace gsp {
+cudaError_t solve_f32(const DevicePlan &, const void *, void *, cudaStream_t, cudaEvent_t *);
+cudaError_t solve_f64(const DevicePlan &, const void *, void *, cudaStream_t, cudaEvent_t *);
+cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *, int, double,
+                             double, double, cudaStream_t);
+cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
+                             double, double, cudaStream_t);
+
+static const int kSupportedN[] = {4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 1024};
+
+bool n_supported(int N) {
+    for (int n : kSupportedN)
+        if (n == N) return true;
+    return false;
+}
+
+cudaError_t launch_solve(const DevicePlan &p, const void *rho, void *u, cudaStream_t s,
+                         cudaEvent_t *ev) {
+    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, s, ev) : solve_f64(p, rho, u, s, ev);
+}
+
+cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
+                                int nterms, double C0, double C2, double scale, cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? symbol_table_f32(p, dA, dw, nterms, C0, C2, scale, s)
+                                  : symbol_table_f64(p, dA, dw, nterms, C0, C2, scale, s);
+}
+}  // namespace gsp
+
+struct poisson_plan_s {
+    gsp::HostTables ht;
+    gsp::DevicePlan dp;
+    int device = 0;
+    size_t elem = 0;         // bytes per real value
+    size_t ws_bytes = 0;
+    size_t table_bytes = 0;
+    void *stage_in = nullptr;   // device staging for poisson_solve_host
+    void *stage_out = nullptr;
+    cudaEvent_t ev[6] = {};
+    bool have_events = false;
+};
+
+static int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return POISSON_OK;
+    if (e == cudaErrorMemoryAllocation) return POISSON_ERR_ALLOC;
+    return POISSON_ERR_CUDA;
+}
+
+static void free_plan(poisson_plan p) {
+    if (!p) return;
+    void *bufs[] = {p->dp.sym, p->dp.tw, p->dp.w1, p->dp.w2, p->dp.w3, p->stage_in, p->stage_out};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (p->have_events)
+        for (auto &e : p->ev) cudaEventDestroy(e);
+    delete p;
+}
+
+extern "C" int poisson_supported_n(int N) { return gsp::n_supported(N) ? 1 : 0; }
+
+extern "C" const char *poisson_strerror(int code) {
+    switch (code) {
+        case POISSON_OK: return "ok";
+        case POISSON_ERR_ARG: return "invalid argument";
+        case POISSON_ERR_ALLOC: return "allocation failed";
+        case POISSON_ERR_CUDA: return "CUDA error";
+        case POISSON_ERR_UNSUPPORTED: return "unsupported size";
+        case POISSON_ERR_TIMEOUT: return "device wait timed out";
+        case POISSON_ERR_NUMERIC: return "requested accuracy not reachable";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double tol, int dtype) {
+    if (!out) return POISSON_ERR_ARG;
+    *out = nullptr;
+    if (dtype != POISSON_F32 && dtype != POISSON_F64) return POISSON_ERR_ARG;
+    if (N < 4 || N > 1024 || (N & 1)) return POISSON_ERR_ARG;
+    if (!gsp::n_supported(N)) return POISSON_ERR_UNSUPPORTED;
+    poisson_plan p = new (std::nothrow) poisson_plan_s();
+    if (!p) return POISSON_ERR_ALLOC;
+    int rc = gsp::build_host_tables(N, L, tol, p->ht);
+    if (rc != POISSON_OK) {
+        delete p;
+        return rc;
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return map_cuda(e);
+    }
+    p->elem = dtype == POISSON_F32 ? 4 : 8;
+    p->dp.N = N;
+    p->dp.dtype = dtype;
+    p->dp.Px = gsp::pitch_for(N);
+    const size_t cx = 2 * p->elem;
+    const size_t K = (size_t)N + 1;
+    const size_t sym_bytes = K * K * K * p->elem;
+    const size_t tw_bytes = (size_t)2 * N * cx;
+    const size_t w1_bytes = (size_t)N * N * p->dp.Px * cx;
+    const size_t w2_bytes = (size_t)N * 2 * N * p->dp.Px * cx;
+    p->ws_bytes = w1_bytes + 2 * w2_bytes;
+    p->table_bytes = sym_bytes + tw_bytes;
+
+    double *dA = nullptr, *dw = nullptr;
+    auto fail = [&](cudaError_t err) {
+        if (dA) cudaFree(dA);
+        if (dw) cudaFree(dw);
+        free_plan(p);
+        return map_cuda(err);
+    };
+    if ((e = cudaMalloc(&p->dp.sym, sym_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&p->dp.tw, tw_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&p->dp.w1, w1_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&p->dp.w2, w2_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&p->dp.w3, w2_bytes)) != cudaSuccess) return fail(e);
+
+    // Twiddles W_{2N}^e from FP64 (long double arithmetic), rounded once to the dtype.
+    std::vector<double> tw;
+    gsp::twiddles(2 * N, tw);
+    if (dtype == POISSON_F32) {
+        std::vector<float> twf(tw.begin(), tw.end());
+        e = cudaMemcpy(p->dp.tw, twf.data(), tw_bytes, cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(p->dp.tw, tw.data(), tw_bytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail(e);
+
+    // Symbol octant on the device, in FP64, from the per-axis factors.
+    const int nterms = (int)p->ht.tau.size();
+    if ((e = cudaMalloc(&dA, p->ht.A.size() * sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&dw, p->ht.w.size() * sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(dA, p->ht.A.data(), p->ht.A.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpy(dw, p->ht.w.data(), p->ht.w.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    const double M = 2.0 * N;
+    const double scale = p->ht.lambda * p->ht.lambda / (M * M * M);
+    if ((e = gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0)) !=
+        cudaSuccess)
+        return fail(e);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
+    cudaFree(dA);
+    cudaFree(dw);
+    dA = dw = nullptr;
+    *out = p;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_plan_destroy(poisson_plan p) {
+    free_plan(p);
+    return POISSON_OK;
+}
+
+static int check_solve_args(poisson_plan p, const void *rho, const void *u) {
+    if (!p || !rho || !u) return POISSON_ERR_ARG;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_solve(poisson_plan p, const void *rho_d, void *u_d, void *stream) {
+    int rc = check_solve_args(p, rho_d, u_d);
+    if (rc) return rc;
+    return map_cuda(gsp::launch_solve(p->dp, rho_d, u_d, (cudaStream_t)stream, nullptr));
+}
+
+extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream) {
+    int rc = check_solve_args(p, rho_h, u_h);
+    if (rc) return rc;
+    const size_t n = (size_t)p->dp.N * p->dp.N * p->dp.N * p->elem;
+    cudaError_t e;
+    if (!p->stage_in) {
+        if ((e = cudaMalloc(&p->stage_in, n)) != cudaSuccess) return map_cuda(e);
+    }
+    if (!p->stage_out) {
+        if ((e = cudaMalloc(&p->stage_out, n)) != cudaSuccess) return map_cuda(e);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(p->stage_in, rho_h, n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = gsp::launch_solve(p->dp, p->stage_in, p->stage_out, s, nullptr)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaMemcpyAsync(u_h, p->stage_out, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return map_cuda(e);
+    return map_cuda(cudaStreamSynchronize(s));
+}
+
+extern "C" int poisson_solve_batched(int count, const poisson_plan *plans,
+                                     const void *const *rho_d, void *const *u_d, void *stream) {
+    if (count < 0) return POISSON_ERR_ARG;
+    if (count == 0) return POISSON_OK;
+    if (!plans || !rho_d || !u_d) return POISSON_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        int rc = check_solve_args(plans[i], rho_d[i], u_d[i]);
+        if (rc) return rc;
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return POISSON_ERR_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        cudaError_t e =
+            gsp::launch_solve(plans[i]->dp, rho_d[i], u_d[i], (cudaStream_t)stream, nullptr);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    return POISSON_OK;
+}
+
+extern "C" int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d, void *stream,
+                                   float *ms) {
+    int rc = check_solve_args(p, rho_d, u_d);
+    if (rc) return rc;
+    if (!ms) return POISSON_ERR_ARG;
+    cudaError_t e;
+    if (!p->have_events) {
+        for (int i = 0; i < 6; ++i)
+            if ((e = cudaEventCreate(&p->ev[i])) != cudaSuccess) return map_cuda(e);
+        p->have_events = true;
+    }
+    if ((e = gsp::launch_solve(p->dp, rho_d, u_d, (cudaStream_t)stream, p->ev)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaEventSynchronize(p->ev[5])) != cudaSuccess) return map_cuda(e);
+    for (int i = 0; i < 5; ++i)
+        if ((e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1])) != cudaSuccess)
+            return map_cuda(e);
+    return POISSON_OK;
+}
+
+extern "C" int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms,
+                                 double *c0, double *c2, size_t *ws_bytes, size_t *table_bytes) {
+    if (!p) return POISSON_ERR_ARG;
+    if (delta) *delta = p->ht.delta;
+    if (eps) *eps = p->ht.eps;
+    if (n_terms) *n_terms = (int)p->ht.tau.size();
+    if (c0) *c0 = p->ht.C0;
+    if (c2) *c2 = p->ht.C2;
+    if (ws_bytes) *ws_bytes = p->ws_bytes;
+    if (table_bytes) *table_bytes = p->table_bytes;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_plan_gauss_sum(poisson_plan p, double *tau, double *w, int cap) {
+    if (!p || cap < 0 || (cap > 0 && (!tau || !w))) return POISSON_ERR_ARG;
+    const int n = std::min(cap, (int)p->ht.tau.size());
+    for (int j = 0; j < n; ++j) {
+        tau[j] = p->ht.tau[j];
+        w[j] = p->ht.w[j];
+    }
+    return POISSON_OK;
+}
+
+extern "C" int poisson_plan_axis_table(poisson_plan p, double *a, size_t cap) {
+    if (!p || (cap > 0 && !a)) return POISSON_ERR_ARG;
+    const size_t n = std::min(cap, p->ht.A.size());
+    if (n) std::memcpy(a, p->ht.A.data(), n * sizeof(double));
+    return POISSON_OK;
+}

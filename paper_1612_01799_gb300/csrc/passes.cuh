@@ -1,0 +1,340 @@
+// The five passes of one solve (Exl, arXiv:1612.01799, Sec. 2/3: zero-padded FFT
+// convolution with the G-tensor plus the near-zone correction, crop to N^3), templated
+// on the arithmetic type and N.  Included by one .cu file per type.
+//
+//   K1 x forward   rho [z][y][x] (N reals per row)  -> w1 [z][y][kx <= N]
+//                  length-2N real DFT of the zero-padded row as an N-point complex FFT of
+//                  the (even, odd) pairs (pruned: the upper N/2 pairs are zero), then the
+//                  standard split into the N+1 Hermitian bins.
+//   K2 y forward   w1 -> w2 [z][ky < 2N][kx]    length 2N, upper half of the input zero
+//   K3 z fused     w2 -> w3 [z < N][ky][kx]     length 2N forward (upper half zero),
+//                  product with the symbol G_tot(|kx|, |ky|, |kz|) scaled by
+//                  lambda^2/(2N)^3, length 2N inverse keeping the lower half.  The
+//                  (2N)^3 spectrum exists only in shared memory.
+//   K4 y inverse   w3 -> w1 [z][y < N][kx]      length 2N inverse, lower half kept
+//   K5 x inverse   w1 -> u [z][y][x]            N+1 Hermitian bins -> N-point complex
+//                  inverse FFT of the (even, odd) pairs, lower N/2 pairs kept (the crop).
+#pragma once
+#include "fft_core.cuh"
+#include "solver.h"
+
+namespace gsp {
+
+// Per-thread element count E and radix sequence of a length-L transform.
+template <int L> struct FftCfg;
+#define GSP_FFT_CFG(LL, EE, ...)                  \
+    template <> struct FftCfg<LL> {              \
+        static constexpr int E = EE;             \
+        using Rs = Radices<__VA_ARGS__>;         \
+    }
+GSP_FFT_CFG(4, 4, 4);
+GSP_FFT_CFG(8, 8, 8);
+GSP_FFT_CFG(16, 16, 16);
+GSP_FFT_CFG(32, 8, 8, 4);
+GSP_FFT_CFG(48, 12, 4, 4, 3);
+GSP_FFT_CFG(64, 8, 8, 8);
+GSP_FFT_CFG(80, 20, 4, 4, 5);
+GSP_FFT_CFG(96, 24, 8, 4, 3);
+GSP_FFT_CFG(128, 16, 16, 8);
+GSP_FFT_CFG(160, 20, 4, 4, 5, 2);
+GSP_FFT_CFG(192, 24, 8, 8, 3);
+GSP_FFT_CFG(256, 16, 16, 16);
+GSP_FFT_CFG(320, 20, 4, 4, 4, 5);
+GSP_FFT_CFG(384, 24, 8, 8, 6);
+GSP_FFT_CFG(512, 16, 16, 8, 4);
+GSP_FFT_CFG(640, 20, 4, 4, 4, 5, 2);
+GSP_FFT_CFG(768, 24, 8, 8, 6, 2);
+GSP_FFT_CFG(1024, 16, 16, 16, 4);
+GSP_FFT_CFG(2048, 16, 16, 16, 8);
+#undef GSP_FFT_CFG
+
+// Columns per CTA of a column pass: 128-byte row segments (16 FP32 or 8 FP64 complex),
+// halved until the block has <= 1024 threads and <= 128 KB of shared memory.
+template <typename Real, int L> __host__ __device__ constexpr int col_tc() {
+    int tc = sizeof(Real) == 4 ? 16 : 8;
+    const int P = L / FftCfg<L>::E;
+    while (tc > 1 && (tc * P > 1024 || tc * L * 2 * (int)sizeof(Real) > 131072)) tc /= 2;
+    return tc;
+}
+// Rows per CTA of an x pass (shared tile (N+1) x (TR+1) complex).
+template <typename Real, int L> __host__ __device__ constexpr int row_tr() {
+    int tr = sizeof(Real) == 4 ? 16 : 8;
+    const int P = L / FftCfg<L>::E;
+    while (tr > 1 && (tr * P > 1024 || (L + 1) * (tr + 1) * 2 * (int)sizeof(Real) > 163840)) tr /= 2;
+    return tr;
+}
+
+template <typename T2> __device__ __forceinline__ T2 ldg2(const T2 *p) { return __ldg(p); }
+
+// ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
+template <typename Real, int N>
+__global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
+k_x_forward(const Real *__restrict__ rho, typename CxT<Real>::T *__restrict__ out,
+            const typename CxT<Real>::T *__restrict__ tw, int nrows, int Px) {
+    using T2 = typename CxT<Real>::T;
+    constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *sm = reinterpret_cast<T2 *>(smraw);  // (N + 1) x SP
+    const int t = threadIdx.x;
+    const long long r0 = (long long)blockIdx.x * TR;
+    const int nr = (int)min((long long)TR, (long long)nrows - r0);
+    // The tile is nr consecutive rows of N reals: contiguous N/2-pair chunks.
+    const T2 *src = reinterpret_cast<const T2 *>(rho) + r0 * (N / 2);
+    for (int e = t; e < nr * (N / 2); e += NT) {
+        const int r = e / (N / 2), m = e - r * (N / 2);
+        sm[m * SP + r] = ldg2(src + e);
+    }
+    __syncthreads();
+    const int c = t % TR, q = t / TR;
+    T2 v[E];
+    Stages<T2, N, E, -1, 1, typename FftCfg<N>::Rs>::template run<true, false, true>(
+        v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
+        [&](int row, T2 x) { sm[row * SP + c] = x; });
+    __syncthreads();
+    // C = FFT_N(pairs).  With Ev_k = (C_k + conj C_{N-k})/2 (DFT of the even samples) and
+    // Od_k = (C_k - conj C_{N-k})/(2i) (odd samples): X_k = Ev_k + W_{2N}^k Od_k,
+    // X_{N-k} = conj(Ev_k - W_{2N}^k Od_k), X_0 = Ev_0 + Od_0, X_N = Ev_0 - Od_0.
+    for (int e = t; e < TR * (N / 2 + 1); e += NT) {
+        const int r = e % TR, k = e / TR;
+        if (r >= nr) continue;
+        const T2 ck = sm[k * SP + r];
+        const T2 cn = sm[((N - k) % N) * SP + r];
+        const T2 ev = cscale(cadd(ck, conj(cn)), (Real)0.5);
+        const T2 od = cscale(rot<-1>(csub(ck, conj(cn))), (Real)0.5);
+        if (k == 0) {
+            sm[r] = mk<T2>(ev.x + od.x, (Real)0);
+            sm[N * SP + r] = mk<T2>(ev.x - od.x, (Real)0);
+        } else {
+            const T2 wo = cmul(ldg2(tw + k), od);
+            sm[k * SP + r] = cadd(ev, wo);
+            if (2 * k != N) sm[(N - k) * SP + r] = conj(csub(ev, wo));
+        }
+    }
+    __syncthreads();
+    T2 *dst = out + r0 * Px;
+    for (int e = t; e < nr * (N + 1); e += NT) {
+        const int r = e / (N + 1), k = e - r * (N + 1);
+        dst[(long long)r * Px + k] = sm[k * SP + r];
+    }
+}
+
+// ---- K2 / K4: y transform over columns kx --------------------------------------------
+// FWD: rows < L/2 of the input are nonzero, all L outputs stored.
+// !FWD: all L inputs, outputs < L/2 stored.
+template <typename Real, int L, bool FWD>
+__global__ void __launch_bounds__(col_tc<Real, L>() * (L / FftCfg<L>::E))
+k_col(const typename CxT<Real>::T *__restrict__ in, typename CxT<Real>::T *__restrict__ out,
+      const typename CxT<Real>::T *__restrict__ tw, int ncols, long long in_row,
+      long long in_outer, long long out_row, long long out_outer) {
+    using T2 = typename CxT<Real>::T;
+    constexpr int E = FftCfg<L>::E, TC = col_tc<Real, L>();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *sm = reinterpret_cast<T2 *>(smraw);  // L x TC
+    const int c = threadIdx.x % TC, q = threadIdx.x / TC;
+    const int col = blockIdx.x * TC + c;
+    const bool valid = col < ncols;
+    const T2 *src = in + (long long)blockIdx.y * in_outer + col;
+    T2 *dst = out + (long long)blockIdx.y * out_outer + col;
+    T2 v[E];
+    Stages<T2, L, E, FWD ? -1 : 1, 1, typename FftCfg<L>::Rs>::template run<FWD, !FWD, false>(
+        v, q, c, sm, TC, tw, 1,
+        [&](int row) { return valid ? ldg2(src + row * in_row) : czero<T2>(); },
+        [&](int row, T2 x) {
+            if (valid) dst[row * out_row] = x;
+        });
+}
+
+// ---- K3: z forward, symbol, z inverse --------------------------------------------------
+template <typename Real, int L>
+__global__ void __launch_bounds__(col_tc<Real, L>() * (L / FftCfg<L>::E))
+k_z_symbol(const typename CxT<Real>::T *__restrict__ in, typename CxT<Real>::T *__restrict__ out,
+           const Real *__restrict__ sym, const typename CxT<Real>::T *__restrict__ tw, int ncols,
+           int Px) {
+    using T2 = typename CxT<Real>::T;
+    constexpr int N = L / 2, E = FftCfg<L>::E, TC = col_tc<Real, L>();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *sm = reinterpret_cast<T2 *>(smraw);  // L x TC
+    const int c = threadIdx.x % TC, q = threadIdx.x / TC;
+    const int col = blockIdx.x * TC + c;
+    const bool valid = col < ncols;
+    // Consecutive blocks take ky and its mirror 2N - ky, which read the same symbol rows.
+    const int by = blockIdx.y;
+    const int ky = (by & 1) ? L - ((by + 1) >> 1) : (by >> 1);
+    const int kya = ky <= N ? ky : L - ky;
+    const long long zs = (long long)L * Px;  // z stride of w2 / w3
+    const T2 *src = in + (long long)ky * Px + col;
+    T2 *dst = out + (long long)ky * Px + col;
+    const long long plane = (long long)(N + 1) * (N + 1);
+    const Real *srow = sym + (long long)kya * (N + 1) + (valid ? col : 0);
+    T2 v[E];
+    Stages<T2, L, E, -1, 1, typename FftCfg<L>::Rs>::template run<true, false, true>(
+        v, q, c, sm, TC, tw, 1,
+        [&](int row) { return valid ? ldg2(src + row * zs) : czero<T2>(); },
+        [&](int row, T2 x) { sm[row * TC + c] = x; });
+    __syncthreads();
+    Stages<T2, L, E, 1, 1, typename FftCfg<L>::Rs>::template run<false, true, false>(
+        v, q, c, sm, TC, tw, 1,
+        [&](int row) {
+            const int kz = row <= N ? row : L - row;
+            const Real g = valid ? __ldg(srow + kz * plane) : (Real)0;
+            return cscale(sm[row * TC + c], g);
+        },
+        [&](int row, T2 x) {
+            if (valid) dst[row * zs] = x;
+        });
+}
+
+// ---- K5: x inverse (Hermitian N+1 bins -> N real samples) -------------------------------
+template <typename Real, int N>
+__global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
+k_x_inverse(const typename CxT<Real>::T *__restrict__ in, Real *__restrict__ u,
+            const typename CxT<Real>::T *__restrict__ tw, int nrows, int Px) {
+    using T2 = typename CxT<Real>::T;
+    constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *sm = reinterpret_cast<T2 *>(smraw);  // (N + 1) x SP
+    const int t = threadIdx.x;
+    const long long r0 = (long long)blockIdx.x * TR;
+    const int nr = (int)min((long long)TR, (long long)nrows - r0);
+    const T2 *src = in + r0 * Px;
+    for (int e = t; e < nr * (N + 1); e += NT) {
+        const int r = e / (N + 1), k = e - r * (N + 1);
+        sm[k * SP + r] = ldg2(src + (long long)r * Px + k);
+    }
+    __syncthreads();
+    // Y_k, k = 0..N (Y_0, Y_N real) -> C_k = Ev_k + i Od_k with Ev_k = Y_k + conj Y_{N-k}
+    // and Od_k = (Y_k - conj Y_{N-k}) W_{2N}^{-k}; the inverse N-point FFT of C gives
+    // y_{2m} + i y_{2m+1}.  C_{N-k} = conj(Ev_k) + i conj(Od_k).
+    for (int e = t; e < TR * (N / 2 + 1); e += NT) {
+        const int r = e % TR, k = e / TR;
+        if (r >= nr) continue;
+        if (k == 0) {
+            const Real y0 = sm[r].x, yn = sm[N * SP + r].x;
+            sm[r] = mk<T2>(y0 + yn, y0 - yn);
+        } else {
+            const T2 yk = sm[k * SP + r], yn = sm[(N - k) * SP + r];
+            const T2 ev = cadd(yk, conj(yn));
+            const T2 od = cmulc(csub(yk, conj(yn)), ldg2(tw + k));
+            sm[k * SP + r] = cadd(ev, rot<1>(od));
+            if (2 * k != N) sm[(N - k) * SP + r] = cadd(conj(ev), rot<1>(conj(od)));
+        }
+    }
+    __syncthreads();
+    const int c = t % TR, q = t / TR;
+    T2 v[E];
+    Stages<T2, N, E, 1, 1, typename FftCfg<N>::Rs>::template run<false, true, true>(
+        v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
+        [&](int row, T2 x) { sm[row * SP + c] = x; });
+    __syncthreads();
+    T2 *dst = reinterpret_cast<T2 *>(u) + r0 * (N / 2);
+    for (int e = t; e < nr * (N / 2); e += NT) {
+        const int r = e / (N / 2), m = e - r * (N / 2);
+        dst[e] = sm[m * SP + r];
+    }
+}
+
+// ---- symbol octant (setup, FP64 arithmetic) ---------------------------------------------
+template <typename Real>
+__global__ void k_symbol_table(Real *__restrict__ sym, const double *__restrict__ A,
+                               const double *__restrict__ w, int nterms, int N, double C0,
+                               double C2, double scale) {
+    extern __shared__ double cj[];
+    const int ky = blockIdx.x, kz = blockIdx.y, K = N + 1;
+    for (int j = threadIdx.x; j < nterms; j += blockDim.x)
+        cj[j] = w[j] * A[(long long)j * K + ky] * A[(long long)j * K + kz];
+    __syncthreads();
+    const double hp2 = 0.25 * 3.141592653589793238462643383279502884 * 3.141592653589793238462643383279502884;
+    for (int kx = threadIdx.x; kx < K; kx += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < nterms; ++j) s += cj[j] * A[(long long)j * K + kx];
+        const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
+        sym[((long long)kz * K + ky) * K + kx] = (Real)(scale * (s + C0 - C2 * hp2 * k2));
+    }
+}
+
+template <class K> static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define GSP_CHECK(x)                          \
+    do {                                      \
+        cudaError_t e_ = (x);                 \
+        if (e_ != cudaSuccess) return e_;     \
+    } while (0)
+
+template <typename Real, int N>
+cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t s, cudaEvent_t *ev) {
+    using T2 = typename CxT<Real>::T;
+    constexpr int L = 2 * N;
+    const int Px = p.Px;
+    T2 *w1 = static_cast<T2 *>(p.w1), *w2 = static_cast<T2 *>(p.w2), *w3 = static_cast<T2 *>(p.w3);
+    const T2 *tw = static_cast<const T2 *>(p.tw);
+    const Real *sym = static_cast<const Real *>(p.sym);
+    constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
+    constexpr int TC = col_tc<Real, L>(), PC = L / FftCfg<L>::E;
+    const size_t smem_row = (size_t)(N + 1) * (TR + 1) * sizeof(T2);
+    const size_t smem_col = (size_t)L * TC * sizeof(T2);
+    const int nrows = N * N;
+    const int ncols = N + 1;
+    const dim3 grow((nrows + TR - 1) / TR);
+    const int ntile = (ncols + TC - 1) / TC;
+
+    if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
+    GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
+    k_x_forward<Real, N><<<grow, TR * PX1, smem_row, s>>>(static_cast<const Real *>(rho), w1, tw,
+                                                           nrows, Px);
+    GSP_CHECK(cudaGetLastError());
+    if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
+
+    GSP_CHECK(set_smem(k_col<Real, L, true>, smem_col));
+    k_col<Real, L, true><<<dim3(ntile, N), TC * PC, smem_col, s>>>(
+        w1, w2, tw, ncols, Px, (long long)N * Px, Px, (long long)L * Px);
+    GSP_CHECK(cudaGetLastError());
+    if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
+
+    GSP_CHECK(set_smem(k_z_symbol<Real, L>, smem_col));
+    k_z_symbol<Real, L><<<dim3(ntile, L), TC * PC, smem_col, s>>>(w2, w3, sym, tw, ncols, Px);
+    GSP_CHECK(cudaGetLastError());
+    if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
+
+    GSP_CHECK(set_smem(k_col<Real, L, false>, smem_col));
+    k_col<Real, L, false><<<dim3(ntile, N), TC * PC, smem_col, s>>>(
+        w3, w1, tw, ncols, Px, (long long)L * Px, Px, (long long)N * Px);
+    GSP_CHECK(cudaGetLastError());
+    if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
+
+    GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
+    k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(w1, static_cast<Real *>(u), tw, nrows, Px);
+    GSP_CHECK(cudaGetLastError());
+    if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
+    return cudaSuccess;
+}
+
+#define GSP_SUPPORTED_N(X) \
+    X(4) X(8) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(1024)
+
+template <typename Real>
+cudaError_t solve_dispatch(const DevicePlan &p, const void *rho, void *u, cudaStream_t s,
+                           cudaEvent_t *ev) {
+    switch (p.N) {
+#define GSP_CASE(n) \
+    case n:         \
+        return solve_n<Real, n>(p, rho, u, s, ev);
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Real>
+cudaError_t symbol_table(const DevicePlan &p, const double *dA, const double *dw, int nterms,
+                         double C0, double C2, double scale, cudaStream_t s) {
+    const int K = p.N + 1;
+    k_symbol_table<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
+        static_cast<Real *>(p.sym), dA, dw, nterms, p.N, C0, C2, scale);
+    return cudaGetLastError();
+}
+
+}  // namespace gsp

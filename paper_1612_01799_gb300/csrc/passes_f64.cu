@@ -1,0 +1,12 @@
+// FP64 instantiation of the solve passes.
+#include "passes.cuh"
+
+namespace gsp {
+cudaError_t solve_f64(const DevicePlan &p, const void *rho, void *u, cudaStream_t s, cudaEvent_t *ev) {
+    return solve_dispatch<double>(p, rho, u, s, ev);
+}
+cudaError_t symbol_table_f64(const DevicePlan &p, const double *dA, const double *dw, int nterms,
+                             double C0, double C2, double scale, cudaStream_t s) {
+    return symbol_table<double>(p, dA, dw, nterms, C0, C2, scale, s);
+}
+}  // namespace gsp

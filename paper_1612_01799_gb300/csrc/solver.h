@@ -1,0 +1,42 @@
+// Internal interface between the C-ABI layer and the CUDA passes.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace gsp {
+
+// Device side of a plan.  Workspace layout (complex values of the plan's dtype):
+//   w1: [z < N][y < N][kx < Px]     after the x pass (and again after the y inverse)
+//   w2: [z < N][ky < 2N][kx < Px]   after the y pass
+//   w3: [z < N][ky < 2N][kx < Px]   after the fused z pass
+// kx runs over the N+1 Hermitian frequencies 0..N of the real x transform; the pitch
+// Px = N+1 rounded up to a multiple of 16 keeps every row 128-byte aligned.
+// sym: symbol octant [kz <= N][ky <= N][kx <= N] (pitch N+1), real, already scaled by
+// lambda^2 / (2N)^3.  tw: W_{2N}^e = exp(-2 pi i e / (2N)), e < 2N.
+struct DevicePlan {
+    int N = 0;
+    int dtype = 0;  // POISSON_F32 / POISSON_F64
+    int Px = 0;
+    void *sym = nullptr;
+    void *tw = nullptr;
+    void *w1 = nullptr;
+    void *w2 = nullptr;
+    void *w3 = nullptr;
+};
+
+inline int pitch_for(int N) { return ((N + 1 + 15) / 16) * 16; }
+
+bool n_supported(int N);
+
+// The five passes of one solve on `s`.  ev: null, or 6 events recorded before pass 1,
+// between the passes and after pass 5.
+cudaError_t launch_solve(const DevicePlan &p, const void *rho, void *u, cudaStream_t s,
+                         cudaEvent_t *ev);
+
+// Fill p.sym from the per-axis factors (FP64, on the device):
+// sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).
+cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
+                                int nterms, double C0, double C2, double scale, cudaStream_t s);
+
+}  // namespace gsp

@@ -1,0 +1,76 @@
+"""The C-ABI library: it builds, loads, exports every function include/poisson.h declares,
+and rejects bad arguments on the host before any device work.  No GPU needed."""
+import ctypes
+import re
+
+import pytest
+
+from paper_1612_01799_gb300 import _lib, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    with open(_lib.HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(poisson_[a-z_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(_lib.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_supported_sizes(lib):
+    for n in (4, 8, 32, 64, 96, 128, 160, 192, 256, 512, 1024):
+        assert lib.poisson_supported_n(n) == 1
+    for n in (0, 2, 3, 7, 33, 100, 1026, 2048, -4):
+        assert lib.poisson_supported_n(n) == 0
+
+
+def test_error_strings(lib):
+    assert lib.poisson_strerror(0) == b"ok"
+    assert lib.poisson_strerror(-1) == b"invalid argument"
+    assert lib.poisson_strerror(-99) == b"unknown error"
+
+
+def test_plan_create_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p(1234)
+    assert lib.poisson_plan_create(None, 32, 8.0, 1e-12, 1) == -1
+    assert lib.poisson_plan_create(ctypes.byref(h), 33, 8.0, 1e-12, 1) == -1     # odd N
+    assert h.value is None                                                        # cleared
+    assert lib.poisson_plan_create(ctypes.byref(h), 2, 8.0, 1e-12, 1) == -1
+    assert lib.poisson_plan_create(ctypes.byref(h), 32, 8.0, 1e-12, 7) == -1     # dtype
+    assert lib.poisson_plan_create(ctypes.byref(h), 100, 8.0, 1e-12, 0) == -4    # no FFT plan
+    assert lib.poisson_plan_create(ctypes.byref(h), 32, -1.0, 1e-12, 0) == -1    # L <= 0
+    assert lib.poisson_plan_create(ctypes.byref(h), 32, float("nan"), 1e-12, 0) == -1
+    assert lib.poisson_plan_create(ctypes.byref(h), 32, 8.0, 0.0, 0) == -1       # tol <= 0
+    assert lib.poisson_plan_create(ctypes.byref(h), 4, 1000.0, 1e-6, 0) == -1    # delta >= 1
+
+
+def test_null_plan_calls_are_errors(lib):
+    assert lib.poisson_plan_destroy(None) == 0
+    assert lib.poisson_solve(None, None, None, None) == -1
+    assert lib.poisson_solve_host(None, None, None, None) == -1
+    assert lib.poisson_solve_timed(None, None, None, None, None) == -1
+    assert lib.poisson_plan_info(None, None, None, None, None, None, None, None) == -1
+    assert lib.poisson_solve_batched(0, None, None, None, None) == 0
+    assert lib.poisson_solve_batched(-1, None, None, None, None) == -1
+    assert lib.poisson_solve_batched(2, None, None, None, None) == -1
+
+
+def test_product_path_has_no_fallback(monkeypatch, tmp_path):
+    """Without the shared library the solver raises instead of computing anything."""
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError):
+        _lib.load()

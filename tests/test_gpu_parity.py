@@ -1,0 +1,157 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the same seeded
+inputs.  Tolerances (relative L2 over the grid): FP64 path <= 1e-12, FP32 path <= 1e-5."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import direct, exact, gauss_sum as ogs, solver as osolver
+from paper_1612_01799_gb300 import densities as D
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01799_gb300 import build
+    build.build()
+    return torch
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def gpu_solve(torch, N, L, tol, dtype, rho):
+    from paper_1612_01799_gb300 import Plan
+    with Plan(N, L, tol, dtype) as p:
+        t = torch.from_numpy(np.ascontiguousarray(rho, dtype=p.np_dtype)).cuda()
+        u = p.solve(t)
+        torch.cuda.synchronize()
+        return u.cpu().numpy().astype(np.float64)
+
+
+def test_config1_single_gaussian_f64(torch_cuda, plan_cache):
+    """Isotropic Gaussian sigma=1, [-8,8]^3, N=32, FP64: oracle parity and closed form."""
+    w = D.config_single_gaussian()
+    rho = w.sample()
+    u = gpu_solve(torch_cuda, 32, 8.0, 1e-12, "f64", rho)
+    uo = osolver.solve(rho, 8.0, 1e-12, plan=plan_cache(32, 8.0, 1e-12))
+    assert rel_l2(u, uo) <= TOL["f64"]
+    x = D.axis(32, 8.0)
+    r = np.sqrt(x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2)
+    assert rel_l2(u, exact.gaussian_iso(r, 1.0)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192])
+def test_parity_sizes(torch_cuda, plan_cache, N, dtype):
+    """Random Gaussian sums on every compiled radix path (2, 3, 5; several tiles and a
+    ragged last column tile), against the oracle element by element."""
+    L = 10.0 if N >= 32 else 4.0
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    w = D.config_aniso4(N=N, seed=100 + N)
+    rho = w.gaussians.sample(N, L)
+    u = gpu_solve(torch_cuda, N, L, tol, dtype, rho)
+    uo = osolver.solve(rho, L, tol, plan=plan_cache(N, L, tol))
+    assert rel_l2(u, uo) <= TOL[dtype]
+    assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_parity_white_noise(torch_cuda, plan_cache, dtype):
+    """A rough density exercises every frequency (all symbol entries matter)."""
+    N, L = 32, 3.0
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    rho = np.random.default_rng(5).standard_normal((N, N, N))
+    u = gpu_solve(torch_cuda, N, L, tol, dtype, rho)
+    uo = osolver.solve(rho, L, tol, plan=plan_cache(N, L, tol))
+    assert rel_l2(u, uo) <= TOL[dtype]
+
+
+def test_plan_tables_match_oracle(torch_cuda, plan_cache):
+    """Host setup of the library vs the oracle's: same Gaussian sum, same per-axis factors,
+    same near-zone constants (written independently)."""
+    from paper_1612_01799_gb300 import Plan
+    for N, L, tol in [(32, 8.0, 1e-12), (64, 10.0, 1e-6), (256, 10.0, 1e-12)]:
+        po = plan_cache(N, L, tol)
+        with Plan(N, L, tol, "f64") as p:
+            info = p.info()
+            tau, w = p.gauss_sum()
+            A = p.axis_table()
+        assert info["n_terms"] == len(po.gs.tau)
+        assert info["delta"] == pytest.approx(po.delta, rel=1e-15)
+        assert np.max(np.abs(tau / po.gs.tau - 1)) <= 1e-14
+        assert np.max(np.abs(w / po.gs.w - 1)) <= 1e-14
+        assert np.max(np.abs(A - po.A)) <= 1e-13
+        assert info["C0"] == pytest.approx(po.C0, rel=1e-12)
+        assert info["C2"] == pytest.approx(po.C2, rel=1e-10)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_config2_full_size(torch_cuda, plan_cache, dtype):
+    """4 anisotropic Gaussians, [-10,10]^3, N = 256 (padded 512^3): the full grid against
+    the FFT oracle."""
+    w = D.config_aniso4()
+    rho = w.sample()
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    u = gpu_solve(torch_cuda, 256, 10.0, tol, dtype, rho)
+    uo = osolver.solve(rho, 10.0, tol, plan=plan_cache(256, 10.0, tol))
+    assert rel_l2(u, uo) <= TOL[dtype]
+
+
+def test_config3_full_size_sampled(torch_cuda):
+    """Bump plus 8 Gaussians, [-6,6]^3, N = 512 (padded 1024^3), FP32: sampled output lines
+    against the oracle's real-space evaluation of the same discrete convolution."""
+    from oracle import gtensor
+    w = D.config_bump8()
+    rho = w.sample()
+    tol = 1e-6
+    u = gpu_solve(torch_cuda, 512, 6.0, tol, "f32", rho)
+    p = gtensor.make_plan(512, 6.0, tol)
+    lines = [(0, 0), (255, 256), (256, 100), (511, 511), (100, 400), (256, 255)]
+    ref = direct.sample_lines(rho, p, lines)
+    got = np.stack([u[z, y] for z, y in lines])
+    assert rel_l2(got, ref) <= TOL["f32"]
+
+
+def test_solve_variants_agree(torch_cuda):
+    """poisson_solve, in place, host buffers, batched and timed give the same bits."""
+    from paper_1612_01799_gb300 import Plan, solve_batched
+    torch = torch_cuda
+    N, L = 64, 10.0
+    rho = D.config_aniso4(N=N, seed=9).sample(np.float32)
+    with Plan(N, L, 1e-6, "f32") as p, Plan(96, L, 1e-6, "f32") as q:
+        t = torch.from_numpy(rho).cuda()
+        u1 = p.solve(t).cpu().numpy()
+        t2 = t.clone()
+        p.solve(t2, out=t2)
+        u_host = p.solve_host(rho)
+        out = torch.empty_like(t)
+        ms = p.solve_timed(t, out)
+        rho96 = D.config_aniso4(N=96, seed=10).sample(np.float32)
+        t96 = torch.from_numpy(rho96).cuda()
+        ub = solve_batched([p, q], [t, t96], [torch.empty_like(t), torch.empty_like(t96)])
+        u96 = q.solve(t96).cpu().numpy()
+        torch.cuda.synchronize()
+        assert np.array_equal(u1, t2.cpu().numpy())
+        assert np.array_equal(u1, u_host)
+        assert np.array_equal(u1, out.cpu().numpy())
+        assert np.array_equal(u1, ub[0].cpu().numpy())
+        assert np.array_equal(u96, ub[1].cpu().numpy())
+        assert len(ms) == 5 and all(m > 0 for m in ms)
+
+
+def test_device_errors_are_codes(torch_cuda):
+    from paper_1612_01799_gb300 import Plan, _lib
+    import ctypes
+    with Plan(32, 8.0, 1e-6, "f32") as p:
+        lib = _lib.load()
+        assert lib.poisson_solve(p.handle, None, None, None) == -1
+        h = ctypes.c_void_p()
+        assert lib.poisson_plan_create(ctypes.byref(h), 64, 8.0, 1e-300, 2) == -1
