@@ -170,11 +170,13 @@ template <int R0> struct Prod<R0> { static constexpr int v = R0; };
 template <typename T2, int L, int E, int D, int R, int NS>
 struct Stage {
     static_assert(E % R == 0, "radix must divide the per-thread element count");
+    static_assert(L % (NS * R) == 0, "radices must divide the length");
     static constexpr int NB = E / R;
     static constexpr int P = L / E;
 
     template <bool PRUNE, class Ld>
     static __device__ __forceinline__ void gather(T2 *v, int q, Ld &&ld) {
+        static_assert(!PRUNE || (NS == 1 && R % 2 == 0), "input pruning needs an even first radix");
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int j = q + P * b;
@@ -207,6 +209,7 @@ struct Stage {
 
     template <bool PRUNE, class St>
     static __device__ __forceinline__ void scatter(const T2 *v, int q, St &&st) {
+        static_assert(!PRUNE || (NS * R == L && R % 2 == 0), "output pruning needs an even last radix");
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int j = q + P * b;
@@ -225,6 +228,7 @@ template <typename T2, int L, int E, int D, int NS, int R, int... Rs>
 struct Stages<T2, L, E, D, NS, Radices<R, Rs...>> {
     using S = Stage<T2, L, E, D, R, NS>;
     static constexpr bool LAST = sizeof...(Rs) == 0;
+    static_assert(!LAST || NS * R == L, "the radices must multiply to the length");
 
     // Runs this stage and the rest.  ld(row) gives stage-0 inputs, st(row, value) takes
     // last-stage outputs.  Intermediate values go through sm[row * SP + c].  Every

@@ -20,7 +20,9 @@
 
 namespace gsp {
 
-// Per-thread element count E and radix sequence of a length-L transform.
+// Per-thread element count E and radix sequence of a length-L transform.  The first and
+// the last radix are even: the pruning rules (inputs r >= R/2 of stage 0 are zero, outputs
+// r >= R/2 of the last stage are dropped) select exactly the rows >= L/2 only then.
 template <int L> struct FftCfg;
 #define GSP_FFT_CFG(LL, EE, ...)                  \
     template <> struct FftCfg<LL> {              \
@@ -31,15 +33,15 @@ GSP_FFT_CFG(4, 4, 4);
 GSP_FFT_CFG(8, 8, 8);
 GSP_FFT_CFG(16, 16, 16);
 GSP_FFT_CFG(32, 8, 8, 4);
-GSP_FFT_CFG(48, 12, 4, 4, 3);
+GSP_FFT_CFG(48, 12, 4, 3, 4);
 GSP_FFT_CFG(64, 8, 8, 8);
-GSP_FFT_CFG(80, 20, 4, 4, 5);
-GSP_FFT_CFG(96, 24, 8, 4, 3);
+GSP_FFT_CFG(80, 20, 4, 5, 4);
+GSP_FFT_CFG(96, 24, 8, 3, 4);
 GSP_FFT_CFG(128, 16, 16, 8);
 GSP_FFT_CFG(160, 20, 4, 4, 5, 2);
-GSP_FFT_CFG(192, 24, 8, 8, 3);
+GSP_FFT_CFG(192, 24, 8, 3, 8);
 GSP_FFT_CFG(256, 16, 16, 16);
-GSP_FFT_CFG(320, 20, 4, 4, 4, 5);
+GSP_FFT_CFG(320, 20, 4, 4, 5, 4);
 GSP_FFT_CFG(384, 24, 8, 8, 6);
 GSP_FFT_CFG(512, 16, 16, 8, 4);
 GSP_FFT_CFG(640, 20, 4, 4, 4, 5, 2);
