@@ -174,10 +174,16 @@ void build_axis_table(const std::vector<double> &tau, int N, std::vector<double>
         double t2 = tau[j] * tau[j];
         for (int n = 0; n < T; ++n) g[n] = wt[n] * std::exp(-t2 * t[n] * t[n]);
         for (int k = 0; k < K; ++k) {
+            // Compensated (Neumaier) summation: thousands of node terms of size ~1/P.
             const double *c = &cosk[(size_t)k * T];
-            double acc = 0.0;
-            for (int n = 0; n < T; ++n) acc += g[n] * c[n];
-            A[(size_t)j * K + k] = 2.0 * acc;
+            double acc = 0.0, comp = 0.0;
+            for (int n = 0; n < T; ++n) {
+                const double term = g[n] * c[n];
+                const double t = acc + term;
+                comp += (std::fabs(acc) >= std::fabs(term)) ? (acc - t) + term : (term - t) + acc;
+                acc = t;
+            }
+            A[(size_t)j * K + k] = 2.0 * (acc + comp);
         }
     });
 }
