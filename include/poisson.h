@@ -135,6 +135,35 @@ int poisson_supported_n(int N);
 /* Human-readable name of a return code. */
 const char *poisson_strerror(int code);
 
+/*
+ * A solve that allocates nothing.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory when they solve, for example code that
+ * issues work while a stream is captured in global capture mode (cudaMalloc is not
+ * allowed then), a real-time loop that must not enter an allocator, or a process whose
+ * device memory is reserved by a framework's caching allocator.  It needs no plan: the
+ * symbol table, the twiddles and the workspace live in one static device array of
+ * POISSON_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit, and
+ * the host-side setup uses fixed static host arrays.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.
+ *   N, L, tol, dtype  as for poisson_plan_create, with N <= POISSON_NOALLOC_MAX_N;
+ *                     a larger N returns POISSON_ERR_UNSUPPORTED.
+ *   rho_d, u_d        device pointers to N^3 values of dtype (u_d may equal rho_d).
+ *   stream            cudaStream_t as void*.
+ * The first call on a device looks up the array's device address; the first call with a
+ * given (N, L, tol, dtype) on a device (and the next one after a call with other
+ * parameters) also computes the tables on the host, copies them into the array and
+ * synchronises `stream`.  Make those set-up calls before any stream capture.  Later calls
+ * with the same parameters only launch the five solve kernels, stream ordered.
+ * All calls share the array and it keeps the last call's contents; nothing in it needs
+ * to start at zero (each pass writes every element the next one reads).  Calls that
+ * overlap on the GPU (on different streams, or from different threads) race on the
+ * array; serialise them.
+ */
+#define POISSON_NOALLOC_MAX_N 64
+#define POISSON_NOALLOC_SCRATCH_BYTES (32u << 20)
+int poisson_solve_noalloc(int N, double L, double tol, int dtype, const void *rho_d, void *u_d,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,7 @@ SIGNATURES = {
     "poisson_plan_axis_table": (c_int, [c_void_p, P(c_double), c_size_t]),
     "poisson_supported_n": (c_int, [c_int]),
     "poisson_strerror": (ctypes.c_char_p, [c_int]),
+    "poisson_solve_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p]),
 }
 
 
