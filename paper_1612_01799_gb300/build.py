@@ -41,7 +41,7 @@ def _stale(target, deps):
 def build(force=False, verbose=False, extra_flags=()):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH + list(extra_flags)
+    flags = ["-std=c++20", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH + list(extra_flags)
     jobs = []
     for src in SOURCES:
         obj = os.path.join(BUILD, src + ".o")

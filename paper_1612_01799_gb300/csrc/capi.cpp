@@ -59,7 +59,8 @@ static int map_cuda(cudaError_t e) {
 
 static void free_plan(poisson_plan p) {
     if (!p) return;
-    void *bufs[] = {p->dp.sym, p->dp.tw, p->dp.w1, p->dp.w2, p->dp.w3, p->stage_in, p->stage_out};
+    void *twc = p->dp.twc != p->dp.tw ? p->dp.twc : nullptr;
+    void *bufs[] = {p->dp.sym, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->stage_in, p->stage_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->have_events)
@@ -104,14 +105,16 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     p->dp.N = N;
     p->dp.dtype = dtype;
     p->dp.Px = gsp::pitch_for(N);
+    p->dp.Ps = gsp::sym_pitch_for(N);
     const size_t cx = 2 * p->elem;
     const size_t K = (size_t)N + 1;
-    const size_t sym_bytes = K * K * K * p->elem;
+    const size_t sym_bytes = K * K * (size_t)p->dp.Ps * p->elem;
     const size_t tw_bytes = (size_t)2 * N * cx;
+    const size_t twc_bytes = dtype == POISSON_F32 ? (size_t)2 * N * 4 * sizeof(float) : 0;
     const size_t w1_bytes = (size_t)N * N * p->dp.Px * cx;
     const size_t w2_bytes = (size_t)N * 2 * N * p->dp.Px * cx;
     p->ws_bytes = w1_bytes + 2 * w2_bytes;
-    p->table_bytes = sym_bytes + tw_bytes;
+    p->table_bytes = sym_bytes + tw_bytes + twc_bytes;
 
     double *dA = nullptr, *dw = nullptr;
     auto fail = [&](cudaError_t err) {
@@ -125,6 +128,16 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     if ((e = cudaMalloc(&p->dp.w1, w1_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.w2, w2_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.w3, w2_bytes)) != cudaSuccess) return fail(e);
+    if (twc_bytes) {
+        if ((e = cudaMalloc(&p->dp.twc, twc_bytes)) != cudaSuccess) return fail(e);
+    } else {
+        p->dp.twc = p->dp.tw;
+    }
+    // Padding columns (kx > N) are carried along by the two-column passes but never used;
+    // zeroed once so they hold finite values.
+    if ((e = cudaMemset(p->dp.w1, 0, w1_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(p->dp.w2, 0, w2_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(p->dp.w3, 0, w2_bytes)) != cudaSuccess) return fail(e);
 
     // Twiddles W_{2N}^e from FP64 (long double arithmetic), rounded once to the dtype.
     std::vector<double> tw;
@@ -132,6 +145,13 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     if (dtype == POISSON_F32) {
         std::vector<float> twf(tw.begin(), tw.end());
         e = cudaMemcpy(p->dp.tw, twf.data(), tw_bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(e);
+        std::vector<float> tw4((size_t)2 * N * 4);
+        for (size_t i = 0; i < (size_t)2 * N; ++i) {
+            tw4[4 * i] = tw4[4 * i + 1] = (float)tw[2 * i];
+            tw4[4 * i + 2] = tw4[4 * i + 3] = (float)tw[2 * i + 1];
+        }
+        e = cudaMemcpy(p->dp.twc, tw4.data(), twc_bytes, cudaMemcpyHostToDevice);
     } else {
         e = cudaMemcpy(p->dp.tw, tw.data(), tw_bytes, cudaMemcpyHostToDevice);
     }

@@ -54,6 +54,7 @@ double h_cos[(kMaxN + 1) * kMaxNodes];
 double h_gx[kOrder], h_gw[kOrder];
 double h_tw[4 * kMaxN];
 float h_twf[4 * kMaxN];
+float h_tw4[8 * kMaxN];
 
 double erfc_inv(double y) {
     double lo = -10.0, hi = 30.0;
@@ -231,12 +232,15 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
         h_tw[2 * e + 1] = (double)-std::sin(a);
         h_twf[2 * e] = (float)h_tw[2 * e];
         h_twf[2 * e + 1] = (float)h_tw[2 * e + 1];
+        h_tw4[4 * e] = h_tw4[4 * e + 1] = h_twf[2 * e];
+        h_tw4[4 * e + 2] = h_tw4[4 * e + 3] = h_twf[2 * e + 1];
     }
 
     // Layout of the array (256-byte aligned pieces).
     const size_t elem = dtype == POISSON_F32 ? 4 : 8, cx = 2 * elem;
     const size_t K = (size_t)N + 1;
     const int Px = gsp::pitch_for(N);
+    const int Ps = gsp::sym_pitch_for(N);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         unsigned char *p = st.base + off;
@@ -247,8 +251,10 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
     dp.N = N;
     dp.dtype = dtype;
     dp.Px = Px;
-    dp.sym = take(K * K * K * elem);
+    dp.Ps = Ps;
+    dp.sym = take(K * K * (size_t)Ps * elem);
     dp.tw = take((size_t)2 * N * cx);
+    dp.twc = dtype == POISSON_F32 ? take((size_t)2 * N * 4 * sizeof(float)) : dp.tw;
     double *dA = reinterpret_cast<double *>(take((size_t)S * K * sizeof(double)));
     double *dw = reinterpret_cast<double *>(take((size_t)S * sizeof(double)));
     dp.w1 = take((size_t)N * N * Px * cx);
@@ -261,10 +267,13 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
         return map_cuda(e);
     if ((e = cudaMemcpyAsync(dw, h_w, (size_t)S * sizeof(double), cudaMemcpyHostToDevice, s)))
         return map_cuda(e);
-    if (dtype == POISSON_F32)
+    if (dtype == POISSON_F32) {
         e = cudaMemcpyAsync(dp.tw, h_twf, (size_t)2 * N * cx, cudaMemcpyHostToDevice, s);
-    else
+        if (e) return map_cuda(e);
+        e = cudaMemcpyAsync(dp.twc, h_tw4, (size_t)2 * N * 4 * sizeof(float), cudaMemcpyHostToDevice, s);
+    } else {
         e = cudaMemcpyAsync(dp.tw, h_tw, (size_t)2 * N * cx, cudaMemcpyHostToDevice, s);
+    }
     if (e) return map_cuda(e);
     const double M = 2.0 * N;
     if ((e = gsp::launch_symbol_table(dp, dA, dw, S, C0, C2, L * L / (M * M * M), s)))

@@ -10,11 +10,19 @@
 //   K3 z fused     w2 -> w3 [z < N][ky][kx]     length 2N forward (upper half zero),
 //                  product with the symbol G_tot(|kx|, |ky|, |kz|) scaled by
 //                  lambda^2/(2N)^3, length 2N inverse keeping the lower half.  The
-//                  (2N)^3 spectrum exists only in shared memory.
+//                  (2N)^3 spectrum exists only in registers and shared memory: the
+//                  inverse runs its radices in reverse order, so it starts from the
+//                  forward's last-stage registers and the symbol is applied there.
 //   K4 y inverse   w3 -> w1 [z][y < N][kx]      length 2N inverse, lower half kept
 //   K5 x inverse   w1 -> u [z][y][x]            N+1 Hermitian bins -> N-point complex
 //                  inverse FFT of the (even, odd) pairs, lower N/2 pairs kept (the crop).
+//
+// The column passes (K2-K4) of the FP32 path process two neighbouring columns per thread
+// with packed FP32x2 arithmetic (type CV); the row passes and the FP64 path use one
+// complex value per slot.
 #pragma once
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "solver.h"
 
@@ -50,13 +58,31 @@ GSP_FFT_CFG(1024, 16, 16, 16, 4);
 GSP_FFT_CFG(2048, 16, 16, 16, 8);
 #undef GSP_FFT_CFG
 
+// Complex types per arithmetic: CS for the row passes, CC (W columns per thread) for the
+// column passes.
+template <typename Real> struct Types;
+template <> struct Types<float> {
+    using CS = CF;
+    using CC = CV;
+    static constexpr int W = 2;
+};
+template <> struct Types<double> {
+    using CS = CD;
+    using CC = CD;
+    static constexpr int W = 1;
+};
+
 // Columns per CTA of a column pass: 128-byte row segments (16 FP32 or 8 FP64 complex),
 // halved until the block has <= 1024 threads and <= 128 KB of shared memory.
 template <typename Real, int L> __host__ __device__ constexpr int col_tc() {
+    const int W = Types<Real>::W;
     int tc = sizeof(Real) == 4 ? 16 : 8;
     const int P = L / FftCfg<L>::E;
-    while (tc > 1 && (tc * P > 1024 || tc * L * 2 * (int)sizeof(Real) > 131072)) tc /= 2;
+    while (tc > W && ((tc / W) * P > 1024 || tc * L * 2 * (int)sizeof(Real) > 131072)) tc /= 2;
     return tc;
+}
+template <typename Real, int L> __host__ __device__ constexpr int col_threads() {
+    return (col_tc<Real, L>() / Types<Real>::W) * (L / FftCfg<L>::E);
 }
 // Rows per CTA of an x pass (shared tile (N+1) x (TR+1) complex).
 template <typename Real, int L> __host__ __device__ constexpr int row_tr() {
@@ -66,17 +92,45 @@ template <typename Real, int L> __host__ __device__ constexpr int row_tr() {
     return tr;
 }
 
-template <typename T2> __device__ __forceinline__ T2 ldg2(const T2 *p) { return __ldg(p); }
+// ---- loads and stores of W neighbouring complex values ---------------------------------
+__device__ __forceinline__ CV ld_cc(const float2 *p) {
+    const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+    return {make_float2(f.x, f.z), make_float2(f.y, f.w)};
+}
+__device__ __forceinline__ void st_cc(float2 *p, CV x) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+}
+__device__ __forceinline__ CD ld_cc(const double2 *p) {
+    const double2 f = __ldg(p);
+    return {f.x, f.y};
+}
+__device__ __forceinline__ void st_cc(double2 *p, CD x) { *p = make_double2(x.re, x.im); }
+__device__ __forceinline__ CF ld_cs(const float2 *p) {
+    const float2 f = *p;
+    return {f.x, f.y};
+}
+__device__ __forceinline__ CD ld_cs(const double2 *p) {
+    const double2 f = *p;
+    return {f.x, f.y};
+}
+// Symbol factors of the W columns.
+__device__ __forceinline__ CV scale_sym(CV x, const float *s) {
+    return cscale2(x, __ldg(reinterpret_cast<const float2 *>(s)));
+}
+__device__ __forceinline__ CD scale_sym(CD x, const double *s) { return cscale(x, __ldg(s)); }
+
+template <typename Real> using Cx2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
 
 // ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
 template <typename Real, int N>
 __global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
-k_x_forward(const Real *__restrict__ rho, typename CxT<Real>::T *__restrict__ out,
-            const typename CxT<Real>::T *__restrict__ tw, int nrows, int Px) {
-    using T2 = typename CxT<Real>::T;
+k_x_forward(const Real *__restrict__ rho, Cx2<Real> *__restrict__ out,
+            const Cx2<Real> *__restrict__ tw, int nrows, int Px) {
+    using C = typename Types<Real>::CS;
+    using T2 = Cx2<Real>;
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *sm = reinterpret_cast<T2 *>(smraw);  // (N + 1) x SP
+    C *sm = reinterpret_cast<C *>(smraw);  // (N + 1) x SP
     const int t = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * TR;
     const int nr = (int)min((long long)TR, (long long)nrows - r0);
@@ -84,14 +138,16 @@ k_x_forward(const Real *__restrict__ rho, typename CxT<Real>::T *__restrict__ ou
     const T2 *src = reinterpret_cast<const T2 *>(rho) + r0 * (N / 2);
     for (int e = t; e < nr * (N / 2); e += NT) {
         const int r = e / (N / 2), m = e - r * (N / 2);
-        sm[m * SP + r] = ldg2(src + e);
+        const T2 f = __ldg(src + e);
+        sm[m * SP + r] = C{f.x, f.y};
     }
     __syncthreads();
     const int c = t % TR, q = t / TR;
-    T2 v[E];
-    Stages<T2, N, E, -1, 1, typename FftCfg<N>::Rs>::template run<true, false, true>(
+    C v[E];
+    constexpr RunOpt opt{false, true, false, false, true};
+    Stages<C, N, E, -1, 1, typename FftCfg<N>::Rs>::template run<opt>(
         v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
-        [&](int row, T2 x) { sm[row * SP + c] = x; });
+        [&](int row, C x) { sm[row * SP + c] = x; });
     __syncthreads();
     // C = FFT_N(pairs).  With Ev_k = (C_k + conj C_{N-k})/2 (DFT of the even samples) and
     // Od_k = (C_k - conj C_{N-k})/(2i) (odd samples): X_k = Ev_k + W_{2N}^k Od_k,
@@ -99,24 +155,28 @@ k_x_forward(const Real *__restrict__ rho, typename CxT<Real>::T *__restrict__ ou
     for (int e = t; e < TR * (N / 2 + 1); e += NT) {
         const int r = e % TR, k = e / TR;
         if (r >= nr) continue;
-        const T2 ck = sm[k * SP + r];
-        const T2 cn = sm[((N - k) % N) * SP + r];
-        const T2 ev = cscale(cadd(ck, conj(cn)), (Real)0.5);
-        const T2 od = cscale(rot<-1>(csub(ck, conj(cn))), (Real)0.5);
+        const C ck = sm[k * SP + r];
+        const C cn = sm[((N - k) % N) * SP + r];
+        const C ev = {(Real)0.5 * (ck.re + cn.re), (Real)0.5 * (ck.im - cn.im)};
+        const C od = {(Real)0.5 * (ck.im + cn.im), (Real)0.5 * (cn.re - ck.re)};
         if (k == 0) {
-            sm[r] = mk<T2>(ev.x + od.x, (Real)0);
-            sm[N * SP + r] = mk<T2>(ev.x - od.x, (Real)0);
+            sm[r] = C{ev.re + od.re, (Real)0};
+            sm[N * SP + r] = C{ev.re - od.re, (Real)0};
         } else {
-            const T2 wo = cmul(ldg2(tw + k), od);
+            const C wo = twmul<-1>(od, __ldg(tw + k));
             sm[k * SP + r] = cadd(ev, wo);
-            if (2 * k != N) sm[(N - k) * SP + r] = conj(csub(ev, wo));
+            if (2 * k != N) {
+                const C d = csub(ev, wo);
+                sm[(N - k) * SP + r] = C{d.re, -d.im};
+            }
         }
     }
     __syncthreads();
     T2 *dst = out + r0 * Px;
     for (int e = t; e < nr * (N + 1); e += NT) {
         const int r = e / (N + 1), k = e - r * (N + 1);
-        dst[(long long)r * Px + k] = sm[k * SP + r];
+        const C x = sm[k * SP + r];
+        dst[(long long)r * Px + k] = T2{x.re, x.im};
     }
 }
 
@@ -124,84 +184,96 @@ k_x_forward(const Real *__restrict__ rho, typename CxT<Real>::T *__restrict__ ou
 // FWD: rows < L/2 of the input are nonzero, all L outputs stored.
 // !FWD: all L inputs, outputs < L/2 stored.
 template <typename Real, int L, bool FWD>
-__global__ void __launch_bounds__(col_tc<Real, L>() * (L / FftCfg<L>::E))
-k_col(const typename CxT<Real>::T *__restrict__ in, typename CxT<Real>::T *__restrict__ out,
-      const typename CxT<Real>::T *__restrict__ tw, int ncols, long long in_row,
+__global__ void __launch_bounds__(col_threads<Real, L>())
+k_col(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out,
+      const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ncols, long long in_row,
       long long in_outer, long long out_row, long long out_outer) {
-    using T2 = typename CxT<Real>::T;
-    constexpr int E = FftCfg<L>::E, TC = col_tc<Real, L>();
+    using C = typename Types<Real>::CC;
+    constexpr int W = Types<Real>::W, E = FftCfg<L>::E, TC = col_tc<Real, L>(), NG = TC / W;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *sm = reinterpret_cast<T2 *>(smraw);  // L x TC
-    const int c = threadIdx.x % TC, q = threadIdx.x / TC;
-    const int col = blockIdx.x * TC + c;
+    C *sm = reinterpret_cast<C *>(smraw);  // L x NG
+    const int g = threadIdx.x % NG, q = threadIdx.x / NG;
+    const int col = blockIdx.x * TC + W * g;
     const bool valid = col < ncols;
-    const T2 *src = in + (long long)blockIdx.y * in_outer + col;
-    T2 *dst = out + (long long)blockIdx.y * out_outer + col;
-    T2 v[E];
-    Stages<T2, L, E, FWD ? -1 : 1, 1, typename FftCfg<L>::Rs>::template run<FWD, !FWD, false>(
-        v, q, c, sm, TC, tw, 1,
-        [&](int row) { return valid ? ldg2(src + row * in_row) : czero<T2>(); },
-        [&](int row, T2 x) {
-            if (valid) dst[row * out_row] = x;
+    const Cx2<Real> *src = in + (long long)blockIdx.y * in_outer + col;
+    Cx2<Real> *dst = out + (long long)blockIdx.y * out_outer + col;
+    C v[E];
+    constexpr RunOpt opt{false, FWD, false, !FWD, false};
+    Stages<C, L, E, FWD ? -1 : 1, 1, typename FftCfg<L>::Rs>::template run<opt>(
+        v, q, g, sm, NG, tw, 1,
+        [&](int row) { return valid ? ld_cc(src + row * in_row) : czero<C>(); },
+        [&](int row, C x) {
+            if (valid) st_cc(dst + row * out_row, x);
         });
 }
 
 // ---- K3: z forward, symbol, z inverse --------------------------------------------------
 template <typename Real, int L>
-__global__ void __launch_bounds__(col_tc<Real, L>() * (L / FftCfg<L>::E))
-k_z_symbol(const typename CxT<Real>::T *__restrict__ in, typename CxT<Real>::T *__restrict__ out,
-           const Real *__restrict__ sym, const typename CxT<Real>::T *__restrict__ tw, int ncols,
-           int Px) {
-    using T2 = typename CxT<Real>::T;
-    constexpr int N = L / 2, E = FftCfg<L>::E, TC = col_tc<Real, L>();
+__global__ void __launch_bounds__(col_threads<Real, L>())
+k_z_symbol(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out, const Real *__restrict__ sym,
+           const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ncols, int Px,
+           int Ps) {
+    using C = typename Types<Real>::CC;
+    using Rs = typename FftCfg<L>::Rs;
+    constexpr int N = L / 2, W = Types<Real>::W, E = FftCfg<L>::E, TC = col_tc<Real, L>(), NG = TC / W;
+    constexpr int P = L / E;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *sm = reinterpret_cast<T2 *>(smraw);  // L x TC
-    const int c = threadIdx.x % TC, q = threadIdx.x / TC;
-    const int col = blockIdx.x * TC + c;
+    C *sm = reinterpret_cast<C *>(smraw);  // L x NG
+    const int g = threadIdx.x % NG, q = threadIdx.x / NG;
+    const int col = blockIdx.x * TC + W * g;
     const bool valid = col < ncols;
     // Consecutive blocks take ky and its mirror 2N - ky, which read the same symbol rows.
     const int by = blockIdx.y;
     const int ky = (by & 1) ? L - ((by + 1) >> 1) : (by >> 1);
     const int kya = ky <= N ? ky : L - ky;
     const long long zs = (long long)L * Px;  // z stride of w2 / w3
-    const T2 *src = in + (long long)ky * Px + col;
-    T2 *dst = out + (long long)ky * Px + col;
-    const long long plane = (long long)(N + 1) * (N + 1);
-    const Real *srow = sym + (long long)kya * (N + 1) + (valid ? col : 0);
-    T2 v[E];
-    Stages<T2, L, E, -1, 1, typename FftCfg<L>::Rs>::template run<true, false, true>(
-        v, q, c, sm, TC, tw, 1,
-        [&](int row) { return valid ? ldg2(src + row * zs) : czero<T2>(); },
-        [&](int row, T2 x) { sm[row * TC + c] = x; });
-    __syncthreads();
-    Stages<T2, L, E, 1, 1, typename FftCfg<L>::Rs>::template run<false, true, false>(
-        v, q, c, sm, TC, tw, 1,
-        [&](int row) {
+    const Cx2<Real> *src = in + (long long)ky * Px + col;
+    Cx2<Real> *dst = out + (long long)ky * Px + col;
+    const long long plane = (long long)(N + 1) * Ps;
+    const Real *srow = sym + (long long)kya * Ps + (valid ? col : 0);
+    C v[E];
+    constexpr RunOpt fwd{false, true, true, false, false};
+    Stages<C, L, E, -1, 1, Rs>::template run<fwd>(
+        v, q, g, sm, NG, tw, 1, [&](int row) { return valid ? ld_cc(src + row * zs) : czero<C>(); },
+        [&](int, C) {});
+    // The forward's last stage (radix RL) left row j + r L/RL of butterfly b in v[b RL + r].
+    constexpr int RL = LastRadix<Rs>::v;
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b) {
+        const int j = q + P * b;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            const int row = j + r * (L / RL);
             const int kz = row <= N ? row : L - row;
-            const Real g = valid ? __ldg(srow + kz * plane) : (Real)0;
-            return cscale(sm[row * TC + c], g);
-        },
-        [&](int row, T2 x) {
-            if (valid) dst[row * zs] = x;
+            v[b * RL + r] = scale_sym(v[b * RL + r], srow + kz * plane);
+        }
+    }
+    constexpr RunOpt inv{true, false, false, true, false};
+    Stages<C, L, E, 1, 1, Reverse<Rs>>::template run<inv>(
+        v, q, g, sm, NG, tw, 1, [&](int) { return czero<C>(); },
+        [&](int row, C x) {
+            if (valid) st_cc(dst + row * zs, x);
         });
 }
 
 // ---- K5: x inverse (Hermitian N+1 bins -> N real samples) -------------------------------
 template <typename Real, int N>
 __global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
-k_x_inverse(const typename CxT<Real>::T *__restrict__ in, Real *__restrict__ u,
-            const typename CxT<Real>::T *__restrict__ tw, int nrows, int Px) {
-    using T2 = typename CxT<Real>::T;
+k_x_inverse(const Cx2<Real> *__restrict__ in, Real *__restrict__ u, const Cx2<Real> *__restrict__ tw,
+            int nrows, int Px) {
+    using C = typename Types<Real>::CS;
+    using T2 = Cx2<Real>;
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *sm = reinterpret_cast<T2 *>(smraw);  // (N + 1) x SP
+    C *sm = reinterpret_cast<C *>(smraw);  // (N + 1) x SP
     const int t = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * TR;
     const int nr = (int)min((long long)TR, (long long)nrows - r0);
     const T2 *src = in + r0 * Px;
     for (int e = t; e < nr * (N + 1); e += NT) {
         const int r = e / (N + 1), k = e - r * (N + 1);
-        sm[k * SP + r] = ldg2(src + (long long)r * Px + k);
+        const T2 f = __ldg(src + (long long)r * Px + k);
+        sm[k * SP + r] = C{f.x, f.y};
     }
     __syncthreads();
     // Y_k, k = 0..N (Y_0, Y_N real) -> C_k = Ev_k + i Od_k with Ev_k = Y_k + conj Y_{N-k}
@@ -211,34 +283,38 @@ k_x_inverse(const typename CxT<Real>::T *__restrict__ in, Real *__restrict__ u,
         const int r = e % TR, k = e / TR;
         if (r >= nr) continue;
         if (k == 0) {
-            const Real y0 = sm[r].x, yn = sm[N * SP + r].x;
-            sm[r] = mk<T2>(y0 + yn, y0 - yn);
+            const Real y0 = sm[r].re, yn = sm[N * SP + r].re;
+            sm[r] = C{y0 + yn, y0 - yn};
         } else {
-            const T2 yk = sm[k * SP + r], yn = sm[(N - k) * SP + r];
-            const T2 ev = cadd(yk, conj(yn));
-            const T2 od = cmulc(csub(yk, conj(yn)), ldg2(tw + k));
-            sm[k * SP + r] = cadd(ev, rot<1>(od));
-            if (2 * k != N) sm[(N - k) * SP + r] = cadd(conj(ev), rot<1>(conj(od)));
+            const C yk = sm[k * SP + r], yn = sm[(N - k) * SP + r];
+            const C ev = {yk.re + yn.re, yk.im - yn.im};
+            const C od = twmul<1>(C{yk.re - yn.re, yk.im + yn.im}, __ldg(tw + k));
+            sm[k * SP + r] = add_rot<1>(ev, od);
+            if (2 * k != N) sm[(N - k) * SP + r] = add_rot<1>(C{ev.re, -ev.im}, C{od.re, -od.im});
         }
     }
     __syncthreads();
     const int c = t % TR, q = t / TR;
-    T2 v[E];
-    Stages<T2, N, E, 1, 1, typename FftCfg<N>::Rs>::template run<false, true, true>(
+    C v[E];
+    constexpr RunOpt opt{false, false, false, true, true};
+    Stages<C, N, E, 1, 1, typename FftCfg<N>::Rs>::template run<opt>(
         v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
-        [&](int row, T2 x) { sm[row * SP + c] = x; });
+        [&](int row, C x) { sm[row * SP + c] = x; });
     __syncthreads();
     T2 *dst = reinterpret_cast<T2 *>(u) + r0 * (N / 2);
     for (int e = t; e < nr * (N / 2); e += NT) {
         const int r = e / (N / 2), m = e - r * (N / 2);
-        dst[e] = sm[m * SP + r];
+        const C x = sm[m * SP + r];
+        dst[e] = T2{x.re, x.im};
     }
 }
 
 // ---- symbol octant (setup, FP64 arithmetic) ---------------------------------------------
+// sym[(kz * (N+1) + ky) * Ps + kx] for kx, ky, kz <= N; the pitch Ps (a multiple of 4)
+// keeps the two-column loads of the FP32 z pass aligned.
 template <typename Real>
 __global__ void k_symbol_table(Real *__restrict__ sym, const double *__restrict__ A,
-                               const double *__restrict__ w, int nterms, int N, double C0,
+                               const double *__restrict__ w, int nterms, int N, int Ps, double C0,
                                double C2, double scale) {
     extern __shared__ double cj[];
     const int ky = blockIdx.x, kz = blockIdx.y, K = N + 1;
@@ -246,11 +322,15 @@ __global__ void k_symbol_table(Real *__restrict__ sym, const double *__restrict_
         cj[j] = w[j] * A[(long long)j * K + ky] * A[(long long)j * K + kz];
     __syncthreads();
     const double hp2 = 0.25 * 3.141592653589793238462643383279502884 * 3.141592653589793238462643383279502884;
-    for (int kx = threadIdx.x; kx < K; kx += blockDim.x) {
-        double s = 0.0;
-        for (int j = 0; j < nterms; ++j) s += cj[j] * A[(long long)j * K + kx];
-        const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
-        sym[((long long)kz * K + ky) * K + kx] = (Real)(scale * (s + C0 - C2 * hp2 * k2));
+    for (int kx = threadIdx.x; kx < Ps; kx += blockDim.x) {
+        double g = 0.0;
+        if (kx < K) {
+            double s = 0.0;
+            for (int j = 0; j < nterms; ++j) s += cj[j] * A[(long long)j * K + kx];
+            const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
+            g = scale * (s + C0 - C2 * hp2 * k2);
+        }
+        sym[((long long)kz * K + ky) * Ps + kx] = (Real)g;
     }
 }
 
@@ -267,16 +347,18 @@ template <class K> static cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t s, cudaEvent_t *ev) {
-    using T2 = typename CxT<Real>::T;
+    using T2 = Cx2<Real>;
+    using TwC = typename TwOf<typename Types<Real>::CC>::T;
     constexpr int L = 2 * N;
     const int Px = p.Px;
     T2 *w1 = static_cast<T2 *>(p.w1), *w2 = static_cast<T2 *>(p.w2), *w3 = static_cast<T2 *>(p.w3);
     const T2 *tw = static_cast<const T2 *>(p.tw);
+    const TwC *twc = static_cast<const TwC *>(p.twc);
     const Real *sym = static_cast<const Real *>(p.sym);
     constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
-    constexpr int TC = col_tc<Real, L>(), PC = L / FftCfg<L>::E;
-    const size_t smem_row = (size_t)(N + 1) * (TR + 1) * sizeof(T2);
-    const size_t smem_col = (size_t)L * TC * sizeof(T2);
+    constexpr int TC = col_tc<Real, L>(), NTC = col_threads<Real, L>();
+    const size_t smem_row = (size_t)(N + 1) * (TR + 1) * 2 * sizeof(Real);
+    const size_t smem_col = (size_t)L * TC * 2 * sizeof(Real);
     const int nrows = N * N;
     const int ncols = N + 1;
     const dim3 grow((nrows + TR - 1) / TR);
@@ -290,19 +372,19 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
     GSP_CHECK(set_smem(k_col<Real, L, true>, smem_col));
-    k_col<Real, L, true><<<dim3(ntile, N), TC * PC, smem_col, s>>>(
-        w1, w2, tw, ncols, Px, (long long)N * Px, Px, (long long)L * Px);
+    k_col<Real, L, true><<<dim3(ntile, N), NTC, smem_col, s>>>(
+        w1, w2, twc, ncols, Px, (long long)N * Px, Px, (long long)L * Px);
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
     GSP_CHECK(set_smem(k_z_symbol<Real, L>, smem_col));
-    k_z_symbol<Real, L><<<dim3(ntile, L), TC * PC, smem_col, s>>>(w2, w3, sym, tw, ncols, Px);
+    k_z_symbol<Real, L><<<dim3(ntile, L), NTC, smem_col, s>>>(w2, w3, sym, twc, ncols, Px, p.Ps);
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
 
     GSP_CHECK(set_smem(k_col<Real, L, false>, smem_col));
-    k_col<Real, L, false><<<dim3(ntile, N), TC * PC, smem_col, s>>>(
-        w3, w1, tw, ncols, Px, (long long)L * Px, Px, (long long)N * Px);
+    k_col<Real, L, false><<<dim3(ntile, N), NTC, smem_col, s>>>(
+        w3, w1, twc, ncols, Px, (long long)L * Px, Px, (long long)N * Px);
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
@@ -335,7 +417,7 @@ cudaError_t symbol_table(const DevicePlan &p, const double *dA, const double *dw
                          double C0, double C2, double scale, cudaStream_t s) {
     const int K = p.N + 1;
     k_symbol_table<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
-        static_cast<Real *>(p.sym), dA, dw, nterms, p.N, C0, C2, scale);
+        static_cast<Real *>(p.sym), dA, dw, nterms, p.N, p.Ps, C0, C2, scale);
     return cudaGetLastError();
 }
 

@@ -12,20 +12,26 @@ namespace gsp {
 //   w3: [z < N][ky < 2N][kx < Px]   after the fused z pass
 // kx runs over the N+1 Hermitian frequencies 0..N of the real x transform; the pitch
 // Px = N+1 rounded up to a multiple of 16 keeps every row 128-byte aligned.
-// sym: symbol octant [kz <= N][ky <= N][kx <= N] (pitch N+1), real, already scaled by
-// lambda^2 / (2N)^3.  tw: W_{2N}^e = exp(-2 pi i e / (2N)), e < 2N.
+// sym: symbol octant [kz <= N][ky <= N][kx < Ps] (Ps = N+1 rounded up to a multiple of
+// 4, entries kx > N zero), real, already scaled by lambda^2 / (2N)^3.
+// tw: W_{2N}^e = exp(-2 pi i e / (2N)), e < 2N, as (re, im) pairs of the dtype.
+// twc: the same twiddles in the form the column passes read: (re, re, im, im) float4 for
+// FP32 (two columns per thread), equal to tw for FP64.
 struct DevicePlan {
     int N = 0;
     int dtype = 0;  // POISSON_F32 / POISSON_F64
     int Px = 0;
+    int Ps = 0;
     void *sym = nullptr;
     void *tw = nullptr;
+    void *twc = nullptr;
     void *w1 = nullptr;
     void *w2 = nullptr;
     void *w3 = nullptr;
 };
 
 inline int pitch_for(int N) { return ((N + 1 + 15) / 16) * 16; }
+inline int sym_pitch_for(int N) { return ((N + 1 + 3) / 4) * 4; }
 
 bool n_supported(int N);
 

@@ -87,6 +87,28 @@ def test_schedule_is_a_dft(L, E, radices):
     assert np.allclose([y[i] for i in range(L // 2)], (np.fft.ifft(x) * L)[:L // 2], atol=1e-10)
 
 
+@pytest.mark.parametrize("L,E,radices", schedules())
+def test_z_pass_chain(L, E, radices):
+    """The fused z pass: forward with the schedule (upper input half zero), a pointwise
+    symbol, then the inverse with the radices reversed keeping the lower output half.
+    The inverse's first stage has the forward's last radix and reads exactly the rows the
+    forward's last stage left in each thread, so no exchange is needed between them."""
+    rng = np.random.default_rng(L + 1)
+    x = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    x[L // 2:] = 0
+    g = rng.standard_normal(L)
+    y = stockham(x, L, E, radices, -1, True, False)
+    P = L // E
+    R_last = radices[-1]
+    # rows held by thread q after the forward's last stage = rows its first inverse stage gathers
+    for q in range(P):
+        held = {q + P * b + r * (L // R_last) for b in range(E // R_last) for r in range(R_last)}
+        assert len(held) == E
+    z = stockham(np.array([y[i] * g[i] for i in range(L)]), L, E, radices[::-1], +1, False, True)
+    ref = np.fft.ifft(np.fft.fft(x) * g) * L
+    assert np.allclose([z[i] for i in range(L // 2)], ref[:L // 2], atol=1e-9)
+
+
 def test_every_supported_n_has_both_schedules():
     lengths = {L for L, _, _ in schedules()}
     with open(PASSES) as f:
