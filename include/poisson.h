@@ -111,6 +111,14 @@ int poisson_solve_batched(int count, const poisson_plan *plans, const void *cons
 int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d, void *stream, float *ms);
 
 /*
+ * Status of the plan's earlier solves: synchronises `stream` (cudaStream_t as void*),
+ * reads the plan's device status word and clears it.  Returns POISSON_OK, or
+ * POISSON_ERR_TIMEOUT if a bounded device-side wait of a solve gave up (its kernel
+ * stopped early and its output is not valid).
+ */
+int poisson_last_status(poisson_plan p, void *stream);
+
+/*
  * Facts of a plan, for checks and reports.  Any output pointer may be NULL.
  *   delta       near-zone radius in scaled coordinates (Sec. 3 heuristic).
  *   eps         Gaussian-sum accuracy actually requested.

@@ -17,6 +17,12 @@ cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *,
                              double, double, cudaStream_t);
 cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
                              double, double, cudaStream_t);
+cudaError_t encode_maps_f32(DevicePlan &);
+cudaError_t encode_maps_f64(DevicePlan &);
+
+cudaError_t encode_tma_maps(DevicePlan &p) {
+    return p.dtype == POISSON_F32 ? encode_maps_f32(p) : encode_maps_f64(p);
+}
 
 static const int kSupportedN[] = {4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 1024};
 
@@ -60,7 +66,8 @@ static int map_cuda(cudaError_t e) {
 static void free_plan(poisson_plan p) {
     if (!p) return;
     void *twc = p->dp.twc != p->dp.tw ? p->dp.twc : nullptr;
-    void *bufs[] = {p->dp.sym, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->stage_in, p->stage_out};
+    void *bufs[] = {p->dp.sym, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->dp.status,
+                    p->stage_in, p->stage_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->have_events)
@@ -138,6 +145,9 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     if ((e = cudaMemset(p->dp.w1, 0, w1_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.w2, 0, w2_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.w3, 0, w2_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&p->dp.status, sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(p->dp.status, 0, sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = gsp::encode_tma_maps(p->dp)) != cudaSuccess) return fail(e);
 
     // Twiddles W_{2N}^e from FP64 (long double arithmetic), rounded once to the dtype.
     std::vector<double> tw;
@@ -254,6 +264,20 @@ extern "C" int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d,
         if ((e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1])) != cudaSuccess)
             return map_cuda(e);
     return POISSON_OK;
+}
+
+extern "C" int poisson_last_status(poisson_plan p, void *stream) {
+    if (!p) return POISSON_ERR_ARG;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, p->dp.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (h == 0) return POISSON_OK;
+    e = cudaMemsetAsync(p->dp.status, 0, sizeof(int), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    return (h & gsp::kStatusTimeoutBit) ? POISSON_ERR_TIMEOUT : POISSON_ERR_CUDA;
 }
 
 extern "C" int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms,

@@ -337,31 +337,40 @@ struct Stages<C, L, E, D, NS, Radices<R, Rs...>> {
     static_assert(!LAST || NS * R == L, "the radices must multiply to the length");
 
     // Runs this stage and the rest.  ld(row) gives stage-0 inputs, st(row, value) takes
-    // last-stage outputs.  Intermediate values go through sm[row * SP + c].  Every
-    // thread of the block must call this (it synchronises the block between stages).
+    // last-stage outputs.  Intermediate values of this thread's column go through
+    // sm[at(row)]; sync() orders the exchange among the threads that share the column
+    // (every one of them must make the same calls).
     // After a to_regs run the last stage's butterfly b, output r of this thread (row
     // j + r L/R_last, j = q + P b) is v[b * R_last + r]: exactly what a run whose first
     // radix is R_last gathers, so a transform in the other direction with the radices in
     // reverse order can continue from_regs without a shared-memory exchange.
-    template <RunOpt O, class Ld, class St>
-    static __device__ __forceinline__ void run(C *v, int q, int c, C *sm, int SP,
-                                               const Tw *__restrict__ tw, int twstride, Ld &&ld,
-                                               St &&st) {
+    template <RunOpt O, class Ld, class St, class At, class Sync>
+    static __device__ __forceinline__ void run_with(C *v, int q, C *sm, const Tw *__restrict__ tw,
+                                                    int twstride, Ld &&ld, St &&st, At &&at, Sync &&sync) {
         if constexpr (!O.from_regs) S::template gather<O.prune_in>(v, q, ld);
         S::compute(v, q, tw, twstride);
         if constexpr (LAST) {
             if constexpr (!O.to_regs) {
-                if constexpr (O.sync_last) __syncthreads();
+                if constexpr (O.sync_last) sync();
                 S::template scatter<O.prune_out>(v, q, st);
             }
         } else {
-            __syncthreads();  // every read of sm before this stage is done
-            S::template scatter<false>(v, q, [&](int row, C x) { sm[row * SP + c] = x; });
-            __syncthreads();
+            sync();  // every read of sm before this stage is done
+            S::template scatter<false>(v, q, [&](int row, C x) { sm[at(row)] = x; });
+            sync();
             constexpr RunOpt next{false, false, O.to_regs, O.prune_out, O.sync_last};
-            Stages<C, L, E, D, NS * R, Radices<Rs...>>::template run<next>(
-                v, q, c, sm, SP, tw, twstride, [&](int row) { return sm[row * SP + c]; }, st);
+            Stages<C, L, E, D, NS * R, Radices<Rs...>>::template run_with<next>(
+                v, q, sm, tw, twstride, [&](int row) { return sm[at(row)]; }, st, at, sync);
         }
+    }
+
+    // Block-wide form: column c at sm[row * SP + c], exchanges ordered by __syncthreads.
+    template <RunOpt O, class Ld, class St>
+    static __device__ __forceinline__ void run(C *v, int q, int c, C *sm, int SP,
+                                               const Tw *__restrict__ tw, int twstride, Ld &&ld,
+                                               St &&st) {
+        run_with<O>(v, q, sm, tw, twstride, ld, st, [&](int row) { return row * SP + c; },
+                    [] { __syncthreads(); });
     }
 };
 

@@ -260,9 +260,14 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
     dp.w1 = take((size_t)N * N * Px * cx);
     dp.w2 = take((size_t)N * 2 * N * Px * cx);
     dp.w3 = take((size_t)N * 2 * N * Px * cx);
+    dp.status = reinterpret_cast<int *>(take(sizeof(int)));
     if (off > kScratchBytes) return POISSON_ERR_UNSUPPORTED;
+    if (gsp::encode_tma_maps(dp) != cudaSuccess) return POISSON_ERR_CUDA;
 
     cudaError_t e;
+    // Workspace padding columns and the status word start at zero.
+    if ((e = cudaMemsetAsync(dp.w1, 0, (size_t)(st.base + off - (unsigned char *)dp.w1), s)))
+        return map_cuda(e);
     if ((e = cudaMemcpyAsync(dA, h_A, (size_t)S * K * sizeof(double), cudaMemcpyHostToDevice, s)))
         return map_cuda(e);
     if ((e = cudaMemcpyAsync(dw, h_w, (size_t)S * sizeof(double), cudaMemcpyHostToDevice, s)))

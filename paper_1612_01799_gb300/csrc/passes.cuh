@@ -121,6 +121,10 @@ __device__ __forceinline__ CD scale_sym(CD x, const double *s) { return cscale(x
 
 template <typename Real> using Cx2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
 
+}  // namespace gsp
+#include "passes_tma.cuh"
+namespace gsp {
+
 // ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
 template <typename Real, int N>
 __global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
@@ -345,6 +349,32 @@ template <class K> static cudaError_t set_smem(K kernel, size_t bytes) {
         if (e_ != cudaSuccess) return e_;     \
     } while (0)
 
+// Blocks of a persistent kernel: as many as fit on all SMs at once.  The occupancy of
+// each kernel is queried once and cached by the kernel's address.
+template <class K> static int persistent_blocks(K kernel, int threads, size_t smem, int ntiles) {
+    struct Entry {
+        const void *fn;
+        int blocks;
+    };
+    static Entry cache[64];
+    static int n = 0;
+    const void *fn = reinterpret_cast<const void *>(kernel);
+    int blocks = 0;
+    for (int i = 0; i < n; ++i)
+        if (cache[i].fn == fn) blocks = cache[i].blocks;
+    if (blocks == 0) {
+        int dev = 0, sms = 1, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        blocks = per_sm * (sms > 0 ? sms : 1);
+        if (n < 64) cache[n++] = Entry{fn, blocks};
+    }
+    return blocks < ntiles ? blocks : ntiles;
+}
+
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t s, cudaEvent_t *ev) {
     using T2 = Cx2<Real>;
@@ -354,15 +384,16 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     T2 *w1 = static_cast<T2 *>(p.w1), *w2 = static_cast<T2 *>(p.w2), *w3 = static_cast<T2 *>(p.w3);
     const T2 *tw = static_cast<const T2 *>(p.tw);
     const TwC *twc = static_cast<const TwC *>(p.twc);
-    const Real *sym = static_cast<const Real *>(p.sym);
     constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
-    constexpr int TC = col_tc<Real, L>(), NTC = col_threads<Real, L>();
     const size_t smem_row = (size_t)(N + 1) * (TR + 1) * 2 * sizeof(Real);
-    const size_t smem_col = (size_t)L * TC * 2 * sizeof(Real);
     const int nrows = N * N;
     const int ncols = N + 1;
     const dim3 grow((nrows + TR - 1) / TR);
-    const int ntile = (ncols + TC - 1) / TC;
+    using L0 = TmaLayout<Real, L, 0>;
+    using L1 = TmaLayout<Real, L, 1>;
+    using L2 = TmaLayout<Real, L, 2>;
+    const int ntx0 = (ncols + L0::TC - 1) / L0::TC, ntx1 = (ncols + L1::TC - 1) / L1::TC,
+              ntx2 = (ncols + L2::TC - 1) / L2::TC;
 
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
     GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
@@ -371,27 +402,97 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
-    GSP_CHECK(set_smem(k_col<Real, L, true>, smem_col));
-    k_col<Real, L, true><<<dim3(ntile, N), NTC, smem_col, s>>>(
-        w1, w2, twc, ncols, Px, (long long)N * Px, Px, (long long)L * Px);
-    GSP_CHECK(cudaGetLastError());
+    {
+        auto k = k_col_tma<Real, L, 0>;
+        GSP_CHECK(set_smem(k, L0::SMEM));
+        const int nt = ntx0 * N;
+        k<<<persistent_blocks(k, tma_threads<Real, L, 0>(), L0::SMEM, nt), tma_threads<Real, L, 0>(),
+            L0::SMEM, s>>>(p.tm_y_in, w2, twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status);
+        GSP_CHECK(cudaGetLastError());
+    }
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
-    GSP_CHECK(set_smem(k_z_symbol<Real, L>, smem_col));
-    k_z_symbol<Real, L><<<dim3(ntile, L), NTC, smem_col, s>>>(w2, w3, sym, twc, ncols, Px, p.Ps);
-    GSP_CHECK(cudaGetLastError());
+    {
+        auto k = k_z_symbol_tma<Real, L>;
+        GSP_CHECK(set_smem(k, L1::SMEM));
+        const int nt = ntx1 * L;
+        k<<<persistent_blocks(k, tma_threads<Real, L, 1>(), L1::SMEM, nt), tma_threads<Real, L, 1>(),
+            L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx1, nt, ncols, Px, p.status);
+        GSP_CHECK(cudaGetLastError());
+    }
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
 
-    GSP_CHECK(set_smem(k_col<Real, L, false>, smem_col));
-    k_col<Real, L, false><<<dim3(ntile, N), NTC, smem_col, s>>>(
-        w3, w1, twc, ncols, Px, (long long)L * Px, Px, (long long)N * Px);
-    GSP_CHECK(cudaGetLastError());
+    {
+        auto k = k_col_tma<Real, L, 2>;
+        GSP_CHECK(set_smem(k, L2::SMEM));
+        const int nt = ntx2 * N;
+        k<<<persistent_blocks(k, tma_threads<Real, L, 2>(), L2::SMEM, nt), tma_threads<Real, L, 2>(),
+            L2::SMEM, s>>>(p.tm_yi_in, w1, twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status);
+        GSP_CHECK(cudaGetLastError());
+    }
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
     GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
     k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(w1, static_cast<Real *>(u), tw, nrows, Px);
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
+    return cudaSuccess;
+}
+
+// ---- TMA descriptors ----------------------------------------------------------------------
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                       const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                       const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                       CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline TensorMapEncodeFn tensor_map_encoder() {
+    static TensorMapEncodeFn fn = []() -> TensorMapEncodeFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<TensorMapEncodeFn>(f);
+    }();
+    return fn;
+}
+
+// 3-D tiled map: dims d (innermost first), byte strides of dims 1 and 2, box b.
+inline cudaError_t encode_3d(CUtensorMap *m, CUtensorMapDataType dt, void *base, cuuint64_t d0,
+                             cuuint64_t d1, cuuint64_t d2, cuuint64_t s1, cuuint64_t s2, cuuint32_t b0,
+                             cuuint32_t b1, cuuint32_t b2) {
+    TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {s1, s2};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename Real, int N>
+cudaError_t encode_n(DevicePlan &p) {
+    constexpr int L = 2 * N;
+    constexpr cuuint64_t u = 2 * sizeof(Real) / 8;            // 8-byte units per complex
+    const cuuint64_t rowb = (cuuint64_t)p.Px * 2 * sizeof(Real);
+    const CUtensorMapDataType U64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    using L0 = TmaLayout<Real, L, 0>;
+    using L1 = TmaLayout<Real, L, 1>;
+    using L2 = TmaLayout<Real, L, 2>;
+    GSP_CHECK(encode_3d(&p.tm_y_in, U64, p.w1, p.Px * u, N, N, rowb, (cuuint64_t)N * rowb,
+                        L0::ROWB / 8, L0::RPC, 1));
+    GSP_CHECK(encode_3d(&p.tm_z_in, U64, p.w2, p.Px * u, L, N, rowb, (cuuint64_t)L * rowb,
+                        L1::ROWB / 8, 1, L1::RPC));
+    const cuuint64_t srow = (cuuint64_t)p.Ps * sizeof(Real);
+    GSP_CHECK(encode_3d(&p.tm_z_sym,
+                        sizeof(Real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                        p.sym, p.Ps, N + 1, N + 1, srow, (cuuint64_t)(N + 1) * srow, L1::TC, 1, L1::SRC));
+    GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, p.Px * u, L, N, rowb, (cuuint64_t)L * rowb,
+                        L2::ROWB / 8, L2::RPC, 1));
     return cudaSuccess;
 }
 
@@ -405,6 +506,19 @@ cudaError_t solve_dispatch(const DevicePlan &p, const void *rho, void *u, cudaSt
 #define GSP_CASE(n) \
     case n:         \
         return solve_n<Real, n>(p, rho, u, s, ev);
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Real>
+cudaError_t encode_dispatch(DevicePlan &p) {
+    switch (p.N) {
+#define GSP_CASE(n) \
+    case n:         \
+        return encode_n<Real, n>(p);
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE
         default:

@@ -9,4 +9,5 @@ cudaError_t symbol_table_f64(const DevicePlan &p, const double *dA, const double
                              double C0, double C2, double scale, cudaStream_t s) {
     return symbol_table<double>(p, dA, dw, nterms, C0, C2, scale, s);
 }
+cudaError_t encode_maps_f64(DevicePlan &p) { return encode_dispatch<double>(p); }
 }  // namespace gsp

@@ -1,0 +1,289 @@
+// Column passes (y forward, z fused, y inverse) with TMA-staged input tiles.
+//
+// Persistent CTAs walk the tiles of a pass (TC consecutive columns of one transform
+// line).  A tile's input is one 3-D TMA box (TC columns x the nonzero input rows, split
+// into copies of at most 256 rows) landing in shared memory and signalled on an mbarrier.
+// As soon as every thread has pulled its stage-0 inputs out of the staging buffer into
+// registers, one thread issues the TMA for the CTA's next tile into the same buffer, so
+// the next tile's HBM read overlaps this tile's FFT stages and stores.  The FFT stages are
+// the register/shared-memory Stockham stages of fft_core.cuh; outputs go straight from
+// the last stage's registers to HBM.  The z pass also stages its symbol rows
+// (TC columns x N+1 kz values of the octant) with a second TMA box per tile.
+// All mbarrier waits are bounded (tma.cuh); on a timeout the whole CTA leaves.
+#pragma once
+#include "tma.cuh"
+
+namespace gsp {
+
+template <class RL> struct FirstRadix;
+template <int R, int... Rs> struct FirstRadix<Radices<R, Rs...>> { static constexpr int v = R; };
+
+// TMA copies of `rows` rows of row_bytes each, and rows per copy: at most 256 rows per
+// copy (the box limit), and every copy's shared-memory destination 128-byte aligned (rows
+// per copy a multiple of 128 / row_bytes).  Rows past the tensor's end are zero-filled by
+// the TMA unit.
+__host__ __device__ constexpr int tma_row_align(int row_bytes) { return row_bytes >= 128 ? 1 : 128 / row_bytes; }
+__host__ __device__ constexpr int tma_rpc_for(int rows, int nc, int row_bytes) {
+    return ((rows + nc - 1) / nc + tma_row_align(row_bytes) - 1) / tma_row_align(row_bytes) *
+           tma_row_align(row_bytes);
+}
+__host__ __device__ constexpr int tma_ncopy(int rows, int row_bytes) {
+    int nc = (rows + 255) / 256;
+    while (tma_rpc_for(rows, nc, row_bytes) > 256) ++nc;
+    return nc;
+}
+__host__ __device__ constexpr int tma_rows_per_copy(int rows, int row_bytes) {
+    return tma_rpc_for(rows, tma_ncopy(rows, row_bytes), row_bytes);
+}
+
+// Shared memory of a TMA column pass with tile width tc (KIND 0: y forward, 1: z fused,
+// 2: y inverse): 128 bytes of alignment slack, the staged input rows, the L-row exchange
+// buffer and the z pass's symbol rows.
+template <typename Real, int L, int KIND> __host__ __device__ constexpr int tma_smem(int tc) {
+    const int s = (int)sizeof(Real);
+    const int lin = KIND == 2 ? L : L / 2;
+    const int rb = tc * 2 * s, sb = tc * s;
+    const int in_rows = tma_ncopy(lin, rb) * tma_rows_per_copy(lin, rb);
+    const int srows = KIND == 1 ? tma_ncopy(L / 2 + 1, sb) * tma_rows_per_copy(L / 2 + 1, sb) : 0;
+    const int bytes = 128 + in_rows * rb + L * tc * 2 * s + srows * sb;
+    return (bytes + 15) / 16 * 16 + 16;
+}
+
+// Columns per CTA of the TMA column passes: 128-byte tile rows (16 FP32 or 8 FP64 complex),
+// half that for the y inverse (it stages all L input rows next to its L-row exchange
+// buffer), narrowed until the block has <= 1024 threads and its shared memory fits in
+// 227 KB.  The narrowest tile keeps every TMA box row a multiple of 16 bytes (symbol
+// rows: tc * sizeof(Real)).
+template <typename Real, int L, int KIND> __host__ __device__ constexpr int tma_tc() {
+    int tc = sizeof(Real) == 4 ? 16 : 8;
+    if (KIND == 2) tc /= 2;
+    const int W = Types<Real>::W;
+    const int P = L / FftCfg<L>::E;
+    const int tc_min = sizeof(Real) == 4 ? 4 : 2;
+    while (tc > tc_min && ((tc / W) * P > 1024 || tma_smem<Real, L, KIND>(tc) > 232448)) tc /= 2;
+    return tc;
+}
+template <typename Real, int L, int KIND> __host__ __device__ constexpr int tma_threads() {
+    return (tma_tc<Real, L, KIND>() / Types<Real>::W) * (L / FftCfg<L>::E);
+}
+
+template <typename Real, int L, int KIND> struct TmaLayout {
+    static constexpr int N = L / 2;
+    static constexpr int TC = tma_tc<Real, L, KIND>();
+    static constexpr int W = Types<Real>::W;
+    static constexpr int NG = TC / W;                                  // column groups (16 B each)
+    static constexpr int P = L / FftCfg<L>::E;                         // threads per group
+    static constexpr int ROWB = TC * 2 * (int)sizeof(Real);            // bytes of one tile row
+    static constexpr int LIN = KIND == 2 ? L : N;                      // input rows per tile
+    static constexpr int NCP = tma_ncopy(LIN, ROWB);
+    static constexpr int RPC = tma_rows_per_copy(LIN, ROWB);
+    static constexpr int IN_ROWS = NCP * RPC;
+    static constexpr int SROWS_N = N + 1;                              // symbol rows (kz <= N)
+    static constexpr int SROWB = TC * (int)sizeof(Real);               // bytes of one symbol row
+    static constexpr int NCS = tma_ncopy(SROWS_N, SROWB);
+    static constexpr int SRC = tma_rows_per_copy(SROWS_N, SROWB);
+    static constexpr int S_ROWS = KIND == 1 ? NCS * SRC : 0;
+    static constexpr int IN_BYTES = IN_ROWS * ROWB;
+    static constexpr int XB_BYTES = L * NG * (int)sizeof(typename Types<Real>::CC);
+    static constexpr int S_BYTES = S_ROWS * SROWB;
+    static constexpr int OFF_XB = IN_BYTES;                             // from the aligned base
+    static constexpr int OFF_S = OFF_XB + XB_BYTES;
+    static constexpr int OFF_BAR = (OFF_S + S_BYTES + 15) / 16 * 16;
+    static constexpr int SMEM = 128 + OFF_BAR + 16;
+    static_assert(SMEM == tma_smem<Real, L, KIND>(TC), "layout and size agree");
+    static_assert(SMEM <= 232448, "shared memory of one CTA");
+    static_assert(NG * P <= 1024, "threads of one CTA");
+    static_assert(ROWB % 16 == 0 && SROWB % 16 == 0, "16-byte TMA box rows");
+    static_assert((RPC * ROWB) % 128 == 0 && IN_BYTES % 128 == 0, "128-byte aligned input copies");
+    static_assert(OFF_S % 128 == 0 && (KIND != 1 || (SRC * SROWB) % 128 == 0), "128-byte aligned symbol copies");
+    static_assert(RPC <= 256 && SRC <= 256, "TMA box rows");
+};
+
+template <typename C> __device__ __forceinline__ C ld_sm_cc(const unsigned char *p);
+template <> __device__ __forceinline__ CV ld_sm_cc<CV>(const unsigned char *p) {
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    return {make_float2(f.x, f.z), make_float2(f.y, f.w)};
+}
+template <> __device__ __forceinline__ CD ld_sm_cc<CD>(const unsigned char *p) {
+    const double2 f = *reinterpret_cast<const double2 *>(p);
+    return {f.x, f.y};
+}
+__device__ __forceinline__ CV scale_sym_sm(CV x, const float *s) {
+    return cscale2(x, *reinterpret_cast<const float2 *>(s));
+}
+__device__ __forceinline__ CD scale_sym_sm(CD x, const double *s) { return cscale(x, *s); }
+
+// Blocks per SM requested from the compiler: enough that 128 registers per thread fit.
+template <int T> __host__ __device__ constexpr int min_blocks_128() { return T >= 512 ? 1 : 512 / T; }
+
+// ---- K2 / K4 -----------------------------------------------------------------------------
+// KIND 0 (y forward): tile = (tx, z); input rows y < N of w1, outputs all 2N rows of w2.
+// KIND 2 (y inverse): tile = (tx, z); input rows ky < 2N of w3, outputs y < N of w1.
+// Thread t serves column group g = t mod NG (16 bytes of each row: two FP32 or one FP64
+// column) as its q = t / NG-th thread, so the lanes of a warp cover consecutive groups of
+// the same rows and every global store of a warp is a contiguous row segment.
+template <typename Real, int L, int KIND>
+__global__ void __launch_bounds__(tma_threads<Real, L, KIND>(), min_blocks_128<tma_threads<Real, L, KIND>()>())
+k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
+          const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
+          int ncols, long long out_row, long long out_outer, int *__restrict__ status) {
+    using C = typename Types<Real>::CC;
+    using Lay = TmaLayout<Real, L, KIND>;
+    using Rs = typename FftCfg<L>::Rs;
+    constexpr bool FWD = KIND == 0;
+    constexpr int E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P, R0 = FirstRadix<Rs>::v;
+    constexpr int TCU = Lay::ROWB / 8;  // box width in 8-byte units
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
+    unsigned char *inb = base;
+    C *xb = reinterpret_cast<C *>(base + Lay::OFF_XB);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Lay::OFF_BAR);
+    constexpr int NG = Lay::NG;
+    const int g = threadIdx.x % NG, q = threadIdx.x / NG;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int tx = t % ntx, outer = t / ntx;
+        mbar_arrive_expect_tx(bar, Lay::IN_BYTES);
+#pragma unroll
+        for (int c = 0; c < Lay::NCP; ++c)
+            tma_load_3d(inb + c * Lay::RPC * Lay::ROWB, &tin, bar, tx * TCU, c * Lay::RPC, outer);
+    };
+    int t = blockIdx.x;
+    if (threadIdx.x == 0 && t < ntiles) issue(t);
+    uint32_t phase = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        const int tx = t % ntx, outer = t / ntx;
+        const int col = tx * TC + W * g;
+        const bool valid = col < ncols;
+        const bool ok = mbar_wait(bar, phase, status);
+        if (__syncthreads_or(!ok)) return;
+        phase ^= 1;
+        C v[E];
+        Stage<C, L, E, FWD ? -1 : 1, R0, 1>::template gather<FWD>(v, q, [&](int row) {
+            return ld_sm_cc<C>(inb + row * Lay::ROWB + g * 16);
+        });
+        __syncthreads();  // the staging buffer is free: fetch the next tile behind this one
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x);
+        }
+        Cx2<Real> *dst = out + (long long)outer * out_outer + col;
+        constexpr RunOpt opt{true, false, false, !FWD, false};
+        Stages<C, L, E, FWD ? -1 : 1, 1, Rs>::template run<opt>(
+            v, q, g, xb, NG, tw, 1, [&](int) { return czero<C>(); },
+            [&](int row, C x) {
+                if (valid) st_cc(dst + row * out_row, x);
+            });
+    }
+}
+
+// ---- K3 ----------------------------------------------------------------------------------
+// Tile = (tx, ky): input z < N rows of w2, symbol rows kz <= N of the octant at |ky|,
+// output z < N rows of w3.
+template <typename Real, int L>
+__global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_128<tma_threads<Real, L, 1>()>())
+k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
+               Cx2<Real> *__restrict__ out,
+               const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
+               int ncols, int Px, int *__restrict__ status) {
+    using C = typename Types<Real>::CC;
+    using Lay = TmaLayout<Real, L, 1>;
+    using Rs = typename FftCfg<L>::Rs;
+    using Rv = Reverse<Rs>;
+    constexpr int N = L / 2, E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P;
+    constexpr int RL = LastRadix<Rs>::v, R0 = FirstRadix<Rs>::v;
+    constexpr int TCU = Lay::ROWB / 8;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
+    unsigned char *inb = base;
+    C *xb = reinterpret_cast<C *>(base + Lay::OFF_XB);
+    Real *sb = reinterpret_cast<Real *>(base + Lay::OFF_S);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Lay::OFF_BAR);  // [0] input, [1] symbol
+    constexpr int NG = Lay::NG;
+    const int g = threadIdx.x % NG, q = threadIdx.x / NG;
+    const long long zs = (long long)L * Px;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // Consecutive tiles take ky and its mirror 2N - ky, which read the same symbol rows.
+    auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
+    auto issue_in = [&](int t) {
+        const int tx = t % ntx, ky = ky_of(t / ntx);
+        mbar_arrive_expect_tx(bar, Lay::IN_BYTES);
+#pragma unroll
+        for (int c = 0; c < Lay::NCP; ++c)
+            tma_load_3d(inb + c * Lay::RPC * Lay::ROWB, &tin, bar, tx * TCU, ky, c * Lay::RPC);
+    };
+    auto issue_sym = [&](int t) {
+        const int tx = t % ntx, ky = ky_of(t / ntx);
+        const int kya = ky <= N ? ky : L - ky;
+        mbar_arrive_expect_tx(bar + 1, Lay::S_BYTES);
+#pragma unroll
+        for (int c = 0; c < Lay::NCS; ++c)
+            tma_load_3d(reinterpret_cast<unsigned char *>(sb) + c * Lay::SRC * Lay::SROWB, &tsym, bar + 1,
+                        tx * TC, kya, c * Lay::SRC);
+    };
+    int t = blockIdx.x;
+    if (threadIdx.x == 0 && t < ntiles) {
+        issue_in(t);
+        issue_sym(t);
+    }
+    uint32_t phase = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        const int tx = t % ntx, ky = ky_of(t / ntx);
+        const int col = tx * TC + W * g;
+        const bool valid = col < ncols;
+        const bool more = t + (int)gridDim.x < ntiles;
+        bool ok = mbar_wait(bar, phase, status);
+        if (__syncthreads_or(!ok)) return;
+        C v[E];
+        Stage<C, L, E, -1, R0, 1>::template gather<true>(v, q, [&](int row) {
+            return ld_sm_cc<C>(inb + row * Lay::ROWB + g * 16);
+        });
+        __syncthreads();
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_in(t + gridDim.x);
+        }
+        constexpr RunOpt fwd{true, false, true, false, false};
+        Stages<C, L, E, -1, 1, Rs>::template run<fwd>(
+            v, q, g, xb, NG, tw, 1, [&](int) { return czero<C>(); }, [&](int, C) {});
+        ok = mbar_wait(bar + 1, phase, status);
+        if (__syncthreads_or(!ok)) return;
+        phase ^= 1;
+        // The forward's last stage (radix RL) left row j + r L/RL of butterfly b in v[b RL + r].
+#pragma unroll
+        for (int b = 0; b < E / RL; ++b) {
+            const int j = q + P * b;
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                const int row = j + r * (L / RL);
+                const int kz = row <= N ? row : L - row;
+                v[b * RL + r] = scale_sym_sm(v[b * RL + r], sb + kz * TC + W * g);
+            }
+        }
+        __syncthreads();  // the symbol buffer is free
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_sym(t + gridDim.x);
+        }
+        Cx2<Real> *dst = out + (long long)ky * Px + col;
+        constexpr RunOpt inv{true, false, false, true, false};
+        Stages<C, L, E, 1, 1, Rv>::template run<inv>(
+            v, q, g, xb, NG, tw, 1, [&](int) { return czero<C>(); },
+            [&](int row, C x) {
+                if (valid) st_cc(dst + row * zs, x);
+            });
+    }
+}
+
+}  // namespace gsp

@@ -1,5 +1,6 @@
 // Internal interface between the C-ABI layer and the CUDA passes.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -28,12 +29,22 @@ struct DevicePlan {
     void *w1 = nullptr;
     void *w2 = nullptr;
     void *w3 = nullptr;
+    int *status = nullptr;  // device status word (bit 0: a bounded wait timed out)
+    // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
+    // y inverse: w3), encoded once for these buffers.
+    CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
 };
+
+constexpr int kStatusTimeoutBit = 1;  // bit of DevicePlan::status set by a timed-out wait
 
 inline int pitch_for(int N) { return ((N + 1 + 15) / 16) * 16; }
 inline int sym_pitch_for(int N) { return ((N + 1 + 3) / 4) * 4; }
 
 bool n_supported(int N);
+
+// Encode the TMA descriptors of p for its buffers.  Returns cudaSuccess or an error
+// (cudaErrorNotSupported when the driver has no tensor-map encoder).
+cudaError_t encode_tma_maps(DevicePlan &p);
 
 // The five passes of one solve on `s`.  ev: null, or 6 events recorded before pass 1,
 // between the passes and after pass 5.
