@@ -113,8 +113,12 @@ __device__ __forceinline__ CV scale_sym_sm(CV x, const float *s) {
 }
 __device__ __forceinline__ CD scale_sym_sm(CD x, const double *s) { return cscale(x, *s); }
 
-// Blocks per SM requested from the compiler: enough that 128 registers per thread fit.
-template <int T> __host__ __device__ constexpr int min_blocks_128() { return T >= 512 ? 1 : 512 / T; }
+// Blocks per SM requested from the compiler: a register budget of 64 per thread for E <= 8
+// values per thread, 128 otherwise.
+template <int T, int E> __host__ __device__ constexpr int min_blocks_for() {
+    const int regs = E <= 8 ? 64 : 128;
+    return 65536 / (T * regs) > 0 ? 65536 / (T * regs) : 1;
+}
 
 // ---- K2 / K4 -----------------------------------------------------------------------------
 // KIND 0 (y forward): tile = (tx, z); input rows y < N of w1, outputs all 2N rows of w2.
@@ -123,7 +127,7 @@ template <int T> __host__ __device__ constexpr int min_blocks_128() { return T >
 // column) as its q = t / NG-th thread, so the lanes of a warp cover consecutive groups of
 // the same rows and every global store of a warp is a contiguous row segment.
 template <typename Real, int L, int KIND>
-__global__ void __launch_bounds__(tma_threads<Real, L, KIND>(), min_blocks_128<tma_threads<Real, L, KIND>()>())
+__global__ void __launch_bounds__(tma_threads<Real, L, KIND>(), min_blocks_for<tma_threads<Real, L, KIND>(), FftCfg<L>::E>())
 k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
           const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
           int ncols, long long out_row, long long out_outer, int *__restrict__ status) {
@@ -186,7 +190,7 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
 // Tile = (tx, ky): input z < N rows of w2, symbol rows kz <= N of the octant at |ky|,
 // output z < N rows of w3.
 template <typename Real, int L>
-__global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_128<tma_threads<Real, L, 1>()>())
+__global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_for<tma_threads<Real, L, 1>(), FftCfg<L>::E>())
 k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
                Cx2<Real> *__restrict__ out,
                const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
