@@ -69,6 +69,14 @@ enum {
  */
 int poisson_plan_create(poisson_plan *out, int N, double L, double tol, int dtype);
 
+/*
+ * A plan whose workspace holds up to max_batch densities (1 <= max_batch <= 64) of this
+ * geometry, so that poisson_solve_batched solves all its entries with one launch per pass.
+ * Same arguments and errors as poisson_plan_create; the workspace grows by max_batch.
+ */
+int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, int dtype,
+                                int max_batch);
+
 /* Free a plan and its device memory.  NULL is accepted.  The caller must make sure no
  * solve on the plan is still running (synchronise its stream first). */
 int poisson_plan_destroy(poisson_plan p);
@@ -95,9 +103,12 @@ int poisson_solve(poisson_plan p, const void *rho_d, void *u_d, void *stream);
 int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream);
 
 /*
- * Solves of several independent densities, possibly of different N, in stream order.
- * plans[i], rho_d[i], u_d[i] as for poisson_solve; all plans on the current device.
- * count >= 0.  A plan must not appear twice in one call (its workspace is shared).
+ * Solves of several independent densities, possibly of different N, stream ordered with
+ * respect to `stream`.  plans[i], rho_d[i], u_d[i] as for poisson_solve; all plans on one
+ * device; count >= 0.  Entries that share a plan are solved together, at most the plan's
+ * max_batch at a time, with one launch per pass; the groups of different plans run
+ * concurrently on streams forked from `stream` and joined back to it, so the call can be
+ * captured into a CUDA graph (the fork streams are created with the device's first plan).
  */
 int poisson_solve_batched(int count, const poisson_plan *plans, const void *const *rho_d,
                           void *const *u_d, void *stream);

@@ -29,14 +29,16 @@ class Plan:
     """A solve plan for the cube [-L, L]^3 with N cell-centred points per axis
     (setup phase: Gaussian sum, G-tensor factors, near-zone constants, symbol table)."""
 
-    def __init__(self, N, L, tol, dtype="f32"):
+    def __init__(self, N, L, tol, dtype="f32", max_batch=1):
         if dtype not in DTYPES:
             raise ValueError("dtype must be 'f32' or 'f64'")
         self.N, self.L, self.tol, self.dtype = int(N), float(L), float(tol), dtype
+        self.max_batch = int(max_batch)
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
-        _lib.check(self._lib.poisson_plan_create(ctypes.byref(self._h), self.N, self.L, self.tol,
-                                                 DTYPES[dtype]), "poisson_plan_create")
+        _lib.check(self._lib.poisson_plan_create_batched(ctypes.byref(self._h), self.N, self.L,
+                                                         self.tol, DTYPES[dtype], self.max_batch),
+                   "poisson_plan_create_batched")
 
     @property
     def handle(self):
@@ -101,6 +103,10 @@ class Plan:
                                                  _stream_handle(stream), ms), "poisson_solve_timed")
         return list(ms)
 
+    def last_status(self, stream=None):
+        """Synchronise the stream and raise if a bounded device wait of a solve gave up."""
+        _lib.check(self._lib.poisson_last_status(self._h, _stream_handle(stream)), "poisson_last_status")
+
     def info(self):
         d, e, c0, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         n = ctypes.c_int()
@@ -145,7 +151,8 @@ class Plan:
 
 
 def solve_batched(plans, rhos, outs, stream=None):
-    """Independent solves (uneven N allowed) through poisson_solve_batched."""
+    """Independent solves (uneven N allowed) through poisson_solve_batched.  Entries that
+    share a plan are solved together (up to the plan's max_batch per launch sequence)."""
     n = len(plans)
     if not (len(rhos) == len(outs) == n):
         raise ValueError("plans, rhos and outs must have the same length")

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -11,8 +12,8 @@
 #include "solver.h"
 
 namespace gsp {
-cudaError_t solve_f32(const DevicePlan &, const void *, void *, cudaStream_t, cudaEvent_t *);
-cudaError_t solve_f64(const DevicePlan &, const void *, void *, cudaStream_t, cudaEvent_t *);
+cudaError_t solve_f32(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *);
+cudaError_t solve_f64(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *);
 cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *, int, double,
                              double, double, cudaStream_t);
 cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
@@ -32,9 +33,38 @@ bool n_supported(int N) {
     return false;
 }
 
-cudaError_t launch_solve(const DevicePlan &p, const void *rho, void *u, cudaStream_t s,
-                         cudaEvent_t *ev) {
-    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, s, ev) : solve_f64(p, rho, u, s, ev);
+cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
+                         cudaStream_t s, cudaEvent_t *ev) {
+    if (count < 1 || count > p.max_batch || count > kMaxBatch) return cudaErrorInvalidValue;
+    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, count, s, ev) : solve_f64(p, rho, u, count, s, ev);
+}
+
+// Streams that poisson_solve_batched forks independent plan groups onto (per device,
+// created with the first plan on the device, so that a batched call can be captured).
+struct ForkPool {
+    static constexpr int kStreams = 8;
+    bool ready = false;
+    cudaStream_t st[kStreams];
+    cudaEvent_t fork, join[kStreams];
+};
+static ForkPool g_pools[64];
+static std::mutex g_pool_mutex;
+
+static cudaError_t fork_pool(int dev, ForkPool **out) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    ForkPool &fp = g_pools[dev];
+    if (!fp.ready) {
+        cudaError_t e;
+        for (int i = 0; i < ForkPool::kStreams; ++i) {
+            if ((e = cudaStreamCreateWithFlags(&fp.st[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&fp.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventCreateWithFlags(&fp.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        fp.ready = true;
+    }
+    *out = &fp;
+    return cudaSuccess;
 }
 
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
@@ -91,10 +121,16 @@ extern "C" const char *poisson_strerror(int code) {
 }
 
 extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double tol, int dtype) {
+    return poisson_plan_create_batched(out, N, L, tol, dtype, 1);
+}
+
+extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, int dtype,
+                                           int max_batch) {
     if (!out) return POISSON_ERR_ARG;
     *out = nullptr;
     if (dtype != POISSON_F32 && dtype != POISSON_F64) return POISSON_ERR_ARG;
     if (N < 4 || N > 1024 || (N & 1)) return POISSON_ERR_ARG;
+    if (max_batch < 1 || max_batch > gsp::kMaxBatch) return POISSON_ERR_ARG;
     if (!gsp::n_supported(N)) return POISSON_ERR_UNSUPPORTED;
     poisson_plan p = new (std::nothrow) poisson_plan_s();
     if (!p) return POISSON_ERR_ALLOC;
@@ -109,6 +145,7 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
         return map_cuda(e);
     }
     p->elem = dtype == POISSON_F32 ? 4 : 8;
+    p->dp.max_batch = max_batch;
     p->dp.N = N;
     p->dp.dtype = dtype;
     p->dp.Px = gsp::pitch_for(N);
@@ -118,9 +155,9 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     const size_t sym_bytes = K * K * (size_t)p->dp.Ps * p->elem;
     const size_t tw_bytes = (size_t)2 * N * cx;
     const size_t twc_bytes = dtype == POISSON_F32 ? (size_t)2 * N * 4 * sizeof(float) : 0;
-    const size_t w1_bytes = (size_t)N * N * p->dp.Px * cx;
-    const size_t w2_bytes = (size_t)N * 2 * N * p->dp.Px * cx;
-    p->ws_bytes = w1_bytes + 2 * w2_bytes;
+    const size_t w1_bytes = (size_t)max_batch * N * N * p->dp.Px * cx;
+    const size_t w2_bytes = (size_t)max_batch * N * 2 * N * p->dp.Px * cx;
+    p->ws_bytes = w1_bytes + 2 * w2_bytes;  // for max_batch densities
     p->table_bytes = sym_bytes + tw_bytes + twc_bytes;
 
     double *dA = nullptr, *dw = nullptr;
@@ -148,6 +185,8 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     if ((e = cudaMalloc(&p->dp.status, sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.status, 0, sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = gsp::encode_tma_maps(p->dp)) != cudaSuccess) return fail(e);
+    gsp::ForkPool *pool = nullptr;
+    if ((e = gsp::fork_pool(p->device, &pool)) != cudaSuccess) return fail(e);
 
     // Twiddles W_{2N}^e from FP64 (long double arithmetic), rounded once to the dtype.
     std::vector<double> tw;
@@ -200,10 +239,18 @@ static int check_solve_args(poisson_plan p, const void *rho, const void *u) {
     return POISSON_OK;
 }
 
+static void one(gsp::PtrArray &a, const void *ptr) {
+    a.p[0] = ptr;
+    for (int i = 1; i < gsp::kMaxBatch; ++i) a.p[i] = nullptr;
+}
+
 extern "C" int poisson_solve(poisson_plan p, const void *rho_d, void *u_d, void *stream) {
     int rc = check_solve_args(p, rho_d, u_d);
     if (rc) return rc;
-    return map_cuda(gsp::launch_solve(p->dp, rho_d, u_d, (cudaStream_t)stream, nullptr));
+    gsp::PtrArray in, out;
+    one(in, rho_d);
+    one(out, u_d);
+    return map_cuda(gsp::launch_solve(p->dp, in, out, 1, (cudaStream_t)stream, nullptr));
 }
 
 extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream) {
@@ -220,8 +267,10 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
     cudaStream_t s = (cudaStream_t)stream;
     if ((e = cudaMemcpyAsync(p->stage_in, rho_h, n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return map_cuda(e);
-    if ((e = gsp::launch_solve(p->dp, p->stage_in, p->stage_out, s, nullptr)) != cudaSuccess)
-        return map_cuda(e);
+    gsp::PtrArray in, out;
+    one(in, p->stage_in);
+    one(out, p->stage_out);
+    if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr)) != cudaSuccess) return map_cuda(e);
     if ((e = cudaMemcpyAsync(u_h, p->stage_out, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return map_cuda(e);
     return map_cuda(cudaStreamSynchronize(s));
@@ -235,13 +284,46 @@ extern "C" int poisson_solve_batched(int count, const poisson_plan *plans,
     for (int i = 0; i < count; ++i) {
         int rc = check_solve_args(plans[i], rho_d[i], u_d[i]);
         if (rc) return rc;
-        for (int k = 0; k < i; ++k)
-            if (plans[k] == plans[i]) return POISSON_ERR_ARG;
+        if (plans[i]->device != plans[0]->device) return POISSON_ERR_ARG;
     }
+    // Group the entries by plan (first-appearance order); each group runs as grouped
+    // launches of at most max_batch densities, groups on separate forked streams.
+    std::vector<poisson_plan> order;
+    std::vector<std::vector<int>> members;
     for (int i = 0; i < count; ++i) {
-        cudaError_t e =
-            gsp::launch_solve(plans[i]->dp, rho_d[i], u_d[i], (cudaStream_t)stream, nullptr);
-        if (e != cudaSuccess) return map_cuda(e);
+        size_t k = 0;
+        while (k < order.size() && order[k] != plans[i]) ++k;
+        if (k == order.size()) {
+            order.push_back(plans[i]);
+            members.emplace_back();
+        }
+        members[k].push_back(i);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    gsp::ForkPool *pool = nullptr;
+    cudaError_t e = gsp::fork_pool(plans[0]->device, &pool);
+    if (e != cudaSuccess) return map_cuda(e);
+    const bool fork = order.size() > 1;
+    if (fork && (e = cudaEventRecord(pool->fork, s)) != cudaSuccess) return map_cuda(e);
+    for (size_t k = 0; k < order.size(); ++k) {
+        const int slot = (int)(k % gsp::ForkPool::kStreams);
+        cudaStream_t ts = fork ? pool->st[slot] : s;
+        if (fork && (e = cudaStreamWaitEvent(ts, pool->fork, 0)) != cudaSuccess) return map_cuda(e);
+        const gsp::DevicePlan &dp = order[k]->dp;
+        const std::vector<int> &m = members[k];
+        for (size_t c0 = 0; c0 < m.size(); c0 += (size_t)dp.max_batch) {
+            const int n = (int)std::min(m.size() - c0, (size_t)dp.max_batch);
+            gsp::PtrArray in, out;
+            for (int i = 0; i < gsp::kMaxBatch; ++i) {
+                in.p[i] = i < n ? rho_d[m[c0 + i]] : nullptr;
+                out.p[i] = i < n ? u_d[m[c0 + i]] : nullptr;
+            }
+            if ((e = gsp::launch_solve(dp, in, out, n, ts, nullptr)) != cudaSuccess) return map_cuda(e);
+        }
+        if (fork) {
+            if ((e = cudaEventRecord(pool->join[slot], ts)) != cudaSuccess) return map_cuda(e);
+            if ((e = cudaStreamWaitEvent(s, pool->join[slot], 0)) != cudaSuccess) return map_cuda(e);
+        }
     }
     return POISSON_OK;
 }
@@ -257,7 +339,10 @@ extern "C" int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d,
             if ((e = cudaEventCreate(&p->ev[i])) != cudaSuccess) return map_cuda(e);
         p->have_events = true;
     }
-    if ((e = gsp::launch_solve(p->dp, rho_d, u_d, (cudaStream_t)stream, p->ev)) != cudaSuccess)
+    gsp::PtrArray in, out;
+    one(in, rho_d);
+    one(out, u_d);
+    if ((e = gsp::launch_solve(p->dp, in, out, 1, (cudaStream_t)stream, p->ev)) != cudaSuccess)
         return map_cuda(e);
     if ((e = cudaEventSynchronize(p->ev[5])) != cudaSuccess) return map_cuda(e);
     for (int i = 0; i < 5; ++i)

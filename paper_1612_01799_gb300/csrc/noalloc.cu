@@ -322,5 +322,9 @@ extern "C" int poisson_solve_noalloc(int N, double L, double tol, int dtype, con
         int rc = setup(st, N, L, tol, dtype, s);
         if (rc) return rc;
     }
-    return map_cuda(gsp::launch_solve(st.dp, rho_d, u_d, s, nullptr));
+    gsp::PtrArray in, out;
+    in.p[0] = rho_d;
+    out.p[0] = u_d;
+    for (int i = 1; i < gsp::kMaxBatch; ++i) in.p[i] = out.p[i] = nullptr;
+    return map_cuda(gsp::launch_solve(st.dp, in, out, 1, s, nullptr));
 }

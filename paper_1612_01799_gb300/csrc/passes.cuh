@@ -126,20 +126,24 @@ template <typename Real> using Cx2 = typename std::conditional<sizeof(Real) == 4
 namespace gsp {
 
 // ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
+// Rows (y, z) of all densities are numbered b N^2 + y + N z; a CTA's TR rows never straddle
+// two densities (TR divides N^2).
 template <typename Real, int N>
 __global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
-k_x_forward(const Real *__restrict__ rho, Cx2<Real> *__restrict__ out,
-            const Cx2<Real> *__restrict__ tw, int nrows, int Px) {
+k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__restrict__ tw,
+            int nrows, int Px) {
     using C = typename Types<Real>::CS;
     using T2 = Cx2<Real>;
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
+    static_assert((N * N) % TR == 0, "row tiles stay inside one density");
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);  // (N + 1) x SP
     const int t = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * TR;
     const int nr = (int)min((long long)TR, (long long)nrows - r0);
+    const int b = (int)(r0 / (N * N));
     // The tile is nr consecutive rows of N reals: contiguous N/2-pair chunks.
-    const T2 *src = reinterpret_cast<const T2 *>(rho) + r0 * (N / 2);
+    const T2 *src = reinterpret_cast<const T2 *>(rho.p[b]) + (r0 - (long long)b * N * N) * (N / 2);
     for (int e = t; e < nr * (N / 2); e += NT) {
         const int r = e / (N / 2), m = e - r * (N / 2);
         const T2 f = __ldg(src + e);
@@ -263,7 +267,7 @@ k_z_symbol(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out, const 
 // ---- K5: x inverse (Hermitian N+1 bins -> N real samples) -------------------------------
 template <typename Real, int N>
 __global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
-k_x_inverse(const Cx2<Real> *__restrict__ in, Real *__restrict__ u, const Cx2<Real> *__restrict__ tw,
+k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> *__restrict__ tw,
             int nrows, int Px) {
     using C = typename Types<Real>::CS;
     using T2 = Cx2<Real>;
@@ -305,7 +309,8 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, Real *__restrict__ u, const Cx2<Re
         v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
         [&](int row, C x) { sm[row * SP + c] = x; });
     __syncthreads();
-    T2 *dst = reinterpret_cast<T2 *>(u) + r0 * (N / 2);
+    const int b = (int)(r0 / (N * N));
+    T2 *dst = reinterpret_cast<T2 *>(const_cast<void *>(u.p[b])) + (r0 - (long long)b * N * N) * (N / 2);
     for (int e = t; e < nr * (N / 2); e += NT) {
         const int r = e / (N / 2), m = e - r * (N / 2);
         const C x = sm[m * SP + r];
@@ -376,7 +381,8 @@ template <class K> static int persistent_blocks(K kernel, int threads, size_t sm
 }
 
 template <typename Real, int N>
-cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t s, cudaEvent_t *ev) {
+cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
+                    cudaEvent_t *ev) {
     using T2 = Cx2<Real>;
     using TwC = typename TwOf<typename Types<Real>::CC>::T;
     constexpr int L = 2 * N;
@@ -386,7 +392,7 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     const TwC *twc = static_cast<const TwC *>(p.twc);
     constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
     const size_t smem_row = (size_t)(N + 1) * (TR + 1) * 2 * sizeof(Real);
-    const int nrows = N * N;
+    const int nrows = B * N * N;
     const int ncols = N + 1;
     const dim3 grow((nrows + TR - 1) / TR);
     using L0 = TmaLayout<Real, L, 0>;
@@ -397,15 +403,14 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
 
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
     GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
-    k_x_forward<Real, N><<<grow, TR * PX1, smem_row, s>>>(static_cast<const Real *>(rho), w1, tw,
-                                                           nrows, Px);
+    k_x_forward<Real, N><<<grow, TR * PX1, smem_row, s>>>(rho, w1, tw, nrows, Px);
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
     {
         auto k = k_col_tma<Real, L, 0>;
         GSP_CHECK(set_smem(k, L0::SMEM));
-        const int nt = ntx0 * N;
+        const int nt = ntx0 * B * N;
         k<<<persistent_blocks(k, tma_threads<Real, L, 0>(), L0::SMEM, nt), tma_threads<Real, L, 0>(),
             L0::SMEM, s>>>(p.tm_y_in, w2, twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status);
         GSP_CHECK(cudaGetLastError());
@@ -415,7 +420,7 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     {
         auto k = k_z_symbol_tma<Real, L>;
         GSP_CHECK(set_smem(k, L1::SMEM));
-        const int nt = ntx1 * L;
+        const int nt = ntx1 * L * B;
         k<<<persistent_blocks(k, tma_threads<Real, L, 1>(), L1::SMEM, nt), tma_threads<Real, L, 1>(),
             L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx1, nt, ncols, Px, p.status);
         GSP_CHECK(cudaGetLastError());
@@ -425,7 +430,7 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     {
         auto k = k_col_tma<Real, L, 2>;
         GSP_CHECK(set_smem(k, L2::SMEM));
-        const int nt = ntx2 * N;
+        const int nt = ntx2 * B * N;
         k<<<persistent_blocks(k, tma_threads<Real, L, 2>(), L2::SMEM, nt), tma_threads<Real, L, 2>(),
             L2::SMEM, s>>>(p.tm_yi_in, w1, twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status);
         GSP_CHECK(cudaGetLastError());
@@ -433,7 +438,7 @@ cudaError_t solve_n(const DevicePlan &p, const void *rho, void *u, cudaStream_t 
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
     GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
-    k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(w1, static_cast<Real *>(u), tw, nrows, Px);
+    k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(w1, u, tw, nrows, Px);
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
     return cudaSuccess;
@@ -483,15 +488,16 @@ cudaError_t encode_n(DevicePlan &p) {
     using L0 = TmaLayout<Real, L, 0>;
     using L1 = TmaLayout<Real, L, 1>;
     using L2 = TmaLayout<Real, L, 2>;
-    GSP_CHECK(encode_3d(&p.tm_y_in, U64, p.w1, p.Px * u, N, N, rowb, (cuuint64_t)N * rowb,
+    const cuuint64_t BN = (cuuint64_t)p.max_batch * N;  // z of all densities, stacked
+    GSP_CHECK(encode_3d(&p.tm_y_in, U64, p.w1, p.Px * u, N, BN, rowb, (cuuint64_t)N * rowb,
                         L0::ROWB / 8, L0::RPC, 1));
-    GSP_CHECK(encode_3d(&p.tm_z_in, U64, p.w2, p.Px * u, L, N, rowb, (cuuint64_t)L * rowb,
+    GSP_CHECK(encode_3d(&p.tm_z_in, U64, p.w2, p.Px * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L1::ROWB / 8, 1, L1::RPC));
     const cuuint64_t srow = (cuuint64_t)p.Ps * sizeof(Real);
     GSP_CHECK(encode_3d(&p.tm_z_sym,
                         sizeof(Real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                         p.sym, p.Ps, N + 1, N + 1, srow, (cuuint64_t)(N + 1) * srow, L1::TC, 1, L1::SRC));
-    GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, p.Px * u, L, N, rowb, (cuuint64_t)L * rowb,
+    GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, p.Px * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L2::ROWB / 8, L2::RPC, 1));
     return cudaSuccess;
 }
@@ -500,12 +506,12 @@ cudaError_t encode_n(DevicePlan &p) {
     X(4) X(8) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(1024)
 
 template <typename Real>
-cudaError_t solve_dispatch(const DevicePlan &p, const void *rho, void *u, cudaStream_t s,
-                           cudaEvent_t *ev) {
+cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B,
+                           cudaStream_t s, cudaEvent_t *ev) {
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
-        return solve_n<Real, n>(p, rho, u, s, ev);
+        return solve_n<Real, n>(p, rho, u, B, s, ev);
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE
         default:

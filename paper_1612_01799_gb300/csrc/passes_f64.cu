@@ -2,8 +2,9 @@
 #include "passes.cuh"
 
 namespace gsp {
-cudaError_t solve_f64(const DevicePlan &p, const void *rho, void *u, cudaStream_t s, cudaEvent_t *ev) {
-    return solve_dispatch<double>(p, rho, u, s, ev);
+cudaError_t solve_f64(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
+                     cudaEvent_t *ev) {
+    return solve_dispatch<double>(p, rho, u, B, s, ev);
 }
 cudaError_t symbol_table_f64(const DevicePlan &p, const double *dA, const double *dw, int nterms,
                              double C0, double C2, double scale, cudaStream_t s) {

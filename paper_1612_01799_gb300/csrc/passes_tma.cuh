@@ -187,8 +187,8 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
 }
 
 // ---- K3 ----------------------------------------------------------------------------------
-// Tile = (tx, ky): input z < N rows of w2, symbol rows kz <= N of the octant at |ky|,
-// output z < N rows of w3.
+// Tile = (tx, ky, b): input z < N rows of density b in w2, symbol rows kz <= N of the
+// octant at |ky|, output z < N rows of density b in w3.
 template <typename Real, int L>
 __global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_for<tma_threads<Real, L, 1>(), FftCfg<L>::E>())
 k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
@@ -221,14 +221,14 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
     // Consecutive tiles take ky and its mirror 2N - ky, which read the same symbol rows.
     auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
     auto issue_in = [&](int t) {
-        const int tx = t % ntx, ky = ky_of(t / ntx);
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), b = t / (ntx * L);
         mbar_arrive_expect_tx(bar, Lay::IN_BYTES);
 #pragma unroll
         for (int c = 0; c < Lay::NCP; ++c)
-            tma_load_3d(inb + c * Lay::RPC * Lay::ROWB, &tin, bar, tx * TCU, ky, c * Lay::RPC);
+            tma_load_3d(inb + c * Lay::RPC * Lay::ROWB, &tin, bar, tx * TCU, ky, b * N + c * Lay::RPC);
     };
     auto issue_sym = [&](int t) {
-        const int tx = t % ntx, ky = ky_of(t / ntx);
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L);
         const int kya = ky <= N ? ky : L - ky;
         mbar_arrive_expect_tx(bar + 1, Lay::S_BYTES);
 #pragma unroll
@@ -243,7 +243,7 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
     }
     uint32_t phase = 0;
     for (; t < ntiles; t += gridDim.x) {
-        const int tx = t % ntx, ky = ky_of(t / ntx);
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
         const int col = tx * TC + W * g;
         const bool valid = col < ncols;
         const bool more = t + (int)gridDim.x < ntiles;
@@ -280,7 +280,7 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
             fence_proxy_async();
             issue_sym(t + gridDim.x);
         }
-        Cx2<Real> *dst = out + (long long)ky * Px + col;
+        Cx2<Real> *dst = out + ((long long)bb * N * L + ky) * Px + col;
         constexpr RunOpt inv{true, false, false, true, false};
         Stages<C, L, E, 1, 1, Rv>::template run<inv>(
             v, q, g, xb, NG, tw, 1, [&](int) { return czero<C>(); },

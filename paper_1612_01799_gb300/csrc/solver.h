@@ -7,10 +7,19 @@
 
 namespace gsp {
 
-// Device side of a plan.  Workspace layout (complex values of the plan's dtype):
-//   w1: [z < N][y < N][kx < Px]     after the x pass (and again after the y inverse)
-//   w2: [z < N][ky < 2N][kx < Px]   after the y pass
-//   w3: [z < N][ky < 2N][kx < Px]   after the fused z pass
+// Densities one grouped launch sequence can carry (kernel-parameter arrays of pointers).
+constexpr int kMaxBatch = 64;
+
+// Per-density pointers of a batch, passed to kernels by value.
+struct PtrArray {
+    const void *p[kMaxBatch];
+};
+
+// Device side of a plan.  Workspace layout (complex values of the plan's dtype) for up to
+// max_batch densities b stacked along z:
+//   w1: [b][z < N][y < N][kx < Px]     after the x pass (and again after the y inverse)
+//   w2: [b][z < N][ky < 2N][kx < Px]   after the y pass
+//   w3: [b][z < N][ky < 2N][kx < Px]   after the fused z pass
 // kx runs over the N+1 Hermitian frequencies 0..N of the real x transform; the pitch
 // Px = N+1 rounded up to a multiple of 16 keeps every row 128-byte aligned.
 // sym: symbol octant [kz <= N][ky <= N][kx < Ps] (Ps = N+1 rounded up to a multiple of
@@ -20,6 +29,7 @@ namespace gsp {
 // FP32 (two columns per thread), equal to tw for FP64.
 struct DevicePlan {
     int N = 0;
+    int max_batch = 1;
     int dtype = 0;  // POISSON_F32 / POISSON_F64
     int Px = 0;
     int Ps = 0;
@@ -46,10 +56,11 @@ bool n_supported(int N);
 // (cudaErrorNotSupported when the driver has no tensor-map encoder).
 cudaError_t encode_tma_maps(DevicePlan &p);
 
-// The five passes of one solve on `s`.  ev: null, or 6 events recorded before pass 1,
-// between the passes and after pass 5.
-cudaError_t launch_solve(const DevicePlan &p, const void *rho, void *u, cudaStream_t s,
-                         cudaEvent_t *ev);
+// The five passes of `count` solves (1 <= count <= p.max_batch) of the plan's geometry on
+// `s`: rho[b] -> u[b].  ev: null, or 6 events recorded before pass 1, between the passes
+// and after pass 5.
+cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
+                         cudaStream_t s, cudaEvent_t *ev);
 
 // Fill p.sym from the per-axis factors (FP64, on the device):
 // sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).

@@ -145,6 +145,7 @@ def test_solve_variants_agree(torch_cuda):
         assert np.array_equal(u1, ub[0].cpu().numpy())
         assert np.array_equal(u96, ub[1].cpu().numpy())
         assert len(ms) == 5 and all(m > 0 for m in ms)
+        p.last_status()
 
 
 def test_device_errors_are_codes(torch_cuda):
