@@ -247,6 +247,30 @@ def run_batched(torch, dev, steps, warmup, seed=4):
                         "anisotropic Gaussians each (seed 4), box [-10,10]^3, FP32"}
 
 
+def run_selector(n_train=384, n_test=128, epochs=3000):
+    """Config 5: train the grid selector on densities 0..n_train-1 (labels from the method's
+    own FP32 solves against exact potentials), then the gain test on the next n_test:
+    fixed N=512 FP64 vs the plain adaptive method vs network + a-posteriori check."""
+    import tempfile as _tf
+    from paper_1612_01799_gb300 import selector as S
+    ws = S.Workspace()
+    try:
+        t0 = time.perf_counter()
+        path = os.path.join(_tf.mkdtemp(), "selector.bin")
+        info = S.fit(list(range(n_train)), ws, path, epochs=epochs)
+        t_fit = time.perf_counter() - t0
+        sel = S.Selector(path, capacity=n_test)
+        res = S.gain_test(list(range(n_train, n_train + n_test)), ws, sel, tol=1e-6)
+        sel.close()
+    finally:
+        ws.close()
+    res["train"] = {"densities": n_train, "epochs": epochs, "final_loss": info["losses"][-1],
+                    "seconds_labels_and_training": t_fit, "calibration": info["calibration"]}
+    res["workload"] = ("config_selector: densities of 1-8 Gaussians, widths log-uniform [0.2, 2], "
+                       "charges U[-1,1], centres U[-2,2]^3 (seed 5), box [-16,16]^3, tol 1e-6 rel-L2")
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -343,6 +367,8 @@ def run_ours(args):
         }
         if not args.no_batched:
             line["batched"] = run_batched(torch, dev, max(3, args.steps // 2), args.warmup)
+        if not args.no_selector and world == 1:
+            line["selector"] = run_selector()
         if not args.no_cpu_baseline and world == 1:
             v, cores, dt = cpu_oracle_baseline(N, steps=args.cpu_steps)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -366,6 +392,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-selector", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

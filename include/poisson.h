@@ -114,6 +114,27 @@ int poisson_solve_batched(int count, const poisson_plan *plans, const void *cons
                           void *const *u_d, void *stream);
 
 /*
+ * One solve as poisson_solve that also returns the a-posteriori indicator of the density's
+ * resolution: eta = sqrt(E_shell / E_total), E the energy |F|^2 of the padded forward
+ * spectrum of rho (all (2N)^3 frequencies, the Hermitian half counted twice) and E_shell its
+ * part with max(|kx|, |ky|, |kz|) >= N - N/8.  The error of the method is driven by the
+ * convergence of the density's finite Fourier series (Sec. 3); a tail that is not small
+ * means N does not resolve rho.  eta: host pointer.  Synchronises `stream`.
+ */
+int poisson_solve_checked(poisson_plan p, const void *rho_d, void *u_d, double *eta, void *stream);
+
+/*
+ * The final residual check: relative L2 and relative l-infinity differences of a against
+ * b over n values, accumulated in FP64 on the device: rel_l2 = ||a - b||_2 / ||b||_2,
+ * rel_linf = max|a - b| / max|b| (the paper's error measure E, Sec. 5, eq. error_infty).
+ * a_d, b_d: device arrays of dtypes a_dtype, b_dtype (POISSON_F32 / POISSON_F64, may
+ * differ); rel_l2, rel_linf: host pointers.  Synchronises `stream`; concurrent calls are
+ * serialised by the library.
+ */
+int poisson_compare(const void *a_d, int a_dtype, const void *b_d, int b_dtype, size_t n,
+                    double *rel_l2, double *rel_linf, void *stream);
+
+/*
  * Per-pass device times of one solve, in milliseconds, measured with CUDA events
  * recorded on `stream` around each of the five passes (x forward, y forward, z
  * forward + symbol + z inverse, y inverse, x inverse).  ms[5] receives them.  The call
@@ -153,6 +174,86 @@ int poisson_supported_n(int N);
 
 /* Human-readable name of a return code. */
 const char *poisson_strerror(int code);
+
+/* Name of the last CUDA error behind a POISSON_ERR_CUDA or POISSON_ERR_ALLOC return on this
+ * host thread ("none" if there was none). */
+const char *poisson_last_cuda_error(void);
+
+/* ---- Inputs and exact potentials for grid selection (not part of a solve) ---------- */
+
+#define POISSON_MAX_GAUSSIANS 8
+
+/*
+ * Sample rho = sum_g q_g prod_q (2 pi s_gq^2)^(-1/2) exp(-(x_q - c_gq)^2 / (2 s_gq^2)) on the
+ * cell-centred N^3 grid of [-L, L]^3 (x fastest) into out_d (device, dtype).  params (host):
+ * ng <= POISSON_MAX_GAUSSIANS records (cx, cy, cz, sx, sy, sz, q).  Stream ordered.
+ */
+int poisson_sample_gaussians(int N, double L, int ng, const double *params, int dtype, void *out_d,
+                             void *stream);
+
+/*
+ * Exact potential of the same Gaussian sum at npts grid points of the N^3 grid on
+ * [-L, L]^3, in FP64: idx_d (device) holds (i, j, k) per point, out_d (device) receives u.
+ * Evaluated through 1/(4 pi r) = (1/(2 pi^{3/2})) int_0^inf exp(-r^2 s^2) ds, which turns the
+ * convolution with a normalised anisotropic Gaussian into a 1-D integral over s.
+ */
+int poisson_gaussian_potential(int N, double L, int ng, const double *params, int npts, const int *idx_d,
+                               double *out_d, void *stream);
+
+/* Relative L2 difference between u_d (N^3 grid, dtype) at the npts points idx_d and the FP64
+ * reference values ref_d there, accumulated in FP64; synchronises `stream`. */
+int poisson_compare_points(const void *u_d, int dtype, int N, int npts, const int *idx_d,
+                           const double *ref_d, double *rel_l2, void *stream);
+
+/* ---- Learned grid selection ------------------------------------------------------------- */
+
+#define POISSON_FEATURES 64
+#define POISSON_MAX_CANDIDATES 16
+
+/*
+ * Features of count 32^3 FP32 density samples (device, each x fastest): log10 of the
+ * power spectrum averaged over 64 radial shells of |k|, relative to the mean power at
+ * k = 0, clamped to [-30, 0].  feat_d: count x 64 (device).
+ */
+int poisson_features32(const float *sample_d, int count, float *feat_d, void *stream);
+
+/* Parameters of the selector MLP 64 -> 64 -> 64 -> 64 -> K (ReLU hidden layers), or -1. */
+int poisson_mlp_nparams(int K);
+
+/* MLP forward for count inputs x_d (count x 64) into y_d (count x K); acts_d: null or
+ * count x 3 x 64 floats that receive the hidden activations for the backward pass. */
+int poisson_mlp_forward(const float *params_d, int K, const float *x_d, int count, float *y_d,
+                        float *acts_d, void *stream);
+
+/* Mean squared error over n outputs: dy_d = 2 (y - t) / n, *loss_d = mean (y - t)^2. */
+int poisson_mlp_loss(const float *y_d, const float *target_d, int n, float *dy_d, float *loss_d,
+                     void *stream);
+
+/* Parameter gradients of the loss for count samples into grad_d (zeroed first). */
+int poisson_mlp_backward(const float *params_d, int K, const float *x_d, const float *acts_d, int count,
+                         const float *dy_d, float *grad_d, void *stream);
+
+/* One Adam step (bias-corrected with step >= 1) on n parameters. */
+int poisson_mlp_adam(float *params_d, const float *grad_d, float *m_d, float *v_d, int n, float lr,
+                     float beta1, float beta2, float eps, int step, void *stream);
+
+typedef struct poisson_selector_s *poisson_selector;
+
+/*
+ * Load a trained selector (file written by the package's training driver) with room for
+ * `capacity` densities per poisson_select_n call.  Allocates device memory.
+ */
+int poisson_selector_load(poisson_selector *out, const char *path, int capacity);
+int poisson_selector_destroy(poisson_selector s);
+
+/*
+ * Grid sizes for count densities from their 32^3 samples (device FP32): the network's
+ * predicted log10 error at each candidate N; N_out[b] (host) is the smallest candidate whose
+ * prediction is <= log10(tol) - margin, else the largest.  pred_out: null or host
+ * count x K predictions.  Synchronises `stream` (N is a host-side shape).
+ */
+int poisson_select_n(poisson_selector s, const float *sample32_d, int count, double tol, int *N_out,
+                     float *pred_out, void *stream);
 
 /*
  * A solve that allocates nothing.  The paper has no counterpart: this entry point exists

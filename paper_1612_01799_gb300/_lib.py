@@ -27,13 +27,31 @@ SIGNATURES = {
     "poisson_solve_batched": (c_int, [c_int, P(c_void_p), P(c_void_p), P(c_void_p), c_void_p]),
     "poisson_solve_timed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(ctypes.c_float)]),
     "poisson_last_status": (c_int, [c_void_p, c_void_p]),
+    "poisson_solve_checked": (c_int, [c_void_p, c_void_p, c_void_p, P(c_double), c_void_p]),
+    "poisson_compare": (c_int, [c_void_p, c_int, c_void_p, c_int, c_size_t, P(c_double), P(c_double), c_void_p]),
     "poisson_plan_info": (c_int, [c_void_p, P(c_double), P(c_double), P(c_int), P(c_double),
                                   P(c_double), P(c_size_t), P(c_size_t)]),
     "poisson_plan_gauss_sum": (c_int, [c_void_p, P(c_double), P(c_double), c_int]),
     "poisson_plan_axis_table": (c_int, [c_void_p, P(c_double), c_size_t]),
     "poisson_supported_n": (c_int, [c_int]),
     "poisson_strerror": (ctypes.c_char_p, [c_int]),
+    "poisson_last_cuda_error": (ctypes.c_char_p, []),
     "poisson_solve_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p]),
+    "poisson_sample_gaussians": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p]),
+    "poisson_gaussian_potential": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p,
+                                           c_void_p]),
+    "poisson_compare_points": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, P(c_double),
+                                       c_void_p]),
+    "poisson_features32": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "poisson_mlp_nparams": (c_int, [c_int]),
+    "poisson_mlp_forward": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "poisson_mlp_loss": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "poisson_mlp_backward": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "poisson_mlp_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, c_int, c_void_p]),
+    "poisson_selector_load": (c_int, [P(c_void_p), ctypes.c_char_p, c_int]),
+    "poisson_selector_destroy": (c_int, [c_void_p]),
+    "poisson_select_n": (c_int, [c_void_p, c_void_p, c_int, c_double, P(c_int), P(ctypes.c_float), c_void_p]),
 }
 
 
@@ -62,4 +80,7 @@ def load():
 
 def check(rc, what):
     if rc != OK:
-        raise PoissonError(rc, what)
+        detail = ""
+        if _lib is not None and rc in (-2, -3):
+            detail = " [%s]" % _lib.poisson_last_cuda_error().decode()
+        raise PoissonError(rc, what + detail)

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -12,8 +13,10 @@
 #include "solver.h"
 
 namespace gsp {
-cudaError_t solve_f32(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *);
-cudaError_t solve_f64(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *);
+cudaError_t solve_f32(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *,
+                      double *);
+cudaError_t solve_f64(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *,
+                      double *);
 cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *, int, double,
                              double, double, cudaStream_t);
 cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
@@ -34,9 +37,10 @@ bool n_supported(int N) {
 }
 
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
-                         cudaStream_t s, cudaEvent_t *ev) {
+                         cudaStream_t s, cudaEvent_t *ev, double *tail) {
     if (count < 1 || count > p.max_batch || count > kMaxBatch) return cudaErrorInvalidValue;
-    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, count, s, ev) : solve_f64(p, rho, u, count, s, ev);
+    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, count, s, ev, tail)
+                                  : solve_f64(p, rho, u, count, s, ev, tail);
 }
 
 // Streams that poisson_solve_batched forks independent plan groups onto (per device,
@@ -87,7 +91,19 @@ struct poisson_plan_s {
     bool have_events = false;
 };
 
+namespace gsp {
+static thread_local cudaError_t t_last_error = cudaSuccess;
+void note_cuda_error(cudaError_t e) {
+    if (e != cudaSuccess) t_last_error = e;
+}
+}  // namespace gsp
+
+extern "C" const char *poisson_last_cuda_error(void) {
+    return gsp::t_last_error == cudaSuccess ? "none" : cudaGetErrorName(gsp::t_last_error);
+}
+
 static int map_cuda(cudaError_t e) {
+    gsp::note_cuda_error(e);
     if (e == cudaSuccess) return POISSON_OK;
     if (e == cudaErrorMemoryAllocation) return POISSON_ERR_ALLOC;
     return POISSON_ERR_CUDA;
@@ -97,7 +113,7 @@ static void free_plan(poisson_plan p) {
     if (!p) return;
     void *twc = p->dp.twc != p->dp.tw ? p->dp.twc : nullptr;
     void *bufs[] = {p->dp.sym, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->dp.status,
-                    p->stage_in, p->stage_out};
+                    p->dp.tail, p->stage_in, p->stage_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->have_events)
@@ -183,6 +199,7 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     if ((e = cudaMemset(p->dp.w2, 0, w2_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.w3, 0, w2_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.status, sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&p->dp.tail, 2 * sizeof(double) * max_batch)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.status, 0, sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = gsp::encode_tma_maps(p->dp)) != cudaSuccess) return fail(e);
     gsp::ForkPool *pool = nullptr;
@@ -348,6 +365,26 @@ extern "C" int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d,
     for (int i = 0; i < 5; ++i)
         if ((e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1])) != cudaSuccess)
             return map_cuda(e);
+    return POISSON_OK;
+}
+
+extern "C" int poisson_solve_checked(poisson_plan p, const void *rho_d, void *u_d, double *eta,
+                                     void *stream) {
+    int rc = check_solve_args(p, rho_d, u_d);
+    if (rc) return rc;
+    if (!eta) return POISSON_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->dp.tail, 0, 2 * sizeof(double), s)) != cudaSuccess) return map_cuda(e);
+    gsp::PtrArray in, out;
+    one(in, rho_d);
+    one(out, u_d);
+    if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr, p->dp.tail)) != cudaSuccess) return map_cuda(e);
+    double h[2] = {0.0, 0.0};
+    if ((e = cudaMemcpyAsync(h, p->dp.tail, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+    *eta = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
     return POISSON_OK;
 }
 

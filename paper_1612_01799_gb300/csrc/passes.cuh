@@ -382,7 +382,7 @@ template <class K> static int persistent_blocks(K kernel, int threads, size_t sm
 
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
-                    cudaEvent_t *ev) {
+                    cudaEvent_t *ev, double *tail) {
     using T2 = Cx2<Real>;
     using TwC = typename TwOf<typename Types<Real>::CC>::T;
     constexpr int L = 2 * N;
@@ -418,11 +418,11 @@ cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
     {
-        auto k = k_z_symbol_tma<Real, L>;
+        auto k = tail ? k_z_symbol_tma<Real, L, true> : k_z_symbol_tma<Real, L, false>;
         GSP_CHECK(set_smem(k, L1::SMEM));
         const int nt = ntx1 * L * B;
         k<<<persistent_blocks(k, tma_threads<Real, L, 1>(), L1::SMEM, nt), tma_threads<Real, L, 1>(),
-            L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx1, nt, ncols, Px, p.status);
+            L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx1, nt, ncols, Px, p.status, tail);
         GSP_CHECK(cudaGetLastError());
     }
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
@@ -507,11 +507,11 @@ cudaError_t encode_n(DevicePlan &p) {
 
 template <typename Real>
 cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B,
-                           cudaStream_t s, cudaEvent_t *ev) {
+                           cudaStream_t s, cudaEvent_t *ev, double *tail) {
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
-        return solve_n<Real, n>(p, rho, u, B, s, ev);
+        return solve_n<Real, n>(p, rho, u, B, s, ev, tail);
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE
         default:

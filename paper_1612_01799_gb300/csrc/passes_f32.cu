@@ -3,8 +3,8 @@
 
 namespace gsp {
 cudaError_t solve_f32(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
-                     cudaEvent_t *ev) {
-    return solve_dispatch<float>(p, rho, u, B, s, ev);
+                     cudaEvent_t *ev, double *tail) {
+    return solve_dispatch<float>(p, rho, u, B, s, ev, tail);
 }
 cudaError_t symbol_table_f32(const DevicePlan &p, const double *dA, const double *dw, int nterms,
                              double C0, double C2, double scale, cudaStream_t s) {

@@ -189,12 +189,21 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
 // ---- K3 ----------------------------------------------------------------------------------
 // Tile = (tx, ky, b): input z < N rows of density b in w2, symbol rows kz <= N of the
 // octant at |ky|, output z < N rows of density b in w3.
-template <typename Real, int L>
+// Energy |F|^2 of the padded spectrum in the registers of one element (both lanes of CV),
+// weighted by column (kx = 0 and N once, 0 < kx < N twice for the mirrored -kx, kx > N
+// padding not at all).
+__device__ __forceinline__ float2 cenergy(CV x) { return f2fma(x.re, x.re, f2mul(x.im, x.im)); }
+__device__ __forceinline__ float cenergy(CD x) { return (float)(x.re * x.re + x.im * x.im); }
+
+// With TAIL, the forward spectrum's energy in the outer shell max(|kx|,|ky|,|kz|) >= 7N/8
+// and its total energy are added (FP32 per thread, FP64 per tile) to tail[2 b], tail[2 b + 1]
+// for density b: the a-posteriori indicator of the density's resolution.
+template <typename Real, int L, bool TAIL>
 __global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_for<tma_threads<Real, L, 1>(), FftCfg<L>::E>())
 k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
                Cx2<Real> *__restrict__ out,
                const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
-               int ncols, int Px, int *__restrict__ status) {
+               int ncols, int Px, int *__restrict__ status, double *__restrict__ tail) {
     using C = typename Types<Real>::CC;
     using Lay = TmaLayout<Real, L, 1>;
     using Rs = typename FftCfg<L>::Rs;
@@ -261,6 +270,49 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
         constexpr RunOpt fwd{true, false, true, false, false};
         Stages<C, L, E, -1, 1, Rs>::template run<fwd>(
             v, q, g, xb, NG, tw, 1, [&](int) { return czero<C>(); }, [&](int, C) {});
+        if constexpr (TAIL) {
+            const int kya = ky <= N ? ky : L - ky;
+            constexpr int SHELL = N - N / 8;
+            float w[W], eshell = 0.f, etot = 0.f;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const int kx = col + i;
+                w[i] = kx > N || !valid ? 0.f : (kx == 0 || kx == N) ? 1.f : 2.f;
+            }
+#pragma unroll
+            for (int b = 0; b < E / RL; ++b) {
+                const int j = q + P * b;
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    const int row = j + r * (L / RL);
+                    const int kz = row <= N ? row : L - row;
+                    float e;
+                    if constexpr (W == 2) {
+                        const float2 en = cenergy(v[b * RL + r]);
+                        e = w[0] * en.x + w[1] * en.y;
+                        if ((kz >= SHELL || kya >= SHELL) || col >= SHELL) eshell += e;
+                        else if (col + 1 >= SHELL) eshell += w[1] * en.y;
+                    } else {
+                        e = w[0] * cenergy(v[b * RL + r]);
+                        if (kz >= SHELL || kya >= SHELL || col >= SHELL) eshell += e;
+                    }
+                    etot += e;
+                }
+            }
+            // Tile sum: warp shuffles, then one FP64 atomic per warp (blocks of fewer than 32
+            // threads, at the smallest sizes, add per thread).
+            if constexpr (tma_threads<Real, L, 1>() >= 32) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    eshell += __shfl_xor_sync(0xffffffffu, eshell, o);
+                    etot += __shfl_xor_sync(0xffffffffu, etot, o);
+                }
+            }
+            if (tma_threads<Real, L, 1>() < 32 || (threadIdx.x & 31) == 0) {
+                atomicAdd(tail + 2 * bb, (double)eshell);
+                atomicAdd(tail + 2 * bb + 1, (double)etot);
+            }
+        }
         ok = mbar_wait(bar + 1, phase, status);
         if (__syncthreads_or(!ok)) return;
         phase ^= 1;

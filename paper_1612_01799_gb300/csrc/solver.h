@@ -40,6 +40,7 @@ struct DevicePlan {
     void *w2 = nullptr;
     void *w3 = nullptr;
     int *status = nullptr;  // device status word (bit 0: a bounded wait timed out)
+    double *tail = nullptr; // 2 max_batch doubles: spectral-tail sums of a checked solve
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers.
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
@@ -52,15 +53,19 @@ inline int sym_pitch_for(int N) { return ((N + 1 + 3) / 4) * 4; }
 
 bool n_supported(int N);
 
+// Record a failed CUDA call for poisson_last_cuda_error() (per host thread).
+void note_cuda_error(cudaError_t e);
+
 // Encode the TMA descriptors of p for its buffers.  Returns cudaSuccess or an error
 // (cudaErrorNotSupported when the driver has no tensor-map encoder).
 cudaError_t encode_tma_maps(DevicePlan &p);
 
 // The five passes of `count` solves (1 <= count <= p.max_batch) of the plan's geometry on
 // `s`: rho[b] -> u[b].  ev: null, or 6 events recorded before pass 1, between the passes
-// and after pass 5.
+// and after pass 5.  tail: null, or 2 count zeroed doubles that receive, per density, the
+// padded spectrum's energy in the outer |k|_inf shell and its total energy.
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
-                         cudaStream_t s, cudaEvent_t *ev);
+                         cudaStream_t s, cudaEvent_t *ev, double *tail = nullptr);
 
 // Fill p.sym from the per-axis factors (FP64, on the device):
 // sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).

@@ -1,0 +1,352 @@
+"""Learned grid selection: train and use the network that picks N for a density.
+
+Every computation runs in the library's kernels (density sampling, solves, the spectral
+tail check, exact potentials, errors, features, MLP forward/backward/Adam); this module
+only orders the calls and keeps the bookkeeping.
+
+Pipeline for a density:
+  1. sample it on the 32^3 grid and compute 64 radial power-spectrum features;
+  2. the network predicts log10 of the relative L2 error of an FP32 solve at each
+     candidate N; take the smallest N whose prediction is below log10(tol) - margin;
+  3. solve at N with the a-posteriori check: eta (the outer-shell energy fraction of the
+     padded spectrum) mapped to an error estimate by a monotone calibration fitted on the
+     training data; if the estimate exceeds tol, move to the next candidate and solve again.
+
+The plain method (start at the smallest candidate and refine with the same check) is the
+fallback and the judge of what the network saves.
+"""
+import ctypes
+import json
+import math
+import time
+
+import numpy as np
+
+from . import _lib
+from . import densities as D
+
+CANDIDATES = (32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512)
+NPTS = 1024          # grid points per (density, N) where the error is measured
+BOX = 16.0           # selector workload box [-16, 16]^3
+FEATURES = 64
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def gaussian_params(g):
+    """(ng, 7) records (cx, cy, cz, sx, sy, sz, q) of a GaussianSum, FP64, C order."""
+    rec = np.concatenate([g.centres, g.sigmas, g.charges[:, None]], axis=1)
+    return np.ascontiguousarray(rec, dtype=np.float64)
+
+
+class Workspace:
+    """Device buffers and plans reused across densities."""
+
+    def __init__(self, candidates=CANDIDATES, tol_plan=1e-6, dtype="f32"):
+        from .api import Plan
+        torch = _torch()
+        self.lib = _lib.load()
+        self.candidates = tuple(candidates)
+        self.dtype = dtype
+        self.plans = {N: Plan(N, BOX, tol_plan, dtype) for N in self.candidates}
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        nmax = max(self.candidates)
+        self.rho = torch.empty(nmax ** 3, dtype=tdt, device="cuda")
+        self.u = torch.empty(nmax ** 3, dtype=tdt, device="cuda")
+        self.idx = torch.empty(NPTS * 3, dtype=torch.int32, device="cuda")
+        self.ref = torch.empty(NPTS, dtype=torch.float64, device="cuda")
+        self.s32 = torch.empty(32 ** 3, dtype=torch.float32, device="cuda")
+
+    def close(self):
+        for p in self.plans.values():
+            p.close()
+
+    def sample(self, params, N, out, dtype_code):
+        P = params.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _lib.check(self.lib.poisson_sample_gaussians(N, BOX, params.shape[0], P, dtype_code, _ptr(out), _stream()),
+                   "poisson_sample_gaussians")
+
+    def solve_error(self, params, N, seed):
+        """FP relative L2 error (against the exact potential at NPTS seeded grid points) and
+        the spectral-tail indicator eta of one checked solve at N."""
+        torch = _torch()
+        code = 0 if self.dtype == "f32" else 1
+        n3 = N ** 3
+        rho, u = self.rho[:n3], self.u[:n3]
+        self.sample(params, N, rho, code)
+        eta = ctypes.c_double()
+        plan = self.plans[N]
+        _lib.check(self.lib.poisson_solve_checked(plan.handle, _ptr(rho), _ptr(u), ctypes.byref(eta), _stream()),
+                   "poisson_solve_checked")
+        err = self.error_at_points(params, N, u, seed)
+        return err, eta.value
+
+    def error_at_points(self, params, N, u, seed):
+        torch = _torch()
+        rng = np.random.default_rng([seed, N])
+        pts = rng.integers(0, N, size=(NPTS, 3)).astype(np.int32)
+        self.idx.copy_(torch.from_numpy(pts.ravel()))
+        P = params.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _lib.check(self.lib.poisson_gaussian_potential(N, BOX, params.shape[0], P, NPTS, _ptr(self.idx),
+                                                       _ptr(self.ref), _stream()), "poisson_gaussian_potential")
+        e = ctypes.c_double()
+        code = 0 if u.dtype == torch.float32 else 1
+        _lib.check(self.lib.poisson_compare_points(_ptr(u), code, N, NPTS, _ptr(self.idx), _ptr(self.ref),
+                                                   ctypes.byref(e), _stream()), "poisson_compare_points")
+        return e.value
+
+    def features(self, params_list):
+        """count x 64 features of the densities' 32^3 samples (device tensor)."""
+        torch = _torch()
+        n = len(params_list)
+        s = torch.empty(n * 32 ** 3, dtype=torch.float32, device="cuda")
+        for i, p in enumerate(params_list):
+            self.sample(p, 32, s[i * 32 ** 3:(i + 1) * 32 ** 3], 0)
+        f = torch.empty(n * FEATURES, dtype=torch.float32, device="cuda")
+        _lib.check(self.lib.poisson_features32(_ptr(s), n, _ptr(f), _stream()), "poisson_features32")
+        return f.view(n, FEATURES), s
+
+
+def density(i, seed=5):
+    return D.config_selector(i, seed=seed, N=64).gaussians
+
+
+def make_dataset(indices, ws, log_floor=-9.0):
+    """Features, log10 errors and log10 eta over the candidate grids for densities `indices`."""
+    params = [gaussian_params(density(i)) for i in indices]
+    feats, _ = ws.features(params)
+    K = len(ws.candidates)
+    lerr = np.zeros((len(indices), K))
+    leta = np.zeros((len(indices), K))
+    for a, (i, p) in enumerate(zip(indices, params)):
+        for k, N in enumerate(ws.candidates):
+            err, eta = ws.solve_error(p, N, seed=1000 + i)
+            lerr[a, k] = max(math.log10(max(err, 1e-300)), log_floor)
+            leta[a, k] = math.log10(max(eta, 1e-300))
+    return feats.cpu().numpy(), lerr, leta
+
+
+class Network:
+    """MLP parameters on the device plus the kernels' training loop."""
+
+    def __init__(self, K, seed=0):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.K = K
+        self.n = self.lib.poisson_mlp_nparams(K)
+        rng = np.random.default_rng(seed)
+        parts = []
+        for fan_in, fan_out in ((64, 64), (64, 64), (64, 64), (64, K)):
+            lim = math.sqrt(6.0 / (fan_in + fan_out))
+            parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+            parts.append(np.zeros(fan_out))
+        p = np.concatenate(parts).astype(np.float32)
+        assert p.size == self.n
+        self.params = torch.from_numpy(p).cuda()
+        self.grad = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.mean = torch.zeros(FEATURES, device="cuda")
+        self.std = torch.ones(FEATURES, device="cuda")
+
+    def forward(self, x, acts=None):
+        torch = _torch()
+        y = torch.empty(x.shape[0] * self.K, dtype=torch.float32, device="cuda")
+        _lib.check(self.lib.poisson_mlp_forward(_ptr(self.params), self.K, _ptr(x), x.shape[0], _ptr(y),
+                                                _ptr(acts) if acts is not None else None, _stream()),
+                   "poisson_mlp_forward")
+        return y.view(x.shape[0], self.K)
+
+    def gradient(self, x, t):
+        """Loss and parameter gradient (into self.grad) for inputs x and targets t."""
+        torch = _torch()
+        B = x.shape[0]
+        acts = torch.empty(B * 3 * 64, dtype=torch.float32, device="cuda")
+        y = self.forward(x, acts)
+        dy = torch.empty_like(y)
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _lib.check(self.lib.poisson_mlp_loss(_ptr(y), _ptr(t), y.numel(), _ptr(dy), _ptr(loss), _stream()),
+                   "poisson_mlp_loss")
+        _lib.check(self.lib.poisson_mlp_backward(_ptr(self.params), self.K, _ptr(x), _ptr(acts), B, _ptr(dy),
+                                                 _ptr(self.grad), _stream()), "poisson_mlp_backward")
+        return loss
+
+    def train(self, x, t, epochs=3000, lr=2e-3):
+        """Full-batch Adam on standardised inputs."""
+        losses = []
+        for step in range(1, epochs + 1):
+            loss = self.gradient(x, t)
+            _lib.check(self.lib.poisson_mlp_adam(_ptr(self.params), _ptr(self.grad), _ptr(self.m), _ptr(self.v),
+                                                 self.n, ctypes.c_float(lr), ctypes.c_float(0.9),
+                                                 ctypes.c_float(0.999), ctypes.c_float(1e-8), step, _stream()),
+                       "poisson_mlp_adam")
+            if step % 500 == 0 or step == epochs:
+                losses.append(float(loss.item()))
+        return losses
+
+
+def calibrate(leta, lerr, quantile=0.98):
+    """Monotone map from log10(eta) to a log10 error bound: a least-squares line, shifted up
+    so that `quantile` of the training pairs lie on or below it."""
+    x, y = leta.ravel(), lerr.ravel()
+    keep = np.isfinite(x) & np.isfinite(y) & (x > -29)
+    x, y = x[keep], y[keep]
+    A = np.stack([np.ones_like(x), x], axis=1)
+    (a, b), *_ = np.linalg.lstsq(A, y, rcond=None)
+    b = max(b, 0.0)
+    shift = np.quantile(y - (a + b * x), quantile)
+    return float(a + shift), float(b)
+
+
+def save(path, net, candidates, margin, cal):
+    torch = _torch()
+    with open(path, "wb") as f:
+        f.write(b"GSPSEL01")
+        f.write(np.int32(len(candidates)).tobytes())
+        f.write(np.asarray(candidates, np.int32).tobytes())
+        f.write(np.float32(margin).tobytes())
+        f.write(net.mean.cpu().numpy().astype(np.float32).tobytes())
+        f.write(net.std.cpu().numpy().astype(np.float32).tobytes())
+        f.write(net.params.cpu().numpy().astype(np.float32).tobytes())
+    with open(path + ".json", "w") as f:
+        json.dump({"candidates": list(candidates), "margin": margin, "calibration": cal}, f)
+
+
+class Selector:
+    """A trained selector loaded through the C-ABI."""
+
+    def __init__(self, path, capacity=512):
+        self.lib = _lib.load()
+        self.h = ctypes.c_void_p()
+        _lib.check(self.lib.poisson_selector_load(ctypes.byref(self.h), path.encode(), capacity),
+                   "poisson_selector_load")
+        with open(path + ".json") as f:
+            meta = json.load(f)
+        self.candidates = tuple(meta["candidates"])
+        self.cal = tuple(meta["calibration"])
+
+    def select(self, samples32, count, tol):
+        N = (ctypes.c_int * count)()
+        pred = (ctypes.c_float * (count * len(self.candidates)))()
+        _lib.check(self.lib.poisson_select_n(self.h, _ptr(samples32), count, tol, N, pred, _stream()),
+                   "poisson_select_n")
+        return list(N), np.frombuffer(pred, dtype=np.float32).reshape(count, -1)
+
+    def check(self, eta, tol):
+        a, b = self.cal
+        return a + b * math.log10(max(eta, 1e-300)) <= math.log10(tol)
+
+    def close(self):
+        if self.h.value:
+            self.lib.poisson_selector_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+
+def fit(train_indices, ws, path, epochs=3000, lr=2e-3, margin=0.3, seed=0):
+    """Generate the training data with the method itself, train the network on the GPU,
+    fit the check's calibration and write the selector file."""
+    torch = _torch()
+    feats, lerr, leta = make_dataset(train_indices, ws)
+    mean = feats.mean(0)
+    std = np.maximum(feats.std(0), 1e-3)
+    K = len(ws.candidates)
+    net = Network(K, seed=seed)
+    net.mean.copy_(torch.from_numpy(mean.astype(np.float32)))
+    net.std.copy_(torch.from_numpy(std.astype(np.float32)))
+    x = torch.from_numpy(((feats - mean) / std).astype(np.float32)).cuda().contiguous()
+    t = torch.from_numpy(lerr.astype(np.float32)).cuda().contiguous()
+    losses = net.train(x, t, epochs=epochs, lr=lr)
+    cal = calibrate(leta, lerr)
+    save(path, net, ws.candidates, margin, cal)
+    return {"losses": losses, "calibration": cal, "train_densities": len(train_indices),
+            "label_mean_log10_err": float(lerr.mean())}
+
+
+def _solve_until_checked(ws, sel, params, start_k, tol):
+    """Solve at candidates from index start_k up until the calibrated check passes."""
+    k = start_k
+    while True:
+        N = ws.candidates[k]
+        n3 = N ** 3
+        ws.sample(params, N, ws.rho[:n3], 0 if ws.dtype == "f32" else 1)
+        eta = ctypes.c_double()
+        _lib.check(ws.lib.poisson_solve_checked(ws.plans[N].handle, _ptr(ws.rho[:n3]), _ptr(ws.u[:n3]),
+                                                ctypes.byref(eta), _stream()), "poisson_solve_checked")
+        if sel.check(eta.value, tol) or k == len(ws.candidates) - 1:
+            return N, k
+        k += 1
+
+
+def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512, fixed_timed=4):
+    """Cost and accuracy of three ways to meet `tol` on the test densities:
+    (i) a fixed N = fixed_N FP64 solve, (ii) the plain method: start at start_N and refine
+    with the a-posteriori check, (iii) the network's N, refined with the same check."""
+    torch = _torch()
+    from .api import Plan
+    params = [gaussian_params(density(i)) for i in test_indices]
+    res = {}
+    # (iii) network + check
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, s32 = ws.features(params)
+    Ns, _ = sel.select(s32, len(params), tol)
+    chosen3 = []
+    for p, n0 in zip(params, Ns):
+        chosen3.append(_solve_until_checked(ws, sel, p, ws.candidates.index(n0), tol))
+    torch.cuda.synchronize()
+    t3 = time.perf_counter() - t0
+    # (ii) plain method + check
+    t0 = time.perf_counter()
+    chosen2 = [_solve_until_checked(ws, sel, p, ws.candidates.index(start_N), tol) for p in params]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter() - t0
+    # accuracy of the grids each strategy ended on (untimed)
+    def errors(chosen):
+        out = []
+        for i, p, (N, _) in zip(test_indices, params, chosen):
+            out.append(ws.solve_error(p, N, seed=5000 + i)[0])
+        return np.array(out)
+    e3, e2 = errors(chosen3), errors(chosen2)
+    # (i) fixed N FP64: timed on the first `fixed_timed` densities, cost scaled to all
+    with Plan(fixed_N, BOX, 1e-12, "f64") as p64:
+        rho = torch.empty(fixed_N ** 3, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(rho)
+        ws.sample(params[0], fixed_N, rho, 1)
+        p64.solve(rho, u)                      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for pr in params[:fixed_timed]:
+            ws.sample(pr, fixed_N, rho, 1)
+            p64.solve(rho, u)
+        torch.cuda.synchronize()
+        t1 = (time.perf_counter() - t0) / fixed_timed * len(params)
+        e1 = np.array([ws.error_at_points(pr, fixed_N, (ws.sample(pr, fixed_N, rho, 1), p64.solve(rho, u))[1],
+                                          seed=5000 + i)
+                       for i, pr in zip(test_indices[:fixed_timed], params[:fixed_timed])])
+    def summary(t, e, chosen):
+        d = {"seconds": t, "met_tol": float(np.mean(e <= tol)), "median_err": float(np.median(e))}
+        if chosen is not None:
+            d["mean_N"] = float(np.mean([c[0] for c in chosen]))
+            d["solves_per_density"] = float(np.mean([1 + c[1] for c in chosen]))
+        return d
+    res["fixed_N%d_f64" % fixed_N] = summary(t1, e1, None)
+    res["fixed_N%d_f64" % fixed_N]["timed_densities"] = fixed_timed
+    res["plain_adaptive_from_N%d_f32" % start_N] = summary(t2, e2, chosen2)
+    res["network_plus_check_f32"] = summary(t3, e3, chosen3)
+    res["network_first_guess_kept"] = float(np.mean([c[0] == n for c, n in zip(chosen3, Ns)]))
+    res["speedup_vs_fixed"] = t1 / t3
+    res["speedup_vs_plain"] = t2 / t3
+    res["densities"] = len(params)
+    res["tol"] = tol
+    return res

@@ -18,7 +18,7 @@ def declared_functions():
     with open(_lib.HEADER) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(poisson_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(poisson_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_and_binding_agree():
