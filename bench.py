@@ -36,7 +36,7 @@ KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_in
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; a
 # source change makes the figure stale and it is reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("5dc039a61f78c8d7", "k_z_symbol", 256): 364039168 + 234190592}
 
 
 def kernel_source_hash():
@@ -187,10 +187,15 @@ def workload_config(N, dtype):
             "l2": "flushed between steps (512 MB write)", "parallelism": "independent solves per GPU"}
 
 
-def time_solves(torch, plan, rho_t, out_t, steps, warmup, flush):
-    """Per-step event times (ms) of whole solves, and per-pass times from the same steps."""
-    for _ in range(warmup):
+def time_solves(torch, plan, rho_t, out_t, steps, warmup, flush, hold_s=0.0):
+    """Per-step event times (ms) of whole solves, and per-pass times from the same steps.
+    Untimed warm-up: at least `warmup` solves, continued for hold_s seconds so that the
+    clock sampler records the GPU under this load right up to the timed steps."""
+    t0, i = time.perf_counter(), 0
+    while i < warmup or time.perf_counter() - t0 < hold_s:
+        flush.zero_()
         plan.solve_timed(rho_t, out_t)
+        i += 1
     torch.cuda.synchronize()
     totals, passes = [], []
     for _ in range(steps):
@@ -265,7 +270,8 @@ def run_selector(n_train=384, n_test=128, epochs=3000):
     finally:
         ws.close()
     res["train"] = {"densities": n_train, "epochs": epochs, "final_loss": info["losses"][-1],
-                    "seconds_labels_and_training": t_fit, "calibration": info["calibration"]}
+                    "seconds_labels_and_training": t_fit,
+                    "check_accepts_eta_below": S.eta_threshold(info["calibration"], 1e-6)}
     res["workload"] = ("config_selector: densities of 1-8 Gaussians, widths log-uniform [0.2, 2], "
                        "charges U[-1,1], centres U[-2,2]^3 (seed 5), box [-16,16]^3, tol 1e-6 rel-L2")
     return res
@@ -304,7 +310,8 @@ def run_ours(args):
         sampler = ClockSampler(dev.index) if dtype == "f32" else None
         if sampler:
             sampler.__enter__()
-        totals, passes = time_solves(torch, plan, rho_t, out_t, steps, args.warmup, flush)
+        totals, passes = time_solves(torch, plan, rho_t, out_t, steps, args.warmup, flush,
+                                     hold_s=1.0 if sampler else 0.0)
         if sampler:
             sampler.__exit__(None, None, None)
         torch.cuda.synchronize()
@@ -314,7 +321,7 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
-        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps,
+        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_split": plan.z_split,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
                           "rho": rho_t, "out": out_t}
 
@@ -340,8 +347,11 @@ def run_ours(args):
         bytes32 = pass_bytes(N, 4)
         dom = max(range(5), key=lambda i: r32["per_pass"][i])
         gbs = [bytes32[i] / (r32["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
+        names = list(KERNEL_NAMES)
+        if r32["z_split"]:
+            names[2] = "k_z_split"
         src_hash = kernel_source_hash()
-        traffic = NCU_TRAFFIC.get((src_hash, KERNEL_NAMES[dom], N))
+        traffic = NCU_TRAFFIC.get((src_hash, names[dom], N))
         r64 = results["f64"]
         bytes64 = pass_bytes(N, 8)
         gbs64 = [bytes64[i] / (r64["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
@@ -352,9 +362,9 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(N, "f32"),
             "roofline": {"bound": "hbm", "achieved": gbs[dom], "peak": peak, "unit": "GB/s",
                          "frac": gbs[dom] / peak, "traffic": traffic,
-                         "kernel": KERNEL_NAMES[dom], "algorithmic_bytes": bytes32[dom],
+                         "kernel": names[dom], "algorithmic_bytes": bytes32[dom],
                          "peak_source": peak_kind},
-            "passes": [{"pass": PASSES[i], "kernel": KERNEL_NAMES[i], "ms": r32["per_pass"][i],
+            "passes": [{"pass": PASSES[i], "kernel": names[i], "ms": r32["per_pass"][i],
                         "GB_s": gbs[i], "frac": gbs[i] / peak} for i in range(5)],
             "f64": {"value": world * N ** 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
                     "steps": r64["steps"],
@@ -363,6 +373,9 @@ def run_ours(args):
             "e2e": {"value": world * N ** 3 / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": N ** 3 * 4, "d2h_bytes_per_step": N ** 3 * 4},
             "gpu_launches": 5 * r32["steps"],
+            "tuning": {"z_pass_f32": "split" if r32["z_split"] else "direct",
+                       "z_pass_f64": "split" if results["f64"]["z_split"] else "direct",
+                       "how": "timed at plan creation, cached per (device, N, dtype)"},
             "clocks": r32["clocks"],
         }
         if not args.no_batched:

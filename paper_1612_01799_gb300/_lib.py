@@ -31,6 +31,8 @@ SIGNATURES = {
     "poisson_compare": (c_int, [c_void_p, c_int, c_void_p, c_int, c_size_t, P(c_double), P(c_double), c_void_p]),
     "poisson_plan_info": (c_int, [c_void_p, P(c_double), P(c_double), P(c_int), P(c_double),
                                   P(c_double), P(c_size_t), P(c_size_t)]),
+    "poisson_plan_get_knob": (c_int, [c_void_p, c_int, P(c_int)]),
+    "poisson_plan_set_knob": (c_int, [c_void_p, c_int, c_int]),
     "poisson_plan_gauss_sum": (c_int, [c_void_p, P(c_double), P(c_double), c_int]),
     "poisson_plan_axis_table": (c_int, [c_void_p, P(c_double), c_size_t]),
     "poisson_supported_n": (c_int, [c_int]),
@@ -59,6 +61,9 @@ class PoissonError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
         super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "unknown"), code))
+
+
+KNOB_Z_SPLIT = 0
 
 
 def load():

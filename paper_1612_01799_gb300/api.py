@@ -117,6 +117,19 @@ class Plan:
         return {"delta": d.value, "eps": e.value, "n_terms": n.value, "C0": c0.value, "C2": c2.value,
                 "ws_bytes": ws.value, "table_bytes": tb.value}
 
+    @property
+    def z_split(self):
+        """Form of the fused z pass in use: 0 length-2N transforms, 1 even/odd length-N split
+        (chosen by timing at plan creation)."""
+        v = ctypes.c_int()
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_Z_SPLIT, ctypes.byref(v)),
+                   "poisson_plan_get_knob")
+        return v.value
+
+    @z_split.setter
+    def z_split(self, value):
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_Z_SPLIT, int(value)), "poisson_plan_set_knob")
+
     def gauss_sum(self):
         n = self.info()["n_terms"]
         tau, w = np.empty(n), np.empty(n)

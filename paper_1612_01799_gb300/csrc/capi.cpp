@@ -23,6 +23,12 @@ cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *,
                              double, double, cudaStream_t);
 cudaError_t encode_maps_f32(DevicePlan &);
 cudaError_t encode_maps_f64(DevicePlan &);
+cudaError_t z_pass_f32(const DevicePlan &, cudaStream_t);
+cudaError_t z_pass_f64(const DevicePlan &, cudaStream_t);
+
+cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? z_pass_f32(p, s) : z_pass_f64(p, s);
+}
 
 cudaError_t encode_tma_maps(DevicePlan &p) {
     return p.dtype == POISSON_F32 ? encode_maps_f32(p) : encode_maps_f64(p);
@@ -75,6 +81,70 @@ cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const dou
                                 int nterms, double C0, double C2, double scale, cudaStream_t s) {
     return p.dtype == POISSON_F32 ? symbol_table_f32(p, dA, dw, nterms, C0, C2, scale, s)
                                   : symbol_table_f64(p, dA, dw, nterms, C0, C2, scale, s);
+}
+
+// ---- autotuning of kernel variants --------------------------------------------------------
+// Decisions per (device, N, dtype), made by the first plan of that shape and reused.
+struct TuneEntry {
+    int dev, N, dtype, zsplit;
+};
+static std::vector<TuneEntry> g_tune;
+static std::mutex g_tune_mutex;
+
+// Mean time (ms) of `reps` z passes of one density after one warm-up pass.
+static cudaError_t time_z(const DevicePlan &p, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps,
+                          float *ms) {
+    cudaError_t e;
+    if ((e = launch_z_pass(p, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(a, s)) != cudaSuccess) return e;
+    for (int i = 0; i < reps; ++i)
+        if ((e = launch_z_pass(p, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b, s)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) return e;
+    if ((e = cudaEventElapsedTime(ms, a, b)) != cudaSuccess) return e;
+    *ms /= reps;
+    return cudaSuccess;
+}
+
+// Choose p.zsplit: the cached decision for this shape, else the faster form timed on p's
+// zeroed workspace.  Only w3 is written, and every solve writes w3 before reading it.
+static cudaError_t autotune(DevicePlan &p, int dev) {
+    p.zsplit = 0;
+    if (!z_split_available(p.N)) return cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (const TuneEntry &t : g_tune)
+            if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
+                p.zsplit = t.zsplit;
+                return cudaSuccess;
+            }
+    }
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        p.zsplit = v;
+        e = time_z(p, s, a, b, 3, &ms[v]);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        p.zsplit = 0;
+        return e;
+    }
+    p.zsplit = ms[1] < ms[0] ? 1 : 0;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const TuneEntry &t : g_tune)  // another thread may have decided meanwhile
+        if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
+            p.zsplit = t.zsplit;
+            return cudaSuccess;
+        }
+    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zsplit});
+    return cudaSuccess;
 }
 }  // namespace gsp
 
@@ -242,7 +312,23 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     cudaFree(dA);
     cudaFree(dw);
     dA = dw = nullptr;
+    if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
     *out = p;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
+    if (!p || !value) return POISSON_ERR_ARG;
+    if (knob != POISSON_KNOB_Z_SPLIT) return POISSON_ERR_ARG;
+    *value = p->dp.zsplit;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
+    if (!p) return POISSON_ERR_ARG;
+    if (knob != POISSON_KNOB_Z_SPLIT || (value != 0 && value != 1)) return POISSON_ERR_ARG;
+    if (value == 1 && !gsp::z_split_available(p->dp.N)) return POISSON_ERR_UNSUPPORTED;
+    p->dp.zsplit = value;
     return POISSON_OK;
 }
 

@@ -380,6 +380,38 @@ template <class K> static int persistent_blocks(K kernel, int threads, size_t sm
     return blocks < ntiles ? blocks : ntiles;
 }
 
+// The fused z pass (K3) of B densities in the form p.zsplit selects: the length-2N
+// transforms (0) or the split into even and odd length-N transforms (1, where
+// zsplit_available; otherwise the direct form runs).
+template <typename Real, int N>
+cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
+    using T2 = Cx2<Real>;
+    using TwC = typename TwOf<typename Types<Real>::CC>::T;
+    constexpr int L = 2 * N;
+    using L1 = TmaLayout<Real, L, 1>;
+    const int ncols = N + 1;
+    const int ntx = (ncols + L1::TC - 1) / L1::TC;
+    const int nt = ntx * L * B;
+    T2 *w3 = static_cast<T2 *>(p.w3);
+    const TwC *twc = static_cast<const TwC *>(p.twc);
+    if constexpr (zsplit_available<L>()) {
+        if (p.zsplit) {
+            auto k = tail ? k_z_split_tma<Real, L, true> : k_z_split_tma<Real, L, false>;
+            constexpr int T = zsplit_threads<Real, L>();
+            GSP_CHECK(set_smem(k, L1::SMEM));
+            k<<<persistent_blocks(k, T, L1::SMEM, nt), T, L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx, nt,
+                                                                      ncols, p.Px, p.status, tail);
+            return cudaGetLastError();
+        }
+    }
+    auto k = tail ? k_z_symbol_tma<Real, L, true> : k_z_symbol_tma<Real, L, false>;
+    constexpr int T = tma_threads<Real, L, 1>();
+    GSP_CHECK(set_smem(k, L1::SMEM));
+    k<<<persistent_blocks(k, T, L1::SMEM, nt), T, L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx, nt, ncols,
+                                                              p.Px, p.status, tail);
+    return cudaGetLastError();
+}
+
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
                     cudaEvent_t *ev, double *tail) {
@@ -396,10 +428,8 @@ cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     const int ncols = N + 1;
     const dim3 grow((nrows + TR - 1) / TR);
     using L0 = TmaLayout<Real, L, 0>;
-    using L1 = TmaLayout<Real, L, 1>;
     using L2 = TmaLayout<Real, L, 2>;
-    const int ntx0 = (ncols + L0::TC - 1) / L0::TC, ntx1 = (ncols + L1::TC - 1) / L1::TC,
-              ntx2 = (ncols + L2::TC - 1) / L2::TC;
+    const int ntx0 = (ncols + L0::TC - 1) / L0::TC, ntx2 = (ncols + L2::TC - 1) / L2::TC;
 
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
     GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
@@ -417,14 +447,7 @@ cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     }
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
-    {
-        auto k = tail ? k_z_symbol_tma<Real, L, true> : k_z_symbol_tma<Real, L, false>;
-        GSP_CHECK(set_smem(k, L1::SMEM));
-        const int nt = ntx1 * L * B;
-        k<<<persistent_blocks(k, tma_threads<Real, L, 1>(), L1::SMEM, nt), tma_threads<Real, L, 1>(),
-            L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx1, nt, ncols, Px, p.status, tail);
-        GSP_CHECK(cudaGetLastError());
-    }
+    GSP_CHECK((z_pass<Real, N>(p, B, s, tail)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
 
     {
@@ -505,6 +528,17 @@ cudaError_t encode_n(DevicePlan &p) {
 #define GSP_SUPPORTED_N(X) \
     X(4) X(8) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(1024)
 
+// The per-N entry points are instantiated in separate translation units (a group of sizes
+// each, compiled in parallel); the dispatch unit of a dtype sees them as extern.
+#define GSP_SIZE_GROUP_A(X) X(4) X(8) X(16) X(32) X(48) X(64) X(80) X(96)
+#define GSP_SIZE_GROUP_B(X) X(128) X(160) X(192) X(256)
+#define GSP_SIZE_GROUP_C(X) X(320) X(384) X(512) X(1024)
+#define GSP_DECLARE_N(EXT, Real, n)                                                                      \
+    EXT template cudaError_t solve_n<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int, \
+                                              cudaStream_t, cudaEvent_t *, double *);                      \
+    EXT template cudaError_t z_pass<Real, n>(const DevicePlan &, int, cudaStream_t, double *);             \
+    EXT template cudaError_t encode_n<Real, n>(DevicePlan &);
+
 template <typename Real>
 cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B,
                            cudaStream_t s, cudaEvent_t *ev, double *tail) {
@@ -516,6 +550,31 @@ cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrAr
 #undef GSP_CASE
         default:
             return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Real>
+cudaError_t z_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    switch (p.N) {
+#define GSP_CASE(n) \
+    case n:         \
+        return z_pass<Real, n>(p, 1, s, nullptr);
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+inline bool zsplit_dispatch(int N) {
+    switch (N) {
+#define GSP_CASE(n) \
+    case n:         \
+        return zsplit_available<2 * n>();
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return false;
     }
 }
 

@@ -1,7 +1,11 @@
-// FP32 instantiation of the solve passes.
+// FP32 dispatch of the solve passes (the per-N code is in passes_f32_[abc].cu).
 #include "passes.cuh"
 
 namespace gsp {
+#define GSP_EXTERN_F32(n) GSP_DECLARE_N(extern, float, n)
+GSP_SUPPORTED_N(GSP_EXTERN_F32)
+#undef GSP_EXTERN_F32
+
 cudaError_t solve_f32(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
                      cudaEvent_t *ev, double *tail) {
     return solve_dispatch<float>(p, rho, u, B, s, ev, tail);
@@ -11,4 +15,6 @@ cudaError_t symbol_table_f32(const DevicePlan &p, const double *dA, const double
     return symbol_table<float>(p, dA, dw, nterms, C0, C2, scale, s);
 }
 cudaError_t encode_maps_f32(DevicePlan &p) { return encode_dispatch<float>(p); }
+cudaError_t z_pass_f32(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<float>(p, s); }
+bool z_split_available(int N) { return zsplit_dispatch(N); }
 }  // namespace gsp

@@ -1,7 +1,11 @@
-// FP64 instantiation of the solve passes.
+// FP64 dispatch of the solve passes (the per-N code is in passes_f64_[abc].cu).
 #include "passes.cuh"
 
 namespace gsp {
+#define GSP_EXTERN_F64(n) GSP_DECLARE_N(extern, double, n)
+GSP_SUPPORTED_N(GSP_EXTERN_F64)
+#undef GSP_EXTERN_F64
+
 cudaError_t solve_f64(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
                      cudaEvent_t *ev, double *tail) {
     return solve_dispatch<double>(p, rho, u, B, s, ev, tail);
@@ -11,4 +15,5 @@ cudaError_t symbol_table_f64(const DevicePlan &p, const double *dA, const double
     return symbol_table<double>(p, dA, dw, nterms, C0, C2, scale, s);
 }
 cudaError_t encode_maps_f64(DevicePlan &p) { return encode_dispatch<double>(p); }
+cudaError_t z_pass_f64(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<double>(p, s); }
 }  // namespace gsp

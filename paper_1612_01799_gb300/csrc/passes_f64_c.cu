@@ -1,0 +1,8 @@
+// FP64 passes for the sizes of group C (see passes.cuh).
+#include "passes.cuh"
+
+namespace gsp {
+#define GSP_INST(n) GSP_DECLARE_N(, double, n)
+GSP_SIZE_GROUP_C(GSP_INST)
+#undef GSP_INST
+}  // namespace gsp

@@ -342,4 +342,208 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
     }
 }
 
+// ---- K3, split form ------------------------------------------------------------------------
+// The pruned length-2N forward transform of a column splits by the parity of the output
+// index: X[2m] is the length-N DFT of x, X[2m+1] the length-N DFT of x_n W_{2N}^n (the
+// inputs x_n, n < N, are the nonzero half).  The kept inverse outputs split the same way:
+// u_z = A_z + conj(W_{2N}^z) B_z for z < N, with A and B the length-N inverse DFTs of the
+// even and odd halves of the spectrum.  Half h of the threads of a column group runs the
+// length-N transforms of parity h.  Where the length-N schedule has one stage fewer than
+// the length-2N one, this saves one shared-memory exchange per direction, for the price of
+// reading the staged input twice and one half-size exchange that adds A and B.
+template <class RL> struct NumStages;
+template <int... Rs> struct NumStages<Radices<Rs...>> { static constexpr int v = sizeof...(Rs); };
+
+template <int L> __host__ __device__ constexpr bool zsplit_available() {
+    if constexpr (L < 8) {
+        return false;
+    } else {
+        using Rh = typename FftCfg<L / 2>::Rs;
+        return NumStages<Rh>::v < NumStages<typename FftCfg<L>::Rs>::v && FirstRadix<Rh>::v % 2 == 0;
+    }
+}
+template <typename Real, int L> __host__ __device__ constexpr int zsplit_threads() {
+    return TmaLayout<Real, L, 1>::NG * 2 * ((L / 2) / FftCfg<L / 2>::E);
+}
+
+template <typename Real, int L, bool TAIL>
+__global__ void __launch_bounds__(zsplit_threads<Real, L>(), min_blocks_for<zsplit_threads<Real, L>(), FftCfg<L / 2>::E>())
+k_z_split_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
+              Cx2<Real> *__restrict__ out,
+              const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
+              int ncols, int Px, int *__restrict__ status, double *__restrict__ tail) {
+    using C = typename Types<Real>::CC;
+    using Lay = TmaLayout<Real, L, 1>;
+    constexpr int N = L / 2;
+    using Rs = typename FftCfg<N>::Rs;
+    using Rv = Reverse<Rs>;
+    constexpr int E = FftCfg<N>::E, PH = N / E, W = Lay::W, TC = Lay::TC, NG = Lay::NG;
+    constexpr int R0 = FirstRadix<Rs>::v, RL = LastRadix<Rs>::v;
+    constexpr int TCU = Lay::ROWB / 8;
+    constexpr int NT = zsplit_threads<Real, L>();
+    static_assert(R0 % 2 == 0, "the A + B exchange splits the first radix's outputs in halves");
+    static_assert(NT <= 1024, "threads of one CTA");
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
+    unsigned char *inb = base;
+    C *xb = reinterpret_cast<C *>(base + Lay::OFF_XB);
+    Real *sb = reinterpret_cast<Real *>(base + Lay::OFF_S);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Lay::OFF_BAR);  // [0] input, [1] symbol
+    const int g = threadIdx.x % NG, q = threadIdx.x / NG;
+    const int h = q / PH, qh = q - h * PH;  // parity of this thread's half, index within it
+    C *xh = xb + h * N * NG;                // the half's exchange rows
+    const long long zs = (long long)L * Px;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
+    auto issue_in = [&](int t) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), b = t / (ntx * L);
+        mbar_arrive_expect_tx(bar, Lay::IN_BYTES);
+#pragma unroll
+        for (int c = 0; c < Lay::NCP; ++c)
+            tma_load_3d(inb + c * Lay::RPC * Lay::ROWB, &tin, bar, tx * TCU, ky, b * N + c * Lay::RPC);
+    };
+    auto issue_sym = [&](int t) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L);
+        const int kya = ky <= N ? ky : L - ky;
+        mbar_arrive_expect_tx(bar + 1, Lay::S_BYTES);
+#pragma unroll
+        for (int c = 0; c < Lay::NCS; ++c)
+            tma_load_3d(reinterpret_cast<unsigned char *>(sb) + c * Lay::SRC * Lay::SROWB, &tsym, bar + 1,
+                        tx * TC, kya, c * Lay::SRC);
+    };
+    int t = blockIdx.x;
+    if (threadIdx.x == 0 && t < ntiles) {
+        issue_in(t);
+        issue_sym(t);
+    }
+    uint32_t phase = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
+        const int col = tx * TC + W * g;
+        const bool valid = col < ncols;
+        const bool more = t + (int)gridDim.x < ntiles;
+        bool ok = mbar_wait(bar, phase, status);
+        if (__syncthreads_or(!ok)) return;
+        C v[E];
+        Stage<C, N, E, -1, R0, 1>::template gather<false>(v, qh, [&](int row) {
+            return ld_sm_cc<C>(inb + row * Lay::ROWB + g * 16);
+        });
+        __syncthreads();
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_in(t + gridDim.x);
+        }
+        if (h) {  // odd outputs: transform x_n W_{2N}^n
+#pragma unroll
+            for (int b = 0; b < E / R0; ++b) {
+                const int j = qh + PH * b;
+#pragma unroll
+                for (int r = 0; r < R0; ++r) v[b * R0 + r] = twmul<-1>(v[b * R0 + r], __ldg(tw + j + r * (N / R0)));
+            }
+        }
+        constexpr RunOpt fwd{true, false, true, false, false};
+        Stages<C, N, E, -1, 1, Rs>::template run<fwd>(
+            v, qh, g, xh, NG, tw, 2, [&](int) { return czero<C>(); }, [&](int, C) {});
+        // v[b RL + r] = X[2m + h], m = qh + PH b + r N/RL.
+        if constexpr (TAIL) {
+            const int kya = ky <= N ? ky : L - ky;
+            constexpr int SHELL = N - N / 8;
+            float w[W], eshell = 0.f, etot = 0.f;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const int kx = col + i;
+                w[i] = kx > N || !valid ? 0.f : (kx == 0 || kx == N) ? 1.f : 2.f;
+            }
+#pragma unroll
+            for (int b = 0; b < E / RL; ++b) {
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    const int k = 2 * (qh + PH * b + r * (N / RL)) + h;
+                    const int kz = k <= N ? k : L - k;
+                    float e;
+                    if constexpr (W == 2) {
+                        const float2 en = cenergy(v[b * RL + r]);
+                        e = w[0] * en.x + w[1] * en.y;
+                        if ((kz >= SHELL || kya >= SHELL) || col >= SHELL) eshell += e;
+                        else if (col + 1 >= SHELL) eshell += w[1] * en.y;
+                    } else {
+                        e = w[0] * cenergy(v[b * RL + r]);
+                        if (kz >= SHELL || kya >= SHELL || col >= SHELL) eshell += e;
+                    }
+                    etot += e;
+                }
+            }
+            if constexpr (NT >= 32) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    eshell += __shfl_xor_sync(0xffffffffu, eshell, o);
+                    etot += __shfl_xor_sync(0xffffffffu, etot, o);
+                }
+            }
+            if (NT < 32 || (threadIdx.x & 31) == 0) {
+                atomicAdd(tail + 2 * bb, (double)eshell);
+                atomicAdd(tail + 2 * bb + 1, (double)etot);
+            }
+        }
+        ok = mbar_wait(bar + 1, phase, status);
+        if (__syncthreads_or(!ok)) return;
+        phase ^= 1;
+#pragma unroll
+        for (int b = 0; b < E / RL; ++b) {
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                const int k = 2 * (qh + PH * b + r * (N / RL)) + h;
+                const int kz = k <= N ? k : L - k;
+                v[b * RL + r] = scale_sym_sm(v[b * RL + r], sb + kz * TC + W * g);
+            }
+        }
+        __syncthreads();  // the symbol buffer is free
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_sym(t + gridDim.x);
+        }
+        constexpr RunOpt inv{true, false, true, false, false};
+        Stages<C, N, E, 1, 1, Rv>::template run<inv>(
+            v, qh, g, xh, NG, tw, 2, [&](int) { return czero<C>(); }, [&](int, C) {});
+        // v[b R0 + r] = A_z (h = 0) or B_z (h = 1), z = qh + PH b + r N/R0.  Half 0 keeps the
+        // rows z < N/2 (r < R0/2) and half 1 the rest; each sends the other half its rows.
+        if (h) {
+#pragma unroll
+            for (int b = 0; b < E / R0; ++b) {
+                const int j = qh + PH * b;
+#pragma unroll
+                for (int r = 0; r < R0; ++r) v[b * R0 + r] = twmul<1>(v[b * R0 + r], __ldg(tw + j + r * (N / R0)));
+            }
+        }
+        __syncthreads();  // every read of the inverse's exchanges is done
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) {
+            const int j = qh + PH * b;
+#pragma unroll
+            for (int r = 0; r < R0; ++r)
+                if ((2 * r < R0) == (h != 0)) xb[(j + r * (N / R0)) * NG + g] = v[b * R0 + r];
+        }
+        __syncthreads();
+        Cx2<Real> *dst = out + ((long long)bb * N * L + ky) * Px + col;
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) {
+            const int j = qh + PH * b;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                if ((2 * r < R0) == (h == 0)) {
+                    const int z = j + r * (N / R0);
+                    const C x = cadd(v[b * R0 + r], xb[z * NG + g]);
+                    if (valid) st_cc(dst + z * zs, x);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace gsp

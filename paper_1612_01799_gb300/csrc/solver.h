@@ -41,6 +41,7 @@ struct DevicePlan {
     void *w3 = nullptr;
     int *status = nullptr;  // device status word (bit 0: a bounded wait timed out)
     double *tail = nullptr; // 2 max_batch doubles: spectral-tail sums of a checked solve
+    int zsplit = 0;         // z pass form: 0 length-2N transforms, 1 even/odd length-N split
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers.
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
@@ -66,6 +67,13 @@ cudaError_t encode_tma_maps(DevicePlan &p);
 // padded spectrum's energy in the outer |k|_inf shell and its total energy.
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
                          cudaStream_t s, cudaEvent_t *ev, double *tail = nullptr);
+
+// Whether the split form of the z pass exists for N (its length-N schedule has fewer
+// stages than the length-2N one).
+bool z_split_available(int N);
+
+// The z pass alone, one density, in the form p.zsplit selects (for timing the forms).
+cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s);
 
 // Fill p.sym from the per-axis factors (FP64, on the device):
 // sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).

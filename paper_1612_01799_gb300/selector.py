@@ -196,17 +196,47 @@ class Network:
         return losses
 
 
-def calibrate(leta, lerr, quantile=0.98):
-    """Monotone map from log10(eta) to a log10 error bound: a least-squares line, shifted up
-    so that `quantile` of the training pairs lie on or below it."""
-    x, y = leta.ravel(), lerr.ravel()
+def calibrate(leta, lerr, quantile=0.98, width=0.25, min_count=4):
+    """Monotone map from log10(eta) to a log10 error bound, as a step function.
+
+    The training pairs are binned by log10(eta) (bins `width` wide); each bin's bound is the
+    `quantile` of its log10 errors (its maximum when it holds fewer than `min_count` pairs),
+    and a running maximum from small to large eta makes the map non-decreasing.  A straight
+    line would not do: the error stops falling at the FP32 round-off floor while eta keeps
+    falling, which flattens a fitted slope until no eta passes the check.
+    Returns {"x0": left edge of bin 0, "width": bin width, "bound": [log10 bound per bin]}."""
+    x, y = np.ravel(leta), np.ravel(lerr)
     keep = np.isfinite(x) & np.isfinite(y) & (x > -29)
     x, y = x[keep], y[keep]
-    A = np.stack([np.ones_like(x), x], axis=1)
-    (a, b), *_ = np.linalg.lstsq(A, y, rcond=None)
-    b = max(b, 0.0)
-    shift = np.quantile(y - (a + b * x), quantile)
-    return float(a + shift), float(b)
+    if x.size == 0:
+        raise ValueError("calibrate: no finite (eta, error) pairs")
+    x0 = math.floor(x.min() / width) * width
+    nb = int(math.floor((x.max() - x0) / width)) + 1
+    b = np.minimum(((x - x0) / width).astype(int), nb - 1)
+    bound, run = [], -math.inf
+    for i in range(nb):
+        yi = y[b == i]
+        if yi.size:
+            q = float(np.quantile(yi, quantile)) if yi.size >= min_count else float(yi.max())
+            run = max(run, q)
+        bound.append(run)
+    return {"x0": float(x0), "width": float(width), "bound": bound}
+
+
+def calibrated_bound(cal, eta):
+    """log10 error bound for eta under a calibration from `calibrate` (+inf beyond the
+    largest eta seen in training, the bin-0 bound below the smallest)."""
+    x = math.log10(max(eta, 1e-300))
+    i = int(math.floor((x - cal["x0"]) / cal["width"]))
+    if i >= len(cal["bound"]):
+        return math.inf
+    return cal["bound"][max(i, 0)]
+
+
+def eta_threshold(cal, tol):
+    """Largest eta (a bin's upper edge) that the check accepts at tol, or 0 if none."""
+    ok = [i for i, b in enumerate(cal["bound"]) if b <= math.log10(tol)]
+    return 10.0 ** (cal["x0"] + (ok[-1] + 1) * cal["width"]) if ok else 0.0
 
 
 def save(path, net, candidates, margin, cal):
@@ -234,7 +264,7 @@ class Selector:
         with open(path + ".json") as f:
             meta = json.load(f)
         self.candidates = tuple(meta["candidates"])
-        self.cal = tuple(meta["calibration"])
+        self.cal = meta["calibration"]
 
     def select(self, samples32, count, tol):
         N = (ctypes.c_int * count)()
@@ -244,8 +274,8 @@ class Selector:
         return list(N), np.frombuffer(pred, dtype=np.float32).reshape(count, -1)
 
     def check(self, eta, tol):
-        a, b = self.cal
-        return a + b * math.log10(max(eta, 1e-300)) <= math.log10(tol)
+        """The a-posteriori acceptance test: calibrated error bound of eta within tol."""
+        return calibrated_bound(self.cal, eta) <= math.log10(tol)
 
     def close(self):
         if self.h.value:
@@ -274,7 +304,8 @@ def fit(train_indices, ws, path, epochs=3000, lr=2e-3, margin=0.3, seed=0):
 
 
 def _solve_until_checked(ws, sel, params, start_k, tol):
-    """Solve at candidates from index start_k up until the calibrated check passes."""
+    """Solve at candidates from index start_k up until the calibrated check passes.
+    Returns (N, index of N, number of solves)."""
     k = start_k
     while True:
         N = ws.candidates[k]
@@ -284,7 +315,7 @@ def _solve_until_checked(ws, sel, params, start_k, tol):
         _lib.check(ws.lib.poisson_solve_checked(ws.plans[N].handle, _ptr(ws.rho[:n3]), _ptr(ws.u[:n3]),
                                                 ctypes.byref(eta), _stream()), "poisson_solve_checked")
         if sel.check(eta.value, tol) or k == len(ws.candidates) - 1:
-            return N, k
+            return N, k, k - start_k + 1
         k += 1
 
 
@@ -314,7 +345,7 @@ def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512, fixed_ti
     # accuracy of the grids each strategy ended on (untimed)
     def errors(chosen):
         out = []
-        for i, p, (N, _) in zip(test_indices, params, chosen):
+        for i, p, (N, _, _) in zip(test_indices, params, chosen):
             out.append(ws.solve_error(p, N, seed=5000 + i)[0])
         return np.array(out)
     e3, e2 = errors(chosen3), errors(chosen2)
@@ -338,7 +369,7 @@ def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512, fixed_ti
         d = {"seconds": t, "met_tol": float(np.mean(e <= tol)), "median_err": float(np.median(e))}
         if chosen is not None:
             d["mean_N"] = float(np.mean([c[0] for c in chosen]))
-            d["solves_per_density"] = float(np.mean([1 + c[1] for c in chosen]))
+            d["solves_per_density"] = float(np.mean([c[2] for c in chosen]))
         return d
     res["fixed_N%d_f64" % fixed_N] = summary(t1, e1, None)
     res["fixed_N%d_f64" % fixed_N]["timed_densities"] = fixed_timed
