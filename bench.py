@@ -31,6 +31,8 @@ N_DEFAULT, L_BOX, TOL32, TOL64 = 256, 10.0, 1e-6, 1e-12
 METRIC = "grid pts/s per solve (N^3/s) FP32 vs FP64 at stated rel-L2 err; % HBM roofline"
 UNIT = "pts/s"
 PASSES = ["x_forward", "y_forward", "z_fwd_symbol_inv", "y_inverse", "x_inverse"]
+Z_FORMS = ["direct", "split", "warp"]
+Z_KERNELS = ["k_z_symbol", "k_z_split", "k_z_warp"]
 KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_inverse"]
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
@@ -321,7 +323,7 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
-        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_split": plan.z_split,
+        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
                           "rho": rho_t, "out": out_t}
 
@@ -348,8 +350,7 @@ def run_ours(args):
         dom = max(range(5), key=lambda i: r32["per_pass"][i])
         gbs = [bytes32[i] / (r32["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
         names = list(KERNEL_NAMES)
-        if r32["z_split"]:
-            names[2] = "k_z_split"
+        names[2] = Z_KERNELS[r32["z_form"]]
         src_hash = kernel_source_hash()
         traffic = NCU_TRAFFIC.get((src_hash, names[dom], N))
         r64 = results["f64"]
@@ -373,8 +374,8 @@ def run_ours(args):
             "e2e": {"value": world * N ** 3 / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": N ** 3 * 4, "d2h_bytes_per_step": N ** 3 * 4},
             "gpu_launches": 5 * r32["steps"],
-            "tuning": {"z_pass_f32": "split" if r32["z_split"] else "direct",
-                       "z_pass_f64": "split" if results["f64"]["z_split"] else "direct",
+            "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
+                       "z_pass_f64": Z_FORMS[results["f64"]["z_form"]],
                        "how": "timed at plan creation, cached per (device, N, dtype)"},
             "clocks": r32["clocks"],
         }

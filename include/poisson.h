@@ -167,17 +167,22 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  * the plan's N and dtype on the plan's own workspace and keeps the fastest; the choice is
  * cached per process, device, N and dtype, so every plan of a shape solves with the same
  * kernels (and gives bit-identical results).  Variants differ only in rounding order.
- *   POISSON_KNOB_Z_SPLIT  form of the fused z pass (Sec. 2, the convolution with the
- *       G-tensor along the last axis): 0 = length-2N transforms, 1 = the pruned length-2N
- *       transforms split into even- and odd-frequency length-N transforms.  Variant 1
- *       exists only where the length-N schedule has fewer stages
- *       (N = 16, 80, 256, 320, 384).
+ *   POISSON_KNOB_Z_FORM  form of the fused z pass (Sec. 2, the convolution with the
+ *       G-tensor along the last axis):
+ *       0 = length-2N transforms, a column pair spread over the threads of a block;
+ *       1 = the pruned length-2N transforms split into even- and odd-frequency length-N
+ *           transforms, where the length-N schedule has fewer stages
+ *           (N = 16, 80, 256, 320, 384);
+ *       2 = one warp per column pair: 16-point DFTs in registers, a radix-2 step between
+ *           lane pairs and one warp-local shared-memory exchange per direction
+ *           (POISSON_F32, N = 256).
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that
- * does not exist for the plan's N.  Not to be called while the plan has work in flight.
+ * does not exist for the plan's N and dtype.  Not to be called while the plan has work in
+ * flight.
  */
-#define POISSON_KNOB_Z_SPLIT 0
+#define POISSON_KNOB_Z_FORM 0
 int poisson_plan_get_knob(poisson_plan p, int knob, int *value);
 int poisson_plan_set_knob(poisson_plan p, int knob, int value);
 

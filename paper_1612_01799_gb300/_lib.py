@@ -63,7 +63,7 @@ class PoissonError(RuntimeError):
         super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "unknown"), code))
 
 
-KNOB_Z_SPLIT = 0
+KNOB_Z_FORM = 0
 
 
 def load():

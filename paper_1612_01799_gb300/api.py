@@ -118,17 +118,17 @@ class Plan:
                 "ws_bytes": ws.value, "table_bytes": tb.value}
 
     @property
-    def z_split(self):
-        """Form of the fused z pass in use: 0 length-2N transforms, 1 even/odd length-N split
-        (chosen by timing at plan creation)."""
+    def z_form(self):
+        """Form of the fused z pass in use (chosen by timing at plan creation): 0 length-2N
+        transforms, 1 even/odd length-N split, 2 one warp per column pair."""
         v = ctypes.c_int()
-        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_Z_SPLIT, ctypes.byref(v)),
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_Z_FORM, ctypes.byref(v)),
                    "poisson_plan_get_knob")
         return v.value
 
-    @z_split.setter
-    def z_split(self, value):
-        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_Z_SPLIT, int(value)), "poisson_plan_set_knob")
+    @z_form.setter
+    def z_form(self, value):
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_Z_FORM, int(value)), "poisson_plan_set_knob")
 
     def gauss_sum(self):
         n = self.info()["n_terms"]

@@ -86,7 +86,7 @@ cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const dou
 // ---- autotuning of kernel variants --------------------------------------------------------
 // Decisions per (device, N, dtype), made by the first plan of that shape and reused.
 struct TuneEntry {
-    int dev, N, dtype, zsplit;
+    int dev, N, dtype, zform;
 };
 static std::vector<TuneEntry> g_tune;
 static std::mutex g_tune_mutex;
@@ -106,16 +106,18 @@ static cudaError_t time_z(const DevicePlan &p, cudaStream_t s, cudaEvent_t a, cu
     return cudaSuccess;
 }
 
-// Choose p.zsplit: the cached decision for this shape, else the faster form timed on p's
-// zeroed workspace.  Only w3 is written, and every solve writes w3 before reading it.
+// Choose p.zform: the cached decision for this shape, else the fastest form that exists,
+// timed on p's zeroed workspace.  Only w3 is written, and every solve writes w3 before
+// reading it.
 static cudaError_t autotune(DevicePlan &p, int dev) {
-    p.zsplit = 0;
-    if (!z_split_available(p.N)) return cudaSuccess;
+    p.zform = 0;
+    const int forms = z_forms(p.N, p.dtype);
+    if (forms == 1) return cudaSuccess;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (const TuneEntry &t : g_tune)
             if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
-                p.zsplit = t.zsplit;
+                p.zform = t.zform;
                 return cudaSuccess;
             }
     }
@@ -124,26 +126,33 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    float ms[2] = {0.f, 0.f};
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-        p.zsplit = v;
-        e = time_z(p, s, a, b, 3, &ms[v]);
+    int best = 0;
+    float best_ms = 0.f;
+    for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+        if (!(forms >> v & 1)) continue;
+        float ms = 0.f;
+        p.zform = v;
+        e = time_z(p, s, a, b, 3, &ms);
+        if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+            best = v;
+            best_ms = ms;
+        }
     }
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) {
-        p.zsplit = 0;
+        p.zform = 0;
         return e;
     }
-    p.zsplit = ms[1] < ms[0] ? 1 : 0;
+    p.zform = best;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const TuneEntry &t : g_tune)  // another thread may have decided meanwhile
         if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
-            p.zsplit = t.zsplit;
+            p.zform = t.zform;
             return cudaSuccess;
         }
-    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zsplit});
+    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform});
     return cudaSuccess;
 }
 }  // namespace gsp
@@ -319,16 +328,16 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
 
 extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
     if (!p || !value) return POISSON_ERR_ARG;
-    if (knob != POISSON_KNOB_Z_SPLIT) return POISSON_ERR_ARG;
-    *value = p->dp.zsplit;
+    if (knob != POISSON_KNOB_Z_FORM) return POISSON_ERR_ARG;
+    *value = p->dp.zform;
     return POISSON_OK;
 }
 
 extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     if (!p) return POISSON_ERR_ARG;
-    if (knob != POISSON_KNOB_Z_SPLIT || (value != 0 && value != 1)) return POISSON_ERR_ARG;
-    if (value == 1 && !gsp::z_split_available(p->dp.N)) return POISSON_ERR_UNSUPPORTED;
-    p->dp.zsplit = value;
+    if (knob != POISSON_KNOB_Z_FORM || value < 0 || value > 2) return POISSON_ERR_ARG;
+    if (!(gsp::z_forms(p->dp.N, p->dp.dtype) >> value & 1)) return POISSON_ERR_UNSUPPORTED;
+    p->dp.zform = value;
     return POISSON_OK;
 }
 

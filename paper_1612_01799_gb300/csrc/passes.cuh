@@ -123,6 +123,7 @@ template <typename Real> using Cx2 = typename std::conditional<sizeof(Real) == 4
 
 }  // namespace gsp
 #include "passes_tma.cuh"
+#include "passes_zwarp.cuh"
 namespace gsp {
 
 // ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
@@ -380,9 +381,13 @@ template <class K> static int persistent_blocks(K kernel, int threads, size_t sm
     return blocks < ntiles ? blocks : ntiles;
 }
 
-// The fused z pass (K3) of B densities in the form p.zsplit selects: the length-2N
-// transforms (0) or the split into even and odd length-N transforms (1, where
-// zsplit_available; otherwise the direct form runs).
+// Whether the warp form of the z pass exists (FP32, N = 256).
+template <typename Real, int N> constexpr bool zwarp_form() { return std::is_same<Real, float>::value && N == ZWarp::N; }
+inline bool zwarp_available(int N) { return N == ZWarp::N; }
+
+// The fused z pass (K3) of B densities in the form p.zform selects: the length-2N
+// transforms (0), the split into even and odd length-N transforms (1, where
+// zsplit_available) or the warp form (2, zwarp_form); an absent form runs as form 0.
 template <typename Real, int N>
 cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
     using T2 = Cx2<Real>;
@@ -394,8 +399,19 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
     const int nt = ntx * L * B;
     T2 *w3 = static_cast<T2 *>(p.w3);
     const TwC *twc = static_cast<const TwC *>(p.twc);
+    if constexpr (zwarp_form<Real, N>()) {
+        if (p.zform == 2) {
+            static_assert(ZWarp::TC == L1::TC, "same tiles as the direct form");
+            auto k = tail ? k_z_warp<true> : k_z_warp<false>;
+            GSP_CHECK(set_smem(k, ZWarp::SMEM));
+            k<<<persistent_blocks(k, ZWarp::NT, ZWarp::SMEM, nt), ZWarp::NT, ZWarp::SMEM, s>>>(
+                p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status,
+                tail);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (zsplit_available<L>()) {
-        if (p.zsplit) {
+        if (p.zform == 1) {
             auto k = tail ? k_z_split_tma<Real, L, true> : k_z_split_tma<Real, L, false>;
             constexpr int T = zsplit_threads<Real, L>();
             GSP_CHECK(set_smem(k, L1::SMEM));
@@ -489,15 +505,15 @@ inline TensorMapEncodeFn tensor_map_encoder() {
 // 3-D tiled map: dims d (innermost first), byte strides of dims 1 and 2, box b.
 inline cudaError_t encode_3d(CUtensorMap *m, CUtensorMapDataType dt, void *base, cuuint64_t d0,
                              cuuint64_t d1, cuuint64_t d2, cuuint64_t s1, cuuint64_t s2, cuuint32_t b0,
-                             cuuint32_t b1, cuuint32_t b2) {
+                             cuuint32_t b1, cuuint32_t b2,
+                             CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE) {
     TensorMapEncodeFn enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[3] = {d0, d1, d2};
     const cuuint64_t strides[2] = {s1, s2};
     const cuuint32_t box[3] = {b0, b1, b2};
     const cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE,
+    CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -522,6 +538,15 @@ cudaError_t encode_n(DevicePlan &p) {
                         p.sym, p.Ps, N + 1, N + 1, srow, (cuuint64_t)(N + 1) * srow, L1::TC, 1, L1::SRC));
     GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, p.Px * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L2::ROWB / 8, L2::RPC, 1));
+    if constexpr (zwarp_form<Real, N>()) {
+        // Columns kx > N lie outside these maps: loads read zeros there, stores skip them.
+        GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp::TC, 1, N,
+                            CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp::TC, 1, N,
+                            CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
+                            (cuuint64_t)(N + 1) * srow, ZWarp::TC, 1, ZWarp::SYM_RPC, CU_TENSOR_MAP_SWIZZLE_64B));
+    }
     return cudaSuccess;
 }
 

@@ -1,0 +1,334 @@
+// Fused z pass (K3), warp form, FP32, length L = 2N = 512 (N = 256).
+//
+// Same operation as k_z_symbol_tma: per column (kx, ky) of w2, the pruned length-2N forward
+// DFT along z, the product with the symbol G(|kx|, |ky|, |kz|), the inverse DFT and the crop
+// to z < N (Sec. 2: convolution with the G-tensor on the zero-padded grid, I_delta folded
+// into the symbol).  Here one warp owns one pair of neighbouring columns (packed FP32x2,
+// type CV), so the exchanges of the transform are warp-local and no block barrier sits
+// inside the transforms.
+//
+// Decomposition of the length-512 forward transform of a column x (x_n = 0 for n >= 256),
+// lane q = q' + 16 s (q' < 16, s < 2), register j < 16:
+//   F1  lane q: A_q[k1] = sum_{r<8} x[q + 32 r] W_16^{r k1}  (16-point DFT, 8 nonzero inputs)
+//   F2  B_q[k1] = A_q[k1] W_512^{q k1}
+//   F3  radix 2 over s between lanes q' and q' + 16 (shuffle):
+//       V[q'][k1][0] = B_q'[k1] + B_{q'+16}[k1],  V[q'][k1][1] = (B_q'[k1] - B_{q'+16}[k1]) W_32^{q'}
+//   F5  exchange through shared memory: lane l = k1 + 16 t gathers V[q'][k1][t], q' < 16
+//   F6  16-point DFT over q':  X[k1 + 16 t + 32 k2] = sum_q' V[q'][k1][t] W_16^{q' k2}
+// so lane l holds X[l + 32 k2] in register k2.  Every step is linear, and the inverse
+// transform is the adjoint: the conjugate transpose of each step in reverse order, which
+// moves data along the same paths and returns the z < N outputs to the lanes and registers
+// the inputs came from.
+//
+// Register maps.  After F1, register j holds k1 = kappa0(j) = 2j (j < 8) or 2(j-8)+1 for
+// the lower half-warp; the upper half holds kappa0(j) ^ 8, obtained by negating its odd
+// inputs (X[k + 8] of a 16-point DFT with 8 nonzero inputs is X[k] of the inputs times
+// (-1)^r).  Then the registers j in K = {0..3, 8..11} of both halves hold k1 values that
+// pair with the partner's register j + 4, and F3 runs the same instructions on every lane:
+// keep v[j], receive the partner's v[j + 4].  The upper half's difference comes out
+// negated; its F3 twiddle carries the sign (-W_32^{q'}).
+//
+// Shared memory (one CTA = one tile of 16 columns x 1 ky x the N input rows, 8 warps):
+//   B   32 KB: the TMA input tile (256 rows x 128 B, 128-byte swizzle), then the tile's
+//       symbol rows (272 x 64 B, 64-byte swizzle), then the next tile's input;
+//   XO  64 KB: warp g owns the 16-byte chunk g ^ (row & 7) of each 128-byte row, for the
+//       exchange (512 slots) and for its outputs (rows z < 256), so the first 32 KB is the
+//       output tile in the TMA store's 128-byte swizzle;
+//   T   4 KB: twiddles W_512^{q k1} as T[k1][q];
+//   three mbarriers (input, symbol, XO free) and three arrival counters.
+// The last warp to finish with B (input read, symbol read) issues the next TMA load into
+// it; the last warp to write its outputs issues the TMA store of the tile and, once the
+// store has read XO, frees XO for the next tile.  All waits are bounded (tma.cuh).
+#pragma once
+#include "tma.cuh"
+
+namespace gsp {
+
+struct ZWarp {
+    static constexpr int L = 512, N = 256, TC = 16, NW = 8, NT = 256;
+    static constexpr int SYM_RPC = 136, SYM_NCP = 2;  // symbol rows per TMA copy, copies
+    static constexpr int IN_BYTES = N * TC * 8;       // 32 KB
+    static constexpr int SYM_BYTES = SYM_NCP * SYM_RPC * TC * 4;
+    static constexpr int OFF_B = 0, OFF_XO = 32768, OFF_T = OFF_XO + 65536, OFF_BAR = OFF_T + 16 * 32 * 8;
+    static constexpr int SMEM = 1024 + OFF_BAR + 64;  // 1 KB alignment slack
+    static_assert(SYM_BYTES <= 32768 && SYM_NCP * SYM_RPC >= N + 1, "symbol rows fit B");
+    static_assert((SYM_RPC * TC * 4) % 512 == 0, "64-byte-swizzled copies start 512-byte aligned");
+};
+
+// CV times the scalar twiddle w = (re, im) (D < 0) or its conjugate (D > 0).
+template <int D> __device__ __forceinline__ CV zw_twmul(CV a, float2 w) {
+    const float2 R = f2(w.x, w.x);
+    const float2 I = f2(w.y, w.y), NI = f2(-w.y, -w.y);
+    if (D < 0) return {f2fma(a.im, NI, f2mul(a.re, R)), f2fma(a.re, I, f2mul(a.im, R))};
+    return {f2fma(a.im, I, f2mul(a.re, R)), f2fma(a.re, NI, f2mul(a.im, R))};
+}
+__device__ __forceinline__ CV zw_neg(CV a) { return {f2mul(a.re, f2(-1.f, -1.f)), f2mul(a.im, f2(-1.f, -1.f))}; }
+// a exp(D i pi / 2)
+template <int D> __device__ __forceinline__ CV zw_rot(CV a) {
+    return D < 0 ? CV{a.im, f2neg(a.re)} : CV{f2neg(a.im), a.re};
+}
+
+// exp(-2 pi i r / 16), r < 8
+__device__ __forceinline__ constexpr float zw_c16(int r) {
+    return r == 0 ? 1.f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
+         : r == 3 ? 0.38268343236508977173f : r == 4 ? 0.f : r == 5 ? -0.38268343236508977173f
+         : r == 6 ? -0.70710678118654752440f : -0.92387953251128675613f;
+}
+__device__ __forceinline__ constexpr float zw_s16(int r) {  // imaginary part
+    return r == 0 ? 0.f : r == 1 ? -0.38268343236508977173f : r == 2 ? -0.70710678118654752440f
+         : r == 3 ? -0.92387953251128675613f : r == 4 ? -1.f : r == 5 ? -0.92387953251128675613f
+         : r == 6 ? -0.70710678118654752440f : -0.38268343236508977173f;
+}
+
+// F1: forward 16-point DFT of v[0..7] (inputs 8..15 zero): v[m] = X[2m], v[8+m] = X[2m+1]
+// (X[2m] = DFT8(a)[m], X[2m+1] = DFT8(a_r W_16^r)[m]).
+__device__ __forceinline__ void zw_f1(CV *v) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (r == 0) v[8] = v[0];
+        else if (r == 4) v[12] = zw_rot<-1>(v[4]);
+        else v[8 + r] = cmulk<-1>(v[r], zw_c16(r), zw_s16(r));
+    }
+    dft<8, -1>(v);
+    dft<8, -1>(v + 8);
+}
+// Adjoint of F1: y_r = IDFT8(v[0..7])[r] + conj(W_16^r) IDFT8(v[8..15])[r], r < 8, in v[0..7].
+__device__ __forceinline__ void zw_f1_adj(CV *v) {
+    dft<8, 1>(v);
+    dft<8, 1>(v + 8);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const CV o = r == 0 ? v[8] : r == 4 ? zw_rot<1>(v[12]) : cmulk<1>(v[8 + r], zw_c16(r), zw_s16(r));
+        v[r] = cadd(v[r], o);
+    }
+}
+
+__device__ __forceinline__ int zw_kappa0(int j) { return j < 8 ? 2 * j : 2 * (j - 8) + 1; }
+// Exchange slot of (reader lane l, position p); conflict-free for both access patterns.
+__device__ __forceinline__ int zw_slot(int l, int p) { return l * 16 + ((p + l) & 15); }
+// Byte offset of row `row` of warp g in a 128-byte-swizzled region.
+__device__ __forceinline__ int zw_sw128(int row, int g) { return row * 128 + ((g ^ (row & 7)) << 4); }
+
+__device__ __forceinline__ void zw_st(unsigned char *p, CV x) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x.re.x, x.re.y, x.im.x, x.im.y);
+}
+__device__ __forceinline__ CV zw_ld(const unsigned char *p) {
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    return {f2(f.x, f.y), f2(f.z, f.w)};
+}
+__device__ __forceinline__ CV zw_shfl16(CV x) {
+    return {f2(__shfl_xor_sync(0xffffffffu, x.re.x, 16), __shfl_xor_sync(0xffffffffu, x.re.y, 16)),
+            f2(__shfl_xor_sync(0xffffffffu, x.im.x, 16), __shfl_xor_sync(0xffffffffu, x.im.y, 16))};
+}
+
+// Tile t = (tx, ky, b): tx the 16-column block, consecutive tiles take ky and its mirror
+// 2N - ky (same symbol rows), b the density.  With TAIL the forward spectrum's shell and
+// total energies are added to tail[2 b], tail[2 b + 1] (as in k_z_symbol_tma).
+template <bool TAIL>
+__global__ void __launch_bounds__(ZWarp::NT, 2)
+k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
+         const __grid_constant__ CUtensorMap tout, const float2 *__restrict__ tw, int ntx, int ntiles,
+         int ncols, int *__restrict__ status, double *__restrict__ tail) {
+    using Z = ZWarp;
+    constexpr int L = Z::L, N = Z::N, NW = Z::NW;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    unsigned char *Bb = base + Z::OFF_B;
+    unsigned char *xo = base + Z::OFF_XO;
+    float2 *T = reinterpret_cast<float2 *>(base + Z::OFF_T);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Z::OFF_BAR);  // input, symbol, XO free
+    int *cnt = reinterpret_cast<int *>(bar + 3);                       // input, symbol, output
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31, s = q >> 4, qp = q & 15;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init(bar + 2, 1);
+        cnt[0] = cnt[1] = cnt[2] = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < 512; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    __syncthreads();
+
+    auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
+    auto issue_in = [&](int t) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), b = t / (ntx * L);
+        mbar_arrive_expect_tx(bar, Z::IN_BYTES);
+        tma_load_3d(Bb, &tin, bar, tx * Z::TC, ky, b * N);
+    };
+    auto issue_sym = [&](int t) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L);
+        const int kya = ky <= N ? ky : L - ky;
+        mbar_arrive_expect_tx(bar + 1, Z::SYM_BYTES);
+#pragma unroll
+        for (int c = 0; c < Z::SYM_NCP; ++c)
+            tma_load_3d(Bb + c * Z::SYM_RPC * Z::TC * 4, &tsym, bar + 1, tx * Z::TC, kya, c * Z::SYM_RPC);
+    };
+    // Arrival of this warp on counter c; true on the lane-0 thread of the tile's last warp.
+    auto last_arrival = [&](int c) {
+        __syncwarp();
+        bool last = false;
+        if (q == 0) {
+            __threadfence_block();
+            last = atomicAdd(cnt + c, 1) % NW == NW - 1;
+            if (last) {
+                __threadfence_block();
+                fence_proxy_async();
+            }
+        }
+        return last;
+    };
+    if (threadIdx.x == 0) {
+        mbar_arrive(bar + 2);  // XO starts free
+        if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
+    }
+
+    // Per-lane constants: F3 twiddle sgn W_32^{q'}, twiddle-table bases of the registers
+    // in K (k1 = kappa0 + 8 s) and outside K (k1 = kappa0 - 8 s), input sign.
+    float2 tw32 = tw[16 * qp];
+    if (s) tw32 = f2(-tw32.x, -tw32.y);
+    const float2 *TK = T + q + 256 * s, *TN = T + q - 256 * s;
+    const float sg = s ? -1.f : 1.f;
+    bool stored = false;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
+        const int kya = ky <= N ? ky : L - ky;
+        const int col = tx * Z::TC + 2 * g;
+        const bool valid = col < ncols;
+        CV v[16];
+        if (!mbar_wait(bar, ph, status)) return;
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float4 f = *reinterpret_cast<const float4 *>(Bb + zw_sw128(q + 32 * r, g));
+                v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
+                if (r & 1) v[r] = {f2mul(v[r].re, f2(sg, sg)), f2mul(v[r].im, f2(sg, sg))};
+            }
+        }
+        if (last_arrival(0)) issue_sym(t);
+        if (valid) {
+            zw_f1(v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const bool inK = (j & 4) == 0;
+                v[j] = zw_twmul<-1>(v[j], (inK ? TK : TN)[32 * zw_kappa0(j)]);
+            }
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                if (j & 4) continue;
+                const CV rcv = zw_shfl16(v[j + 4]);
+                const CV a = v[j];
+                v[j] = cadd(a, rcv);
+                v[j + 4] = zw_twmul<-1>(csub(a, rcv), tw32);
+            }
+        }
+        if (!mbar_wait(bar + 2, ph, status)) return;
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                if (j & 4) continue;
+#pragma unroll
+                for (int tt = 0; tt < 2; ++tt) {
+                    const int l = (zw_kappa0(j) ^ (8 * s)) + 16 * tt;
+                    zw_st(xo + zw_sw128(zw_slot(l, qp), g), v[j + 4 * tt]);
+                }
+            }
+        }
+        __syncwarp();
+        if (valid) {
+#pragma unroll
+            for (int p = 0; p < 16; ++p) v[p] = zw_ld(xo + zw_sw128(zw_slot(q, p), g));
+            dft<16, -1>(v);  // v[k2] = X[q + 32 k2]
+        }
+        if constexpr (TAIL) {
+            constexpr int SHELL = N - N / 8;
+            float eshell = 0.f, etot = 0.f;
+            if (valid) {
+                const float w0 = (col == 0 || col == N) ? 1.f : 2.f;
+                const float w1 = col + 1 > N ? 0.f : (col + 1 == N) ? 1.f : 2.f;
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) {
+                    const int kf = q + 32 * k2;
+                    const int kz = kf <= N ? kf : L - kf;
+                    const float2 en = cenergy(v[k2]);
+                    const bool sh = kz >= SHELL || kya >= SHELL;
+                    etot += w0 * en.x + w1 * en.y;
+                    if (sh || col >= SHELL) eshell += w0 * en.x;
+                    if (sh || col + 1 >= SHELL) eshell += w1 * en.y;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                eshell += __shfl_xor_sync(0xffffffffu, eshell, o);
+                etot += __shfl_xor_sync(0xffffffffu, etot, o);
+            }
+            if (valid && q == 0) {
+                atomicAdd(tail + 2 * bb, (double)eshell);
+                atomicAdd(tail + 2 * bb + 1, (double)etot);
+            }
+        }
+        if (!mbar_wait(bar + 1, ph, status)) return;
+        if (valid) {
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const int kz = k2 < 8 ? q + 32 * k2 : L - q - 32 * k2;
+                const int A = kz * 64 + 8 * g;
+                const float2 sy = *reinterpret_cast<const float2 *>(Bb + (A ^ (((A >> 7) & 3) << 4)));
+                v[k2] = cscale2(v[k2], sy);
+            }
+        }
+        if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
+        if (valid) {
+            dft<16, 1>(v);
+#pragma unroll
+            for (int p = 0; p < 16; ++p) zw_st(xo + zw_sw128(zw_slot(q, p), g), v[p]);
+        }
+        __syncwarp();
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                if (j & 4) continue;
+#pragma unroll
+                for (int tt = 0; tt < 2; ++tt) {
+                    const int l = (zw_kappa0(j) ^ (8 * s)) + 16 * tt;
+                    v[j + 4 * tt] = zw_ld(xo + zw_sw128(zw_slot(l, qp), g));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                if (j & 4) continue;
+                const CV b = zw_twmul<1>(v[j + 4], tw32);
+                const CV a = v[j];
+                v[j] = cadd(a, b);
+                v[j + 4] = zw_shfl16(csub(a, b));
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const bool inK = (j & 4) == 0;
+                v[j] = zw_twmul<1>(v[j], (inK ? TK : TN)[32 * zw_kappa0(j)]);
+            }
+            zw_f1_adj(v);
+        }
+        __syncwarp();  // every lane's exchange reads are done: the slots take the outputs
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                CV x = v[r];
+                if (r & 1) x = {f2mul(x.re, f2(sg, sg)), f2mul(x.im, f2(sg, sg))};
+                *reinterpret_cast<float4 *>(xo + zw_sw128(q + 32 * r, g)) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+            }
+        }
+        fence_proxy_async();
+        if (last_arrival(2)) {
+            tma_store_3d(&tout, xo, tx * Z::TC, ky, bb * N);
+            bulk_commit();
+            bulk_wait_read0();
+            stored = true;
+            mbar_arrive(bar + 2);
+        }
+    }
+    if (stored) bulk_wait0();
+}
+
+}  // namespace gsp

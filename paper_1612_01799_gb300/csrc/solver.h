@@ -41,10 +41,14 @@ struct DevicePlan {
     void *w3 = nullptr;
     int *status = nullptr;  // device status word (bit 0: a bounded wait timed out)
     double *tail = nullptr; // 2 max_batch doubles: spectral-tail sums of a checked solve
-    int zsplit = 0;         // z pass form: 0 length-2N transforms, 1 even/odd length-N split
+    // z pass form: 0 length-2N transforms, 1 even/odd length-N split, 2 warp form (one
+    // warp per column pair, FP32, N = 256)
+    int zform = 0;
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
-    // y inverse: w3), encoded once for these buffers.
+    // y inverse: w3), encoded once for these buffers; and of the warp-form z pass (w2 in,
+    // symbol, w3 out; 128- and 64-byte swizzled boxes), encoded where that form exists.
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
+    CUtensorMap tm_zw_in, tm_zw_sym, tm_zw_out;
 };
 
 constexpr int kStatusTimeoutBit = 1;  // bit of DevicePlan::status set by a timed-out wait
@@ -68,11 +72,12 @@ cudaError_t encode_tma_maps(DevicePlan &p);
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
                          cudaStream_t s, cudaEvent_t *ev, double *tail = nullptr);
 
-// Whether the split form of the z pass exists for N (its length-N schedule has fewer
-// stages than the length-2N one).
-bool z_split_available(int N);
+// Forms of the z pass that exist for (N, dtype), as a bit mask over DevicePlan::zform:
+// bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;
+// bit 2 for FP32 at N = 256.
+int z_forms(int N, int dtype);
 
-// The z pass alone, one density, in the form p.zsplit selects (for timing the forms).
+// The z pass alone, one density, in the form p.zform selects (for timing the forms).
 cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s);
 
 // Fill p.sym from the per-axis factors (FP64, on the device):

@@ -183,7 +183,8 @@ class Network:
         return loss
 
     def train(self, x, t, epochs=3000, lr=2e-3):
-        """Full-batch Adam on standardised inputs."""
+        """Full-batch Adam on standardised inputs.  Returns the loss before the first step
+        and every 500 steps after it (and at the last step)."""
         losses = []
         for step in range(1, epochs + 1):
             loss = self.gradient(x, t)
@@ -191,7 +192,7 @@ class Network:
                                                  self.n, ctypes.c_float(lr), ctypes.c_float(0.9),
                                                  ctypes.c_float(0.999), ctypes.c_float(1e-8), step, _stream()),
                        "poisson_mlp_adam")
-            if step % 500 == 0 or step == epochs:
+            if step == 1 or step % 500 == 0 or step == epochs:
                 losses.append(float(loss.item()))
         return losses
 

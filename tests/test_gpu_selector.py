@@ -157,7 +157,7 @@ def test_selector_end_to_end_small(env, tmp_path):
     try:
         path = str(tmp_path / "sel.bin")
         info = S.fit(list(range(24)), ws, path, epochs=600, lr=3e-3)
-        assert info["losses"][-1] < info["losses"][0]
+        assert info["losses"][-1] < 0.1 * info["losses"][0]
         sel = S.Selector(path, capacity=32)
         params = [S.gaussian_params(S.density(i)) for i in range(24, 32)]
         _, s32 = ws.features(params)

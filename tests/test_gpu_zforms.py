@@ -1,7 +1,7 @@
-"""Both forms of the fused z pass against the oracle: the length-2N transforms and the
-split into even- and odd-frequency length-N transforms (forced through the plan's knob,
-whatever the autotuner chose), the knob API's error codes, and the split form's
-spectral-tail sums."""
+"""Every form of the fused z pass against the oracle: the length-2N transforms, the split
+into even- and odd-frequency length-N transforms and the warp form (forced through the
+plan's knob, whatever the autotuner chose), the knob API's error codes, and the split and
+warp forms' spectral-tail sums and batched solves."""
 import ctypes
 
 import numpy as np
@@ -14,6 +14,11 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
 SPLIT_N = (16, 80, 256, 320, 384)
+WARP_N = (256,)
+
+
+def forms(N, dtype):
+    return [0] + ([1] if N in SPLIT_N else []) + ([2] if dtype == "f32" and N in WARP_N else [])
 
 
 @pytest.fixture(scope="module")
@@ -33,31 +38,35 @@ def rel_l2(a, b):
 def solve_form(torch, N, L, tol, dtype, rho, form):
     from paper_1612_01799_gb300 import Plan
     with Plan(N, L, tol, dtype) as p:
-        assert p.z_split in (0, 1)
-        p.z_split = form
-        assert p.z_split == form
+        assert p.z_form in forms(N, dtype)
+        p.z_form = form
+        assert p.z_form == form
         t = torch.from_numpy(np.ascontiguousarray(rho, dtype=p.np_dtype)).cuda()
         u = p.solve(t)
         torch.cuda.synchronize()
         return u.cpu().numpy().astype(np.float64)
 
 
-def test_knob_codes(torch_cuda):
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_knob_codes(torch_cuda, dtype):
     from paper_1612_01799_gb300 import Plan, _lib
     lib = _lib.load()
     for N in (4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384):
-        with Plan(N, 4.0, 1e-6, "f32") as p:
-            if N in SPLIT_N:
-                p.z_split = 1
-                p.z_split = 0
-            else:
-                assert p.z_split == 0
-                assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_SPLIT, 1) == -4
+        with Plan(N, 4.0, 1e-6, dtype) as p:
+            have = forms(N, dtype)
+            assert p.z_form in have
+            for f in (0, 1, 2):
+                if f in have:
+                    p.z_form = f
+                    assert p.z_form == f
+                else:
+                    assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, f) == -4
             assert lib.poisson_plan_set_knob(p.handle, 7, 0) == -1
-            assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_SPLIT, 2) == -1
+            assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, 3) == -1
+            assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, -1) == -1
             v = ctypes.c_int()
             assert lib.poisson_plan_get_knob(p.handle, 7, ctypes.byref(v)) == -1
-            assert lib.poisson_plan_get_knob(None, _lib.KNOB_Z_SPLIT, ctypes.byref(v)) == -1
+            assert lib.poisson_plan_get_knob(None, _lib.KNOB_Z_FORM, ctypes.byref(v)) == -1
 
 
 def test_tuning_is_per_shape(torch_cuda):
@@ -65,7 +74,7 @@ def test_tuning_is_per_shape(torch_cuda):
     from paper_1612_01799_gb300 import Plan
     for dtype in ("f32", "f64"):
         with Plan(256, 10.0, 1e-6, dtype) as a, Plan(256, 3.0, 1e-9, dtype, max_batch=2) as b:
-            assert a.z_split == b.z_split
+            assert a.z_form == b.z_form
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -75,7 +84,7 @@ def test_forms_full_grid_small(torch_cuda, plan_cache, N, dtype):
     tol = 1e-12 if dtype == "f64" else 1e-6
     rho = D.config_aniso4(N=N, seed=200 + N).gaussians.sample(N, L)
     uo = osolver.solve(rho, L, tol, plan=plan_cache(N, L, tol))
-    for form in (0, 1):
+    for form in forms(N, dtype):
         u = solve_form(torch_cuda, N, L, tol, dtype, rho, form)
         assert rel_l2(u, uo) <= TOL[dtype], form
         assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max(), form
@@ -87,7 +96,7 @@ def test_forms_full_grid_n256(torch_cuda, plan_cache, dtype):
     rho = D.config_aniso4().sample()
     tol = 1e-12 if dtype == "f64" else 1e-6
     uo = osolver.solve(rho, 10.0, tol, plan=plan_cache(256, 10.0, tol))
-    for form in (0, 1):
+    for form in forms(256, dtype):
         u = solve_form(torch_cuda, 256, 10.0, tol, dtype, rho, form)
         assert rel_l2(u, uo) <= TOL[dtype], form
 
@@ -102,23 +111,25 @@ def test_forms_sampled_large(torch_cuda, N, dtype):
     rho = D.config_aniso4(N=N, seed=300 + N).gaussians.sample(N, L)
     lines = [(0, 0), (N // 2, N // 2 - 1), (N - 1, N - 1), (N // 3, 2 * N // 3), (N - 2, 1)]
     ref = direct.sample_lines(rho, gtensor.make_plan(N, L, tol), lines)
-    for form in (0, 1):
+    for form in forms(N, dtype):
         u = solve_form(torch_cuda, N, L, tol, dtype, rho, form)
         got = np.stack([u[z, y] for z, y in lines])
         assert rel_l2(got, ref) <= TOL[dtype], form
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_split_form_tail(torch_cuda, dtype):
-    """The checked solve in the split form: same potential as the unchecked one, and eta
-    as defined on the padded spectrum."""
+@pytest.mark.parametrize("form,N,dtype", [(1, 80, "f64"), (1, 80, "f32"), (2, 256, "f32")])
+def test_form_tail(torch_cuda, form, N, dtype):
+    """The checked solve in a non-default form: same potential as the unchecked one, and
+    eta as defined on the padded spectrum.  The box [-6,6]^3 truncates the Gaussians, so
+    eta (2.5e-4 at N = 256) stands far above the FP32 transforms' rounding floor (about
+    1e-7 here; on [-10,10]^3 the exact eta, 1.6e-8, lies below it)."""
     torch = torch_cuda
     from paper_1612_01799_gb300 import Plan, _lib
     lib = _lib.load()
-    N, L = 80, 6.0
+    L = 6.0
     rho = D.config_aniso4(N=N, seed=31).gaussians.sample(N, L)
     with Plan(N, L, 1e-6, dtype) as p:
-        p.z_split = 1
+        p.z_form = form
         t = torch.from_numpy(rho.astype(p.np_dtype)).cuda()
         u1 = p.solve(t)
         u2 = torch.empty_like(t)
@@ -129,3 +140,21 @@ def test_split_form_tail(torch_cuda, dtype):
         assert torch.equal(u1, u2)
     ref = OS.spectral_tail(rho.astype(np.float32 if dtype == "f32" else np.float64))
     assert eta.value == pytest.approx(ref, rel=2e-3 if dtype == "f32" else 1e-6, abs=1e-12)
+
+
+def test_warp_form_batched(torch_cuda):
+    """Three densities through one grouped launch sequence in the warp form: each equals
+    its single solve bit for bit, and the plan reports no timed-out wait."""
+    torch = torch_cuda
+    from paper_1612_01799_gb300 import Plan, solve_batched
+    N, L = 256, 10.0
+    rhos = [torch.from_numpy(D.config_aniso4(N=N, seed=40 + i).gaussians.sample(N, L).astype(np.float32)).cuda()
+            for i in range(3)]
+    with Plan(N, L, 1e-6, "f32", max_batch=3) as p:
+        p.z_form = 2
+        outs = [torch.empty_like(r) for r in rhos]
+        solve_batched([p] * 3, rhos, outs)
+        torch.cuda.synchronize()
+        for r, o in zip(rhos, outs):
+            assert torch.equal(p.solve(r), o)
+        p.last_status()
