@@ -31,14 +31,19 @@
 // Shared memory (one CTA = one tile of 16 columns x 1 ky x the N input rows, 8 warps):
 //   B   32 KB: the TMA input tile (256 rows x 128 B, 128-byte swizzle), then the tile's
 //       symbol rows (272 x 64 B, 64-byte swizzle), then the next tile's input;
-//   XO  64 KB: warp g owns the 16-byte chunk g ^ (row & 7) of each 128-byte row, for the
-//       exchange (512 slots) and for its outputs (rows z < 256), so the first 32 KB is the
-//       output tile in the TMA store's 128-byte swizzle;
+//   XO  64 KB: 512 rows of 128 B; warp g owns the 16-byte chunk g ^ (row & 7) of every row,
+//       for its exchange slots (all 512 rows) and for its outputs (rows z < 256), so the
+//       first 32 KB is the output tile in the TMA store's 128-byte swizzle;
 //   T   4 KB: twiddles W_512^{q k1} as T[k1][q];
 //   three mbarriers (input, symbol, XO free) and three arrival counters.
 // The last warp to finish with B (input read, symbol read) issues the next TMA load into
 // it; the last warp to write its outputs issues the TMA store of the tile and, once the
-// store has read XO, frees XO for the next tile.  All waits are bounded (tma.cuh).
+// store has read XO, frees XO for the next tile's exchange.  All waits are bounded.
+//
+// Exchange slots: reader lane l takes position p from row 16 l + (p ^ (l & 7)).  The bank
+// group (row & 7, XOR the warp) differs across the eight lanes of every quarter-warp
+// access in both directions, and both addresses are a lane constant XOR a compile-time
+// constant (bits 4-9) plus a compile-time offset.
 #pragma once
 #include "tma.cuh"
 
@@ -104,16 +109,21 @@ __device__ __forceinline__ void zw_f1_adj(CV *v) {
 }
 
 __device__ __forceinline__ int zw_kappa0(int j) { return j < 8 ? 2 * j : 2 * (j - 8) + 1; }
-// Exchange slot of (reader lane l, position p); conflict-free for both access patterns.
-__device__ __forceinline__ int zw_slot(int l, int p) { return l * 16 + ((p + l) & 15); }
 // Byte offset of row `row` of warp g in a 128-byte-swizzled region.
 __device__ __forceinline__ int zw_sw128(int row, int g) { return row * 128 + ((g ^ (row & 7)) << 4); }
 
-__device__ __forceinline__ void zw_st(unsigned char *p, CV x) {
-    *reinterpret_cast<float4 *>(p) = make_float4(x.re.x, x.re.y, x.im.x, x.im.y);
+// Exchange slots by shared-memory address (layout re.x, re.y, im.x, im.y).
+__device__ __forceinline__ void zw_sts(uint32_t a, CV x) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x.re.x), "f"(x.re.y), "f"(x.im.x),
+                 "f"(x.im.y)
+                 : "memory");
 }
-__device__ __forceinline__ CV zw_ld(const unsigned char *p) {
-    const float4 f = *reinterpret_cast<const float4 *>(p);
+__device__ __forceinline__ CV zw_lds(uint32_t a) {
+    float4 f;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(f.x), "=f"(f.y), "=f"(f.z), "=f"(f.w)
+                 : "r"(a)
+                 : "memory");
     return {f2(f.x, f.y), f2(f.z, f.w)};
 }
 __device__ __forceinline__ CV zw_shfl16(CV x) {
@@ -183,12 +193,22 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
 
-    // Per-lane constants: F3 twiddle sgn W_32^{q'}, twiddle-table bases of the registers
-    // in K (k1 = kappa0 + 8 s) and outside K (k1 = kappa0 - 8 s), input sign.
+    // Per-lane constants.  F3 twiddle sgn W_32^{q'}; twiddle-table bases of the registers
+    // in K (k1 = kappa0 + 8 s) and outside K (k1 = kappa0 - 8 s); input/output sign.
     float2 tw32 = tw[16 * qp];
     if (s) tw32 = f2(-tw32.x, -tw32.y);
-    const float2 *TK = T + q + 256 * s, *TN = T + q - 256 * s;
+    const int tkb = q + 256 * s, tnb = q - 256 * s;
     const float sg = s ? -1.f : 1.f;
+    // Exchange: writer base (position qp; row 16 l + (qp ^ (l & 7)) for reader
+    // l = kappa0 + 8 s + 16 t) and reader base (reader q; row 16 q + (p ^ (q & 7))).
+    const uint32_t aw = smem_addr(xo) + 16384 * s + 128 * qp + 16 * (g ^ (qp & 7));
+    const uint32_t ar = smem_addr(xo) + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
+    // Input/output rows q + 32 r of this warp's 16-byte chunk.
+    const int io = zw_sw128(q, g);
+    // Symbol rows: this lane holds kz = kb + 32 k2 (k2 < 8) and 2N - kb - 32 k2 (k2 >= 8).
+    const int kb = q;
+    const int sym_lo = 64 * kb + ((8 * g) ^ (((kb >> 1) & 3) << 4));
+    const int sym_hi = 64 * (L - kb) + ((8 * g) ^ ((((L - kb) >> 1) & 3) << 4));
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
@@ -201,7 +221,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) {
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const float4 f = *reinterpret_cast<const float4 *>(Bb + zw_sw128(q + 32 * r, g));
+                const float4 f = *reinterpret_cast<const float4 *>(Bb + io + 4096 * r);
                 v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
                 if (r & 1) v[r] = {f2mul(v[r].re, f2(sg, sg)), f2mul(v[r].im, f2(sg, sg))};
             }
@@ -210,10 +230,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) {
             zw_f1(v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const bool inK = (j & 4) == 0;
-                v[j] = zw_twmul<-1>(v[j], (inK ? TK : TN)[32 * zw_kappa0(j)]);
-            }
+            for (int j = 0; j < 16; ++j) v[j] = zw_twmul<-1>(v[j], T[((j & 4) ? tnb : tkb) + 32 * zw_kappa0(j)]);
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
                 if (j & 4) continue;
@@ -223,23 +240,21 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
                 v[j + 4] = zw_twmul<-1>(csub(a, rcv), tw32);
             }
         }
-        if (!mbar_wait(bar + 2, ph, status)) return;
+        if (!mbar_wait(bar + 2, ph, status)) return;  // the previous tile's store has read XO
         if (valid) {
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
                 if (j & 4) continue;
+                const int k0 = zw_kappa0(j);
 #pragma unroll
-                for (int tt = 0; tt < 2; ++tt) {
-                    const int l = (zw_kappa0(j) ^ (8 * s)) + 16 * tt;
-                    zw_st(xo + zw_sw128(zw_slot(l, qp), g), v[j + 4 * tt]);
-                }
+                for (int tt = 0; tt < 2; ++tt) zw_sts((aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt, v[j + 4 * tt]);
             }
         }
         __syncwarp();
         if (valid) {
 #pragma unroll
-            for (int p = 0; p < 16; ++p) v[p] = zw_ld(xo + zw_sw128(zw_slot(q, p), g));
-            dft<16, -1>(v);  // v[k2] = X[q + 32 k2]
+            for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (144 * (p & 7))) + 1024 * (p >> 3));
+            dft<16, -1>(v);  // v[k2] = X[kb + 32 k2]
         }
         if constexpr (TAIL) {
             constexpr int SHELL = N - N / 8;
@@ -249,8 +264,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
                 const float w1 = col + 1 > N ? 0.f : (col + 1 == N) ? 1.f : 2.f;
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2) {
-                    const int kf = q + 32 * k2;
-                    const int kz = kf <= N ? kf : L - kf;
+                    const int kz = k2 < 8 ? kb + 32 * k2 : L - kb - 32 * k2;
                     const float2 en = cenergy(v[k2]);
                     const bool sh = kz >= SHELL || kya >= SHELL;
                     etot += w0 * en.x + w1 * en.y;
@@ -272,28 +286,24 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) {
 #pragma unroll
             for (int k2 = 0; k2 < 16; ++k2) {
-                const int kz = k2 < 8 ? q + 32 * k2 : L - q - 32 * k2;
-                const int A = kz * 64 + 8 * g;
-                const float2 sy = *reinterpret_cast<const float2 *>(Bb + (A ^ (((A >> 7) & 3) << 4)));
-                v[k2] = cscale2(v[k2], sy);
+                const int off = k2 < 8 ? sym_lo + 2048 * k2 : sym_hi - 2048 * k2;
+                v[k2] = cscale2(v[k2], *reinterpret_cast<const float2 *>(Bb + off));
             }
         }
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
         if (valid) {
             dft<16, 1>(v);
 #pragma unroll
-            for (int p = 0; p < 16; ++p) zw_st(xo + zw_sw128(zw_slot(q, p), g), v[p]);
+            for (int p = 0; p < 16; ++p) zw_sts((ar ^ (144 * (p & 7))) + 1024 * (p >> 3), v[p]);
         }
         __syncwarp();
         if (valid) {
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
                 if (j & 4) continue;
+                const int k0 = zw_kappa0(j);
 #pragma unroll
-                for (int tt = 0; tt < 2; ++tt) {
-                    const int l = (zw_kappa0(j) ^ (8 * s)) + 16 * tt;
-                    v[j + 4 * tt] = zw_ld(xo + zw_sw128(zw_slot(l, qp), g));
-                }
+                for (int tt = 0; tt < 2; ++tt) v[j + 4 * tt] = zw_lds((aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt);
             }
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
@@ -304,10 +314,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
                 v[j + 4] = zw_shfl16(csub(a, b));
             }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const bool inK = (j & 4) == 0;
-                v[j] = zw_twmul<1>(v[j], (inK ? TK : TN)[32 * zw_kappa0(j)]);
-            }
+            for (int j = 0; j < 16; ++j) v[j] = zw_twmul<1>(v[j], T[((j & 4) ? tnb : tkb) + 32 * zw_kappa0(j)]);
             zw_f1_adj(v);
         }
         __syncwarp();  // every lane's exchange reads are done: the slots take the outputs
@@ -316,7 +323,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             for (int r = 0; r < 8; ++r) {
                 CV x = v[r];
                 if (r & 1) x = {f2mul(x.re, f2(sg, sg)), f2mul(x.im, f2(sg, sg))};
-                *reinterpret_cast<float4 *>(xo + zw_sw128(q + 32 * r, g)) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+                *reinterpret_cast<float4 *>(xo + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
             }
         }
         fence_proxy_async();
