@@ -279,10 +279,21 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
     const long long r0 = (long long)blockIdx.x * TR;
     const int nr = (int)min((long long)TR, (long long)nrows - r0);
     const T2 *src = in + r0 * Px;
-    for (int e = t; e < nr * (N + 1); e += NT) {
-        const int r = e / (N + 1), k = e - r * (N + 1);
-        const T2 f = __ldg(src + (long long)r * Px + k);
-        sm[k * SP + r] = C{f.x, f.y};
+    // Loads in batches of up to 16 per thread, each batch issued before its stores.
+    constexpr int NI = (TR * (N + 1) + NT - 1) / NT, NB = 16;
+#pragma unroll
+    for (int i0 = 0; i0 < NI; i0 += NB) {
+        T2 f[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int e = t + (i0 + i) * NT;
+            if (i0 + i < NI && e < nr * (N + 1)) f[i] = __ldg(src + (long long)(e / (N + 1)) * Px + e % (N + 1));
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int e = t + (i0 + i) * NT;
+            if (i0 + i < NI && e < nr * (N + 1)) sm[(e % (N + 1)) * SP + e / (N + 1)] = C{f[i].x, f[i].y};
+        }
     }
     __syncthreads();
     // Y_k, k = 0..N (Y_0, Y_N real) -> C_k = Ev_k + i Od_k with Ev_k = Y_k + conj Y_{N-k}
@@ -528,15 +539,15 @@ cudaError_t encode_n(DevicePlan &p) {
     using L1 = TmaLayout<Real, L, 1>;
     using L2 = TmaLayout<Real, L, 2>;
     const cuuint64_t BN = (cuuint64_t)p.max_batch * N;  // z of all densities, stacked
-    GSP_CHECK(encode_3d(&p.tm_y_in, U64, p.w1, p.Px * u, N, BN, rowb, (cuuint64_t)N * rowb,
+    GSP_CHECK(encode_3d(&p.tm_y_in, U64, p.w1, (N + 1) * u, N, BN, rowb, (cuuint64_t)N * rowb,
                         L0::ROWB / 8, L0::RPC, 1));
-    GSP_CHECK(encode_3d(&p.tm_z_in, U64, p.w2, p.Px * u, L, BN, rowb, (cuuint64_t)L * rowb,
+    GSP_CHECK(encode_3d(&p.tm_z_in, U64, p.w2, (N + 1) * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L1::ROWB / 8, 1, L1::RPC));
     const cuuint64_t srow = (cuuint64_t)p.Ps * sizeof(Real);
     GSP_CHECK(encode_3d(&p.tm_z_sym,
                         sizeof(Real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                        p.sym, p.Ps, N + 1, N + 1, srow, (cuuint64_t)(N + 1) * srow, L1::TC, 1, L1::SRC));
-    GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, p.Px * u, L, BN, rowb, (cuuint64_t)L * rowb,
+                        p.sym, N + 1, N + 1, N + 1, srow, (cuuint64_t)(N + 1) * srow, L1::TC, 1, L1::SRC));
+    GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, (N + 1) * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L2::ROWB / 8, L2::RPC, 1));
     if constexpr (zwarp_form<Real, N>()) {
         // Columns kx > N lie outside these maps: loads read zeros there, stores skip them.
