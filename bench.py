@@ -32,6 +32,7 @@ METRIC = "grid pts/s per solve (N^3/s) FP32 vs FP64 at stated rel-L2 err; % HBM 
 UNIT = "pts/s"
 PASSES = ["x_forward", "y_forward", "z_fwd_symbol_inv", "y_inverse", "x_inverse"]
 Z_FORMS = ["direct", "split", "warp"]
+Y_FORMS = ["block", "warp"]
 Z_KERNELS = ["k_z_symbol", "k_z_split", "k_z_warp"]
 KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_inverse"]
 
@@ -323,7 +324,7 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
-        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form,
+        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form, "y_form": plan.y_form,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
                           "rho": rho_t, "out": out_t}
 
@@ -351,6 +352,8 @@ def run_ours(args):
         gbs = [bytes32[i] / (r32["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
         names = list(KERNEL_NAMES)
         names[2] = Z_KERNELS[r32["z_form"]]
+        if r32["y_form"] == 1:
+            names[1], names[3] = "k_y_warp<fwd>", "k_y_warp<inv>"
         src_hash = kernel_source_hash()
         traffic = NCU_TRAFFIC.get((src_hash, names[dom], N))
         r64 = results["f64"]
@@ -376,6 +379,7 @@ def run_ours(args):
             "gpu_launches": 5 * r32["steps"],
             "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
                        "z_pass_f64": Z_FORMS[results["f64"]["z_form"]],
+                       "y_passes_f32": Y_FORMS[r32["y_form"]], "y_passes_f64": Y_FORMS[results["f64"]["y_form"]],
                        "how": "timed at plan creation, cached per (device, N, dtype)"},
             "clocks": r32["clocks"],
         }

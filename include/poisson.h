@@ -176,6 +176,9 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       2 = one warp per column pair: 16-point DFTs in registers, a radix-2 step between
  *           lane pairs and one warp-local shared-memory exchange per direction
  *           (POISSON_F32, N = 256).
+ *   POISSON_KNOB_Y_FORM  form of the two y passes (Sec. 2, the zero-padded transforms
+ *       along the middle axis): 0 = a column pair spread over the threads of a block;
+ *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, N = 256).
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that
@@ -183,6 +186,7 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  * flight.
  */
 #define POISSON_KNOB_Z_FORM 0
+#define POISSON_KNOB_Y_FORM 1
 int poisson_plan_get_knob(poisson_plan p, int knob, int *value);
 int poisson_plan_set_knob(poisson_plan p, int knob, int value);
 

@@ -64,6 +64,7 @@ class PoissonError(RuntimeError):
 
 
 KNOB_Z_FORM = 0
+KNOB_Y_FORM = 1
 
 
 def load():

@@ -130,6 +130,19 @@ class Plan:
     def z_form(self, value):
         _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_Z_FORM, int(value)), "poisson_plan_set_knob")
 
+    @property
+    def y_form(self):
+        """Form of the y passes in use (chosen by timing at plan creation): 0 a column pair
+        spread over a block, 1 one warp per column pair."""
+        v = ctypes.c_int()
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_Y_FORM, ctypes.byref(v)),
+                   "poisson_plan_get_knob")
+        return v.value
+
+    @y_form.setter
+    def y_form(self, value):
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_Y_FORM, int(value)), "poisson_plan_set_knob")
+
     def gauss_sum(self):
         n = self.info()["n_terms"]
         tau, w = np.empty(n), np.empty(n)

@@ -25,6 +25,11 @@ cudaError_t encode_maps_f32(DevicePlan &);
 cudaError_t encode_maps_f64(DevicePlan &);
 cudaError_t z_pass_f32(const DevicePlan &, cudaStream_t);
 cudaError_t z_pass_f64(const DevicePlan &, cudaStream_t);
+cudaError_t y_passes_f32(const DevicePlan &, cudaStream_t);
+cudaError_t y_passes_f64(const DevicePlan &, cudaStream_t);
+cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? y_passes_f32(p, s) : y_passes_f64(p, s);
+}
 
 cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s) {
     return p.dtype == POISSON_F32 ? z_pass_f32(p, s) : z_pass_f64(p, s);
@@ -86,19 +91,19 @@ cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const dou
 // ---- autotuning of kernel variants --------------------------------------------------------
 // Decisions per (device, N, dtype), made by the first plan of that shape and reused.
 struct TuneEntry {
-    int dev, N, dtype, zform;
+    int dev, N, dtype, zform, yform;
 };
 static std::vector<TuneEntry> g_tune;
 static std::mutex g_tune_mutex;
 
-// Mean time (ms) of `reps` z passes of one density after one warm-up pass.
-static cudaError_t time_z(const DevicePlan &p, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps,
-                          float *ms) {
+// Mean time (ms) of `reps` runs of `run` (one density) after one warm-up run.
+template <class Run>
+static cudaError_t time_runs(Run &&run, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps, float *ms) {
     cudaError_t e;
-    if ((e = launch_z_pass(p, s)) != cudaSuccess) return e;
+    if ((e = run()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(a, s)) != cudaSuccess) return e;
     for (int i = 0; i < reps; ++i)
-        if ((e = launch_z_pass(p, s)) != cudaSuccess) return e;
+        if ((e = run()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(b, s)) != cudaSuccess) return e;
     if ((e = cudaEventSynchronize(b)) != cudaSuccess) return e;
     if ((e = cudaEventElapsedTime(ms, a, b)) != cudaSuccess) return e;
@@ -106,18 +111,43 @@ static cudaError_t time_z(const DevicePlan &p, cudaStream_t s, cudaEvent_t a, cu
     return cudaSuccess;
 }
 
-// Choose p.zform: the cached decision for this shape, else the fastest form that exists,
-// timed on p's zeroed workspace.  Only w3 is written, and every solve writes w3 before
-// reading it.
+// Index of the fastest set bit of `forms` (form v timed with *field = v), or an error.
+template <class Run>
+static cudaError_t pick_form(int forms, int *field, Run &&run, cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
+    int best = 0;
+    float best_ms = 0.f;
+    for (int v = 0; v < 3; ++v) {
+        if (!(forms >> v & 1)) continue;
+        float ms = 0.f;
+        *field = v;
+        cudaError_t e = time_runs(run, s, a, b, 3, &ms);
+        if (e != cudaSuccess) {
+            *field = 0;
+            return e;
+        }
+        if (v == 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    *field = best;
+    return cudaSuccess;
+}
+
+// Choose p.zform and p.yform: the cached decision for this shape, else the fastest forms
+// that exist, timed on p's zeroed workspace.  The z pass writes only w3, the y passes w2
+// and w1, and every solve writes each of them before reading it.
 static cudaError_t autotune(DevicePlan &p, int dev) {
     p.zform = 0;
-    const int forms = z_forms(p.N, p.dtype);
-    if (forms == 1) return cudaSuccess;
+    p.yform = 0;
+    const int zf = z_forms(p.N, p.dtype), yf = y_forms(p.N, p.dtype);
+    if (zf == 1 && yf == 1) return cudaSuccess;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (const TuneEntry &t : g_tune)
             if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
                 p.zform = t.zform;
+                p.yform = t.yform;
                 return cudaSuccess;
             }
     }
@@ -126,33 +156,23 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    int best = 0;
-    float best_ms = 0.f;
-    for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
-        if (!(forms >> v & 1)) continue;
-        float ms = 0.f;
-        p.zform = v;
-        e = time_z(p, s, a, b, 3, &ms);
-        if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
-            best = v;
-            best_ms = ms;
-        }
-    }
+    if (e == cudaSuccess) e = pick_form(zf, &p.zform, [&] { return launch_z_pass(p, s); }, s, a, b);
+    if (e == cudaSuccess) e = pick_form(yf, &p.yform, [&] { return launch_y_passes(p, s); }, s, a, b);
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) {
-        p.zform = 0;
+        p.zform = p.yform = 0;
         return e;
     }
-    p.zform = best;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const TuneEntry &t : g_tune)  // another thread may have decided meanwhile
         if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
             p.zform = t.zform;
+            p.yform = t.yform;
             return cudaSuccess;
         }
-    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform});
+    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform, p.yform});
     return cudaSuccess;
 }
 }  // namespace gsp
@@ -328,16 +348,21 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
 
 extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
     if (!p || !value) return POISSON_ERR_ARG;
-    if (knob != POISSON_KNOB_Z_FORM) return POISSON_ERR_ARG;
-    *value = p->dp.zform;
+    if (knob == POISSON_KNOB_Z_FORM) *value = p->dp.zform;
+    else if (knob == POISSON_KNOB_Y_FORM) *value = p->dp.yform;
+    else return POISSON_ERR_ARG;
     return POISSON_OK;
 }
 
 extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     if (!p) return POISSON_ERR_ARG;
-    if (knob != POISSON_KNOB_Z_FORM || value < 0 || value > 2) return POISSON_ERR_ARG;
-    if (!(gsp::z_forms(p->dp.N, p->dp.dtype) >> value & 1)) return POISSON_ERR_UNSUPPORTED;
-    p->dp.zform = value;
+    if ((knob != POISSON_KNOB_Z_FORM && knob != POISSON_KNOB_Y_FORM) || value < 0 || value > 2)
+        return POISSON_ERR_ARG;
+    const bool z = knob == POISSON_KNOB_Z_FORM;
+    if (!z && value > 1) return POISSON_ERR_ARG;
+    const int forms = z ? gsp::z_forms(p->dp.N, p->dp.dtype) : gsp::y_forms(p->dp.N, p->dp.dtype);
+    if (!(forms >> value & 1)) return POISSON_ERR_UNSUPPORTED;
+    (z ? p->dp.zform : p->dp.yform) = value;
     return POISSON_OK;
 }
 

@@ -439,6 +439,48 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
     return cudaGetLastError();
 }
 
+// The y passes (K2 forward, K4 inverse) of B densities in the form p.yform selects: 0 the
+// block form (k_col_tma), 1 the warp form (k_y_warp, ywarp_form); an absent form runs as 0.
+template <typename Real, int N> constexpr bool ywarp_form() { return std::is_same<Real, float>::value && N == YWarp::N; }
+
+template <typename Real, int N>
+cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
+    using T2 = Cx2<Real>;
+    using TwC = typename TwOf<typename Types<Real>::CC>::T;
+    constexpr int L = 2 * N;
+    const int ncols = N + 1;
+    if constexpr (ywarp_form<Real, N>()) {
+        if (p.yform == 1) {
+            const int ntx = (ncols + YWarp::TC - 1) / YWarp::TC, nt = ntx * B * N;
+            auto k = fwd ? k_y_warp<true> : k_y_warp<false>;
+            const int smem = fwd ? YWarp::SMEM_F : YWarp::SMEM_I;
+            GSP_CHECK(set_smem(k, smem));
+            k<<<persistent_blocks(k, YWarp::NT, smem, nt), YWarp::NT, smem, s>>>(
+                fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1, static_cast<const float2 *>(p.tw), ntx, nt,
+                ncols, p.status);
+            return cudaGetLastError();
+        }
+    }
+    const TwC *twc = static_cast<const TwC *>(p.twc);
+    const int Px = p.Px;
+    if (fwd) {
+        using L0 = TmaLayout<Real, L, 0>;
+        const int ntx0 = (ncols + L0::TC - 1) / L0::TC, nt = ntx0 * B * N;
+        auto k = k_col_tma<Real, L, 0>;
+        GSP_CHECK(set_smem(k, L0::SMEM));
+        k<<<persistent_blocks(k, tma_threads<Real, L, 0>(), L0::SMEM, nt), tma_threads<Real, L, 0>(), L0::SMEM, s>>>(
+            p.tm_y_in, static_cast<T2 *>(p.w2), twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status);
+    } else {
+        using L2 = TmaLayout<Real, L, 2>;
+        const int ntx2 = (ncols + L2::TC - 1) / L2::TC, nt = ntx2 * B * N;
+        auto k = k_col_tma<Real, L, 2>;
+        GSP_CHECK(set_smem(k, L2::SMEM));
+        k<<<persistent_blocks(k, tma_threads<Real, L, 2>(), L2::SMEM, nt), tma_threads<Real, L, 2>(), L2::SMEM, s>>>(
+            p.tm_yi_in, static_cast<T2 *>(p.w1), twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status);
+    }
+    return cudaGetLastError();
+}
+
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
                     cudaEvent_t *ev, double *tail) {
@@ -454,9 +496,6 @@ cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     const int nrows = B * N * N;
     const int ncols = N + 1;
     const dim3 grow((nrows + TR - 1) / TR);
-    using L0 = TmaLayout<Real, L, 0>;
-    using L2 = TmaLayout<Real, L, 2>;
-    const int ntx0 = (ncols + L0::TC - 1) / L0::TC, ntx2 = (ncols + L2::TC - 1) / L2::TC;
 
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
     GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
@@ -464,27 +503,13 @@ cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     GSP_CHECK(cudaGetLastError());
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
-    {
-        auto k = k_col_tma<Real, L, 0>;
-        GSP_CHECK(set_smem(k, L0::SMEM));
-        const int nt = ntx0 * B * N;
-        k<<<persistent_blocks(k, tma_threads<Real, L, 0>(), L0::SMEM, nt), tma_threads<Real, L, 0>(),
-            L0::SMEM, s>>>(p.tm_y_in, w2, twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status);
-        GSP_CHECK(cudaGetLastError());
-    }
+    GSP_CHECK((y_pass<Real, N>(p, B, s, true)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
     GSP_CHECK((z_pass<Real, N>(p, B, s, tail)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
 
-    {
-        auto k = k_col_tma<Real, L, 2>;
-        GSP_CHECK(set_smem(k, L2::SMEM));
-        const int nt = ntx2 * B * N;
-        k<<<persistent_blocks(k, tma_threads<Real, L, 2>(), L2::SMEM, nt), tma_threads<Real, L, 2>(),
-            L2::SMEM, s>>>(p.tm_yi_in, w1, twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status);
-        GSP_CHECK(cudaGetLastError());
-    }
+    GSP_CHECK((y_pass<Real, N>(p, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
     GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
@@ -549,6 +574,15 @@ cudaError_t encode_n(DevicePlan &p) {
                         p.sym, N + 1, N + 1, N + 1, srow, (cuuint64_t)(N + 1) * srow, L1::TC, 1, L1::SRC));
     GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, (N + 1) * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L2::ROWB / 8, L2::RPC, 1));
+    if constexpr (ywarp_form<Real, N>()) {
+        // 256-row boxes of w1, w2, w3 (16 columns x y or ky rows x 1 plane), 128-byte swizzle.
+        GSP_CHECK(encode_3d(&p.tm_yw1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, YWarp::TC, 256, 1,
+                            CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_yw2, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp::TC, 256, 1,
+                            CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp::TC, 256, 1,
+                            CU_TENSOR_MAP_SWIZZLE_128B));
+    }
     if constexpr (zwarp_form<Real, N>()) {
         // Columns kx > N lie outside these maps: loads read zeros there, stores skip them.
         GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp::TC, 1, N,
@@ -573,6 +607,7 @@ cudaError_t encode_n(DevicePlan &p) {
     EXT template cudaError_t solve_n<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int, \
                                               cudaStream_t, cudaEvent_t *, double *);                      \
     EXT template cudaError_t z_pass<Real, n>(const DevicePlan &, int, cudaStream_t, double *);             \
+    EXT template cudaError_t y_pass<Real, n>(const DevicePlan &, int, cudaStream_t, bool);                 \
     EXT template cudaError_t encode_n<Real, n>(DevicePlan &);
 
 template <typename Real>
@@ -595,6 +630,21 @@ cudaError_t z_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
 #define GSP_CASE(n) \
     case n:         \
         return z_pass<Real, n>(p, 1, s, nullptr);
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Real>
+cudaError_t y_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    switch (p.N) {
+#define GSP_CASE(n)                                                   \
+    case n: {                                                         \
+        cudaError_t e = y_pass<Real, n>(p, 1, s, true);               \
+        return e != cudaSuccess ? e : y_pass<Real, n>(p, 1, s, false); \
+    }
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE
         default:

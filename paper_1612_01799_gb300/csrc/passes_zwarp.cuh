@@ -131,6 +131,86 @@ __device__ __forceinline__ CV zw_shfl16(CV x) {
             f2(__shfl_xor_sync(0xffffffffu, x.im.x, 16), __shfl_xor_sync(0xffffffffu, x.im.y, 16))};
 }
 
+
+// Per-lane constants of the warp-form transform (lane q = q' + 16 s of warp g, exchange
+// region at shared address xo with warp g owning chunk g ^ (row & 7) of its 512 rows).
+struct ZwLane {
+    float2 tw32;   // F3 twiddle sgn W_32^{q'} (sgn = -1 on the upper half-warp)
+    int tkb, tnb;  // twiddle-table bases of the registers in K (k1 = kappa0 + 8 s) and outside
+    float sg;      // sign of the odd inputs / outputs of the upper half-warp
+    uint32_t aw;   // exchange writer base: position q' of reader l = kappa0 + 8 s + 16 t
+    uint32_t ar;   // exchange reader base: reader q, row 16 q + (p ^ (q & 7))
+};
+__device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_t xo, int g, int q) {
+    const int s = q >> 4, qp = q & 15;
+    ZwLane z;
+    z.tw32 = tw[16 * qp];
+    if (s) z.tw32 = f2(-z.tw32.x, -z.tw32.y);
+    z.tkb = q + 256 * s;
+    z.tnb = q - 256 * s;
+    z.sg = s ? -1.f : 1.f;
+    z.aw = xo + 16384 * s + 128 * qp + 16 * (g ^ (qp & 7));
+    z.ar = xo + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
+    return z;
+}
+__device__ __forceinline__ CV zw_sign(CV x, float sg) { return {f2mul(x.re, f2(sg, sg)), f2mul(x.im, f2(sg, sg))}; }
+
+// F1 (inputs v[0..7], odd ones already signed), F2 and F3 with its twiddle.
+__device__ __forceinline__ void zw_front(CV *v, const ZwLane &z, const float2 *T) {
+    zw_f1(v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = zw_twmul<-1>(v[j], T[((j & 4) ? z.tnb : z.tkb) + 32 * zw_kappa0(j)]);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        if (j & 4) continue;
+        const CV rcv = zw_shfl16(v[j + 4]);
+        const CV a = v[j];
+        v[j] = cadd(a, rcv);
+        v[j + 4] = zw_twmul<-1>(csub(a, rcv), z.tw32);
+    }
+}
+// F5: write the values this lane holds as writer, gather its 16 as reader.
+__device__ __forceinline__ void zw_exchange(CV *v, const ZwLane &z) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        if (j & 4) continue;
+        const int k0 = zw_kappa0(j);
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt) zw_sts((z.aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt, v[j + 4 * tt]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 16; ++p) v[p] = zw_lds((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3));
+}
+// Adjoint of F5.
+__device__ __forceinline__ void zw_exchange_adj(CV *v, const ZwLane &z) {
+#pragma unroll
+    for (int p = 0; p < 16; ++p) zw_sts((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3), v[p]);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        if (j & 4) continue;
+        const int k0 = zw_kappa0(j);
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt) v[j + 4 * tt] = zw_lds((z.aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt);
+    }
+}
+// Adjoints of F3 (with its twiddle), F2 and F1: the outputs r < 8 in v[0..7], odd ones
+// still to be signed.
+__device__ __forceinline__ void zw_back(CV *v, const ZwLane &z, const float2 *T) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        if (j & 4) continue;
+        const CV b = zw_twmul<1>(v[j + 4], z.tw32);
+        const CV a = v[j];
+        v[j] = cadd(a, b);
+        v[j + 4] = zw_shfl16(csub(a, b));
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = zw_twmul<1>(v[j], T[((j & 4) ? z.tnb : z.tkb) + 32 * zw_kappa0(j)]);
+    zw_f1_adj(v);
+}
+
 // Tile t = (tx, ky, b): tx the 16-column block, consecutive tiles take ky and its mirror
 // 2N - ky (same symbol rows), b the density.  With TAIL the forward spectrum's shell and
 // total energies are added to tail[2 b], tail[2 b + 1] (as in k_z_symbol_tma).
@@ -193,16 +273,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
 
-    // Per-lane constants.  F3 twiddle sgn W_32^{q'}; twiddle-table bases of the registers
-    // in K (k1 = kappa0 + 8 s) and outside K (k1 = kappa0 - 8 s); input/output sign.
-    float2 tw32 = tw[16 * qp];
-    if (s) tw32 = f2(-tw32.x, -tw32.y);
-    const int tkb = q + 256 * s, tnb = q - 256 * s;
-    const float sg = s ? -1.f : 1.f;
-    // Exchange: writer base (position qp; row 16 l + (qp ^ (l & 7)) for reader
-    // l = kappa0 + 8 s + 16 t) and reader base (reader q; row 16 q + (p ^ (q & 7))).
-    const uint32_t aw = smem_addr(xo) + 16384 * s + 128 * qp + 16 * (g ^ (qp & 7));
-    const uint32_t ar = smem_addr(xo) + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
+    const ZwLane zl = zw_lane(tw, smem_addr(xo), g, q);
     // Input/output rows q + 32 r of this warp's 16-byte chunk.
     const int io = zw_sw128(q, g);
     // Symbol rows: this lane holds kz = kb + 32 k2 (k2 < 8) and 2N - kb - 32 k2 (k2 >= 8).
@@ -223,37 +294,14 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             for (int r = 0; r < 8; ++r) {
                 const float4 f = *reinterpret_cast<const float4 *>(Bb + io + 4096 * r);
                 v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
-                if (r & 1) v[r] = {f2mul(v[r].re, f2(sg, sg)), f2mul(v[r].im, f2(sg, sg))};
+                if (r & 1) v[r] = zw_sign(v[r], zl.sg);
             }
         }
         if (last_arrival(0)) issue_sym(t);
-        if (valid) {
-            zw_f1(v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = zw_twmul<-1>(v[j], T[((j & 4) ? tnb : tkb) + 32 * zw_kappa0(j)]);
-#pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                if (j & 4) continue;
-                const CV rcv = zw_shfl16(v[j + 4]);
-                const CV a = v[j];
-                v[j] = cadd(a, rcv);
-                v[j + 4] = zw_twmul<-1>(csub(a, rcv), tw32);
-            }
-        }
+        if (valid) zw_front(v, zl, T);
         if (!mbar_wait(bar + 2, ph, status)) return;  // the previous tile's store has read XO
         if (valid) {
-#pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                if (j & 4) continue;
-                const int k0 = zw_kappa0(j);
-#pragma unroll
-                for (int tt = 0; tt < 2; ++tt) zw_sts((aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt, v[j + 4 * tt]);
-            }
-        }
-        __syncwarp();
-        if (valid) {
-#pragma unroll
-            for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (144 * (p & 7))) + 1024 * (p >> 3));
+            zw_exchange(v, zl);
             dft<16, -1>(v);  // v[k2] = X[kb + 32 k2]
         }
         if constexpr (TAIL) {
@@ -293,36 +341,15 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
         if (valid) {
             dft<16, 1>(v);
-#pragma unroll
-            for (int p = 0; p < 16; ++p) zw_sts((ar ^ (144 * (p & 7))) + 1024 * (p >> 3), v[p]);
-        }
-        __syncwarp();
-        if (valid) {
-#pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                if (j & 4) continue;
-                const int k0 = zw_kappa0(j);
-#pragma unroll
-                for (int tt = 0; tt < 2; ++tt) v[j + 4 * tt] = zw_lds((aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt);
-            }
-#pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                if (j & 4) continue;
-                const CV b = zw_twmul<1>(v[j + 4], tw32);
-                const CV a = v[j];
-                v[j] = cadd(a, b);
-                v[j + 4] = zw_shfl16(csub(a, b));
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = zw_twmul<1>(v[j], T[((j & 4) ? tnb : tkb) + 32 * zw_kappa0(j)]);
-            zw_f1_adj(v);
+            zw_exchange_adj(v, zl);
+            zw_back(v, zl, T);
         }
         __syncwarp();  // every lane's exchange reads are done: the slots take the outputs
         if (valid) {
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 CV x = v[r];
-                if (r & 1) x = {f2mul(x.re, f2(sg, sg)), f2mul(x.im, f2(sg, sg))};
+                if (r & 1) x = zw_sign(x, zl.sg);
                 *reinterpret_cast<float4 *>(xo + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
             }
         }
@@ -333,6 +360,143 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             bulk_wait_read0();
             stored = true;
             mbar_arrive(bar + 2);
+        }
+    }
+    if (stored) bulk_wait0();
+}
+
+}  // namespace gsp
+
+namespace gsp {
+
+// ---- K2 / K4, warp form (FP32, N = 256) -------------------------------------------------
+// The y passes with the transform halves of k_z_warp: the forward half (F1..F6) alone for
+// the y forward (N input rows, all 2N output rows kept), the adjoint half alone for the
+// y inverse (2N input rows, rows y < N kept).  Tile t = (tx, zz): 16 columns kx, plane
+// zz = b N + z.  As in k_z_warp, warp g owns the 16-byte chunk g ^ (row & 7) of each
+// 128-byte row of the exchange/output buffer, so a warp exchanges and writes its outputs
+// in its own chunks without waiting for the other warps; the last warp to finish a tile
+// issues the TMA store.
+//   y forward: a 32 KB input buffer (prefetched for the CTA's next tile as soon as every
+//     warp has read its inputs) and a 64 KB exchange/output buffer (2N rows), freed for
+//     the next tile's exchange once the store has read it;
+//   y inverse: one 64 KB buffer for the 2N input rows, the exchange and the N output rows;
+//     the next tile's load follows the store's read of it.
+struct YWarp {
+    static constexpr int L = 512, N = 256, TC = 16, NW = 8, NT = 256;
+    static constexpr int OFF_T = 16 * 32 * 8;                       // after the buffers below
+    static constexpr int F_IN = 0, F_XB = 32768, F_T = F_XB + 65536, F_BAR = F_T + OFF_T;
+    static constexpr int I_XB = 0, I_T = 65536, I_BAR = I_T + OFF_T;
+    static constexpr int SMEM_F = 1024 + F_BAR + 64, SMEM_I = 1024 + I_BAR + 64;
+};
+
+template <bool FWD>
+__global__ void __launch_bounds__(YWarp::NT, 2)
+k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+         const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status) {
+    using Y = YWarp;
+    constexpr int NW = Y::NW;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    unsigned char *inb = base + (FWD ? Y::F_IN : Y::I_XB);
+    unsigned char *xb = base + (FWD ? Y::F_XB : Y::I_XB);
+    float2 *T = reinterpret_cast<float2 *>(base + (FWD ? Y::F_T : Y::I_T));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (FWD ? Y::F_BAR : Y::I_BAR));  // input, buffer free
+    int *cnt = reinterpret_cast<int *>(bar + 2);                                         // inputs read, outputs
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        cnt[0] = cnt[1] = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < 512; i += Y::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    __syncthreads();
+    auto issue_in = [&](int t) {
+        const int tx = t % ntx, zz = t / ntx;
+        mbar_arrive_expect_tx(bar, FWD ? 32768 : 65536);
+        tma_load_3d(inb, &tin, bar, tx * Y::TC, 0, zz);
+        if (!FWD) tma_load_3d(inb + 32768, &tin, bar, tx * Y::TC, 256, zz);
+    };
+    auto last_arrival = [&](int c) {
+        __syncwarp();
+        bool last = false;
+        if (q == 0) {
+            __threadfence_block();
+            last = atomicAdd(cnt + c, 1) % NW == NW - 1;
+            if (last) {
+                __threadfence_block();
+                fence_proxy_async();
+            }
+        }
+        return last;
+    };
+    if (threadIdx.x == 0) {
+        if (FWD) mbar_arrive(bar + 1);  // the exchange/output buffer starts free
+        if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
+    }
+    const ZwLane zl = zw_lane(tw, smem_addr(xb), g, q);
+    const int io = zw_sw128(q, g);
+    bool stored = false;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        const int tx = t % ntx, zz = t / ntx;
+        const bool valid = tx * Y::TC + 2 * g < ncols;
+        const bool more = t + (int)gridDim.x < ntiles;
+        CV v[16];
+        if (!mbar_wait(bar, ph, status)) return;
+        if constexpr (FWD) {
+            if (valid) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const float4 f = *reinterpret_cast<const float4 *>(inb + io + 4096 * r);
+                    v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
+                    if (r & 1) v[r] = zw_sign(v[r], zl.sg);
+                }
+            }
+            if (last_arrival(0) && more) issue_in(t + gridDim.x);
+            if (valid) zw_front(v, zl, T);
+            if (!mbar_wait(bar + 1, ph, status)) return;  // the previous tile's store has read xb
+            if (valid) {
+                zw_exchange(v, zl);
+                dft<16, -1>(v);  // v[k2] = X[q + 32 k2]
+            }
+            __syncwarp();
+            if (valid) {
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2)
+                    *reinterpret_cast<float4 *>(xb + io + 4096 * k2) =
+                        make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
+            }
+        } else {
+            if (valid) {
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) {
+                    const float4 f = *reinterpret_cast<const float4 *>(xb + io + 4096 * k2);
+                    v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
+                }
+                dft<16, 1>(v);
+                __syncwarp();  // every lane has read its inputs: its chunks take exchange slots
+                zw_exchange_adj(v, zl);
+                zw_back(v, zl, T);
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    CV x = v[r];
+                    if (r & 1) x = zw_sign(x, zl.sg);
+                    *reinterpret_cast<float4 *>(xb + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+                }
+            }
+        }
+        fence_proxy_async();
+        if (last_arrival(1)) {
+            tma_store_3d(&tout, xb, tx * Y::TC, 0, zz);
+            if (FWD) tma_store_3d(&tout, xb + 32768, tx * Y::TC, 256, zz);
+            bulk_commit();
+            bulk_wait_read0();
+            stored = true;
+            if (FWD) mbar_arrive(bar + 1);
+            else if (more) issue_in(t + gridDim.x);
         }
     }
     if (stored) bulk_wait0();

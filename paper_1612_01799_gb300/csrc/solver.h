@@ -44,11 +44,15 @@ struct DevicePlan {
     // z pass form: 0 length-2N transforms, 1 even/odd length-N split, 2 warp form (one
     // warp per column pair, FP32, N = 256)
     int zform = 0;
+    // y pass form: 0 block form (a column pair spread over a block), 1 warp form (FP32,
+    // N = 256)
+    int yform = 0;
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers; and of the warp-form z pass (w2 in,
     // symbol, w3 out; 128- and 64-byte swizzled boxes), encoded where that form exists.
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
     CUtensorMap tm_zw_in, tm_zw_sym, tm_zw_out;
+    CUtensorMap tm_yw1, tm_yw2, tm_yw3;  // warp-form y passes: 256-row boxes of w1, w2, w3
 };
 
 constexpr int kStatusTimeoutBit = 1;  // bit of DevicePlan::status set by a timed-out wait
@@ -76,6 +80,13 @@ cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArra
 // bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;
 // bit 2 for FP32 at N = 256.
 int z_forms(int N, int dtype);
+
+// Forms of the y passes that exist for (N, dtype), as a bit mask over DevicePlan::yform:
+// bit 0 always; bit 1 for FP32 at N = 256.
+int y_forms(int N, int dtype);
+
+// The two y passes alone, one density, in the form p.yform selects (for timing the forms).
+cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s);
 
 // The z pass alone, one density, in the form p.zform selects (for timing the forms).
 cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s);
