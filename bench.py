@@ -304,6 +304,10 @@ def run_ours(args):
     for dtype in ("f32", "f64"):
         tol = TOL32 if dtype == "f32" else TOL64
         plan = Plan(N, L_BOX, tol, dtype)
+        if dtype == "f32" and args.z_form is not None:
+            plan.z_form = Z_FORMS.index(args.z_form)
+        if dtype == "f32" and args.y_form is not None:
+            plan.y_form = Y_FORMS.index(args.y_form)
         rho_t = torch.from_numpy(rho64.astype(plan.np_dtype)).to(dev)
         out_t = torch.empty_like(rho_t)
         steps = args.steps if dtype == "f32" else max(3, args.steps // 4)
@@ -380,7 +384,8 @@ def run_ours(args):
             "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
                        "z_pass_f64": Z_FORMS[results["f64"]["z_form"]],
                        "y_passes_f32": Y_FORMS[r32["y_form"]], "y_passes_f64": Y_FORMS[results["f64"]["y_form"]],
-                       "how": "timed at plan creation, cached per (device, N, dtype)"},
+                       "how": ("pinned by --z-form/--y-form" if args.z_form or args.y_form else
+                               "timed at plan creation, cached per (device, N, dtype)")},
             "clocks": r32["clocks"],
         }
         if not args.no_batched:
@@ -411,6 +416,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
+    ap.add_argument("--z-form", choices=Z_FORMS, default=None,
+                    help="pin the FP32 z-pass form (default: the plan's timed choice); for profiling")
+    ap.add_argument("--y-form", choices=Y_FORMS, default=None,
+                    help="pin the FP32 y-pass form (default: the plan's timed choice); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
