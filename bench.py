@@ -131,6 +131,27 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank):
+    """Seed of the density a rank solves: every rank its own density of the same family
+    (independent solves, weak scaling; no data crosses ranks)."""
+    return 2 + rank
+
+
+def max_over_ranks(torch, value, device):
+    """The largest of the ranks' values (every rank gets it): the job's time is its
+    slowest rank's.  A single process returns its own value."""
+    if not torch.distributed.is_available() or not torch.distributed.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, N, seconds):
+    """Whole-job grid points per second: every rank solved N^3 points in `seconds`."""
+    return world * N ** 3 / seconds
+
+
 def cpu_oracle_baseline(N, steps=1):
     """The oracle as it stands on the host cores: setup once (untimed, as for the GPU plan),
     then `steps` full solves of the same workload.  Returns (pts/s, cores, seconds)."""
@@ -296,7 +317,7 @@ def run_ours(args):
     N = args.N
     dev = torch.device("cuda", torch.cuda.current_device())
     # Each rank solves its own density of the same family (weak scaling).
-    wl = D.config_aniso4(N=N, seed=2 + rank)
+    wl = D.config_aniso4(N=N, seed=rank_seed(rank))
     rho64 = wl.sample()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -322,11 +343,7 @@ def run_ours(args):
         if sampler:
             sampler.__exit__(None, None, None)
         torch.cuda.synchronize()
-        ms = statistics.mean(totals)
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(torch, statistics.mean(totals), dev)
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
         results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form, "y_form": plan.y_form,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
@@ -343,10 +360,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         p32.solve_host(host_in, host_out)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(torch, e2e_s, dev)
 
     if rank == 0:
         peak, peak_kind = load_peaks()
@@ -364,7 +378,7 @@ def run_ours(args):
         bytes64 = pass_bytes(N, 8)
         gbs64 = [bytes64[i] / (r64["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
         line = {
-            "metric": METRIC, "value": world * N ** 3 / (r32["ms"] * 1e-3), "unit": UNIT,
+            "metric": METRIC, "value": aggregate_rate(world, N, r32["ms"] * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(N, "f32"),
@@ -374,11 +388,11 @@ def run_ours(args):
                          "peak_source": peak_kind},
             "passes": [{"pass": PASSES[i], "kernel": names[i], "ms": r32["per_pass"][i],
                         "GB_s": gbs[i], "frac": gbs[i] / peak} for i in range(5)],
-            "f64": {"value": world * N ** 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
+            "f64": {"value": aggregate_rate(world, N, r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
                     "steps": r64["steps"],
                     "passes": [{"pass": PASSES[i], "ms": r64["per_pass"][i], "GB_s": gbs64[i],
                                 "frac": gbs64[i] / peak} for i in range(5)]},
-            "e2e": {"value": world * N ** 3 / e2e_s, "unit": UNIT,
+            "e2e": {"value": aggregate_rate(world, N, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": N ** 3 * 4, "d2h_bytes_per_step": N ** 3 * 4},
             "gpu_launches": 5 * r32["steps"],
             "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
