@@ -34,6 +34,8 @@ PASSES = ["x_forward", "y_forward", "z_fwd_symbol_inv", "y_inverse", "x_inverse"
 Z_FORMS = ["direct", "split", "warp"]
 Y_FORMS = ["block", "warp"]
 Z_KERNELS = ["k_z_symbol", "k_z_split", "k_z_warp"]
+# forms of the x and y passes: "block" (tiles staged in shared memory, columns or rows spread
+# over a block) and "warp" (one warp or half-warp per column or row pair)
 KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_inverse"]
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
@@ -329,6 +331,8 @@ def run_ours(args):
             plan.z_form = Z_FORMS.index(args.z_form)
         if dtype == "f32" and args.y_form is not None:
             plan.y_form = Y_FORMS.index(args.y_form)
+        if dtype == "f32" and args.x_form is not None:
+            plan.x_form = Y_FORMS.index(args.x_form)
         rho_t = torch.from_numpy(rho64.astype(plan.np_dtype)).to(dev)
         out_t = torch.empty_like(rho_t)
         steps = args.steps if dtype == "f32" else max(3, args.steps // 4)
@@ -345,7 +349,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms = max_over_ranks(torch, statistics.mean(totals), dev)
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
-        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form, "y_form": plan.y_form,
+        results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form, "y_form": plan.y_form, "x_form": plan.x_form,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
                           "rho": rho_t, "out": out_t}
 
@@ -372,6 +376,8 @@ def run_ours(args):
         names[2] = Z_KERNELS[r32["z_form"]]
         if r32["y_form"] == 1:
             names[1], names[3] = "k_y_warp<fwd>", "k_y_warp<inv>"
+        if r32["x_form"] == 1:
+            names[0], names[4] = "k_x_warp_fwd", "k_x_warp_inv"
         src_hash = kernel_source_hash()
         traffic = NCU_TRAFFIC.get((src_hash, names[dom], N))
         r64 = results["f64"]
@@ -398,7 +404,8 @@ def run_ours(args):
             "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
                        "z_pass_f64": Z_FORMS[results["f64"]["z_form"]],
                        "y_passes_f32": Y_FORMS[r32["y_form"]], "y_passes_f64": Y_FORMS[results["f64"]["y_form"]],
-                       "how": ("pinned by --z-form/--y-form" if args.z_form or args.y_form else
+                       "x_passes_f32": Y_FORMS[r32["x_form"]], "x_passes_f64": Y_FORMS[results["f64"]["x_form"]],
+                       "how": ("pinned by --z-form/--y-form/--x-form" if args.z_form or args.y_form or args.x_form else
                                "timed at plan creation, cached per (device, N, dtype)")},
             "clocks": r32["clocks"],
         }
@@ -434,6 +441,8 @@ def main():
                     help="pin the FP32 z-pass form (default: the plan's timed choice); for profiling")
     ap.add_argument("--y-form", choices=Y_FORMS, default=None,
                     help="pin the FP32 y-pass form (default: the plan's timed choice); for profiling")
+    ap.add_argument("--x-form", choices=Y_FORMS, default=None,
+                    help="pin the FP32 x-pass form (default: the plan's timed choice); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -179,6 +179,10 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *   POISSON_KNOB_Y_FORM  form of the two y passes (Sec. 2, the zero-padded transforms
  *       along the middle axis): 0 = a column pair spread over the threads of a block;
  *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, N = 256).
+ *   POISSON_KNOB_X_FORM  form of the two x passes (Sec. 2, the real transforms along the
+ *       first axis and the crop): 0 = a tile of rows staged in shared memory; 1 = one
+ *       half-warp per pair of rows, read and written straight from device memory
+ *       (POISSON_F32, N = 256).
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that
@@ -187,6 +191,7 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  */
 #define POISSON_KNOB_Z_FORM 0
 #define POISSON_KNOB_Y_FORM 1
+#define POISSON_KNOB_X_FORM 2
 int poisson_plan_get_knob(poisson_plan p, int knob, int *value);
 int poisson_plan_set_knob(poisson_plan p, int knob, int value);
 

@@ -143,6 +143,19 @@ class Plan:
     def y_form(self, value):
         _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_Y_FORM, int(value)), "poisson_plan_set_knob")
 
+    @property
+    def x_form(self):
+        """Form of the x passes in use (chosen by timing at plan creation): 0 a tile of rows
+        staged in shared memory, 1 one half-warp per pair of rows."""
+        v = ctypes.c_int()
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_X_FORM, ctypes.byref(v)),
+                   "poisson_plan_get_knob")
+        return v.value
+
+    @x_form.setter
+    def x_form(self, value):
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_X_FORM, int(value)), "poisson_plan_set_knob")
+
     def gauss_sum(self):
         n = self.info()["n_terms"]
         tau, w = np.empty(n), np.empty(n)

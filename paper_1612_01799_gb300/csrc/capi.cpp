@@ -27,6 +27,11 @@ cudaError_t z_pass_f32(const DevicePlan &, cudaStream_t);
 cudaError_t z_pass_f64(const DevicePlan &, cudaStream_t);
 cudaError_t y_passes_f32(const DevicePlan &, cudaStream_t);
 cudaError_t y_passes_f64(const DevicePlan &, cudaStream_t);
+cudaError_t x_passes_f32(const DevicePlan &, cudaStream_t);
+cudaError_t x_passes_f64(const DevicePlan &, cudaStream_t);
+cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? x_passes_f32(p, s) : x_passes_f64(p, s);
+}
 cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s) {
     return p.dtype == POISSON_F32 ? y_passes_f32(p, s) : y_passes_f64(p, s);
 }
@@ -91,7 +96,7 @@ cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const dou
 // ---- autotuning of kernel variants --------------------------------------------------------
 // Decisions per (device, N, dtype), made by the first plan of that shape and reused.
 struct TuneEntry {
-    int dev, N, dtype, zform, yform;
+    int dev, N, dtype, zform, yform, xform;
 };
 static std::vector<TuneEntry> g_tune;
 static std::mutex g_tune_mutex;
@@ -134,20 +139,23 @@ static cudaError_t pick_form(int forms, int *field, Run &&run, cudaStream_t s, c
     return cudaSuccess;
 }
 
-// Choose p.zform and p.yform: the cached decision for this shape, else the fastest forms
-// that exist, timed on p's zeroed workspace.  The z pass writes only w3, the y passes w2
-// and w1, and every solve writes each of them before reading it.
+// Choose p.zform, p.yform and p.xform: the cached decision for this shape, else the fastest
+// forms that exist, timed on p's zeroed workspace.  The z pass writes only w3, the y passes
+// w2 and w1, the x passes (timed with w2 as density and output) w1 and w2, and every solve
+// writes each of them before reading it.
 static cudaError_t autotune(DevicePlan &p, int dev) {
     p.zform = 0;
     p.yform = 0;
-    const int zf = z_forms(p.N, p.dtype), yf = y_forms(p.N, p.dtype);
-    if (zf == 1 && yf == 1) return cudaSuccess;
+    p.xform = 0;
+    const int zf = z_forms(p.N, p.dtype), yf = y_forms(p.N, p.dtype), xf = x_forms(p.N, p.dtype);
+    if (zf == 1 && yf == 1 && xf == 1) return cudaSuccess;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (const TuneEntry &t : g_tune)
             if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
                 p.zform = t.zform;
                 p.yform = t.yform;
+                p.xform = t.xform;
                 return cudaSuccess;
             }
     }
@@ -158,11 +166,12 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e == cudaSuccess) e = pick_form(zf, &p.zform, [&] { return launch_z_pass(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(yf, &p.yform, [&] { return launch_y_passes(p, s); }, s, a, b);
+    if (e == cudaSuccess) e = pick_form(xf, &p.xform, [&] { return launch_x_passes(p, s); }, s, a, b);
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) {
-        p.zform = p.yform = 0;
+        p.zform = p.yform = p.xform = 0;
         return e;
     }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -170,9 +179,10 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
         if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
             p.zform = t.zform;
             p.yform = t.yform;
+            p.xform = t.xform;
             return cudaSuccess;
         }
-    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform, p.yform});
+    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform, p.yform, p.xform});
     return cudaSuccess;
 }
 }  // namespace gsp
@@ -350,19 +360,29 @@ extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
     if (!p || !value) return POISSON_ERR_ARG;
     if (knob == POISSON_KNOB_Z_FORM) *value = p->dp.zform;
     else if (knob == POISSON_KNOB_Y_FORM) *value = p->dp.yform;
+    else if (knob == POISSON_KNOB_X_FORM) *value = p->dp.xform;
     else return POISSON_ERR_ARG;
     return POISSON_OK;
 }
 
 extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     if (!p) return POISSON_ERR_ARG;
-    if ((knob != POISSON_KNOB_Z_FORM && knob != POISSON_KNOB_Y_FORM) || value < 0 || value > 2)
+    int forms, *field;
+    if (knob == POISSON_KNOB_Z_FORM) {
+        forms = gsp::z_forms(p->dp.N, p->dp.dtype);
+        field = &p->dp.zform;
+    } else if (knob == POISSON_KNOB_Y_FORM) {
+        forms = gsp::y_forms(p->dp.N, p->dp.dtype);
+        field = &p->dp.yform;
+    } else if (knob == POISSON_KNOB_X_FORM) {
+        forms = gsp::x_forms(p->dp.N, p->dp.dtype);
+        field = &p->dp.xform;
+    } else {
         return POISSON_ERR_ARG;
-    const bool z = knob == POISSON_KNOB_Z_FORM;
-    if (!z && value > 1) return POISSON_ERR_ARG;
-    const int forms = z ? gsp::z_forms(p->dp.N, p->dp.dtype) : gsp::y_forms(p->dp.N, p->dp.dtype);
+    }
+    if (value < 0 || value > (knob == POISSON_KNOB_Z_FORM ? 2 : 1)) return POISSON_ERR_ARG;
     if (!(forms >> value & 1)) return POISSON_ERR_UNSUPPORTED;
-    (z ? p->dp.zform : p->dp.yform) = value;
+    *field = value;
     return POISSON_OK;
 }
 

@@ -439,6 +439,44 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
     return cudaGetLastError();
 }
 
+// The x passes (K1 forward, K5 inverse) of B densities in the form p.xform selects: 0 the
+// block form (k_x_forward / k_x_inverse), 1 the warp form (k_x_warp_*, FP32, N = 256).
+template <typename Real, int N> constexpr bool xwarp_form() { return std::is_same<Real, float>::value && N == XWarp::N; }
+
+template <typename Real, int N>
+cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s, bool fwd) {
+    using T2 = Cx2<Real>;
+    const int nrows = B * N * N;
+    if constexpr (xwarp_form<Real, N>()) {
+        if (p.xform == 1) {
+            GSP_CHECK(set_smem(k_x_warp_fwd<N>, XWarp::SMEM));
+            GSP_CHECK(set_smem(k_x_warp_inv<N>, XWarp::SMEM));
+            const int npairs = nrows / 2;
+            const int grid = fwd ? persistent_blocks(k_x_warp_fwd<N>, XWarp::NT, XWarp::SMEM, (npairs + 15) / 16)
+                                 : persistent_blocks(k_x_warp_inv<N>, XWarp::NT, XWarp::SMEM, (npairs + 15) / 16);
+            if (fwd)
+                k_x_warp_fwd<N><<<grid, XWarp::NT, XWarp::SMEM, s>>>(rho, static_cast<float2 *>(p.w1),
+                                                                   static_cast<const float2 *>(p.tw), npairs, p.Px);
+            else
+                k_x_warp_inv<N><<<grid, XWarp::NT, XWarp::SMEM, s>>>(static_cast<const float2 *>(p.w1), u,
+                                                                   static_cast<const float2 *>(p.tw), npairs, p.Px);
+            return cudaGetLastError();
+        }
+    }
+    constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
+    const size_t smem_row = (size_t)(N + 1) * (TR + 1) * 2 * sizeof(Real);
+    const dim3 grow((nrows + TR - 1) / TR);
+    const T2 *tw = static_cast<const T2 *>(p.tw);
+    if (fwd) {
+        GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
+        k_x_forward<Real, N><<<grow, TR * PX1, smem_row, s>>>(rho, static_cast<T2 *>(p.w1), tw, nrows, p.Px);
+    } else {
+        GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
+        k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(static_cast<const T2 *>(p.w1), u, tw, nrows, p.Px);
+    }
+    return cudaGetLastError();
+}
+
 // The y passes (K2 forward, K4 inverse) of B densities in the form p.yform selects: 0 the
 // block form (k_col_tma), 1 the warp form (k_y_warp, ywarp_form); an absent form runs as 0.
 template <typename Real, int N> constexpr bool ywarp_form() { return std::is_same<Real, float>::value && N == YWarp::N; }
@@ -484,23 +522,9 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
                     cudaEvent_t *ev, double *tail) {
-    using T2 = Cx2<Real>;
-    using TwC = typename TwOf<typename Types<Real>::CC>::T;
-    constexpr int L = 2 * N;
-    const int Px = p.Px;
-    T2 *w1 = static_cast<T2 *>(p.w1), *w2 = static_cast<T2 *>(p.w2), *w3 = static_cast<T2 *>(p.w3);
-    const T2 *tw = static_cast<const T2 *>(p.tw);
-    const TwC *twc = static_cast<const TwC *>(p.twc);
-    constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
-    const size_t smem_row = (size_t)(N + 1) * (TR + 1) * 2 * sizeof(Real);
-    const int nrows = B * N * N;
-    const int ncols = N + 1;
-    const dim3 grow((nrows + TR - 1) / TR);
 
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
-    GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
-    k_x_forward<Real, N><<<grow, TR * PX1, smem_row, s>>>(rho, w1, tw, nrows, Px);
-    GSP_CHECK(cudaGetLastError());
+    GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, true)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
     GSP_CHECK((y_pass<Real, N>(p, B, s, true)));
@@ -512,9 +536,7 @@ cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     GSP_CHECK((y_pass<Real, N>(p, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
-    GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
-    k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(w1, u, tw, nrows, Px);
-    GSP_CHECK(cudaGetLastError());
+    GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
     return cudaSuccess;
 }
@@ -608,6 +630,8 @@ cudaError_t encode_n(DevicePlan &p) {
                                               cudaStream_t, cudaEvent_t *, double *);                      \
     EXT template cudaError_t z_pass<Real, n>(const DevicePlan &, int, cudaStream_t, double *);             \
     EXT template cudaError_t y_pass<Real, n>(const DevicePlan &, int, cudaStream_t, bool);                 \
+    EXT template cudaError_t x_pass<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int,   \
+                                             cudaStream_t, bool);                                          \
     EXT template cudaError_t encode_n<Real, n>(DevicePlan &);
 
 template <typename Real>
@@ -644,6 +668,25 @@ cudaError_t y_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
     case n: {                                                         \
         cudaError_t e = y_pass<Real, n>(p, 1, s, true);               \
         return e != cudaSuccess ? e : y_pass<Real, n>(p, 1, s, false); \
+    }
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+// The two x passes of one density on spare workspace (w2 as the density and the output),
+// for timing the forms.
+template <typename Real>
+cudaError_t x_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    PtrArray a{};
+    a.p[0] = p.w2;
+    switch (p.N) {
+#define GSP_CASE(n)                                                          \
+    case n: {                                                                \
+        cudaError_t e = x_pass<Real, n>(p, a, a, 1, s, true);                \
+        return e != cudaSuccess ? e : x_pass<Real, n>(p, a, a, 1, s, false); \
     }
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE

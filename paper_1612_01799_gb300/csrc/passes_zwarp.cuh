@@ -153,6 +153,7 @@ __device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_
     z.ar = xo + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
     return z;
 }
+__device__ __forceinline__ CV cconj_cv(CV a) { return {a.re, f2neg(a.im)}; }
 __device__ __forceinline__ CV zw_sign(CV x, float sg) { return {f2mul(x.re, f2(sg, sg)), f2mul(x.im, f2(sg, sg))}; }
 
 // F1 (inputs v[0..7], odd ones already signed), F2 and F3 with its twiddle.
@@ -500,6 +501,187 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         }
     }
     if (stored) bulk_wait0();
+}
+
+}  // namespace gsp
+
+namespace gsp {
+
+// ---- K1 / K5, warp form (FP32, N = 256) -------------------------------------------------
+// The x passes with one half-warp per pair of adjacent rows (2i, 2i+1) in the two lanes of
+// a packed FP32x2 value.  The length-2N real transform of a row is, as in k_x_forward, the
+// N-point complex FFT of its (even, odd) sample pairs z_m (m < N/2 nonzero) and the
+// Hermitian split.  N = 256 = 16 x 16: lane q' holds z[q' + 16 r] (r < 8); F1 (pruned
+// 16-point DFT), F2 (twiddles W_256^{q' k1}), a half-warp exchange through shared memory
+// (lane k1 gathers position q' from slot 16 k1 + (q' ^ (k1 & 7))), F6 (16-point DFT):
+// lane k1 holds C[k1 + 16 k2] in register k2.  The split pairs C_k with C_{N-k} through the
+// same slots (slot k), so each lane computes X_k and X_{N-k} for its k <= N/2.  The inverse
+// runs the same steps backwards: the combine of (Y_k, Y_{N-k}) into (C_k, C_{N-k}), the
+// slots, then the adjoint transform (F6^H, exchange, F2^H, F1^H keeping z[m], m < N/2).
+// Rows are read and written straight from HBM: 16 lanes x 8 bytes = one 128-byte line per
+// row and instruction.  Persistent CTAs; the x forward loads the next row pair while it
+// transforms the current one.
+struct XWarp {
+    static constexpr int N = 256, NT = 256;
+    static constexpr int OFF_X = 0, OFF_T = OFF_X + 16 * 4096, OFF_T2 = OFF_T + 256 * 8;
+    static constexpr int SMEM = OFF_T2 + 129 * 8;
+};
+
+// Twiddle tables of the x passes from W_512^e: T[k1 * 16 + q'] = W_256^{q' k1},
+// T2[k] = W_512^k (k <= N/2).
+__device__ __forceinline__ void xw_tables(float2 *T, float2 *T2, const float2 *__restrict__ tw) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) T[i] = tw[2 * (i & 15) * (i >> 4)];
+    for (int i = threadIdx.x; i <= 128; i += blockDim.x) T2[i] = tw[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(XWarp::NT, 2)
+k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restrict__ tw, int npairs, int Px) {
+    static_assert(N == XWarp::N, "the half-warp schedule is 16 x 16");
+    constexpr int NN = N * N;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *T = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T);
+    float2 *T2 = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T2);
+    xw_tables(T, T2, tw);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
+    const uint32_t xs = smem_addr(smraw + XWarp::OFF_X) + 4096 * hw;
+    const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
+    const int stride = gridDim.x * (XWarp::NT / 16);
+    auto load = [&](int i, float2 *f) {
+        const int b = (2 * i) / NN;
+        const float2 *s = reinterpret_cast<const float2 *>(rho.p[b]) + (long long)(2 * i - b * NN) * (N / 2) + qq;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            f[2 * r] = __ldg(s + 16 * r);
+            f[2 * r + 1] = __ldg(s + N / 2 + 16 * r);
+        }
+    };
+    int i = blockIdx.x * (XWarp::NT / 16) + hw;
+    float2 f[16];
+    if (i < npairs) load(i, f);
+    for (; i < npairs; i += stride) {
+        CV v[16];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = {f2(f[2 * r].x, f[2 * r + 1].x), f2(f[2 * r].y, f[2 * r + 1].y)};
+        if (i + stride < npairs) load(i + stride, f);
+        zw_f1(v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = zw_twmul<-1>(v[j], T[zw_kappa0(j) * 16 + qq]);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k0 = zw_kappa0(j);
+            zw_sts((aw ^ (16 * (k0 & 7))) + 256 * k0, v[j]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (16 * (p & 7))) + 16 * (p & 8));
+        dft<16, -1>(v);  // v[k2] = C[qq + 16 k2]
+        __syncwarp();
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) zw_sts(xs + 16 * (qq + 16 * k2), v[k2]);
+        __syncwarp();
+        float2 *d0 = out + (long long)(2 * i) * Px, *d1 = d0 + Px;
+        const float2 h = f2(0.5f, 0.5f);
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            const int k = qq + 16 * k2;
+            if (k > N / 2) continue;
+            const CV ck = v[k2], cn = zw_lds(xs + 16 * ((N - k) & (N - 1)));
+            const CV ev = {f2mul(h, f2add(ck.re, cn.re)), f2mul(h, f2sub(ck.im, cn.im))};
+            const CV od = {f2mul(h, f2add(ck.im, cn.im)), f2mul(h, f2sub(cn.re, ck.re))};
+            if (k == 0) {
+                const float2 x0 = f2add(ev.re, od.re), xn = f2sub(ev.re, od.re);
+                d0[0] = f2(x0.x, 0.f);
+                d1[0] = f2(x0.y, 0.f);
+                d0[N] = f2(xn.x, 0.f);
+                d1[N] = f2(xn.y, 0.f);
+            } else {
+                const CV t = zw_twmul<-1>(od, T2[k]);
+                const CV xk = cadd(ev, t);
+                d0[k] = f2(xk.re.x, xk.im.x);
+                d1[k] = f2(xk.re.y, xk.im.y);
+                if (2 * k != N) {
+                    const CV xn = csub(ev, t);
+                    d0[N - k] = f2(xn.re.x, -xn.im.x);
+                    d1[N - k] = f2(xn.re.y, -xn.im.y);
+                }
+            }
+        }
+        __syncwarp();  // the slots are read before the next pair's exchange writes them
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(XWarp::NT, 2)
+k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__restrict__ tw, int npairs, int Px) {
+    static_assert(N == XWarp::N, "the half-warp schedule is 16 x 16");
+    constexpr int NN = N * N;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *T = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T);
+    float2 *T2 = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T2);
+    xw_tables(T, T2, tw);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
+    const uint32_t xs = smem_addr(smraw + XWarp::OFF_X) + 4096 * hw;
+    const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
+    const int stride = gridDim.x * (XWarp::NT / 16);
+    for (int i = blockIdx.x * (XWarp::NT / 16) + hw; i < npairs; i += stride) {
+        const float2 *s0 = in + (long long)(2 * i) * Px, *s1 = s0 + Px;
+        float2 yk0[9], yk1[9], yn0[9], yn1[9];
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            const int k = qq + 16 * k2;
+            if (k > N / 2) continue;
+            yk0[k2] = __ldg(s0 + k);
+            yk1[k2] = __ldg(s1 + k);
+            yn0[k2] = __ldg(s0 + (N - k));
+            yn1[k2] = __ldg(s1 + (N - k));
+        }
+        CV v[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            const int k = qq + 16 * k2;
+            if (k > N / 2) continue;
+            if (k == 0) {
+                v[0] = {f2(yk0[0].x + yn0[0].x, yk1[0].x + yn1[0].x), f2(yk0[0].x - yn0[0].x, yk1[0].x - yn1[0].x)};
+            } else {
+                const CV yk = {f2(yk0[k2].x, yk1[k2].x), f2(yk0[k2].y, yk1[k2].y)};
+                const CV yn = {f2(yn0[k2].x, yn1[k2].x), f2(yn0[k2].y, yn1[k2].y)};
+                const CV ev = {f2add(yk.re, yn.re), f2sub(yk.im, yn.im)};
+                const CV od = zw_twmul<1>(CV{f2sub(yk.re, yn.re), f2add(yk.im, yn.im)}, T2[k]);
+                v[k2] = add_rot<1>(ev, od);
+                if (2 * k != N) zw_sts(xs + 16 * (N - k), add_rot<1>(cconj_cv(ev), cconj_cv(od)));
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k2 = 8; k2 < 16; ++k2) {
+            const int k = qq + 16 * k2;
+            if (k != N / 2) v[k2] = zw_lds(xs + 16 * k);
+        }
+        __syncwarp();
+        dft<16, 1>(v);
+#pragma unroll
+        for (int p = 0; p < 16; ++p) zw_sts((ar ^ (16 * (p & 7))) + 16 * (p & 8), v[p]);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k0 = zw_kappa0(j);
+            v[j] = zw_lds((aw ^ (16 * (k0 & 7))) + 256 * k0);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = zw_twmul<1>(v[j], T[zw_kappa0(j) * 16 + qq]);
+        zw_f1_adj(v);
+        const int b = (2 * i) / NN;
+        float2 *d = reinterpret_cast<float2 *>(const_cast<void *>(u.p[b])) + (long long)(2 * i - b * NN) * (N / 2) + qq;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            d[16 * r] = f2(v[r].re.x, v[r].im.x);
+            d[N / 2 + 16 * r] = f2(v[r].re.y, v[r].im.y);
+        }
+        __syncwarp();  // the slots are read before the next pair writes them
+    }
 }
 
 }  // namespace gsp

@@ -47,6 +47,9 @@ struct DevicePlan {
     // y pass form: 0 block form (a column pair spread over a block), 1 warp form (FP32,
     // N = 256)
     int yform = 0;
+    // x pass form: 0 block form (a tile of rows staged in shared memory), 1 warp form (a
+    // half-warp per row pair, FP32, N = 256)
+    int xform = 0;
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers; and of the warp-form z pass (w2 in,
     // symbol, w3 out; 128- and 64-byte swizzled boxes), encoded where that form exists.
@@ -80,6 +83,13 @@ cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArra
 // bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;
 // bit 2 for FP32 at N = 256.
 int z_forms(int N, int dtype);
+
+// Forms of the x passes that exist for (N, dtype), as a bit mask over DevicePlan::xform:
+// bit 0 always; bit 1 for FP32 at N = 256.
+int x_forms(int N, int dtype);
+
+// The two x passes alone, one density on spare workspace, in the form p.xform selects.
+cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s);
 
 // Forms of the y passes that exist for (N, dtype), as a bit mask over DevicePlan::yform:
 // bit 0 always; bit 1 for FP32 at N = 256.

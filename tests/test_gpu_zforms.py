@@ -25,6 +25,9 @@ def yforms(N, dtype):
     return [0] + ([1] if dtype == "f32" and N in WARP_N else [])
 
 
+xforms = yforms
+
+
 @pytest.fixture(scope="module")
 def torch_cuda():
     torch = pytest.importorskip("torch")
@@ -39,16 +42,20 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def solve_form(torch, N, L, tol, dtype, rho, form, yform=None):
+def solve_form(torch, N, L, tol, dtype, rho, form, yform=None, xform=None):
     from paper_1612_01799_gb300 import Plan
     with Plan(N, L, tol, dtype) as p:
         assert p.z_form in forms(N, dtype)
         assert p.y_form in yforms(N, dtype)
+        assert p.x_form in xforms(N, dtype)
         p.z_form = form
         assert p.z_form == form
         if yform is not None:
             p.y_form = yform
             assert p.y_form == yform
+        if xform is not None:
+            p.x_form = xform
+            assert p.x_form == xform
         t = torch.from_numpy(np.ascontiguousarray(rho, dtype=p.np_dtype)).cuda()
         u = p.solve(t)
         torch.cuda.synchronize()
@@ -77,6 +84,13 @@ def test_knob_codes(torch_cuda, dtype):
                 else:
                     assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Y_FORM, f) == -4
             assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Y_FORM, 2) == -1
+            for f in (0, 1):
+                if f in xforms(N, dtype):
+                    p.x_form = f
+                    assert p.x_form == f
+                else:
+                    assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_X_FORM, f) == -4
+            assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_X_FORM, 2) == -1
             assert lib.poisson_plan_set_knob(p.handle, 7, 0) == -1
             assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, 3) == -1
             assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, -1) == -1
@@ -90,7 +104,7 @@ def test_tuning_is_per_shape(torch_cuda):
     from paper_1612_01799_gb300 import Plan
     for dtype in ("f32", "f64"):
         with Plan(256, 10.0, 1e-6, dtype) as a, Plan(256, 3.0, 1e-9, dtype, max_batch=2) as b:
-            assert a.z_form == b.z_form and a.y_form == b.y_form
+            assert a.z_form == b.z_form and a.y_form == b.y_form and a.x_form == b.x_form
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -112,11 +126,12 @@ def test_forms_full_grid_n256(torch_cuda, plan_cache, dtype):
     rho = D.config_aniso4().sample()
     tol = 1e-12 if dtype == "f64" else 1e-6
     uo = osolver.solve(rho, 10.0, tol, plan=plan_cache(256, 10.0, tol))
-    for form in forms(256, dtype):
-        for yform in yforms(256, dtype):
-            u = solve_form(torch_cuda, 256, 10.0, tol, dtype, rho, form, yform)
-            assert rel_l2(u, uo) <= TOL[dtype], (form, yform)
-            assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max(), (form, yform)
+    combos = [(f, 0, 0) for f in forms(256, dtype)] + [(f, 1, x) for f in forms(256, dtype)
+                                                        for x in xforms(256, dtype) if dtype == "f32"]
+    for form, yform, xform in combos:
+        u = solve_form(torch_cuda, 256, 10.0, tol, dtype, rho, form, yform, xform)
+        assert rel_l2(u, uo) <= TOL[dtype], (form, yform, xform)
+        assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max(), (form, yform, xform)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -160,8 +175,8 @@ def test_form_tail(torch_cuda, form, N, dtype):
     assert eta.value == pytest.approx(ref, rel=2e-3 if dtype == "f32" else 1e-6, abs=1e-12)
 
 
-@pytest.mark.parametrize("yform", [0, 1])
-def test_warp_form_batched(torch_cuda, yform):
+@pytest.mark.parametrize("yform,xform", [(0, 0), (1, 0), (1, 1)])
+def test_warp_form_batched(torch_cuda, yform, xform):
     """Three densities through one grouped launch sequence in the warp forms: each equals
     its single solve bit for bit, and the plan reports no timed-out wait."""
     torch = torch_cuda
@@ -172,6 +187,7 @@ def test_warp_form_batched(torch_cuda, yform):
     with Plan(N, L, 1e-6, "f32", max_batch=3) as p:
         p.z_form = 2
         p.y_form = yform
+        p.x_form = xform
         outs = [torch.empty_like(r) for r in rhos]
         solve_batched([p] * 3, rhos, outs)
         torch.cuda.synchronize()
