@@ -181,8 +181,8 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, N = 256).
  *   POISSON_KNOB_X_FORM  form of the two x passes (Sec. 2, the real transforms along the
  *       first axis and the crop): 0 = a tile of rows staged in shared memory; 1 = one
- *       half-warp per pair of rows, read and written straight from device memory
- *       (POISSON_F32, N = 256).
+ *       half-warp (N = 256) or warp (N = 512) per pair of rows, read and written straight
+ *       from device memory (POISSON_F32, N = 256 and 512).
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that

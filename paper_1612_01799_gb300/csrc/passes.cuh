@@ -440,8 +440,11 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
 }
 
 // The x passes (K1 forward, K5 inverse) of B densities in the form p.xform selects: 0 the
-// block form (k_x_forward / k_x_inverse), 1 the warp form (k_x_warp_*, FP32, N = 256).
-template <typename Real, int N> constexpr bool xwarp_form() { return std::is_same<Real, float>::value && N == XWarp::N; }
+// block form (k_x_forward / k_x_inverse), 1 the warp form (FP32: k_x_warp_* at N = 256,
+// k_x_warp2_* at N = 512).
+template <typename Real, int N> constexpr bool xwarp_form() {
+    return std::is_same<Real, float>::value && (N == XWarp::N || N == XWarp2::N);
+}
 
 template <typename Real, int N>
 cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s, bool fwd) {
@@ -449,17 +452,29 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
     const int nrows = B * N * N;
     if constexpr (xwarp_form<Real, N>()) {
         if (p.xform == 1) {
-            GSP_CHECK(set_smem(k_x_warp_fwd<N>, XWarp::SMEM));
-            GSP_CHECK(set_smem(k_x_warp_inv<N>, XWarp::SMEM));
             const int npairs = nrows / 2;
-            const int grid = fwd ? persistent_blocks(k_x_warp_fwd<N>, XWarp::NT, XWarp::SMEM, (npairs + 15) / 16)
-                                 : persistent_blocks(k_x_warp_inv<N>, XWarp::NT, XWarp::SMEM, (npairs + 15) / 16);
-            if (fwd)
-                k_x_warp_fwd<N><<<grid, XWarp::NT, XWarp::SMEM, s>>>(rho, static_cast<float2 *>(p.w1),
-                                                                   static_cast<const float2 *>(p.tw), npairs, p.Px);
-            else
-                k_x_warp_inv<N><<<grid, XWarp::NT, XWarp::SMEM, s>>>(static_cast<const float2 *>(p.w1), u,
-                                                                   static_cast<const float2 *>(p.tw), npairs, p.Px);
+            const float2 *tw = static_cast<const float2 *>(p.tw);
+            if constexpr (N == XWarp2::N) {
+                GSP_CHECK(set_smem(k_x_warp2_fwd<N>, XWarp2::SMEM));
+                GSP_CHECK(set_smem(k_x_warp2_inv<N>, XWarp2::SMEM));
+                const int nw = (npairs + XWarp2::NW - 1) / XWarp2::NW;
+                if (fwd)
+                    k_x_warp2_fwd<N><<<persistent_blocks(k_x_warp2_fwd<N>, XWarp2::NT, XWarp2::SMEM, nw), XWarp2::NT,
+                                       XWarp2::SMEM, s>>>(rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px);
+                else
+                    k_x_warp2_inv<N><<<persistent_blocks(k_x_warp2_inv<N>, XWarp2::NT, XWarp2::SMEM, nw), XWarp2::NT,
+                                       XWarp2::SMEM, s>>>(static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
+            } else {
+                GSP_CHECK(set_smem(k_x_warp_fwd<N>, XWarp::SMEM));
+                GSP_CHECK(set_smem(k_x_warp_inv<N>, XWarp::SMEM));
+                const int nw = (npairs + 15) / 16;
+                if (fwd)
+                    k_x_warp_fwd<N><<<persistent_blocks(k_x_warp_fwd<N>, XWarp::NT, XWarp::SMEM, nw), XWarp::NT,
+                                      XWarp::SMEM, s>>>(rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px);
+                else
+                    k_x_warp_inv<N><<<persistent_blocks(k_x_warp_inv<N>, XWarp::NT, XWarp::SMEM, nw), XWarp::NT,
+                                      XWarp::SMEM, s>>>(static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
+            }
             return cudaGetLastError();
         }
     }

@@ -141,10 +141,11 @@ struct ZwLane {
     uint32_t aw;   // exchange writer base: position q' of reader l = kappa0 + 8 s + 16 t
     uint32_t ar;   // exchange reader base: reader q, row 16 q + (p ^ (q & 7))
 };
-__device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_t xo, int g, int q) {
+// tw: W_512^e (twstride 1) or W_1024^e (twstride 2).
+__device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_t xo, int g, int q, int twstride = 1) {
     const int s = q >> 4, qp = q & 15;
     ZwLane z;
-    z.tw32 = tw[16 * qp];
+    z.tw32 = tw[16 * qp * twstride];
     if (s) z.tw32 = f2(-z.tw32.x, -z.tw32.y);
     z.tkb = q + 256 * s;
     z.tnb = q - 256 * s;
@@ -679,6 +680,165 @@ k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__re
         for (int r = 0; r < 8; ++r) {
             d[16 * r] = f2(v[r].re.x, v[r].im.x);
             d[N / 2 + 16 * r] = f2(v[r].re.y, v[r].im.y);
+        }
+        __syncwarp();  // the slots are read before the next pair writes them
+    }
+}
+
+}  // namespace gsp
+
+namespace gsp {
+
+// ---- K1 / K5, warp form at N = 512 (FP32) -------------------------------------------------
+// The same row-pair scheme as k_x_warp_fwd / k_x_warp_inv with one full warp per pair of
+// rows: the N = 512-point complex FFT of the (even, odd) sample pairs (256 nonzero) is the
+// pruned length-512 transform of the z pass's warp form (F1..F6: lane q ends with
+// C[q + 32 k2] in register k2), and the Hermitian split pairs C_k with C_{N-k} through the
+// warp's 512 slots (slot k in row k, chunk g ^ (k & 7)).  The inverse combines
+// (Y_k, Y_{N-k}) into (C_k, C_{N-k}) and runs the adjoint half.  The twiddle table of the
+// plan is W_1024^e here.
+struct XWarp2 {
+    static constexpr int N = 512, NW = 8, NT = 256;
+    static constexpr int OFF_XO = 0, OFF_T = 65536, OFF_T2 = OFF_T + 16 * 32 * 8;
+    static constexpr int SMEM = 1024 + OFF_T2 + 257 * 8;
+};
+
+template <int N>
+__global__ void __launch_bounds__(XWarp2::NT, 2)
+k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restrict__ tw, int npairs, int Px) {
+    static_assert(N == XWarp2::N, "one warp per row pair: 512 = 16 x 2 x 16");
+    constexpr long long NN = (long long)N * N;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    unsigned char *xo = base + XWarp2::OFF_XO;
+    float2 *T = reinterpret_cast<float2 *>(base + XWarp2::OFF_T);
+    float2 *T2 = reinterpret_cast<float2 *>(base + XWarp2::OFF_T2);
+    for (int i = threadIdx.x; i < 512; i += XWarp2::NT) T[i] = tw[2 * (i & 31) * (i >> 5)];
+    for (int i = threadIdx.x; i <= N / 2; i += XWarp2::NT) T2[i] = tw[i];
+    __syncthreads();
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
+    const ZwLane zl = zw_lane(tw, smem_addr(xo), g, q, 2);
+    const int stride = gridDim.x * XWarp2::NW;
+    auto load = [&](long long i, float2 *f) {
+        const int b = (int)((2 * i) / NN);
+        const float2 *s = reinterpret_cast<const float2 *>(rho.p[b]) + (2 * i - b * NN) * (N / 2) + q;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            f[2 * r] = __ldg(s + 32 * r);
+            f[2 * r + 1] = __ldg(s + N / 2 + 32 * r);
+        }
+    };
+    long long i = (long long)blockIdx.x * XWarp2::NW + g;
+    float2 f[16];
+    if (i < npairs) load(i, f);
+    for (; i < npairs; i += stride) {
+        CV v[16];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            v[r] = {f2(f[2 * r].x, f[2 * r + 1].x), f2(f[2 * r].y, f[2 * r + 1].y)};
+            if (r & 1) v[r] = zw_sign(v[r], zl.sg);
+        }
+        if (i + stride < npairs) load(i + stride, f);
+        zw_front(v, zl, T);
+        zw_exchange(v, zl);
+        dft<16, -1>(v);  // v[k2] = C[q + 32 k2]
+        __syncwarp();
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) zw_sts(smem_addr(xo) + zw_sw128(q + 32 * k2, g), v[k2]);
+        __syncwarp();
+        float2 *d0 = out + (2 * i) * Px, *d1 = d0 + Px;
+        const float2 h = f2(0.5f, 0.5f);
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            const int k = q + 32 * k2;
+            if (k > N / 2) continue;
+            const CV ck = v[k2], cn = zw_lds(smem_addr(xo) + zw_sw128((N - k) & (N - 1), g));
+            const CV ev = {f2mul(h, f2add(ck.re, cn.re)), f2mul(h, f2sub(ck.im, cn.im))};
+            const CV od = {f2mul(h, f2add(ck.im, cn.im)), f2mul(h, f2sub(cn.re, ck.re))};
+            if (k == 0) {
+                const float2 x0 = f2add(ev.re, od.re), xn = f2sub(ev.re, od.re);
+                d0[0] = f2(x0.x, 0.f);
+                d1[0] = f2(x0.y, 0.f);
+                d0[N] = f2(xn.x, 0.f);
+                d1[N] = f2(xn.y, 0.f);
+            } else {
+                const CV t = zw_twmul<-1>(od, T2[k]);
+                const CV xk = cadd(ev, t);
+                d0[k] = f2(xk.re.x, xk.im.x);
+                d1[k] = f2(xk.re.y, xk.im.y);
+                if (2 * k != N) {
+                    const CV xn = csub(ev, t);
+                    d0[N - k] = f2(xn.re.x, -xn.im.x);
+                    d1[N - k] = f2(xn.re.y, -xn.im.y);
+                }
+            }
+        }
+        __syncwarp();  // the slots are read before the next pair's exchange writes them
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(XWarp2::NT, 2)
+k_x_warp2_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__restrict__ tw, int npairs, int Px) {
+    static_assert(N == XWarp2::N, "one warp per row pair: 512 = 16 x 2 x 16");
+    constexpr long long NN = (long long)N * N;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    unsigned char *xo = base + XWarp2::OFF_XO;
+    float2 *T = reinterpret_cast<float2 *>(base + XWarp2::OFF_T);
+    float2 *T2 = reinterpret_cast<float2 *>(base + XWarp2::OFF_T2);
+    for (int i = threadIdx.x; i < 512; i += XWarp2::NT) T[i] = tw[2 * (i & 31) * (i >> 5)];
+    for (int i = threadIdx.x; i <= N / 2; i += XWarp2::NT) T2[i] = tw[i];
+    __syncthreads();
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
+    const ZwLane zl = zw_lane(tw, smem_addr(xo), g, q, 2);
+    const int stride = gridDim.x * XWarp2::NW;
+    for (long long i = (long long)blockIdx.x * XWarp2::NW + g; i < npairs; i += stride) {
+        const float2 *s0 = in + (2 * i) * Px, *s1 = s0 + Px;
+        float2 yk0[9], yk1[9], yn0[9], yn1[9];
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            const int k = q + 32 * k2;
+            if (k > N / 2) continue;
+            yk0[k2] = __ldg(s0 + k);
+            yk1[k2] = __ldg(s1 + k);
+            yn0[k2] = __ldg(s0 + (N - k));
+            yn1[k2] = __ldg(s1 + (N - k));
+        }
+        CV v[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            const int k = q + 32 * k2;
+            if (k > N / 2) continue;
+            if (k == 0) {
+                v[0] = {f2(yk0[0].x + yn0[0].x, yk1[0].x + yn1[0].x), f2(yk0[0].x - yn0[0].x, yk1[0].x - yn1[0].x)};
+            } else {
+                const CV yk = {f2(yk0[k2].x, yk1[k2].x), f2(yk0[k2].y, yk1[k2].y)};
+                const CV yn = {f2(yn0[k2].x, yn1[k2].x), f2(yn0[k2].y, yn1[k2].y)};
+                const CV ev = {f2add(yk.re, yn.re), f2sub(yk.im, yn.im)};
+                const CV od = zw_twmul<1>(CV{f2sub(yk.re, yn.re), f2add(yk.im, yn.im)}, T2[k]);
+                v[k2] = add_rot<1>(ev, od);
+                if (2 * k != N) zw_sts(smem_addr(xo) + zw_sw128(N - k, g), add_rot<1>(cconj_cv(ev), cconj_cv(od)));
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k2 = 8; k2 < 16; ++k2) {
+            const int k = q + 32 * k2;
+            if (k != N / 2) v[k2] = zw_lds(smem_addr(xo) + zw_sw128(k, g));
+        }
+        __syncwarp();
+        dft<16, 1>(v);
+        zw_exchange_adj(v, zl);
+        zw_back(v, zl, T);
+        const int b = (int)((2 * i) / NN);
+        float2 *d = reinterpret_cast<float2 *>(const_cast<void *>(u.p[b])) + (2 * i - b * NN) * (N / 2) + q;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            CV x = v[r];
+            if (r & 1) x = zw_sign(x, zl.sg);
+            d[32 * r] = f2(x.re.x, x.im.x);
+            d[N / 2 + 32 * r] = f2(x.re.y, x.im.y);
         }
         __syncwarp();  // the slots are read before the next pair writes them
     }

@@ -48,7 +48,7 @@ struct DevicePlan {
     // N = 256)
     int yform = 0;
     // x pass form: 0 block form (a tile of rows staged in shared memory), 1 warp form (a
-    // half-warp per row pair, FP32, N = 256)
+    // half-warp or warp per row pair, FP32, N = 256 and 512)
     int xform = 0;
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers; and of the warp-form z pass (w2 in,
@@ -85,7 +85,7 @@ cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArra
 int z_forms(int N, int dtype);
 
 // Forms of the x passes that exist for (N, dtype), as a bit mask over DevicePlan::xform:
-// bit 0 always; bit 1 for FP32 at N = 256.
+// bit 0 always; bit 1 for FP32 at N = 256 and 512.
 int x_forms(int N, int dtype);
 
 // The two x passes alone, one density on spare workspace, in the form p.xform selects.

@@ -25,7 +25,8 @@ def yforms(N, dtype):
     return [0] + ([1] if dtype == "f32" and N in WARP_N else [])
 
 
-xforms = yforms
+def xforms(N, dtype):
+    return [0] + ([1] if dtype == "f32" and N in (256, 512) else [])
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +68,7 @@ def solve_form(torch, N, L, tol, dtype, rho, form, yform=None, xform=None):
 def test_knob_codes(torch_cuda, dtype):
     from paper_1612_01799_gb300 import Plan, _lib
     lib = _lib.load()
-    for N in (4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384):
+    for N in (4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512):
         with Plan(N, 4.0, 1e-6, dtype) as p:
             have = forms(N, dtype)
             assert p.z_form in have
@@ -194,3 +195,16 @@ def test_warp_form_batched(torch_cuda, yform, xform):
         for r, o in zip(rhos, outs):
             assert torch.equal(p.solve(r), o)
         p.last_status()
+
+
+@pytest.mark.parametrize("xform", [0, 1])
+def test_x_forms_sampled_n512(torch_cuda, xform):
+    """N = 512 (the padded 1024^3 grid) in both x forms, FP32: output lines against the
+    oracle's real-space evaluation of the discrete convolution."""
+    N, L, tol = 512, 10.0, 1e-6
+    rho = D.config_aniso4(N=N, seed=512).gaussians.sample(N, L)
+    lines = [(0, 0), (N // 2, N // 2 - 1), (N - 1, N - 1), (N // 3, 2 * N // 3)]
+    ref = direct.sample_lines(rho, gtensor.make_plan(N, L, tol), lines)
+    u = solve_form(torch_cuda, N, L, tol, "f32", rho, 0, None, xform)
+    got = np.stack([u[z, y] for z, y in lines])
+    assert rel_l2(got, ref) <= TOL["f32"]
