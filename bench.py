@@ -278,6 +278,30 @@ def run_batched(torch, dev, steps, warmup, seed=4):
                         "anisotropic Gaussians each (seed 4), box [-10,10]^3, FP32"}
 
 
+def run_large(torch, dev, flush, steps, warmup, peak, N=512):
+    """Config 3, the large single solve (padded 1024^3), FP32: per-pass times against the
+    HBM roofline.  Reported next to the headline, not as it."""
+    import numpy as np
+    from paper_1612_01799_gb300 import Plan
+    from paper_1612_01799_gb300 import densities as D
+    wl = D.config_bump8(N=N)
+    rho = torch.from_numpy(wl.sample(np.float32)).to(dev)
+    with Plan(N, wl.L, TOL32, "f32") as plan:
+        out = torch.empty_like(rho)
+        totals, passes = time_solves(torch, plan, rho, out, steps, warmup, flush)
+        plan.last_status()
+        forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form]}
+    ms = statistics.mean(totals)
+    per = [statistics.mean(p[i] for p in passes) for i in range(5)]
+    b = pass_bytes(N, 4)
+    return {"value": N ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "dtype": "f32",
+            "passes": [{"pass": PASSES[i], "ms": per[i], "GB_s": b[i] / (per[i] * 1e-3) / 1e9,
+                        "frac": b[i] / (per[i] * 1e-3) / 1e9 / peak} for i in range(5)],
+            "forms": forms,
+            "workload": "config_large: (1-r^2/16)^4 on r<4 plus 8 Gaussians (widths U[0.3,1], seed 3), box "
+                        "[-6,6]^3, N=512 per axis, padded 1024^3, FP32, L2 flushed between steps"}
+
+
 def run_selector(n_train=384, n_test=128, epochs=3000):
     """Config 5: train the grid selector on densities 0..n_train-1 (labels from the method's
     own FP32 solves against exact potentials), then the gain test on the next n_test:
@@ -409,6 +433,8 @@ def run_ours(args):
                                "timed at plan creation, cached per (device, N, dtype)")},
             "clocks": r32["clocks"],
         }
+        if not args.no_large and world == 1:
+            line["large"] = run_large(torch, dev, flush, max(3, args.steps // 2), args.warmup, peak)
         if not args.no_batched:
             line["batched"] = run_batched(torch, dev, max(3, args.steps // 2), args.warmup)
         if not args.no_selector and world == 1:
@@ -436,6 +462,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the N=512 single-solve section")
     ap.add_argument("--no-selector", action="store_true")
     ap.add_argument("--z-form", choices=Z_FORMS, default=None,
                     help="pin the FP32 z-pass form (default: the plan's timed choice); for profiling")
