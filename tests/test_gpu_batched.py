@@ -79,3 +79,32 @@ def test_batched_graph_capture(torch_cuda):
         assert torch.equal(p.solve(r), o)
     for p in plans_by_n.values():
         p.close()
+
+
+def test_graph_capture_warp_forms(torch_cuda):
+    """A batched solve at N = 256 in the warp forms of all passes (persistent kernels with
+    TMA copies and mbarriers) captured in a CUDA graph and replayed on new inputs: equal to
+    the direct solves bit for bit."""
+    from paper_1612_01799_gb300 import Plan, solve_batched
+    torch = torch_cuda
+    spec = [(256, 21), (256, 22)]
+    rhos = _inputs(torch, spec)
+    with Plan(256, 10.0, 1e-6, "f32", max_batch=2) as p:
+        p.z_form, p.y_form, p.x_form = 2, 1, 1
+        outs = [torch.empty_like(r) for r in rhos]
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            solve_batched([p, p], rhos, outs, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            solve_batched([p, p], rhos, outs, stream=s)
+        for r, n in zip(rhos, _inputs(torch, [(256, 31), (256, 32)])):
+            r.copy_(n)
+        g.replay()
+        torch.cuda.synchronize()
+        for r, o in zip(rhos, outs):
+            assert torch.equal(p.solve(r), o)
+        p.last_status()
