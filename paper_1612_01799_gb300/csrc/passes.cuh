@@ -393,8 +393,11 @@ template <class K> static int persistent_blocks(K kernel, int threads, size_t sm
 }
 
 // Whether the warp form of the z pass exists (FP32, N = 256).
-template <typename Real, int N> constexpr bool zwarp_form() { return std::is_same<Real, float>::value && N == ZWarp::N; }
-inline bool zwarp_available(int N) { return N == ZWarp::N; }
+// The warp forms of the z and y passes and the half-warp x passes exist for FP32 at
+// N = 16 E1, E1 in {16, 12, 10}; the full-warp x passes at N = 512.
+inline constexpr bool warp_n(int N) { return N == 256 || N == 192 || N == 160; }
+template <typename Real, int N> constexpr bool zwarp_form() { return std::is_same<Real, float>::value && warp_n(N); }
+inline bool zwarp_available(int N) { return warp_n(N); }
 
 // The fused z pass (K3) of B densities in the form p.zform selects: the length-2N
 // transforms (0), the split into even and odd length-N transforms (1, where
@@ -412,10 +415,11 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
     const TwC *twc = static_cast<const TwC *>(p.twc);
     if constexpr (zwarp_form<Real, N>()) {
         if (p.zform == 2) {
-            static_assert(ZWarp::TC == L1::TC, "same tiles as the direct form");
-            auto k = tail ? k_z_warp<true> : k_z_warp<false>;
-            GSP_CHECK(set_smem(k, ZWarp::SMEM));
-            k<<<persistent_blocks(k, ZWarp::NT, ZWarp::SMEM, nt), ZWarp::NT, ZWarp::SMEM, s>>>(
+            using Z = ZWarp<N / 16>;
+            static_assert(Z::TC == L1::TC, "same tiles as the direct form");
+            auto k = tail ? k_z_warp<N / 16, true> : k_z_warp<N / 16, false>;
+            GSP_CHECK(set_smem(k, Z::SMEM));
+            k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s>>>(
                 p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status,
                 tail);
             return cudaGetLastError();
@@ -443,7 +447,7 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
 // block form (k_x_forward / k_x_inverse), 1 the warp form (FP32: k_x_warp_* at N = 256,
 // k_x_warp2_* at N = 512).
 template <typename Real, int N> constexpr bool xwarp_form() {
-    return std::is_same<Real, float>::value && (N == XWarp::N || N == XWarp2::N);
+    return std::is_same<Real, float>::value && (warp_n(N) || N == XWarp2::N);
 }
 
 template <typename Real, int N>
@@ -465,15 +469,16 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
                     k_x_warp2_inv<N><<<persistent_blocks(k_x_warp2_inv<N>, XWarp2::NT, XWarp2::SMEM, nw), XWarp2::NT,
                                        XWarp2::SMEM, s>>>(static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
             } else {
-                GSP_CHECK(set_smem(k_x_warp_fwd<N>, XWarp::SMEM));
-                GSP_CHECK(set_smem(k_x_warp_inv<N>, XWarp::SMEM));
+                using X = XWarp<N>;
+                GSP_CHECK(set_smem(k_x_warp_fwd<N>, X::SMEM));
+                GSP_CHECK(set_smem(k_x_warp_inv<N>, X::SMEM));
                 const int nw = (npairs + 15) / 16;
                 if (fwd)
-                    k_x_warp_fwd<N><<<persistent_blocks(k_x_warp_fwd<N>, XWarp::NT, XWarp::SMEM, nw), XWarp::NT,
-                                      XWarp::SMEM, s>>>(rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px);
+                    k_x_warp_fwd<N><<<persistent_blocks(k_x_warp_fwd<N>, X::NT, X::SMEM, nw), X::NT, X::SMEM, s>>>(
+                        rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px);
                 else
-                    k_x_warp_inv<N><<<persistent_blocks(k_x_warp_inv<N>, XWarp::NT, XWarp::SMEM, nw), XWarp::NT,
-                                      XWarp::SMEM, s>>>(static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
+                    k_x_warp_inv<N><<<persistent_blocks(k_x_warp_inv<N>, X::NT, X::SMEM, nw), X::NT, X::SMEM, s>>>(
+                        static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
             }
             return cudaGetLastError();
         }
@@ -494,7 +499,7 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
 
 // The y passes (K2 forward, K4 inverse) of B densities in the form p.yform selects: 0 the
 // block form (k_col_tma), 1 the warp form (k_y_warp, ywarp_form); an absent form runs as 0.
-template <typename Real, int N> constexpr bool ywarp_form() { return std::is_same<Real, float>::value && N == YWarp::N; }
+template <typename Real, int N> constexpr bool ywarp_form() { return std::is_same<Real, float>::value && warp_n(N); }
 
 template <typename Real, int N>
 cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
@@ -504,11 +509,12 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
     const int ncols = N + 1;
     if constexpr (ywarp_form<Real, N>()) {
         if (p.yform == 1) {
-            const int ntx = (ncols + YWarp::TC - 1) / YWarp::TC, nt = ntx * B * N;
-            auto k = fwd ? k_y_warp<true> : k_y_warp<false>;
-            const int smem = fwd ? YWarp::SMEM_F : YWarp::SMEM_I;
+            using Y = YWarp<N / 16>;
+            const int ntx = (ncols + Y::TC - 1) / Y::TC, nt = ntx * B * N;
+            auto k = fwd ? k_y_warp<N / 16, true> : k_y_warp<N / 16, false>;
+            const int smem = fwd ? Y::SMEM_F : Y::SMEM_I;
             GSP_CHECK(set_smem(k, smem));
-            k<<<persistent_blocks(k, YWarp::NT, smem, nt), YWarp::NT, smem, s>>>(
+            k<<<persistent_blocks(k, Y::NT, smem, nt), Y::NT, smem, s>>>(
                 fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1, static_cast<const float2 *>(p.tw), ntx, nt,
                 ncols, p.status);
             return cudaGetLastError();
@@ -612,22 +618,23 @@ cudaError_t encode_n(DevicePlan &p) {
     GSP_CHECK(encode_3d(&p.tm_yi_in, U64, p.w3, (N + 1) * u, L, BN, rowb, (cuuint64_t)L * rowb,
                         L2::ROWB / 8, L2::RPC, 1));
     if constexpr (ywarp_form<Real, N>()) {
-        // 256-row boxes of w1, w2, w3 (16 columns x y or ky rows x 1 plane), 128-byte swizzle.
-        GSP_CHECK(encode_3d(&p.tm_yw1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, YWarp::TC, 256, 1,
+        // N-row boxes of w1, w2, w3 (16 columns x N rows of y or ky x 1 plane), 128-byte swizzle.
+        GSP_CHECK(encode_3d(&p.tm_yw1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16>::TC, N, 1,
                             CU_TENSOR_MAP_SWIZZLE_128B));
-        GSP_CHECK(encode_3d(&p.tm_yw2, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp::TC, 256, 1,
+        GSP_CHECK(encode_3d(&p.tm_yw2, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16>::TC, N, 1,
                             CU_TENSOR_MAP_SWIZZLE_128B));
-        GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp::TC, 256, 1,
+        GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16>::TC, N, 1,
                             CU_TENSOR_MAP_SWIZZLE_128B));
     }
     if constexpr (zwarp_form<Real, N>()) {
         // Columns kx > N lie outside these maps: loads read zeros there, stores skip them.
-        GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp::TC, 1, N,
+        GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp<N / 16>::TC, 1, N,
                             CU_TENSOR_MAP_SWIZZLE_128B));
-        GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp::TC, 1, N,
+        GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp<N / 16>::TC, 1, N,
                             CU_TENSOR_MAP_SWIZZLE_128B));
         GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
-                            (cuuint64_t)(N + 1) * srow, ZWarp::TC, 1, ZWarp::SYM_RPC, CU_TENSOR_MAP_SWIZZLE_64B));
+                            (cuuint64_t)(N + 1) * srow, ZWarp<N / 16>::TC, 1, ZWarp<N / 16>::SYM_RPC,
+                            CU_TENSOR_MAP_SWIZZLE_64B));
     }
     return cudaSuccess;
 }

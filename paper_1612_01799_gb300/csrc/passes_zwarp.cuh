@@ -1,4 +1,10 @@
-// Fused z pass (K3), warp form, FP32, length L = 2N = 512 (N = 256).
+// Warp forms of the passes, FP32.  The fused z pass (K3) at N = 16 E1, L = 2N = 32 E1 for a
+// first-stage length E1 in {16, 12, 10} (N = 256, 192, 160); the y passes (K2, K4) on its
+// transform halves; the x passes (K1, K5) at N = 16 E1 with a half-warp per row pair and at
+// N = 512 with a warp per row pair.  The description below is for E1 = 16; for E1 < 16
+// the first stage is a pruned E1-point DFT (E1 / 2 nonzero inputs), the lane-pair radix 2
+// pairs the halves of its outputs the same way, and only the 2 E1 lanes l with
+// (l & 7) < E1 / 2 gather after the exchange (the others idle through the 16-point DFTs).
 //
 // Same operation as k_z_symbol_tma: per column (kx, ky) of w2, the pruned length-2N forward
 // DFT along z, the product with the symbol G(|kx|, |ky|, |kz|), the inverse DFT and the crop
@@ -49,14 +55,18 @@
 
 namespace gsp {
 
-struct ZWarp {
-    static constexpr int L = 512, N = 256, TC = 16, NW = 8, NT = 256;
-    static constexpr int SYM_RPC = 136, SYM_NCP = 2;  // symbol rows per TMA copy, copies
-    static constexpr int IN_BYTES = N * TC * 8;       // 32 KB
+template <int E1> struct ZWarp {
+    static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N, TC = 16, NW = 8, NT = 256;
+    static constexpr int SYM_NCP = (N + 1 + 255) / 256;                              // symbol TMA copies
+    static constexpr int SYM_RPC = ((N + 1 + SYM_NCP - 1) / SYM_NCP + 7) / 8 * 8;    // rows per copy
+    static constexpr int IN_BYTES = N * TC * 8;
     static constexpr int SYM_BYTES = SYM_NCP * SYM_RPC * TC * 4;
-    static constexpr int OFF_B = 0, OFF_XO = 32768, OFF_T = OFF_XO + 65536, OFF_BAR = OFF_T + 16 * 32 * 8;
+    static constexpr int B_BYTES = IN_BYTES > SYM_BYTES ? IN_BYTES : SYM_BYTES;
+    static constexpr int OFF_B = 0, OFF_XO = (B_BYTES + 1023) / 1024 * 1024, OFF_T = OFF_XO + 65536;
+    static constexpr int OFF_BAR = OFF_T + E1 * 32 * 8;
     static constexpr int SMEM = 1024 + OFF_BAR + 64;  // 1 KB alignment slack
-    static_assert(SYM_BYTES <= 32768 && SYM_NCP * SYM_RPC >= N + 1, "symbol rows fit B");
+    static_assert(E1 == 16 || E1 == 12 || E1 == 10, "first stage: a pruned DFT of E1 / 2 inputs");
+    static_assert(SYM_NCP * SYM_RPC >= N + 1 && SYM_RPC <= 256, "symbol rows fit the TMA boxes");
     static_assert((SYM_RPC * TC * 4) % 512 == 0, "64-byte-swizzled copies start 512-byte aligned");
 };
 
@@ -73,42 +83,63 @@ template <int D> __device__ __forceinline__ CV zw_rot(CV a) {
     return D < 0 ? CV{a.im, f2neg(a.re)} : CV{f2neg(a.im), a.re};
 }
 
-// exp(-2 pi i r / 16), r < 8
-__device__ __forceinline__ constexpr float zw_c16(int r) {
-    return r == 0 ? 1.f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
-         : r == 3 ? 0.38268343236508977173f : r == 4 ? 0.f : r == 5 ? -0.38268343236508977173f
-         : r == 6 ? -0.70710678118654752440f : -0.92387953251128675613f;
+// exp(-2 pi i r / E) = (zw_cw, zw_sw), r < E / 2, E in {10, 12, 16}.
+__host__ __device__ constexpr float zw_cw(int E, int r) {
+    return E == 16 ? (r == 0 ? 1.f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
+                      : r == 3 ? 0.38268343236508977173f : r == 4 ? 0.f : r == 5 ? -0.38268343236508977173f
+                      : r == 6 ? -0.70710678118654752440f : -0.92387953251128675613f)
+         : E == 12 ? (r == 0 ? 1.f : r == 1 ? 0.86602540378443864676f : r == 2 ? 0.5f : r == 3 ? 0.f
+                      : r == 4 ? -0.5f : -0.86602540378443864676f)
+                   : (r == 0 ? 1.f : r == 1 ? 0.80901699437494742410f : r == 2 ? 0.30901699437494742410f
+                      : r == 3 ? -0.30901699437494742410f : -0.80901699437494742410f);
 }
-__device__ __forceinline__ constexpr float zw_s16(int r) {  // imaginary part
-    return r == 0 ? 0.f : r == 1 ? -0.38268343236508977173f : r == 2 ? -0.70710678118654752440f
-         : r == 3 ? -0.92387953251128675613f : r == 4 ? -1.f : r == 5 ? -0.92387953251128675613f
-         : r == 6 ? -0.70710678118654752440f : -0.38268343236508977173f;
+__host__ __device__ constexpr float zw_sw(int E, int r) {
+    return E == 16 ? (r == 0 ? 0.f : r == 1 ? -0.38268343236508977173f : r == 2 ? -0.70710678118654752440f
+                      : r == 3 ? -0.92387953251128675613f : r == 4 ? -1.f : r == 5 ? -0.92387953251128675613f
+                      : r == 6 ? -0.70710678118654752440f : -0.38268343236508977173f)
+         : E == 12 ? (r == 0 ? 0.f : r == 1 ? -0.5f : r == 2 ? -0.86602540378443864676f : r == 3 ? -1.f
+                      : r == 4 ? -0.86602540378443864676f : -0.5f)
+                   : (r == 0 ? 0.f : r == 1 ? -0.58778525229247312917f : r == 2 ? -0.95105651629515357212f
+                      : r == 3 ? -0.95105651629515357212f : -0.58778525229247312917f);
 }
 
-// F1: forward 16-point DFT of v[0..7] (inputs 8..15 zero): v[m] = X[2m], v[8+m] = X[2m+1]
-// (X[2m] = DFT8(a)[m], X[2m+1] = DFT8(a_r W_16^r)[m]).
-__device__ __forceinline__ void zw_f1(CV *v) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        if (r == 0) v[8] = v[0];
-        else if (r == 4) v[12] = zw_rot<-1>(v[4]);
-        else v[8 + r] = cmulk<-1>(v[r], zw_c16(r), zw_s16(r));
+// Register maps of the first stage (E1 outputs, H = E1 / 2): register j holds
+// k1 = kappa0(j) on the lower half-warp (2j for j < H, 2(j - H) + 1 otherwise); the keep
+// set K holds kappa0 < H, and partner(j) is the register holding kappa0(j) + H.
+template <int E1> struct ZwMap {
+    static constexpr int H = E1 / 2;
+    __host__ __device__ static constexpr int kappa0(int j) { return j < H ? 2 * j : 2 * (j - H) + 1; }
+    __host__ __device__ static constexpr bool inK(int j) { return kappa0(j) < H; }
+    __host__ __device__ static constexpr int partner(int j) {
+        return (kappa0(j) + H) % 2 == 0 ? (kappa0(j) + H) / 2 : H + (kappa0(j) + H - 1) / 2;
     }
-    dft<8, -1>(v);
-    dft<8, -1>(v + 8);
-}
-// Adjoint of F1: y_r = IDFT8(v[0..7])[r] + conj(W_16^r) IDFT8(v[8..15])[r], r < 8, in v[0..7].
-__device__ __forceinline__ void zw_f1_adj(CV *v) {
-    dft<8, 1>(v);
-    dft<8, 1>(v + 8);
+};
+
+// F1: forward E1-point DFT of v[0..H-1] (inputs H..E1-1 zero): v[m] = X[2m], v[H+m] = X[2m+1]
+// (X[2m] = DFT_H(a)[m], X[2m+1] = DFT_H(a_r W_E1^r)[m]).
+template <int E1> __device__ __forceinline__ void zw_f1(CV *v) {
+    constexpr int H = E1 / 2;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const CV o = r == 0 ? v[8] : r == 4 ? zw_rot<1>(v[12]) : cmulk<1>(v[8 + r], zw_c16(r), zw_s16(r));
+    for (int r = 0; r < H; ++r) {
+        if (r == 0) v[H] = v[0];
+        else if (4 * r == E1) v[H + r] = zw_rot<-1>(v[r]);
+        else v[H + r] = cmulk<-1>(v[r], zw_cw(E1, r), zw_sw(E1, r));
+    }
+    dft<H, -1>(v);
+    dft<H, -1>(v + H);
+}
+// Adjoint of F1: y_r = IDFT_H(v[0..H-1])[r] + conj(W_E1^r) IDFT_H(v[H..E1-1])[r], r < H, in v[0..H-1].
+template <int E1> __device__ __forceinline__ void zw_f1_adj(CV *v) {
+    constexpr int H = E1 / 2;
+    dft<H, 1>(v);
+    dft<H, 1>(v + H);
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        const CV o = r == 0 ? v[H] : 4 * r == E1 ? zw_rot<1>(v[H + r]) : cmulk<1>(v[H + r], zw_cw(E1, r), zw_sw(E1, r));
         v[r] = cadd(v[r], o);
     }
 }
 
-__device__ __forceinline__ int zw_kappa0(int j) { return j < 8 ? 2 * j : 2 * (j - 8) + 1; }
 // Byte offset of row `row` of warp g in a 128-byte-swizzled region.
 __device__ __forceinline__ int zw_sw128(int row, int g) { return row * 128 + ((g ^ (row & 7)) << 4); }
 
@@ -136,93 +167,105 @@ __device__ __forceinline__ CV zw_shfl16(CV x) {
 // region at shared address xo with warp g owning chunk g ^ (row & 7) of its 512 rows).
 struct ZwLane {
     float2 tw32;   // F3 twiddle sgn W_32^{q'} (sgn = -1 on the upper half-warp)
-    int tkb, tnb;  // twiddle-table bases of the registers in K (k1 = kappa0 + 8 s) and outside
+    int tkb, tnb;  // twiddle-table bases of the registers in K (k1 = kappa0 + H s) and outside
     float sg;      // sign of the odd inputs / outputs of the upper half-warp
     uint32_t aw;   // exchange writer base: position q' of reader l = kappa0 + 8 s + 16 t
     uint32_t ar;   // exchange reader base: reader q, row 16 q + (p ^ (q & 7))
+    bool rd;       // lane q gathers after the exchange ((q & 7) < H)
 };
-// tw: W_512^e (twstride 1) or W_1024^e (twstride 2).
+// tw: W_L^e (twstride 1) or W_2L^e (twstride 2), L = 32 E1.
+template <int E1>
 __device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_t xo, int g, int q, int twstride = 1) {
+    constexpr int H = E1 / 2;
     const int s = q >> 4, qp = q & 15;
     ZwLane z;
-    z.tw32 = tw[16 * qp * twstride];
+    z.tw32 = tw[E1 * qp * twstride];
     if (s) z.tw32 = f2(-z.tw32.x, -z.tw32.y);
-    z.tkb = q + 256 * s;
-    z.tnb = q - 256 * s;
+    z.tkb = q + 32 * H * s;
+    z.tnb = q - 32 * H * s;
     z.sg = s ? -1.f : 1.f;
     z.aw = xo + 16384 * s + 128 * qp + 16 * (g ^ (qp & 7));
     z.ar = xo + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
+    z.rd = (q & 7) < H;
     return z;
 }
 __device__ __forceinline__ CV cconj_cv(CV a) { return {a.re, f2neg(a.im)}; }
 __device__ __forceinline__ CV zw_sign(CV x, float sg) { return {f2mul(x.re, f2(sg, sg)), f2mul(x.im, f2(sg, sg))}; }
 
-// F1 (inputs v[0..7], odd ones already signed), F2 and F3 with its twiddle.
-__device__ __forceinline__ void zw_front(CV *v, const ZwLane &z, const float2 *T) {
-    zw_f1(v);
+// F1 (inputs v[0..H-1], odd ones already signed), F2 and F3 with its twiddle.
+template <int E1> __device__ __forceinline__ void zw_front(CV *v, const ZwLane &z, const float2 *T) {
+    using M = ZwMap<E1>;
+    zw_f1<E1>(v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = zw_twmul<-1>(v[j], T[((j & 4) ? z.tnb : z.tkb) + 32 * zw_kappa0(j)]);
+    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<-1>(v[j], T[(M::inK(j) ? z.tkb : z.tnb) + 32 * M::kappa0(j)]);
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        if (j & 4) continue;
-        const CV rcv = zw_shfl16(v[j + 4]);
+    for (int j = 0; j < E1; ++j) {
+        if (!M::inK(j)) continue;
+        const CV rcv = zw_shfl16(v[M::partner(j)]);
         const CV a = v[j];
         v[j] = cadd(a, rcv);
-        v[j + 4] = zw_twmul<-1>(csub(a, rcv), z.tw32);
+        v[M::partner(j)] = zw_twmul<-1>(csub(a, rcv), z.tw32);
     }
 }
-// F5: write the values this lane holds as writer, gather its 16 as reader.
-__device__ __forceinline__ void zw_exchange(CV *v, const ZwLane &z) {
+// F5: write the values this lane holds as writer, gather its 16 as reader (reader lanes).
+template <int E1> __device__ __forceinline__ void zw_exchange(CV *v, const ZwLane &z) {
+    using M = ZwMap<E1>;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        if (j & 4) continue;
-        const int k0 = zw_kappa0(j);
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt) zw_sts((z.aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt, v[j + 4 * tt]);
+    for (int j = 0; j < E1; ++j) {
+        if (!M::inK(j)) continue;
+        const int k0 = M::kappa0(j);
+        zw_sts((z.aw ^ (144 * k0)) + 2048 * k0, v[j]);
+        zw_sts((z.aw ^ (144 * k0)) + 2048 * k0 + 32768, v[M::partner(j)]);
     }
     __syncwarp();
+    if (z.rd) {
 #pragma unroll
-    for (int p = 0; p < 16; ++p) v[p] = zw_lds((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3));
+        for (int p = 0; p < 16; ++p) v[p] = zw_lds((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3));
+    }
 }
 // Adjoint of F5.
-__device__ __forceinline__ void zw_exchange_adj(CV *v, const ZwLane &z) {
+template <int E1> __device__ __forceinline__ void zw_exchange_adj(CV *v, const ZwLane &z) {
+    using M = ZwMap<E1>;
+    if (z.rd) {
 #pragma unroll
-    for (int p = 0; p < 16; ++p) zw_sts((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3), v[p]);
+        for (int p = 0; p < 16; ++p) zw_sts((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3), v[p]);
+    }
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        if (j & 4) continue;
-        const int k0 = zw_kappa0(j);
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt) v[j + 4 * tt] = zw_lds((z.aw ^ (144 * k0)) + 2048 * k0 + 32768 * tt);
+    for (int j = 0; j < E1; ++j) {
+        if (!M::inK(j)) continue;
+        const int k0 = M::kappa0(j);
+        v[j] = zw_lds((z.aw ^ (144 * k0)) + 2048 * k0);
+        v[M::partner(j)] = zw_lds((z.aw ^ (144 * k0)) + 2048 * k0 + 32768);
     }
 }
-// Adjoints of F3 (with its twiddle), F2 and F1: the outputs r < 8 in v[0..7], odd ones
+// Adjoints of F3 (with its twiddle), F2 and F1: the outputs r < H in v[0..H-1], odd ones
 // still to be signed.
-__device__ __forceinline__ void zw_back(CV *v, const ZwLane &z, const float2 *T) {
+template <int E1> __device__ __forceinline__ void zw_back(CV *v, const ZwLane &z, const float2 *T) {
+    using M = ZwMap<E1>;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        if (j & 4) continue;
-        const CV b = zw_twmul<1>(v[j + 4], z.tw32);
+    for (int j = 0; j < E1; ++j) {
+        if (!M::inK(j)) continue;
+        const CV b = zw_twmul<1>(v[M::partner(j)], z.tw32);
         const CV a = v[j];
         v[j] = cadd(a, b);
-        v[j + 4] = zw_shfl16(csub(a, b));
+        v[M::partner(j)] = zw_shfl16(csub(a, b));
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = zw_twmul<1>(v[j], T[((j & 4) ? z.tnb : z.tkb) + 32 * zw_kappa0(j)]);
-    zw_f1_adj(v);
+    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<1>(v[j], T[(M::inK(j) ? z.tkb : z.tnb) + 32 * M::kappa0(j)]);
+    zw_f1_adj<E1>(v);
 }
 
 // Tile t = (tx, ky, b): tx the 16-column block, consecutive tiles take ky and its mirror
 // 2N - ky (same symbol rows), b the density.  With TAIL the forward spectrum's shell and
 // total energies are added to tail[2 b], tail[2 b + 1] (as in k_z_symbol_tma).
-template <bool TAIL>
-__global__ void __launch_bounds__(ZWarp::NT, 2)
+template <int E1, bool TAIL>
+__global__ void __launch_bounds__(ZWarp<E1>::NT, 2)
 k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
          const __grid_constant__ CUtensorMap tout, const float2 *__restrict__ tw, int ntx, int ntiles,
          int ncols, int *__restrict__ status, double *__restrict__ tail) {
-    using Z = ZWarp;
-    constexpr int L = Z::L, N = Z::N, NW = Z::NW;
+    using Z = ZWarp<E1>;
+    constexpr int L = Z::L, N = Z::N, NW = Z::NW, H = Z::H;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *Bb = base + Z::OFF_B;
@@ -239,7 +282,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         cnt[0] = cnt[1] = cnt[2] = 0;
         fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < 512; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    for (int i = threadIdx.x; i < E1 * 32; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
 
     auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
@@ -275,11 +318,11 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
 
-    const ZwLane zl = zw_lane(tw, smem_addr(xo), g, q);
+    const ZwLane zl = zw_lane<E1>(tw, smem_addr(xo), g, q);
     // Input/output rows q + 32 r of this warp's 16-byte chunk.
     const int io = zw_sw128(q, g);
-    // Symbol rows: this lane holds kz = kb + 32 k2 (k2 < 8) and 2N - kb - 32 k2 (k2 >= 8).
-    const int kb = q;
+    // Symbol rows: reader q holds kz = kb + 2 E1 k2 (k2 < 8) and 2N - kb - 2 E1 k2 (k2 >= 8).
+    const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
     const int sym_lo = 64 * kb + ((8 * g) ^ (((kb >> 1) & 3) << 4));
     const int sym_hi = 64 * (L - kb) + ((8 * g) ^ ((((L - kb) >> 1) & 3) << 4));
     bool stored = false;
@@ -293,28 +336,28 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (!mbar_wait(bar, ph, status)) return;
         if (valid) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < H; ++r) {
                 const float4 f = *reinterpret_cast<const float4 *>(Bb + io + 4096 * r);
                 v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
                 if (r & 1) v[r] = zw_sign(v[r], zl.sg);
             }
         }
         if (last_arrival(0)) issue_sym(t);
-        if (valid) zw_front(v, zl, T);
+        if (valid) zw_front<E1>(v, zl, T);
         if (!mbar_wait(bar + 2, ph, status)) return;  // the previous tile's store has read XO
         if (valid) {
-            zw_exchange(v, zl);
-            dft<16, -1>(v);  // v[k2] = X[kb + 32 k2]
+            zw_exchange<E1>(v, zl);
+            if (zl.rd) dft<16, -1>(v);  // v[k2] = X[kb + 2 E1 k2]
         }
         if constexpr (TAIL) {
             constexpr int SHELL = N - N / 8;
             float eshell = 0.f, etot = 0.f;
-            if (valid) {
+            if (valid && zl.rd) {
                 const float w0 = (col == 0 || col == N) ? 1.f : 2.f;
                 const float w1 = col + 1 > N ? 0.f : (col + 1 == N) ? 1.f : 2.f;
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2) {
-                    const int kz = k2 < 8 ? kb + 32 * k2 : L - kb - 32 * k2;
+                    const int kz = k2 < 8 ? kb + 2 * E1 * k2 : L - kb - 2 * E1 * k2;
                     const float2 en = cenergy(v[k2]);
                     const bool sh = kz >= SHELL || kya >= SHELL;
                     etot += w0 * en.x + w1 * en.y;
@@ -333,23 +376,30 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             }
         }
         if (!mbar_wait(bar + 1, ph, status)) return;
-        if (valid) {
+        if (valid && zl.rd) {
 #pragma unroll
             for (int k2 = 0; k2 < 16; ++k2) {
-                const int off = k2 < 8 ? sym_lo + 2048 * k2 : sym_hi - 2048 * k2;
+                int off;
+                if constexpr ((2 * E1) % 8 == 0) {  // (kz >> 1) & 3 is the lane's own
+                    off = k2 < 8 ? sym_lo + 128 * E1 * k2 : sym_hi - 128 * E1 * k2;
+                } else {
+                    const int kz = k2 < 8 ? kb + 2 * E1 * k2 : L - kb - 2 * E1 * k2;
+                    const int A = 64 * kz + 8 * g;
+                    off = A ^ (((A >> 7) & 3) << 4);
+                }
                 v[k2] = cscale2(v[k2], *reinterpret_cast<const float2 *>(Bb + off));
             }
         }
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
         if (valid) {
-            dft<16, 1>(v);
-            zw_exchange_adj(v, zl);
-            zw_back(v, zl, T);
+            if (zl.rd) dft<16, 1>(v);
+            zw_exchange_adj<E1>(v, zl);
+            zw_back<E1>(v, zl, T);
         }
         __syncwarp();  // every lane's exchange reads are done: the slots take the outputs
         if (valid) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < H; ++r) {
                 CV x = v[r];
                 if (r & 1) x = zw_sign(x, zl.sg);
                 *reinterpret_cast<float4 *>(xo + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
@@ -384,20 +434,22 @@ namespace gsp {
 //     the next tile's exchange once the store has read it;
 //   y inverse: one 64 KB buffer for the 2N input rows, the exchange and the N output rows;
 //     the next tile's load follows the store's read of it.
-struct YWarp {
-    static constexpr int L = 512, N = 256, TC = 16, NW = 8, NT = 256;
-    static constexpr int OFF_T = 16 * 32 * 8;                       // after the buffers below
-    static constexpr int F_IN = 0, F_XB = 32768, F_T = F_XB + 65536, F_BAR = F_T + OFF_T;
-    static constexpr int I_XB = 0, I_T = 65536, I_BAR = I_T + OFF_T;
+template <int E1> struct YWarp {
+    static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N, TC = 16, NW = 8, NT = 256;
+    static constexpr int T_BYTES = E1 * 32 * 8;
+    static constexpr int F_IN = 0, F_XB = (N * 128 + 1023) / 1024 * 1024, F_T = F_XB + 65536;
+    static constexpr int F_BAR = F_T + T_BYTES;
+    static constexpr int I_XB = 0, I_T = 65536, I_BAR = I_T + T_BYTES;
     static constexpr int SMEM_F = 1024 + F_BAR + 64, SMEM_I = 1024 + I_BAR + 64;
+    static_assert((N * 128) % 1024 == 0, "the second half of a 2N-row tile starts 1024-byte aligned");
 };
 
-template <bool FWD>
-__global__ void __launch_bounds__(YWarp::NT, 2)
+template <int E1, bool FWD>
+__global__ void __launch_bounds__(YWarp<E1>::NT, 2)
 k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
          const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status) {
-    using Y = YWarp;
-    constexpr int NW = Y::NW;
+    using Y = YWarp<E1>;
+    constexpr int NW = Y::NW, N = Y::N, H = Y::H;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *inb = base + (FWD ? Y::F_IN : Y::I_XB);
@@ -412,13 +464,13 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         cnt[0] = cnt[1] = 0;
         fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < 512; i += Y::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    for (int i = threadIdx.x; i < E1 * 32; i += Y::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
     auto issue_in = [&](int t) {
         const int tx = t % ntx, zz = t / ntx;
-        mbar_arrive_expect_tx(bar, FWD ? 32768 : 65536);
+        mbar_arrive_expect_tx(bar, (FWD ? 1 : 2) * N * 128);
         tma_load_3d(inb, &tin, bar, tx * Y::TC, 0, zz);
-        if (!FWD) tma_load_3d(inb + 32768, &tin, bar, tx * Y::TC, 256, zz);
+        if (!FWD) tma_load_3d(inb + N * 128, &tin, bar, tx * Y::TC, N, zz);
     };
     auto last_arrival = [&](int c) {
         __syncwarp();
@@ -437,8 +489,11 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (FWD) mbar_arrive(bar + 1);  // the exchange/output buffer starts free
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
-    const ZwLane zl = zw_lane(tw, smem_addr(xb), g, q);
+    const ZwLane zl = zw_lane<E1>(tw, smem_addr(xb), g, q);
     const int io = zw_sw128(q, g);
+    // Rows of the 2N-point spectrum a reader holds: kb + 2 E1 k2.
+    const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
+    auto krow = [&](int k2) { return zw_sw128(kb + 2 * E1 * k2, g); };
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
@@ -450,40 +505,41 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if constexpr (FWD) {
             if (valid) {
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < H; ++r) {
                     const float4 f = *reinterpret_cast<const float4 *>(inb + io + 4096 * r);
                     v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
                     if (r & 1) v[r] = zw_sign(v[r], zl.sg);
                 }
             }
             if (last_arrival(0) && more) issue_in(t + gridDim.x);
-            if (valid) zw_front(v, zl, T);
+            if (valid) zw_front<E1>(v, zl, T);
             if (!mbar_wait(bar + 1, ph, status)) return;  // the previous tile's store has read xb
             if (valid) {
-                zw_exchange(v, zl);
-                dft<16, -1>(v);  // v[k2] = X[q + 32 k2]
+                zw_exchange<E1>(v, zl);
+                if (zl.rd) dft<16, -1>(v);  // v[k2] = X[kb + 2 E1 k2]
             }
             __syncwarp();
-            if (valid) {
+            if (valid && zl.rd) {
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2)
-                    *reinterpret_cast<float4 *>(xb + io + 4096 * k2) =
-                        make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
+                    *reinterpret_cast<float4 *>(xb + krow(k2)) = make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
             }
         } else {
             if (valid) {
+                if (zl.rd) {
 #pragma unroll
-                for (int k2 = 0; k2 < 16; ++k2) {
-                    const float4 f = *reinterpret_cast<const float4 *>(xb + io + 4096 * k2);
-                    v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
+                    for (int k2 = 0; k2 < 16; ++k2) {
+                        const float4 f = *reinterpret_cast<const float4 *>(xb + krow(k2));
+                        v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
+                    }
+                    dft<16, 1>(v);
                 }
-                dft<16, 1>(v);
                 __syncwarp();  // every lane has read its inputs: its chunks take exchange slots
-                zw_exchange_adj(v, zl);
-                zw_back(v, zl, T);
+                zw_exchange_adj<E1>(v, zl);
+                zw_back<E1>(v, zl, T);
                 __syncwarp();
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < H; ++r) {
                     CV x = v[r];
                     if (r & 1) x = zw_sign(x, zl.sg);
                     *reinterpret_cast<float4 *>(xb + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
@@ -493,7 +549,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         fence_proxy_async();
         if (last_arrival(1)) {
             tma_store_3d(&tout, xb, tx * Y::TC, 0, zz);
-            if (FWD) tma_store_3d(&tout, xb + 32768, tx * Y::TC, 256, zz);
+            if (FWD) tma_store_3d(&tout, xb + N * 128, tx * Y::TC, N, zz);
             bulk_commit();
             bulk_wait_read0();
             stored = true;
@@ -522,73 +578,80 @@ namespace gsp {
 // Rows are read and written straight from HBM: 16 lanes x 8 bytes = one 128-byte line per
 // row and instruction.  Persistent CTAs; the x forward loads the next row pair while it
 // transforms the current one.
-struct XWarp {
-    static constexpr int N = 256, NT = 256;
-    static constexpr int OFF_X = 0, OFF_T = OFF_X + 16 * 4096, OFF_T2 = OFF_T + 256 * 8;
-    static constexpr int SMEM = OFF_T2 + 129 * 8;
+template <int N> struct XWarp {
+    static constexpr int E1 = N / 16, H = E1 / 2, NT = 256;
+    static constexpr int OFF_X = 0, OFF_T = OFF_X + 16 * 4096, OFF_T2 = OFF_T + E1 * 16 * 8;
+    static constexpr int SMEM = OFF_T2 + (N / 2 + 1) * 8;
+    static_assert(E1 == 16 || E1 == 12 || E1 == 10, "N = 16 E1 with a pruned first stage of E1 / 2 inputs");
 };
 
-// Twiddle tables of the x passes from W_512^e: T[k1 * 16 + q'] = W_256^{q' k1},
-// T2[k] = W_512^k (k <= N/2).
-__device__ __forceinline__ void xw_tables(float2 *T, float2 *T2, const float2 *__restrict__ tw) {
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) T[i] = tw[2 * (i & 15) * (i >> 4)];
-    for (int i = threadIdx.x; i <= 128; i += blockDim.x) T2[i] = tw[i];
+// Twiddle tables of the x passes from W_2N^e: T[k1 * 16 + q'] = W_N^{q' k1}, T2[k] = W_2N^k
+// (k <= N/2).
+template <int N> __device__ __forceinline__ void xw_tables(float2 *T, float2 *T2, const float2 *__restrict__ tw) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) T[i] = tw[2 * (i & 15) * (i >> 4)];
+    for (int i = threadIdx.x; i <= N / 2; i += blockDim.x) T2[i] = tw[i];
 }
 
 template <int N>
-__global__ void __launch_bounds__(XWarp::NT, 2)
+__global__ void __launch_bounds__(XWarp<N>::NT, 2)
 k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restrict__ tw, int npairs, int Px) {
-    static_assert(N == XWarp::N, "the half-warp schedule is 16 x 16");
-    constexpr int NN = N * N;
+    using X = XWarp<N>;
+    using M = ZwMap<X::E1>;
+    constexpr int E1 = X::E1, H = X::H, NN = N * N;
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *T = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T);
-    float2 *T2 = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T2);
-    xw_tables(T, T2, tw);
+    float2 *T = reinterpret_cast<float2 *>(smraw + X::OFF_T);
+    float2 *T2 = reinterpret_cast<float2 *>(smraw + X::OFF_T2);
+    xw_tables<N>(T, T2, tw);
     __syncthreads();
     const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
-    const uint32_t xs = smem_addr(smraw + XWarp::OFF_X) + 4096 * hw;
+    const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
     const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
-    const int stride = gridDim.x * (XWarp::NT / 16);
+    const bool rd = qq < E1;  // lane qq gathers k1 = qq after the exchange
+    const int stride = gridDim.x * (X::NT / 16);
     auto load = [&](int i, float2 *f) {
         const int b = (2 * i) / NN;
         const float2 *s = reinterpret_cast<const float2 *>(rho.p[b]) + (long long)(2 * i - b * NN) * (N / 2) + qq;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < H; ++r) {
             f[2 * r] = __ldg(s + 16 * r);
             f[2 * r + 1] = __ldg(s + N / 2 + 16 * r);
         }
     };
-    int i = blockIdx.x * (XWarp::NT / 16) + hw;
-    float2 f[16];
+    int i = blockIdx.x * (X::NT / 16) + hw;
+    float2 f[2 * H];
     if (i < npairs) load(i, f);
     for (; i < npairs; i += stride) {
         CV v[16];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = {f2(f[2 * r].x, f[2 * r + 1].x), f2(f[2 * r].y, f[2 * r + 1].y)};
+        for (int r = 0; r < H; ++r) v[r] = {f2(f[2 * r].x, f[2 * r + 1].x), f2(f[2 * r].y, f[2 * r + 1].y)};
         if (i + stride < npairs) load(i + stride, f);
-        zw_f1(v);
+        zw_f1<E1>(v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = zw_twmul<-1>(v[j], T[zw_kappa0(j) * 16 + qq]);
+        for (int j = 0; j < E1; ++j) v[j] = zw_twmul<-1>(v[j], T[M::kappa0(j) * 16 + qq]);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int k0 = zw_kappa0(j);
+        for (int j = 0; j < E1; ++j) {
+            const int k0 = M::kappa0(j);
             zw_sts((aw ^ (16 * (k0 & 7))) + 256 * k0, v[j]);
         }
         __syncwarp();
+        if (rd) {
 #pragma unroll
-        for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (16 * (p & 7))) + 16 * (p & 8));
-        dft<16, -1>(v);  // v[k2] = C[qq + 16 k2]
+            for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (16 * (p & 7))) + 16 * (p & 8));
+            dft<16, -1>(v);  // v[k2] = C[qq + E1 k2]
+        }
         __syncwarp();
+        if (rd) {
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) zw_sts(xs + 16 * (qq + 16 * k2), v[k2]);
+            for (int k2 = 0; k2 < 16; ++k2) zw_sts(xs + 16 * (qq + E1 * k2), v[k2]);
+        }
         __syncwarp();
         float2 *d0 = out + (long long)(2 * i) * Px, *d1 = d0 + Px;
         const float2 h = f2(0.5f, 0.5f);
 #pragma unroll
         for (int k2 = 0; k2 < 9; ++k2) {
-            const int k = qq + 16 * k2;
-            if (k > N / 2) continue;
-            const CV ck = v[k2], cn = zw_lds(xs + 16 * ((N - k) & (N - 1)));
+            const int k = qq + E1 * k2;
+            if (!rd || k > N / 2) continue;
+            const CV ck = v[k2], cn = zw_lds(xs + 16 * (k == 0 ? 0 : N - k));
             const CV ev = {f2mul(h, f2add(ck.re, cn.re)), f2mul(h, f2sub(ck.im, cn.im))};
             const CV od = {f2mul(h, f2add(ck.im, cn.im)), f2mul(h, f2sub(cn.re, ck.re))};
             if (k == 0) {
@@ -614,70 +677,80 @@ k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restr
 }
 
 template <int N>
-__global__ void __launch_bounds__(XWarp::NT, 2)
+__global__ void __launch_bounds__(XWarp<N>::NT, 2)
 k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__restrict__ tw, int npairs, int Px) {
-    static_assert(N == XWarp::N, "the half-warp schedule is 16 x 16");
-    constexpr int NN = N * N;
+    using X = XWarp<N>;
+    using M = ZwMap<X::E1>;
+    constexpr int E1 = X::E1, H = X::H, NN = N * N;
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *T = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T);
-    float2 *T2 = reinterpret_cast<float2 *>(smraw + XWarp::OFF_T2);
-    xw_tables(T, T2, tw);
+    float2 *T = reinterpret_cast<float2 *>(smraw + X::OFF_T);
+    float2 *T2 = reinterpret_cast<float2 *>(smraw + X::OFF_T2);
+    xw_tables<N>(T, T2, tw);
     __syncthreads();
     const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
-    const uint32_t xs = smem_addr(smraw + XWarp::OFF_X) + 4096 * hw;
+    const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
     const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
-    const int stride = gridDim.x * (XWarp::NT / 16);
-    for (int i = blockIdx.x * (XWarp::NT / 16) + hw; i < npairs; i += stride) {
+    const bool rd = qq < E1;  // lane qq gathers k1 = qq after the exchange
+    const int stride = gridDim.x * (X::NT / 16);
+    for (int i = blockIdx.x * (X::NT / 16) + hw; i < npairs; i += stride) {
         const float2 *s0 = in + (long long)(2 * i) * Px, *s1 = s0 + Px;
-        float2 yk0[9], yk1[9], yn0[9], yn1[9];
-#pragma unroll
-        for (int k2 = 0; k2 < 9; ++k2) {
-            const int k = qq + 16 * k2;
-            if (k > N / 2) continue;
-            yk0[k2] = __ldg(s0 + k);
-            yk1[k2] = __ldg(s1 + k);
-            yn0[k2] = __ldg(s0 + (N - k));
-            yn1[k2] = __ldg(s1 + (N - k));
-        }
         CV v[16];
+        // (Y_k, Y_{N-k}) -> (C_k, C_{N-k}) for k = qq + E1 k2 <= N/2, in two batches of loads.
 #pragma unroll
-        for (int k2 = 0; k2 < 9; ++k2) {
-            const int k = qq + 16 * k2;
-            if (k > N / 2) continue;
-            if (k == 0) {
-                v[0] = {f2(yk0[0].x + yn0[0].x, yk1[0].x + yn1[0].x), f2(yk0[0].x - yn0[0].x, yk1[0].x - yn1[0].x)};
-            } else {
-                const CV yk = {f2(yk0[k2].x, yk1[k2].x), f2(yk0[k2].y, yk1[k2].y)};
-                const CV yn = {f2(yn0[k2].x, yn1[k2].x), f2(yn0[k2].y, yn1[k2].y)};
-                const CV ev = {f2add(yk.re, yn.re), f2sub(yk.im, yn.im)};
-                const CV od = zw_twmul<1>(CV{f2sub(yk.re, yn.re), f2add(yk.im, yn.im)}, T2[k]);
-                v[k2] = add_rot<1>(ev, od);
-                if (2 * k != N) zw_sts(xs + 16 * (N - k), add_rot<1>(cconj_cv(ev), cconj_cv(od)));
+        for (int k20 = 0; k20 < 9; k20 += 5) {
+            float2 yk0[5], yk1[5], yn0[5], yn1[5];
+#pragma unroll
+            for (int d2 = 0; d2 < 5; ++d2) {
+                const int k2 = k20 + d2, k = qq + E1 * k2;
+                if (k2 > 8 || !rd || k > N / 2) continue;
+                yk0[d2] = __ldg(s0 + k);
+                yk1[d2] = __ldg(s1 + k);
+                yn0[d2] = __ldg(s0 + (N - k));
+                yn1[d2] = __ldg(s1 + (N - k));
+            }
+#pragma unroll
+            for (int d2 = 0; d2 < 5; ++d2) {
+                const int k2 = k20 + d2, k = qq + E1 * k2;
+                if (k2 > 8 || !rd || k > N / 2) continue;
+                if (k == 0) {
+                    v[0] = {f2(yk0[0].x + yn0[0].x, yk1[0].x + yn1[0].x), f2(yk0[0].x - yn0[0].x, yk1[0].x - yn1[0].x)};
+                } else {
+                    const CV yk = {f2(yk0[d2].x, yk1[d2].x), f2(yk0[d2].y, yk1[d2].y)};
+                    const CV yn = {f2(yn0[d2].x, yn1[d2].x), f2(yn0[d2].y, yn1[d2].y)};
+                    const CV ev = {f2add(yk.re, yn.re), f2sub(yk.im, yn.im)};
+                    const CV od = zw_twmul<1>(CV{f2sub(yk.re, yn.re), f2add(yk.im, yn.im)}, T2[k]);
+                    v[k2] = add_rot<1>(ev, od);
+                    if (2 * k != N) zw_sts(xs + 16 * (N - k), add_rot<1>(cconj_cv(ev), cconj_cv(od)));
+                }
             }
         }
         __syncwarp();
+        if (rd) {
 #pragma unroll
-        for (int k2 = 8; k2 < 16; ++k2) {
-            const int k = qq + 16 * k2;
-            if (k != N / 2) v[k2] = zw_lds(xs + 16 * k);
+            for (int k2 = 8; k2 < 16; ++k2) {
+                const int k = qq + E1 * k2;
+                if (k != N / 2) v[k2] = zw_lds(xs + 16 * k);
+            }
         }
         __syncwarp();
-        dft<16, 1>(v);
+        if (rd) {
+            dft<16, 1>(v);
 #pragma unroll
-        for (int p = 0; p < 16; ++p) zw_sts((ar ^ (16 * (p & 7))) + 16 * (p & 8), v[p]);
+            for (int p = 0; p < 16; ++p) zw_sts((ar ^ (16 * (p & 7))) + 16 * (p & 8), v[p]);
+        }
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int k0 = zw_kappa0(j);
+        for (int j = 0; j < E1; ++j) {
+            const int k0 = M::kappa0(j);
             v[j] = zw_lds((aw ^ (16 * (k0 & 7))) + 256 * k0);
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = zw_twmul<1>(v[j], T[zw_kappa0(j) * 16 + qq]);
-        zw_f1_adj(v);
+        for (int j = 0; j < E1; ++j) v[j] = zw_twmul<1>(v[j], T[M::kappa0(j) * 16 + qq]);
+        zw_f1_adj<E1>(v);
         const int b = (2 * i) / NN;
         float2 *d = reinterpret_cast<float2 *>(const_cast<void *>(u.p[b])) + (long long)(2 * i - b * NN) * (N / 2) + qq;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < H; ++r) {
             d[16 * r] = f2(v[r].re.x, v[r].im.x);
             d[N / 2 + 16 * r] = f2(v[r].re.y, v[r].im.y);
         }
@@ -717,7 +790,7 @@ k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__rest
     for (int i = threadIdx.x; i <= N / 2; i += XWarp2::NT) T2[i] = tw[i];
     __syncthreads();
     const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
-    const ZwLane zl = zw_lane(tw, smem_addr(xo), g, q, 2);
+    const ZwLane zl = zw_lane<16>(tw, smem_addr(xo), g, q, 2);
     const int stride = gridDim.x * XWarp2::NW;
     auto load = [&](long long i, float2 *f) {
         const int b = (int)((2 * i) / NN);
@@ -739,8 +812,8 @@ k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__rest
             if (r & 1) v[r] = zw_sign(v[r], zl.sg);
         }
         if (i + stride < npairs) load(i + stride, f);
-        zw_front(v, zl, T);
-        zw_exchange(v, zl);
+        zw_front<16>(v, zl, T);
+        zw_exchange<16>(v, zl);
         dft<16, -1>(v);  // v[k2] = C[q + 32 k2]
         __syncwarp();
 #pragma unroll
@@ -791,7 +864,7 @@ k_x_warp2_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__r
     for (int i = threadIdx.x; i <= N / 2; i += XWarp2::NT) T2[i] = tw[i];
     __syncthreads();
     const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
-    const ZwLane zl = zw_lane(tw, smem_addr(xo), g, q, 2);
+    const ZwLane zl = zw_lane<16>(tw, smem_addr(xo), g, q, 2);
     const int stride = gridDim.x * XWarp2::NW;
     for (long long i = (long long)blockIdx.x * XWarp2::NW + g; i < npairs; i += stride) {
         const float2 *s0 = in + (2 * i) * Px, *s1 = s0 + Px;
@@ -829,8 +902,8 @@ k_x_warp2_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__r
         }
         __syncwarp();
         dft<16, 1>(v);
-        zw_exchange_adj(v, zl);
-        zw_back(v, zl, T);
+        zw_exchange_adj<16>(v, zl);
+        zw_back<16>(v, zl, T);
         const int b = (int)((2 * i) / NN);
         float2 *d = reinterpret_cast<float2 *>(const_cast<void *>(u.p[b])) + (2 * i - b * NN) * (N / 2) + q;
 #pragma unroll

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
 SPLIT_N = (16, 80, 256, 320, 384)
-WARP_N = (256,)
+WARP_N = (160, 192, 256)
 
 
 def forms(N, dtype):
@@ -26,7 +26,7 @@ def yforms(N, dtype):
 
 
 def xforms(N, dtype):
-    return [0] + ([1] if dtype == "f32" and N in (256, 512) else [])
+    return [0] + ([1] if dtype == "f32" and (N in WARP_N or N == 512) else [])
 
 
 @pytest.fixture(scope="module")
@@ -151,7 +151,8 @@ def test_forms_sampled_large(torch_cuda, N, dtype):
         assert rel_l2(got, ref) <= TOL[dtype], form
 
 
-@pytest.mark.parametrize("form,N,dtype", [(1, 80, "f64"), (1, 80, "f32"), (2, 256, "f32")])
+@pytest.mark.parametrize("form,N,dtype", [(1, 80, "f64"), (1, 80, "f32"), (2, 256, "f32"), (2, 192, "f32"),
+                                          (2, 160, "f32")])
 def test_form_tail(torch_cuda, form, N, dtype):
     """The checked solve in a non-default form: same potential as the unchecked one, and
     eta as defined on the padded spectrum.  The box [-6,6]^3 truncates the Gaussians, so
@@ -176,13 +177,13 @@ def test_form_tail(torch_cuda, form, N, dtype):
     assert eta.value == pytest.approx(ref, rel=2e-3 if dtype == "f32" else 1e-6, abs=1e-12)
 
 
-@pytest.mark.parametrize("yform,xform", [(0, 0), (1, 0), (1, 1)])
-def test_warp_form_batched(torch_cuda, yform, xform):
+@pytest.mark.parametrize("N,yform,xform", [(256, 0, 0), (256, 1, 0), (256, 1, 1), (192, 1, 1), (160, 1, 1)])
+def test_warp_form_batched(torch_cuda, N, yform, xform):
     """Three densities through one grouped launch sequence in the warp forms: each equals
     its single solve bit for bit, and the plan reports no timed-out wait."""
     torch = torch_cuda
     from paper_1612_01799_gb300 import Plan, solve_batched
-    N, L = 256, 10.0
+    L = 10.0
     rhos = [torch.from_numpy(D.config_aniso4(N=N, seed=40 + i).gaussians.sample(N, L).astype(np.float32)).cuda()
             for i in range(3)]
     with Plan(N, L, 1e-6, "f32", max_batch=3) as p:
@@ -208,3 +209,16 @@ def test_x_forms_sampled_n512(torch_cuda, xform):
     u = solve_form(torch_cuda, N, L, tol, "f32", rho, 0, None, xform)
     got = np.stack([u[z, y] for z, y in lines])
     assert rel_l2(got, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("N", [160, 192])
+def test_warp_forms_full_grid(torch_cuda, plan_cache, N):
+    """N = 160 and 192 (first-stage lengths 10 and 12 of the warp forms), FP32: every form
+    combination against the oracle on the whole grid."""
+    L, tol = 10.0, 1e-6
+    rho = D.config_aniso4(N=N, seed=400 + N).gaussians.sample(N, L)
+    uo = osolver.solve(rho, L, tol, plan=plan_cache(N, L, tol))
+    for form, yform, xform in [(0, 0, 0), (2, 0, 0), (0, 1, 0), (0, 0, 1), (2, 1, 1)]:
+        u = solve_form(torch_cuda, N, L, tol, "f32", rho, form, yform, xform)
+        assert rel_l2(u, uo) <= TOL["f32"], (form, yform, xform)
+        assert np.max(np.abs(u - uo)) <= 50 * TOL["f32"] * np.abs(uo).max(), (form, yform, xform)
