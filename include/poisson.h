@@ -173,16 +173,17 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       1 = the pruned length-2N transforms split into even- and odd-frequency length-N
  *           transforms, where the length-N schedule has fewer stages
  *           (N = 16, 80, 256, 320, 384);
- *       2 = one warp per column pair: 16-point DFTs in registers, a radix-2 step between
- *           lane pairs and one warp-local shared-memory exchange per direction
- *           (POISSON_F32, N = 256).
+ *       2 = one warp per column pair: an E1-point DFT (N = 16 E1) and a 16-point DFT in
+ *           registers, a radix-2 step between lane pairs and one warp-local
+ *           shared-memory exchange per direction (POISSON_F32, N = 64, 96, 128, 160,
+ *           192, 256).
  *   POISSON_KNOB_Y_FORM  form of the two y passes (Sec. 2, the zero-padded transforms
  *       along the middle axis): 0 = a column pair spread over the threads of a block;
- *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, N = 256).
+ *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, the same N).
  *   POISSON_KNOB_X_FORM  form of the two x passes (Sec. 2, the real transforms along the
  *       first axis and the crop): 0 = a tile of rows staged in shared memory; 1 = one
- *       half-warp (N = 256) or warp (N = 512) per pair of rows, read and written straight
- *       from device memory (POISSON_F32, N = 256 and 512).
+ *       half-warp (N = 64 ... 256 as for the z pass) or warp (N = 512) per pair of rows,
+ *       read and written straight from device memory (POISSON_F32).
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that

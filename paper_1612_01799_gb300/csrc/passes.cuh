@@ -394,8 +394,10 @@ template <class K> static int persistent_blocks(K kernel, int threads, size_t sm
 
 // Whether the warp form of the z pass exists (FP32, N = 256).
 // The warp forms of the z and y passes and the half-warp x passes exist for FP32 at
-// N = 16 E1, E1 in {16, 12, 10}; the full-warp x passes at N = 512.
-inline constexpr bool warp_n(int N) { return N == 256 || N == 192 || N == 160; }
+// N = 16 E1, E1 in {16, 12, 10, 8, 6, 4}; the full-warp x passes at N = 512.
+inline constexpr bool warp_n(int N) {
+    return N == 256 || N == 192 || N == 160 || N == 128 || N == 96 || N == 64;
+}
 template <typename Real, int N> constexpr bool zwarp_form() { return std::is_same<Real, float>::value && warp_n(N); }
 inline bool zwarp_available(int N) { return warp_n(N); }
 

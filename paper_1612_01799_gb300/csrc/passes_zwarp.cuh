@@ -1,7 +1,8 @@
 // Warp forms of the passes, FP32.  The fused z pass (K3) at N = 16 E1, L = 2N = 32 E1 for a
-// first-stage length E1 in {16, 12, 10} (N = 256, 192, 160); the y passes (K2, K4) on its
+// first-stage length E1 (N = 256, 192, 160, 128, 96, 64); the y passes (K2, K4) on its
 // transform halves; the x passes (K1, K5) at N = 16 E1 with a half-warp per row pair and at
-// N = 512 with a warp per row pair.  The description below is for E1 = 16; for E1 < 16
+// N = 512 with a warp per row pair (E1 in {4, 6, 8, 10, 12, 16}: N = 64 ... 256).  The
+// description below is for E1 = 16; for E1 < 16
 // the first stage is a pruned E1-point DFT (E1 / 2 nonzero inputs), the lane-pair radix 2
 // pairs the halves of its outputs the same way, and only the 2 E1 lanes l with
 // (l & 7) < E1 / 2 gather after the exchange (the others idle through the 16-point DFTs).
@@ -65,7 +66,8 @@ template <int E1> struct ZWarp {
     static constexpr int OFF_B = 0, OFF_XO = (B_BYTES + 1023) / 1024 * 1024, OFF_T = OFF_XO + 65536;
     static constexpr int OFF_BAR = OFF_T + E1 * 32 * 8;
     static constexpr int SMEM = 1024 + OFF_BAR + 64;  // 1 KB alignment slack
-    static_assert(E1 == 16 || E1 == 12 || E1 == 10, "first stage: a pruned DFT of E1 / 2 inputs");
+    static_assert(E1 == 16 || E1 == 12 || E1 == 10 || E1 == 8 || E1 == 6 || E1 == 4,
+                  "first stage: a pruned DFT of E1 / 2 inputs");
     static_assert(SYM_NCP * SYM_RPC >= N + 1 && SYM_RPC <= 256, "symbol rows fit the TMA boxes");
     static_assert((SYM_RPC * TC * 4) % 512 == 0, "64-byte-swizzled copies start 512-byte aligned");
 };
@@ -83,9 +85,12 @@ template <int D> __device__ __forceinline__ CV zw_rot(CV a) {
     return D < 0 ? CV{a.im, f2neg(a.re)} : CV{f2neg(a.im), a.re};
 }
 
-// exp(-2 pi i r / E) = (zw_cw, zw_sw), r < E / 2, E in {10, 12, 16}.
+// exp(-2 pi i r / E) = (zw_cw, zw_sw), r < E / 2, E in {4, 6, 8, 10, 12, 16}.
 __host__ __device__ constexpr float zw_cw(int E, int r) {
-    return E == 16 ? (r == 0 ? 1.f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
+    return E == 4 ? (r == 0 ? 1.f : 0.f)
+         : E == 6 ? (r == 0 ? 1.f : r == 1 ? 0.5f : -0.5f)
+         : E == 8 ? (r == 0 ? 1.f : r == 1 ? 0.70710678118654752440f : r == 2 ? 0.f : -0.70710678118654752440f)
+         : E == 16 ? (r == 0 ? 1.f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
                       : r == 3 ? 0.38268343236508977173f : r == 4 ? 0.f : r == 5 ? -0.38268343236508977173f
                       : r == 6 ? -0.70710678118654752440f : -0.92387953251128675613f)
          : E == 12 ? (r == 0 ? 1.f : r == 1 ? 0.86602540378443864676f : r == 2 ? 0.5f : r == 3 ? 0.f
@@ -94,7 +99,10 @@ __host__ __device__ constexpr float zw_cw(int E, int r) {
                       : r == 3 ? -0.30901699437494742410f : -0.80901699437494742410f);
 }
 __host__ __device__ constexpr float zw_sw(int E, int r) {
-    return E == 16 ? (r == 0 ? 0.f : r == 1 ? -0.38268343236508977173f : r == 2 ? -0.70710678118654752440f
+    return E == 4 ? (r == 0 ? 0.f : -1.f)
+         : E == 6 ? (r == 0 ? 0.f : -0.86602540378443864676f)
+         : E == 8 ? (r == 0 ? 0.f : r == 1 ? -0.70710678118654752440f : r == 2 ? -1.f : -0.70710678118654752440f)
+         : E == 16 ? (r == 0 ? 0.f : r == 1 ? -0.38268343236508977173f : r == 2 ? -0.70710678118654752440f
                       : r == 3 ? -0.92387953251128675613f : r == 4 ? -1.f : r == 5 ? -0.92387953251128675613f
                       : r == 6 ? -0.70710678118654752440f : -0.38268343236508977173f)
          : E == 12 ? (r == 0 ? 0.f : r == 1 ? -0.5f : r == 2 ? -0.86602540378443864676f : r == 3 ? -1.f
@@ -582,7 +590,8 @@ template <int N> struct XWarp {
     static constexpr int E1 = N / 16, H = E1 / 2, NT = 256;
     static constexpr int OFF_X = 0, OFF_T = OFF_X + 16 * 4096, OFF_T2 = OFF_T + E1 * 16 * 8;
     static constexpr int SMEM = OFF_T2 + (N / 2 + 1) * 8;
-    static_assert(E1 == 16 || E1 == 12 || E1 == 10, "N = 16 E1 with a pruned first stage of E1 / 2 inputs");
+    static_assert(E1 == 16 || E1 == 12 || E1 == 10 || E1 == 8 || E1 == 6 || E1 == 4,
+                  "N = 16 E1 with a pruned first stage of E1 / 2 inputs");
 };
 
 // Twiddle tables of the x passes from W_2N^e: T[k1 * 16 + q'] = W_N^{q' k1}, T2[k] = W_2N^k

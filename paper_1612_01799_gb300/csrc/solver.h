@@ -42,13 +42,13 @@ struct DevicePlan {
     int *status = nullptr;  // device status word (bit 0: a bounded wait timed out)
     double *tail = nullptr; // 2 max_batch doubles: spectral-tail sums of a checked solve
     // z pass form: 0 length-2N transforms, 1 even/odd length-N split, 2 warp form (one
-    // warp per column pair, FP32, N = 256)
+    // warp per column pair, FP32, N = 64 ... 256)
     int zform = 0;
     // y pass form: 0 block form (a column pair spread over a block), 1 warp form (FP32,
-    // N = 256)
+    // N = 64 ... 256)
     int yform = 0;
     // x pass form: 0 block form (a tile of rows staged in shared memory), 1 warp form (a
-    // half-warp or warp per row pair, FP32, N = 256 and 512)
+    // half-warp or warp per row pair, FP32, N = 64 ... 256 and 512)
     int xform = 0;
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers; and of the warp-form z pass (w2 in,
@@ -81,18 +81,18 @@ cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArra
 
 // Forms of the z pass that exist for (N, dtype), as a bit mask over DevicePlan::zform:
 // bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;
-// bit 2 for FP32 at N = 256.
+// bit 2 for FP32 at N = 64, 96, 128, 160, 192, 256.
 int z_forms(int N, int dtype);
 
 // Forms of the x passes that exist for (N, dtype), as a bit mask over DevicePlan::xform:
-// bit 0 always; bit 1 for FP32 at N = 256 and 512.
+// bit 0 always; bit 1 for FP32 at N = 64, 96, 128, 160, 192, 256 and 512.
 int x_forms(int N, int dtype);
 
 // The two x passes alone, one density on spare workspace, in the form p.xform selects.
 cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s);
 
 // Forms of the y passes that exist for (N, dtype), as a bit mask over DevicePlan::yform:
-// bit 0 always; bit 1 for FP32 at N = 256.
+// bit 0 always; bit 1 for FP32 at N = 64, 96, 128, 160, 192, 256.
 int y_forms(int N, int dtype);
 
 // The two y passes alone, one density, in the form p.yform selects (for timing the forms).

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
 SPLIT_N = (16, 80, 256, 320, 384)
-WARP_N = (160, 192, 256)
+WARP_N = (64, 96, 128, 160, 192, 256)
 
 
 def forms(N, dtype):
@@ -177,7 +177,8 @@ def test_form_tail(torch_cuda, form, N, dtype):
     assert eta.value == pytest.approx(ref, rel=2e-3 if dtype == "f32" else 1e-6, abs=1e-12)
 
 
-@pytest.mark.parametrize("N,yform,xform", [(256, 0, 0), (256, 1, 0), (256, 1, 1), (192, 1, 1), (160, 1, 1)])
+@pytest.mark.parametrize("N,yform,xform", [(256, 0, 0), (256, 1, 0), (256, 1, 1), (192, 1, 1), (160, 1, 1),
+                                           (128, 1, 1), (96, 1, 1), (64, 1, 1)])
 def test_warp_form_batched(torch_cuda, N, yform, xform):
     """Three densities through one grouped launch sequence in the warp forms: each equals
     its single solve bit for bit, and the plan reports no timed-out wait."""
@@ -211,9 +212,9 @@ def test_x_forms_sampled_n512(torch_cuda, xform):
     assert rel_l2(got, ref) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("N", [160, 192])
+@pytest.mark.parametrize("N", [64, 96, 128, 160, 192])
 def test_warp_forms_full_grid(torch_cuda, plan_cache, N):
-    """N = 160 and 192 (first-stage lengths 10 and 12 of the warp forms), FP32: every form
+    """N = 64 ... 192 (first-stage lengths 4 ... 12 of the warp forms), FP32: every form
     combination against the oracle on the whole grid."""
     L, tol = 10.0, 1e-6
     rho = D.config_aniso4(N=N, seed=400 + N).gaussians.sample(N, L)
