@@ -151,6 +151,17 @@ int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d, void *stre
 int poisson_last_status(poisson_plan p, void *stream);
 
 /*
+ * Test hook of the failure detection above (no counterpart in the paper): launches on
+ * `stream` one device-side wait of the kind every TMA pass uses, on an mbarrier that nothing
+ * completes, bounded at `polls` polls (1 <= polls <= 2^24).  The wait gives up, records the
+ * timeout bit in the plan's status word and the kernel returns: no fault, no trap, no hang,
+ * and the context stays usable.  The next poisson_last_status on the plan then returns
+ * POISSON_ERR_TIMEOUT (and clears the word).  No solve output is touched.
+ * Returns POISSON_ERR_ARG for a null plan or polls out of range.
+ */
+int poisson_selftest_wait(poisson_plan p, long long polls, void *stream);
+
+/*
  * Facts of a plan, for checks and reports.  Any output pointer may be NULL.
  *   delta       near-zone radius in scaled coordinates (Sec. 3 heuristic).
  *   eps         Gaussian-sum accuracy actually requested.

@@ -542,6 +542,11 @@ extern "C" int poisson_last_status(poisson_plan p, void *stream) {
     return (h & gsp::kStatusTimeoutBit) ? POISSON_ERR_TIMEOUT : POISSON_ERR_CUDA;
 }
 
+extern "C" int poisson_selftest_wait(poisson_plan p, long long polls, void *stream) {
+    if (!p || polls < 1 || polls > (1ll << 24)) return POISSON_ERR_ARG;
+    return map_cuda(gsp::launch_wait_selftest(p->dp, polls, (cudaStream_t)stream));
+}
+
 extern "C" int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms,
                                  double *c0, double *c2, size_t *ws_bytes, size_t *table_bytes) {
     if (!p) return POISSON_ERR_ARG;

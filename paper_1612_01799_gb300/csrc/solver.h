@@ -101,6 +101,10 @@ cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s);
 // The z pass alone, one density, in the form p.zform selects (for timing the forms).
 cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s);
 
+// One bounded device-side wait that nothing completes, `polls` polls on p's status word
+// (the test hook of poisson_selftest_wait).
+cudaError_t launch_wait_selftest(const DevicePlan &p, long long polls, cudaStream_t s);
+
 // Fill p.sym from the per-axis factors (FP64, on the device):
 // sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,

@@ -53,9 +53,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity.  Returns false (and sets the timeout
-// bit of *status) if the phase did not complete within kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
-    for (long long it = 0; it < kWaitLimit; ++it)
+// bit of *status) if the phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status,
+                                          long long limit = kWaitLimit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, kStatusTimeout);
     return false;
