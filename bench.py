@@ -33,6 +33,7 @@ UNIT = "pts/s"
 PASSES = ["x_forward", "y_forward", "z_fwd_symbol_inv", "y_inverse", "x_inverse"]
 Z_FORMS = ["direct", "split", "warp"]
 Y_FORMS = ["block", "warp"]
+XY_FORMS = ["separate", "fused"]
 Z_KERNELS = ["k_z_symbol", "k_z_split", "k_z_warp"]
 # forms of the x and y passes: "block" (tiles staged in shared memory, columns or rows spread
 # over a block) and "warp" (one warp or half-warp per column or row pair)
@@ -46,7 +47,7 @@ NCU_TRAFFIC = {("865f54a3e7fab488", "k_z_warp", 256): 368838656 + 234386944}
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft_core.cuh", "passes.cuh", "passes_tma.cuh", "passes_zwarp.cuh", "tma.cuh"):
+    for f in ("fft_core.cuh", "passes.cuh", "passes_tma.cuh", "passes_zwarp.cuh", "passes_xy.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_1612_01799_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -62,6 +63,19 @@ def pass_bytes(N, s):
             2 * (2 * N * N * K * c) + K ** 3 * s,       # z fused: w2 in, w3 out, symbol octant
             2 * N * N * K * c + N * N * K * c,          # y inverse: w3 in, w1 out
             N * N * K * c + N ** 3 * s]                 # x inverse: w1 in, u out
+
+
+def pass_table(N, s, per_pass, xyform, names):
+    """(pass, kernel, ms, algorithmic bytes) of the launches of one solve.  With the fused
+    x-y form the forward x and y passes are one kernel (rho in, w2 out: w1 stays in L2) and
+    so are the inverse y and x passes (w3 in, u out); their times sit in entries 0 and 3."""
+    b = pass_bytes(N, s)
+    if not xyform:
+        return [(PASSES[i], names[i], per_pass[i], b[i]) for i in range(5)]
+    K, c = N + 1, 2 * s
+    return [("xy_forward", "k_xy_fwd", per_pass[0], N ** 3 * s + 2 * N * N * K * c),
+            (PASSES[2], names[2], per_pass[2], b[2]),
+            ("yx_inverse", "k_yx_inv", per_pass[3], 2 * N * N * K * c + N ** 3 * s)]
 
 
 def load_peaks():
@@ -290,13 +304,15 @@ def run_large(torch, dev, flush, steps, warmup, peak, N=512):
         out = torch.empty_like(rho)
         totals, passes = time_solves(torch, plan, rho, out, steps, warmup, flush)
         plan.last_status()
-        forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form]}
+        forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form],
+                 "xy": XY_FORMS[plan.xy_form]}
+        xyform = plan.xy_form
     ms = statistics.mean(totals)
     per = [statistics.mean(p[i] for p in passes) for i in range(5)]
-    b = pass_bytes(N, 4)
+    rows = pass_table(N, 4, per, xyform, [None] * 5)
     return {"value": N ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "dtype": "f32",
-            "passes": [{"pass": PASSES[i], "ms": per[i], "GB_s": b[i] / (per[i] * 1e-3) / 1e9,
-                        "frac": b[i] / (per[i] * 1e-3) / 1e9 / peak} for i in range(5)],
+            "passes": [{"pass": n, "ms": t, "GB_s": b / (t * 1e-3) / 1e9,
+                        "frac": b / (t * 1e-3) / 1e9 / peak} for n, _, t, b in rows],
             "forms": forms,
             "workload": "config_large: (1-r^2/16)^4 on r<4 plus 8 Gaussians (widths U[0.3,1], seed 3), box "
                         "[-6,6]^3, N=512 per axis, padded 1024^3, FP32, L2 flushed between steps"}
@@ -357,6 +373,8 @@ def run_ours(args):
             plan.y_form = Y_FORMS.index(args.y_form)
         if dtype == "f32" and args.x_form is not None:
             plan.x_form = Y_FORMS.index(args.x_form)
+        if dtype == "f32" and args.xy_form is not None:
+            plan.xy_form = XY_FORMS.index(args.xy_form)
         rho_t = torch.from_numpy(rho64.astype(plan.np_dtype)).to(dev)
         out_t = torch.empty_like(rho_t)
         steps = args.steps if dtype == "f32" else max(3, args.steps // 4)
@@ -374,6 +392,7 @@ def run_ours(args):
         ms = max_over_ranks(torch, statistics.mean(totals), dev)
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
         results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form, "y_form": plan.y_form, "x_form": plan.x_form,
+                          "xy_form": plan.xy_form,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
                           "rho": rho_t, "out": out_t}
 
@@ -393,20 +412,20 @@ def run_ours(args):
     if rank == 0:
         peak, peak_kind = load_peaks()
         r32 = results["f32"]
-        bytes32 = pass_bytes(N, 4)
-        dom = max(range(5), key=lambda i: r32["per_pass"][i])
-        gbs = [bytes32[i] / (r32["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
         names = list(KERNEL_NAMES)
         names[2] = Z_KERNELS[r32["z_form"]]
         if r32["y_form"] == 1:
             names[1], names[3] = "k_y_warp<fwd>", "k_y_warp<inv>"
         if r32["x_form"] == 1:
             names[0], names[4] = "k_x_warp_fwd", "k_x_warp_inv"
+        rows32 = pass_table(N, 4, r32["per_pass"], r32["xy_form"], names)
+        gbs = [b / (t * 1e-3) / 1e9 for _, _, t, b in rows32]
+        dom = max(range(len(rows32)), key=lambda i: rows32[i][2])
         src_hash = kernel_source_hash()
-        traffic = NCU_TRAFFIC.get((src_hash, names[dom], N))
+        traffic = NCU_TRAFFIC.get((src_hash, rows32[dom][1], N))
         r64 = results["f64"]
-        bytes64 = pass_bytes(N, 8)
-        gbs64 = [bytes64[i] / (r64["per_pass"][i] * 1e-3) / 1e9 for i in range(5)]
+        rows64 = pass_table(N, 8, r64["per_pass"], r64["xy_form"], [None] * 5)
+        gbs64 = [b / (t * 1e-3) / 1e9 for _, _, t, b in rows64]
         line = {
             "metric": METRIC, "value": aggregate_rate(world, N, r32["ms"] * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"],
@@ -414,22 +433,24 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(N, "f32"),
             "roofline": {"bound": "hbm", "achieved": gbs[dom], "peak": peak, "unit": "GB/s",
                          "frac": gbs[dom] / peak, "traffic": traffic,
-                         "kernel": names[dom], "algorithmic_bytes": bytes32[dom],
+                         "kernel": rows32[dom][1], "algorithmic_bytes": rows32[dom][3],
                          "peak_source": peak_kind},
-            "passes": [{"pass": PASSES[i], "kernel": names[i], "ms": r32["per_pass"][i],
-                        "GB_s": gbs[i], "frac": gbs[i] / peak} for i in range(5)],
+            "passes": [{"pass": n, "kernel": k, "ms": t, "GB_s": gbs[i], "frac": gbs[i] / peak}
+                       for i, (n, k, t, _) in enumerate(rows32)],
             "f64": {"value": aggregate_rate(world, N, r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
                     "steps": r64["steps"],
-                    "passes": [{"pass": PASSES[i], "ms": r64["per_pass"][i], "GB_s": gbs64[i],
-                                "frac": gbs64[i] / peak} for i in range(5)]},
+                    "passes": [{"pass": n, "ms": t, "GB_s": gbs64[i], "frac": gbs64[i] / peak}
+                               for i, (n, _, t, _) in enumerate(rows64)]},
             "e2e": {"value": aggregate_rate(world, N, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": N ** 3 * 4, "d2h_bytes_per_step": N ** 3 * 4},
-            "gpu_launches": 5 * r32["steps"],
+            "gpu_launches": len(rows32) * r32["steps"],
             "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
                        "z_pass_f64": Z_FORMS[results["f64"]["z_form"]],
                        "y_passes_f32": Y_FORMS[r32["y_form"]], "y_passes_f64": Y_FORMS[results["f64"]["y_form"]],
                        "x_passes_f32": Y_FORMS[r32["x_form"]], "x_passes_f64": Y_FORMS[results["f64"]["x_form"]],
-                       "how": ("pinned by --z-form/--y-form/--x-form" if args.z_form or args.y_form or args.x_form else
+                       "xy_passes_f32": XY_FORMS[r32["xy_form"]],
+                       "how": ("pinned by --z-form/--y-form/--x-form/--xy-form"
+                               if args.z_form or args.y_form or args.x_form or args.xy_form else
                                "timed at plan creation, cached per (device, N, dtype)")},
             "clocks": r32["clocks"],
         }
@@ -470,6 +491,8 @@ def main():
                     help="pin the FP32 y-pass form (default: the plan's timed choice); for profiling")
     ap.add_argument("--x-form", choices=Y_FORMS, default=None,
                     help="pin the FP32 x-pass form (default: the plan's timed choice); for profiling")
+    ap.add_argument("--xy-form", choices=XY_FORMS, default=None,
+                    help="pin the FP32 x-y form, separate passes or fused (default: the plan's timed choice)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -137,8 +137,11 @@ int poisson_compare(const void *a_d, int a_dtype, const void *b_d, int b_dtype, 
 /*
  * Per-pass device times of one solve, in milliseconds, measured with CUDA events
  * recorded on `stream` around each of the five passes (x forward, y forward, z
- * forward + symbol + z inverse, y inverse, x inverse).  ms[5] receives them.  The call
- * synchronises the stream.  Same arguments and aliasing rules as poisson_solve.
+ * forward + symbol + z inverse, y inverse, x inverse).  ms[5] receives them.  With the
+ * fused x-y form (POISSON_KNOB_XY_FORM = 1) the forward x and y passes are one kernel,
+ * timed in ms[0] with ms[1] = 0, and the inverse y and x passes are one kernel, timed in
+ * ms[3] with ms[4] = 0.  The call synchronises the stream.  Same arguments and aliasing
+ * rules as poisson_solve.
  */
 int poisson_solve_timed(poisson_plan p, const void *rho_d, void *u_d, void *stream, float *ms);
 
@@ -195,6 +198,12 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       first axis and the crop): 0 = a tile of rows staged in shared memory; 1 = one
  *       half-warp (N = 64 ... 256 as for the z pass) or warp (N = 512) per pair of rows,
  *       read and written straight from device memory (POISSON_F32).
+ *   POISSON_KNOB_XY_FORM  whether the x and y passes run as separate launches (0, in the
+ *       forms of the two knobs above) or fused (1: one persistent kernel per direction
+ *       whose row tasks (x) and column-tile tasks (y) hand each z-plane over through a
+ *       ring of plane slots that stays in L2, so the x spectrum never goes to device
+ *       memory; the bodies are the warp forms; POISSON_F32, N = 64, 96, 128, 160, 192,
+ *       256).
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that
@@ -204,6 +213,7 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
 #define POISSON_KNOB_Z_FORM 0
 #define POISSON_KNOB_Y_FORM 1
 #define POISSON_KNOB_X_FORM 2
+#define POISSON_KNOB_XY_FORM 3
 int poisson_plan_get_knob(poisson_plan p, int knob, int *value);
 int poisson_plan_set_knob(poisson_plan p, int knob, int value);
 

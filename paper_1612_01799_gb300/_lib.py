@@ -67,6 +67,7 @@ class PoissonError(RuntimeError):
 KNOB_Z_FORM = 0
 KNOB_Y_FORM = 1
 KNOB_X_FORM = 2
+KNOB_XY_FORM = 3
 
 
 def load():

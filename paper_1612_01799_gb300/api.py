@@ -156,6 +156,19 @@ class Plan:
     def x_form(self, value):
         _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_X_FORM, int(value)), "poisson_plan_set_knob")
 
+    @property
+    def xy_form(self):
+        """Whether the x and y passes run separately (0) or fused (1: one kernel per
+        direction, the x spectrum handed over through an L2-resident ring of planes)."""
+        v = ctypes.c_int()
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_XY_FORM, ctypes.byref(v)),
+                   "poisson_plan_get_knob")
+        return v.value
+
+    @xy_form.setter
+    def xy_form(self, value):
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_XY_FORM, int(value)), "poisson_plan_set_knob")
+
     def gauss_sum(self):
         n = self.info()["n_terms"]
         tau, w = np.empty(n), np.empty(n)

@@ -29,6 +29,11 @@ cudaError_t y_passes_f32(const DevicePlan &, cudaStream_t);
 cudaError_t y_passes_f64(const DevicePlan &, cudaStream_t);
 cudaError_t x_passes_f32(const DevicePlan &, cudaStream_t);
 cudaError_t x_passes_f64(const DevicePlan &, cudaStream_t);
+cudaError_t xy_passes_f32(const DevicePlan &, cudaStream_t);
+cudaError_t xy_passes_f64(const DevicePlan &, cudaStream_t);
+cudaError_t launch_xy_passes(const DevicePlan &p, cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? xy_passes_f32(p, s) : xy_passes_f64(p, s);
+}
 cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s) {
     return p.dtype == POISSON_F32 ? x_passes_f32(p, s) : x_passes_f64(p, s);
 }
@@ -96,7 +101,7 @@ cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const dou
 // ---- autotuning of kernel variants --------------------------------------------------------
 // Decisions per (device, N, dtype), made by the first plan of that shape and reused.
 struct TuneEntry {
-    int dev, N, dtype, zform, yform, xform;
+    int dev, N, dtype, zform, yform, xform, xyform;
 };
 static std::vector<TuneEntry> g_tune;
 static std::mutex g_tune_mutex;
@@ -139,16 +144,19 @@ static cudaError_t pick_form(int forms, int *field, Run &&run, cudaStream_t s, c
     return cudaSuccess;
 }
 
-// Choose p.zform, p.yform and p.xform: the cached decision for this shape, else the fastest
-// forms that exist, timed on p's zeroed workspace.  The z pass writes only w3, the y passes
-// w2 and w1, the x passes (timed with w2 as density and output) w1 and w2, and every solve
-// writes each of them before reading it.
+// Choose p.zform, p.yform, p.xform and p.xyform: the cached decision for this shape, else
+// the fastest forms that exist, timed on p's zeroed workspace.  The z pass writes only w3,
+// the y passes w2 and w1, the x passes (timed with w2 as density and output) w1 and w2, the
+// x-y passes all three, and every solve writes each of them before reading it.  The x-y
+// form is timed last, against the separate passes in the y and x forms just chosen.
 static cudaError_t autotune(DevicePlan &p, int dev) {
     p.zform = 0;
     p.yform = 0;
     p.xform = 0;
+    p.xyform = 0;
     const int zf = z_forms(p.N, p.dtype), yf = y_forms(p.N, p.dtype), xf = x_forms(p.N, p.dtype);
-    if (zf == 1 && yf == 1 && xf == 1) return cudaSuccess;
+    const int xyf = p.sync ? xy_forms(p.N, p.dtype) : 1;
+    if (zf == 1 && yf == 1 && xf == 1 && xyf == 1) return cudaSuccess;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (const TuneEntry &t : g_tune)
@@ -156,6 +164,7 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
                 p.zform = t.zform;
                 p.yform = t.yform;
                 p.xform = t.xform;
+                p.xyform = t.xyform;
                 return cudaSuccess;
             }
     }
@@ -167,11 +176,12 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
     if (e == cudaSuccess) e = pick_form(zf, &p.zform, [&] { return launch_z_pass(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(yf, &p.yform, [&] { return launch_y_passes(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(xf, &p.xform, [&] { return launch_x_passes(p, s); }, s, a, b);
+    if (e == cudaSuccess) e = pick_form(xyf, &p.xyform, [&] { return launch_xy_passes(p, s); }, s, a, b);
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) {
-        p.zform = p.yform = p.xform = 0;
+        p.zform = p.yform = p.xform = p.xyform = 0;
         return e;
     }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -180,9 +190,10 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
             p.zform = t.zform;
             p.yform = t.yform;
             p.xform = t.xform;
+            p.xyform = t.xyform;
             return cudaSuccess;
         }
-    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform, p.yform, p.xform});
+    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform, p.yform, p.xform, p.xyform});
     return cudaSuccess;
 }
 }  // namespace gsp
@@ -222,7 +233,7 @@ static void free_plan(poisson_plan p) {
     if (!p) return;
     void *twc = p->dp.twc != p->dp.tw ? p->dp.twc : nullptr;
     void *bufs[] = {p->dp.sym, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->dp.status,
-                    p->dp.tail, p->stage_in, p->stage_out};
+                    p->dp.tail, p->dp.sync, p->stage_in, p->stage_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->have_events)
@@ -310,6 +321,11 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     if ((e = cudaMalloc(&p->dp.status, sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.tail, 2 * sizeof(double) * max_batch)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.status, 0, sizeof(int))) != cudaSuccess) return fail(e);
+    if (gsp::xy_forms(N, dtype) != 1) {
+        const size_t sync_bytes = sizeof(int) * (size_t)gsp::xy_sync_ints();
+        if ((e = cudaMalloc(&p->dp.sync, sync_bytes)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemset(p->dp.sync, 0, sync_bytes)) != cudaSuccess) return fail(e);
+    }
     if ((e = gsp::encode_tma_maps(p->dp)) != cudaSuccess) return fail(e);
     gsp::ForkPool *pool = nullptr;
     if ((e = gsp::fork_pool(p->device, &pool)) != cudaSuccess) return fail(e);
@@ -361,6 +377,7 @@ extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
     if (knob == POISSON_KNOB_Z_FORM) *value = p->dp.zform;
     else if (knob == POISSON_KNOB_Y_FORM) *value = p->dp.yform;
     else if (knob == POISSON_KNOB_X_FORM) *value = p->dp.xform;
+    else if (knob == POISSON_KNOB_XY_FORM) *value = p->dp.xyform;
     else return POISSON_ERR_ARG;
     return POISSON_OK;
 }
@@ -377,6 +394,9 @@ extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     } else if (knob == POISSON_KNOB_X_FORM) {
         forms = gsp::x_forms(p->dp.N, p->dp.dtype);
         field = &p->dp.xform;
+    } else if (knob == POISSON_KNOB_XY_FORM) {
+        forms = p->dp.sync ? gsp::xy_forms(p->dp.N, p->dp.dtype) : 1;
+        field = &p->dp.xyform;
     } else {
         return POISSON_ERR_ARG;
     }

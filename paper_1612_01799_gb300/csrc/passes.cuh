@@ -124,6 +124,7 @@ template <typename Real> using Cx2 = typename std::conditional<sizeof(Real) == 4
 }  // namespace gsp
 #include "passes_tma.cuh"
 #include "passes_zwarp.cuh"
+#include "passes_xy.cuh"
 namespace gsp {
 
 // ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
@@ -542,24 +543,70 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
     return cudaGetLastError();
 }
 
+// The fused x and y passes (p.xyform == 1, k_xy_fwd / k_yx_inv): FP32 at the warp-form
+// sizes, on plans that carry a counter block.  The ring lives in the workspace the pass does
+// not touch otherwise: w3 on the way in, w2 on the way out (2N max_batch slots of N rows).
+template <typename Real, int N> constexpr bool xy_fused_form() { return std::is_same<Real, float>::value && warp_n(N); }
+template <typename Real, int N> bool xy_fused_on(const DevicePlan &p) {
+    return xy_fused_form<Real, N>() && p.xyform == 1 && p.sync != nullptr;
+}
+
+template <typename Real, int N>
+cudaError_t xy_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s, bool fwd) {
+    if constexpr (xy_fused_form<Real, N>()) {
+        using X = XYWarp<N / 16>;
+        const int P = B * N, S = X::NX + X::NY;
+        const int smem = fwd ? X::SMEM_F : X::SMEM_I;
+        int G;
+        if (fwd) {
+            GSP_CHECK(set_smem(k_xy_fwd<N / 16>, smem));
+            G = persistent_blocks(k_xy_fwd<N / 16>, X::NT, smem, P * S);
+        } else {
+            GSP_CHECK(set_smem(k_yx_inv<N / 16>, smem));
+            G = persistent_blocks(k_yx_inv<N / 16>, X::NT, smem, P * S);
+        }
+        // Steps (planes) the resident CTAs hold at once; the consumers trail the producers
+        // by D steps so that a plane's producers have finished when its consumers start, and
+        // a slot comes back R > D steps after its plane was produced.
+        const int inflight = (G + S - 1) / S;
+        const int R = std::min(std::min(kRingMax, 2 * N * p.max_batch), 3 * inflight + 4);
+        const int D = std::min(std::min(inflight + inflight / 2 + 2, R - 1), P);
+        const XYOrder ord{P, D, fwd ? X::NX : X::NY, fwd ? X::NY : X::NX};
+        const float2 *tw = static_cast<const float2 *>(p.tw);
+        if (fwd)
+            k_xy_fwd<N / 16><<<G, X::NT, smem, s>>>(rho, static_cast<float2 *>(p.w3), p.tm_rf, p.tm_yw2, tw, ord, R,
+                                                    p.Px, p.sync, p.status);
+        else
+            k_yx_inv<N / 16><<<G, X::NT, smem, s>>>(p.tm_yw3, static_cast<float2 *>(p.w2), u, tw, ord, R, p.Px,
+                                                    p.sync, p.status);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The five passes.  With the fused x-y form the forward x and y passes are one launch
+// (timed as the x forward, ev[1] and ev[2] recorded together) and so are the inverse y and
+// x passes (timed as the y inverse).
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
                     cudaEvent_t *ev, double *tail) {
-
+    const bool fused = xy_fused_on<Real, N>(p);
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
-    GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, true)));
+    if (fused) GSP_CHECK((xy_pass<Real, N>(p, rho, u, B, s, true)));
+    else GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, true)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
-    GSP_CHECK((y_pass<Real, N>(p, B, s, true)));
+    if (!fused) GSP_CHECK((y_pass<Real, N>(p, B, s, true)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
     GSP_CHECK((z_pass<Real, N>(p, B, s, tail)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
 
-    GSP_CHECK((y_pass<Real, N>(p, B, s, false)));
+    if (fused) GSP_CHECK((xy_pass<Real, N>(p, rho, u, B, s, false)));
+    else GSP_CHECK((y_pass<Real, N>(p, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
-    GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, false)));
+    if (!fused) GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
     return cudaSuccess;
 }
@@ -627,6 +674,9 @@ cudaError_t encode_n(DevicePlan &p) {
                             CU_TENSOR_MAP_SWIZZLE_128B));
         GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16>::TC, N, 1,
                             CU_TENSOR_MAP_SWIZZLE_128B));
+        // The fused forward pass's ring of N-row plane slots in w3.
+        GSP_CHECK(encode_3d(&p.tm_rf, U64, p.w3, N + 1, N, 2 * BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16>::TC, N,
+                            1, CU_TENSOR_MAP_SWIZZLE_128B));
     }
     if constexpr (zwarp_form<Real, N>()) {
         // Columns kx > N lie outside these maps: loads read zeros there, stores skip them.
@@ -656,6 +706,8 @@ cudaError_t encode_n(DevicePlan &p) {
     EXT template cudaError_t y_pass<Real, n>(const DevicePlan &, int, cudaStream_t, bool);                 \
     EXT template cudaError_t x_pass<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int,   \
                                              cudaStream_t, bool);                                          \
+    EXT template cudaError_t xy_pass<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int,  \
+                                              cudaStream_t, bool);                                         \
     EXT template cudaError_t encode_n<Real, n>(DevicePlan &);
 
 template <typename Real>
@@ -711,6 +763,32 @@ cudaError_t x_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
     case n: {                                                                \
         cudaError_t e = x_pass<Real, n>(p, a, a, 1, s, true);                \
         return e != cudaSuccess ? e : x_pass<Real, n>(p, a, a, 1, s, false); \
+    }
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+// The forward and inverse x and y passes of one density on spare workspace, in the form
+// p.xyform selects (for timing the forms): separately w2 -> w1 -> w2 and w3 -> w1 -> w2;
+// fused w1 -> w2 (ring in w3) and w3 -> w1 (ring in w2).
+template <typename Real>
+cudaError_t xy_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    switch (p.N) {
+#define GSP_CASE(n)                                                                  \
+    case n: {                                                                        \
+        PtrArray a{};                                                                \
+        a.p[0] = xy_fused_on<Real, n>(p) ? p.w1 : p.w2;                              \
+        if (xy_fused_on<Real, n>(p)) {                                               \
+            cudaError_t e = xy_pass<Real, n>(p, a, a, 1, s, true);                   \
+            return e != cudaSuccess ? e : xy_pass<Real, n>(p, a, a, 1, s, false);    \
+        }                                                                            \
+        cudaError_t e = x_pass<Real, n>(p, a, a, 1, s, true);                        \
+        if (e == cudaSuccess) e = y_pass<Real, n>(p, 1, s, true);                    \
+        if (e == cudaSuccess) e = y_pass<Real, n>(p, 1, s, false);                   \
+        return e != cudaSuccess ? e : x_pass<Real, n>(p, a, a, 1, s, false);         \
     }
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE

@@ -18,6 +18,9 @@ cudaError_t encode_maps_f32(DevicePlan &p) { return encode_dispatch<float>(p); }
 cudaError_t z_pass_f32(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<float>(p, s); }
 cudaError_t y_passes_f32(const DevicePlan &p, cudaStream_t s) { return y_pass_dispatch<float>(p, s); }
 cudaError_t x_passes_f32(const DevicePlan &p, cudaStream_t s) { return x_pass_dispatch<float>(p, s); }
+cudaError_t xy_passes_f32(const DevicePlan &p, cudaStream_t s) { return xy_pass_dispatch<float>(p, s); }
+int xy_sync_ints() { return kSyncInts; }
+int xy_forms(int N, int dtype) { return 1 | (dtype == 0 && warp_n(N) ? 2 : 0); }
 int x_forms(int N, int dtype) { return 1 | (dtype == 0 && (warp_n(N) || N == XWarp2::N) ? 2 : 0); }
 int y_forms(int N, int dtype) { return 1 | (dtype == 0 && warp_n(N) ? 2 : 0); }
 int z_forms(int N, int dtype) {

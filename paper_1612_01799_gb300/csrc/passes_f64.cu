@@ -18,4 +18,5 @@ cudaError_t encode_maps_f64(DevicePlan &p) { return encode_dispatch<double>(p); 
 cudaError_t z_pass_f64(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<double>(p, s); }
 cudaError_t y_passes_f64(const DevicePlan &p, cudaStream_t s) { return y_pass_dispatch<double>(p, s); }
 cudaError_t x_passes_f64(const DevicePlan &p, cudaStream_t s) { return x_pass_dispatch<double>(p, s); }
+cudaError_t xy_passes_f64(const DevicePlan &p, cudaStream_t s) { return xy_pass_dispatch<double>(p, s); }
 }  // namespace gsp

@@ -452,6 +452,57 @@ template <int E1> struct YWarp {
     static_assert((N * 128) % 1024 == 0, "the second half of a 2N-row tile starts 1024-byte aligned");
 };
 
+// y forward of warp g's column pair, first half: its N input rows from the 128-byte-swizzled
+// tile at inb (row y at inb + io + 4096 (y / 32) for lane y % 32), F1 to F3.
+template <int E1>
+__device__ __forceinline__ void yw_fwd_front(CV *v, const unsigned char *inb, int io, const ZwLane &zl, const float2 *T) {
+#pragma unroll
+    for (int r = 0; r < E1 / 2; ++r) {
+        const float4 f = *reinterpret_cast<const float4 *>(inb + io + 4096 * r);
+        v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
+        if (r & 1) v[r] = zw_sign(v[r], zl.sg);
+    }
+    zw_front<E1>(v, zl, T);
+}
+// Second half: the exchange through xb, the 16-point DFTs, and the 2N spectrum rows to xb
+// (reader lane with base kb holds rows kb + 2 E1 k2, chunk g ^ (row & 7)).
+template <int E1>
+__device__ __forceinline__ void yw_fwd_back(CV *v, const ZwLane &zl, unsigned char *xb, int kb, int g) {
+    zw_exchange<E1>(v, zl);
+    if (zl.rd) dft<16, -1>(v);  // v[k2] = X[kb + 2 E1 k2]
+    __syncwarp();
+    if (zl.rd) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2)
+            *reinterpret_cast<float4 *>(xb + zw_sw128(kb + 2 * E1 * k2, g)) =
+                make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
+    }
+}
+// y inverse of warp g's column pair: the 2N spectrum rows from xb, the N kept rows back to xb
+// in the input tile's layout (row y at xb + io + 4096 (y / 32)).
+template <int E1>
+__device__ __forceinline__ void yw_inv(CV *v, const ZwLane &zl, unsigned char *xb, int kb, int io, int g,
+                                       const float2 *T) {
+    if (zl.rd) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const float4 f = *reinterpret_cast<const float4 *>(xb + zw_sw128(kb + 2 * E1 * k2, g));
+            v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
+        }
+        dft<16, 1>(v);
+    }
+    __syncwarp();  // every lane has read its inputs: its chunks take exchange slots
+    zw_exchange_adj<E1>(v, zl);
+    zw_back<E1>(v, zl, T);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < E1 / 2; ++r) {
+        CV x = v[r];
+        if (r & 1) x = zw_sign(x, zl.sg);
+        *reinterpret_cast<float4 *>(xb + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+    }
+}
+
 template <int E1, bool FWD>
 __global__ void __launch_bounds__(YWarp<E1>::NT, 2)
 k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
@@ -501,7 +552,6 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     const int io = zw_sw128(q, g);
     // Rows of the 2N-point spectrum a reader holds: kb + 2 E1 k2.
     const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
-    auto krow = [&](int k2) { return zw_sw128(kb + 2 * E1 * k2, g); };
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
@@ -511,48 +561,12 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         CV v[16];
         if (!mbar_wait(bar, ph, status)) return;
         if constexpr (FWD) {
-            if (valid) {
-#pragma unroll
-                for (int r = 0; r < H; ++r) {
-                    const float4 f = *reinterpret_cast<const float4 *>(inb + io + 4096 * r);
-                    v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
-                    if (r & 1) v[r] = zw_sign(v[r], zl.sg);
-                }
-            }
+            if (valid) yw_fwd_front<E1>(v, inb, io, zl, T);
             if (last_arrival(0) && more) issue_in(t + gridDim.x);
-            if (valid) zw_front<E1>(v, zl, T);
             if (!mbar_wait(bar + 1, ph, status)) return;  // the previous tile's store has read xb
-            if (valid) {
-                zw_exchange<E1>(v, zl);
-                if (zl.rd) dft<16, -1>(v);  // v[k2] = X[kb + 2 E1 k2]
-            }
-            __syncwarp();
-            if (valid && zl.rd) {
-#pragma unroll
-                for (int k2 = 0; k2 < 16; ++k2)
-                    *reinterpret_cast<float4 *>(xb + krow(k2)) = make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
-            }
+            if (valid) yw_fwd_back<E1>(v, zl, xb, kb, g);
         } else {
-            if (valid) {
-                if (zl.rd) {
-#pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) {
-                        const float4 f = *reinterpret_cast<const float4 *>(xb + krow(k2));
-                        v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
-                    }
-                    dft<16, 1>(v);
-                }
-                __syncwarp();  // every lane has read its inputs: its chunks take exchange slots
-                zw_exchange_adj<E1>(v, zl);
-                zw_back<E1>(v, zl, T);
-                __syncwarp();
-#pragma unroll
-                for (int r = 0; r < H; ++r) {
-                    CV x = v[r];
-                    if (r & 1) x = zw_sign(x, zl.sg);
-                    *reinterpret_cast<float4 *>(xb + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
-                }
-            }
+            if (valid) yw_inv<E1>(v, zl, xb, kb, io, g, T);
         }
         fence_proxy_async();
         if (last_arrival(1)) {
@@ -601,12 +615,85 @@ template <int N> __device__ __forceinline__ void xw_tables(float2 *T, float2 *T2
     for (int i = threadIdx.x; i <= N / 2; i += blockDim.x) T2[i] = tw[i];
 }
 
+// Lane qq's samples of row pair i (rows 2i, 2i+1 of the stacked densities): f[2r], f[2r+1]
+// are the pairs z[qq + 16 r] of the two rows.
+template <int N> __device__ __forceinline__ void xw_load(const PtrArray &rho, int i, int qq, float2 *f) {
+    constexpr int H = N / 32, NN = N * N;
+    const int b = (2 * i) / NN;
+    const float2 *s = reinterpret_cast<const float2 *>(rho.p[b]) + (long long)(2 * i - b * NN) * (N / 2) + qq;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        f[2 * r] = __ldg(s + 16 * r);
+        f[2 * r + 1] = __ldg(s + N / 2 + 16 * r);
+    }
+}
+
+// Forward x transform of one loaded row pair by a half-warp (lane qq, 4 KB of exchange slots
+// at shared address xs): the N+1 Hermitian bins X_k of both rows to d0[k], d1[k].
+template <int N>
+__device__ __forceinline__ void xw_fwd_pair(const float2 *f, uint32_t xs, int qq, const float2 *T, const float2 *T2,
+                                            float2 *d0, float2 *d1) {
+    using M = ZwMap<N / 16>;
+    constexpr int E1 = N / 16, H = E1 / 2;
+    const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
+    const bool rd = qq < E1;  // lane qq gathers k1 = qq after the exchange
+    CV v[16];
+#pragma unroll
+    for (int r = 0; r < H; ++r) v[r] = {f2(f[2 * r].x, f[2 * r + 1].x), f2(f[2 * r].y, f[2 * r + 1].y)};
+    zw_f1<E1>(v);
+#pragma unroll
+    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<-1>(v[j], T[M::kappa0(j) * 16 + qq]);
+#pragma unroll
+    for (int j = 0; j < E1; ++j) {
+        const int k0 = M::kappa0(j);
+        zw_sts((aw ^ (16 * (k0 & 7))) + 256 * k0, v[j]);
+    }
+    __syncwarp();
+    if (rd) {
+#pragma unroll
+        for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (16 * (p & 7))) + 16 * (p & 8));
+        dft<16, -1>(v);  // v[k2] = C[qq + E1 k2]
+    }
+    __syncwarp();
+    if (rd) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) zw_sts(xs + 16 * (qq + E1 * k2), v[k2]);
+    }
+    __syncwarp();
+    const float2 h = f2(0.5f, 0.5f);
+#pragma unroll
+    for (int k2 = 0; k2 < 9; ++k2) {
+        const int k = qq + E1 * k2;
+        if (!rd || k > N / 2) continue;
+        const CV ck = v[k2], cn = zw_lds(xs + 16 * (k == 0 ? 0 : N - k));
+        const CV ev = {f2mul(h, f2add(ck.re, cn.re)), f2mul(h, f2sub(ck.im, cn.im))};
+        const CV od = {f2mul(h, f2add(ck.im, cn.im)), f2mul(h, f2sub(cn.re, ck.re))};
+        if (k == 0) {
+            const float2 x0 = f2add(ev.re, od.re), xn = f2sub(ev.re, od.re);
+            d0[0] = f2(x0.x, 0.f);
+            d1[0] = f2(x0.y, 0.f);
+            d0[N] = f2(xn.x, 0.f);
+            d1[N] = f2(xn.y, 0.f);
+        } else {
+            const CV t = zw_twmul<-1>(od, T2[k]);
+            const CV xk = cadd(ev, t);
+            d0[k] = f2(xk.re.x, xk.im.x);
+            d1[k] = f2(xk.re.y, xk.im.y);
+            if (2 * k != N) {
+                const CV xn = csub(ev, t);
+                d0[N - k] = f2(xn.re.x, -xn.im.x);
+                d1[N - k] = f2(xn.re.y, -xn.im.y);
+            }
+        }
+    }
+    __syncwarp();  // the slots are read before the next pair's exchange writes them
+}
+
 template <int N>
 __global__ void __launch_bounds__(XWarp<N>::NT, 2)
 k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restrict__ tw, int npairs, int Px) {
     using X = XWarp<N>;
-    using M = ZwMap<X::E1>;
-    constexpr int E1 = X::E1, H = X::H, NN = N * N;
+    constexpr int H = X::H;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *T = reinterpret_cast<float2 *>(smraw + X::OFF_T);
     float2 *T2 = reinterpret_cast<float2 *>(smraw + X::OFF_T2);
@@ -614,83 +701,99 @@ k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restr
     __syncthreads();
     const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
     const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
+    const int stride = gridDim.x * (X::NT / 16);
+    int i = blockIdx.x * (X::NT / 16) + hw;
+    float2 f[2 * H], g[2 * H];
+    if (i < npairs) xw_load<N>(rho, i, qq, f);
+    for (; i < npairs; i += stride) {
+#pragma unroll
+        for (int r = 0; r < 2 * H; ++r) g[r] = f[r];
+        if (i + stride < npairs) xw_load<N>(rho, i + stride, qq, f);
+        float2 *d0 = out + (long long)(2 * i) * Px;
+        xw_fwd_pair<N>(g, xs, qq, T, T2, d0, d0 + Px);
+    }
+}
+
+// Load of a value of the x passes' input rows: through the read-only path (ldg) for rows no
+// kernel writes while they are read, else through L2 only (rows rewritten during the kernel).
+template <bool CG> __device__ __forceinline__ float2 xw_ld(const float2 *p) { return CG ? __ldcg(p) : __ldg(p); }
+
+// Inverse x transform of one row pair by a half-warp: the N+1 bins of rows s0, s1 to the
+// N/2 sample pairs of both rows (lane qq writes pairs qq + 16 r of row 0 at d[16 r] and of
+// row 1 at d[N/2 + 16 r]).  The bins are loaded in batches of NB per lane and row.
+template <int N, bool CG, int NB = 5>
+__device__ __forceinline__ void xw_inv_pair(const float2 *s0, const float2 *s1, uint32_t xs, int qq, const float2 *T,
+                                            const float2 *T2, float2 *d) {
+    using M = ZwMap<N / 16>;
+    constexpr int E1 = N / 16, H = E1 / 2;
     const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
     const bool rd = qq < E1;  // lane qq gathers k1 = qq after the exchange
-    const int stride = gridDim.x * (X::NT / 16);
-    auto load = [&](int i, float2 *f) {
-        const int b = (2 * i) / NN;
-        const float2 *s = reinterpret_cast<const float2 *>(rho.p[b]) + (long long)(2 * i - b * NN) * (N / 2) + qq;
+    CV v[16];
+    // (Y_k, Y_{N-k}) -> (C_k, C_{N-k}) for k = qq + E1 k2 <= N/2, in batches of loads.
 #pragma unroll
-        for (int r = 0; r < H; ++r) {
-            f[2 * r] = __ldg(s + 16 * r);
-            f[2 * r + 1] = __ldg(s + N / 2 + 16 * r);
+    for (int k20 = 0; k20 < 9; k20 += NB) {
+        float2 yk0[NB], yk1[NB], yn0[NB], yn1[NB];
+#pragma unroll
+        for (int d2 = 0; d2 < NB; ++d2) {
+            const int k2 = k20 + d2, k = qq + E1 * k2;
+            if (k2 > 8 || !rd || k > N / 2) continue;
+            yk0[d2] = xw_ld<CG>(s0 + k);
+            yk1[d2] = xw_ld<CG>(s1 + k);
+            yn0[d2] = xw_ld<CG>(s0 + (N - k));
+            yn1[d2] = xw_ld<CG>(s1 + (N - k));
         }
-    };
-    int i = blockIdx.x * (X::NT / 16) + hw;
-    float2 f[2 * H];
-    if (i < npairs) load(i, f);
-    for (; i < npairs; i += stride) {
-        CV v[16];
 #pragma unroll
-        for (int r = 0; r < H; ++r) v[r] = {f2(f[2 * r].x, f[2 * r + 1].x), f2(f[2 * r].y, f[2 * r + 1].y)};
-        if (i + stride < npairs) load(i + stride, f);
-        zw_f1<E1>(v);
-#pragma unroll
-        for (int j = 0; j < E1; ++j) v[j] = zw_twmul<-1>(v[j], T[M::kappa0(j) * 16 + qq]);
-#pragma unroll
-        for (int j = 0; j < E1; ++j) {
-            const int k0 = M::kappa0(j);
-            zw_sts((aw ^ (16 * (k0 & 7))) + 256 * k0, v[j]);
-        }
-        __syncwarp();
-        if (rd) {
-#pragma unroll
-            for (int p = 0; p < 16; ++p) v[p] = zw_lds((ar ^ (16 * (p & 7))) + 16 * (p & 8));
-            dft<16, -1>(v);  // v[k2] = C[qq + E1 k2]
-        }
-        __syncwarp();
-        if (rd) {
-#pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) zw_sts(xs + 16 * (qq + E1 * k2), v[k2]);
-        }
-        __syncwarp();
-        float2 *d0 = out + (long long)(2 * i) * Px, *d1 = d0 + Px;
-        const float2 h = f2(0.5f, 0.5f);
-#pragma unroll
-        for (int k2 = 0; k2 < 9; ++k2) {
-            const int k = qq + E1 * k2;
-            if (!rd || k > N / 2) continue;
-            const CV ck = v[k2], cn = zw_lds(xs + 16 * (k == 0 ? 0 : N - k));
-            const CV ev = {f2mul(h, f2add(ck.re, cn.re)), f2mul(h, f2sub(ck.im, cn.im))};
-            const CV od = {f2mul(h, f2add(ck.im, cn.im)), f2mul(h, f2sub(cn.re, ck.re))};
+        for (int d2 = 0; d2 < NB; ++d2) {
+            const int k2 = k20 + d2, k = qq + E1 * k2;
+            if (k2 > 8 || !rd || k > N / 2) continue;
             if (k == 0) {
-                const float2 x0 = f2add(ev.re, od.re), xn = f2sub(ev.re, od.re);
-                d0[0] = f2(x0.x, 0.f);
-                d1[0] = f2(x0.y, 0.f);
-                d0[N] = f2(xn.x, 0.f);
-                d1[N] = f2(xn.y, 0.f);
+                v[0] = {f2(yk0[0].x + yn0[0].x, yk1[0].x + yn1[0].x), f2(yk0[0].x - yn0[0].x, yk1[0].x - yn1[0].x)};
             } else {
-                const CV t = zw_twmul<-1>(od, T2[k]);
-                const CV xk = cadd(ev, t);
-                d0[k] = f2(xk.re.x, xk.im.x);
-                d1[k] = f2(xk.re.y, xk.im.y);
-                if (2 * k != N) {
-                    const CV xn = csub(ev, t);
-                    d0[N - k] = f2(xn.re.x, -xn.im.x);
-                    d1[N - k] = f2(xn.re.y, -xn.im.y);
-                }
+                const CV yk = {f2(yk0[d2].x, yk1[d2].x), f2(yk0[d2].y, yk1[d2].y)};
+                const CV yn = {f2(yn0[d2].x, yn1[d2].x), f2(yn0[d2].y, yn1[d2].y)};
+                const CV ev = {f2add(yk.re, yn.re), f2sub(yk.im, yn.im)};
+                const CV od = zw_twmul<1>(CV{f2sub(yk.re, yn.re), f2add(yk.im, yn.im)}, T2[k]);
+                v[k2] = add_rot<1>(ev, od);
+                if (2 * k != N) zw_sts(xs + 16 * (N - k), add_rot<1>(cconj_cv(ev), cconj_cv(od)));
             }
         }
-        __syncwarp();  // the slots are read before the next pair's exchange writes them
     }
+    __syncwarp();
+    if (rd) {
+#pragma unroll
+        for (int k2 = 8; k2 < 16; ++k2) {
+            const int k = qq + E1 * k2;
+            if (k != N / 2) v[k2] = zw_lds(xs + 16 * k);
+        }
+    }
+    __syncwarp();
+    if (rd) {
+        dft<16, 1>(v);
+#pragma unroll
+        for (int p = 0; p < 16; ++p) zw_sts((ar ^ (16 * (p & 7))) + 16 * (p & 8), v[p]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < E1; ++j) {
+        const int k0 = M::kappa0(j);
+        v[j] = zw_lds((aw ^ (16 * (k0 & 7))) + 256 * k0);
+    }
+#pragma unroll
+    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<1>(v[j], T[M::kappa0(j) * 16 + qq]);
+    zw_f1_adj<E1>(v);
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        d[16 * r] = f2(v[r].re.x, v[r].im.x);
+        d[N / 2 + 16 * r] = f2(v[r].re.y, v[r].im.y);
+    }
+    __syncwarp();  // the slots are read before the next pair writes them
 }
 
 template <int N>
 __global__ void __launch_bounds__(XWarp<N>::NT, 2)
 k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__restrict__ tw, int npairs, int Px) {
     using X = XWarp<N>;
-    using M = ZwMap<X::E1>;
-    constexpr int E1 = X::E1, H = X::H, NN = N * N;
+    constexpr int NN = N * N;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *T = reinterpret_cast<float2 *>(smraw + X::OFF_T);
     float2 *T2 = reinterpret_cast<float2 *>(smraw + X::OFF_T2);
@@ -698,72 +801,12 @@ k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__re
     __syncthreads();
     const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
     const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
-    const uint32_t aw = xs + 16 * qq, ar = xs + 256 * qq + 16 * (qq & 7);
-    const bool rd = qq < E1;  // lane qq gathers k1 = qq after the exchange
     const int stride = gridDim.x * (X::NT / 16);
     for (int i = blockIdx.x * (X::NT / 16) + hw; i < npairs; i += stride) {
-        const float2 *s0 = in + (long long)(2 * i) * Px, *s1 = s0 + Px;
-        CV v[16];
-        // (Y_k, Y_{N-k}) -> (C_k, C_{N-k}) for k = qq + E1 k2 <= N/2, in two batches of loads.
-#pragma unroll
-        for (int k20 = 0; k20 < 9; k20 += 5) {
-            float2 yk0[5], yk1[5], yn0[5], yn1[5];
-#pragma unroll
-            for (int d2 = 0; d2 < 5; ++d2) {
-                const int k2 = k20 + d2, k = qq + E1 * k2;
-                if (k2 > 8 || !rd || k > N / 2) continue;
-                yk0[d2] = __ldg(s0 + k);
-                yk1[d2] = __ldg(s1 + k);
-                yn0[d2] = __ldg(s0 + (N - k));
-                yn1[d2] = __ldg(s1 + (N - k));
-            }
-#pragma unroll
-            for (int d2 = 0; d2 < 5; ++d2) {
-                const int k2 = k20 + d2, k = qq + E1 * k2;
-                if (k2 > 8 || !rd || k > N / 2) continue;
-                if (k == 0) {
-                    v[0] = {f2(yk0[0].x + yn0[0].x, yk1[0].x + yn1[0].x), f2(yk0[0].x - yn0[0].x, yk1[0].x - yn1[0].x)};
-                } else {
-                    const CV yk = {f2(yk0[d2].x, yk1[d2].x), f2(yk0[d2].y, yk1[d2].y)};
-                    const CV yn = {f2(yn0[d2].x, yn1[d2].x), f2(yn0[d2].y, yn1[d2].y)};
-                    const CV ev = {f2add(yk.re, yn.re), f2sub(yk.im, yn.im)};
-                    const CV od = zw_twmul<1>(CV{f2sub(yk.re, yn.re), f2add(yk.im, yn.im)}, T2[k]);
-                    v[k2] = add_rot<1>(ev, od);
-                    if (2 * k != N) zw_sts(xs + 16 * (N - k), add_rot<1>(cconj_cv(ev), cconj_cv(od)));
-                }
-            }
-        }
-        __syncwarp();
-        if (rd) {
-#pragma unroll
-            for (int k2 = 8; k2 < 16; ++k2) {
-                const int k = qq + E1 * k2;
-                if (k != N / 2) v[k2] = zw_lds(xs + 16 * k);
-            }
-        }
-        __syncwarp();
-        if (rd) {
-            dft<16, 1>(v);
-#pragma unroll
-            for (int p = 0; p < 16; ++p) zw_sts((ar ^ (16 * (p & 7))) + 16 * (p & 8), v[p]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < E1; ++j) {
-            const int k0 = M::kappa0(j);
-            v[j] = zw_lds((aw ^ (16 * (k0 & 7))) + 256 * k0);
-        }
-#pragma unroll
-        for (int j = 0; j < E1; ++j) v[j] = zw_twmul<1>(v[j], T[M::kappa0(j) * 16 + qq]);
-        zw_f1_adj<E1>(v);
+        const float2 *s0 = in + (long long)(2 * i) * Px;
         const int b = (2 * i) / NN;
         float2 *d = reinterpret_cast<float2 *>(const_cast<void *>(u.p[b])) + (long long)(2 * i - b * NN) * (N / 2) + qq;
-#pragma unroll
-        for (int r = 0; r < H; ++r) {
-            d[16 * r] = f2(v[r].re.x, v[r].im.x);
-            d[N / 2 + 16 * r] = f2(v[r].re.y, v[r].im.y);
-        }
-        __syncwarp();  // the slots are read before the next pair writes them
+        xw_inv_pair<N, false>(s0, s0 + Px, xs, qq, T, T2, d);
     }
 }
 

@@ -50,12 +50,19 @@ struct DevicePlan {
     // x pass form: 0 block form (a tile of rows staged in shared memory), 1 warp form (a
     // half-warp or warp per row pair, FP32, N = 64 ... 256 and 512)
     int xform = 0;
+    // x-y form: 0 the x and y passes as separate launches, 1 fused (k_xy_fwd / k_yx_inv:
+    // the x spectrum passes through an L2-resident ring of plane slots; FP32, N = 64 ... 256,
+    // plans with a counter block)
+    int xyform = 0;
+    // Counter block of the fused x-y passes (kSyncInts ints, zero between launches), or null.
+    int *sync = nullptr;
     // TMA descriptors of the column passes' inputs (y forward: w1, z: w2 and the symbol,
     // y inverse: w3), encoded once for these buffers; and of the warp-form z pass (w2 in,
     // symbol, w3 out; 128- and 64-byte swizzled boxes), encoded where that form exists.
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
     CUtensorMap tm_zw_in, tm_zw_sym, tm_zw_out;
-    CUtensorMap tm_yw1, tm_yw2, tm_yw3;  // warp-form y passes: 256-row boxes of w1, w2, w3
+    CUtensorMap tm_yw1, tm_yw2, tm_yw3;  // warp-form y passes: N-row boxes of w1, w2, w3
+    CUtensorMap tm_rf;                   // fused forward x-y pass: N-row boxes of its ring in w3
 };
 
 constexpr int kStatusTimeoutBit = 1;  // bit of DevicePlan::status set by a timed-out wait
@@ -97,6 +104,17 @@ int y_forms(int N, int dtype);
 
 // The two y passes alone, one density, in the form p.yform selects (for timing the forms).
 cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s);
+
+// Forms of the x-y passes that exist for (N, dtype), as a bit mask over
+// DevicePlan::xyform: bit 0 always; bit 1 for FP32 at N = 64, 96, 128, 160, 192, 256.
+int xy_forms(int N, int dtype);
+
+// Ints of the counter block DevicePlan::sync.
+int xy_sync_ints();
+
+// The forward and inverse x and y passes alone, one density, in the forms p.xyform (and,
+// when separate, p.xform and p.yform) select (for timing the forms).
+cudaError_t launch_xy_passes(const DevicePlan &p, cudaStream_t s);
 
 // The z pass alone, one density, in the form p.zform selects (for timing the forms).
 cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s);

@@ -81,16 +81,18 @@ def test_batched_graph_capture(torch_cuda):
         p.close()
 
 
-def test_graph_capture_warp_forms(torch_cuda):
+@pytest.mark.parametrize("xyform", [0, 1])
+def test_graph_capture_warp_forms(torch_cuda, xyform):
     """A batched solve at N = 256 in the warp forms of all passes (persistent kernels with
-    TMA copies and mbarriers) captured in a CUDA graph and replayed on new inputs: equal to
-    the direct solves bit for bit."""
+    TMA copies and mbarriers), separate or with the fused x-y passes (whose counters must
+    be back at zero for every replay), captured in a CUDA graph and replayed twice on new
+    inputs: equal to the direct solves bit for bit."""
     from paper_1612_01799_gb300 import Plan, solve_batched
     torch = torch_cuda
     spec = [(256, 21), (256, 22)]
     rhos = _inputs(torch, spec)
     with Plan(256, 10.0, 1e-6, "f32", max_batch=2) as p:
-        p.z_form, p.y_form, p.x_form = 2, 1, 1
+        p.z_form, p.y_form, p.x_form, p.xy_form = 2, 1, 1, xyform
         outs = [torch.empty_like(r) for r in rhos]
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -101,10 +103,11 @@ def test_graph_capture_warp_forms(torch_cuda):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
             solve_batched([p, p], rhos, outs, stream=s)
-        for r, n in zip(rhos, _inputs(torch, [(256, 31), (256, 32)])):
-            r.copy_(n)
-        g.replay()
-        torch.cuda.synchronize()
-        for r, o in zip(rhos, outs):
-            assert torch.equal(p.solve(r), o)
+        for seeds in ((31, 32), (41, 42)):
+            for r, n in zip(rhos, _inputs(torch, [(256, seeds[0]), (256, seeds[1])])):
+                r.copy_(n)
+            g.replay()
+            torch.cuda.synchronize()
+            for r, o in zip(rhos, outs):
+                assert torch.equal(p.solve(r), o)
         p.last_status()

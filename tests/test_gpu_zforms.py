@@ -29,6 +29,10 @@ def xforms(N, dtype):
     return [0] + ([1] if dtype == "f32" and (N in WARP_N or N == 512) else [])
 
 
+def xyforms(N, dtype):
+    return [0] + ([1] if dtype == "f32" and N in WARP_N else [])
+
+
 @pytest.fixture(scope="module")
 def torch_cuda():
     torch = pytest.importorskip("torch")
@@ -43,14 +47,17 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def solve_form(torch, N, L, tol, dtype, rho, form, yform=None, xform=None):
+def solve_form(torch, N, L, tol, dtype, rho, form, yform=None, xform=None, xyform=0):
     from paper_1612_01799_gb300 import Plan
     with Plan(N, L, tol, dtype) as p:
         assert p.z_form in forms(N, dtype)
         assert p.y_form in yforms(N, dtype)
         assert p.x_form in xforms(N, dtype)
+        assert p.xy_form in xyforms(N, dtype)
         p.z_form = form
         assert p.z_form == form
+        p.xy_form = xyform
+        assert p.xy_form == xyform
         if yform is not None:
             p.y_form = yform
             assert p.y_form == yform
@@ -92,6 +99,13 @@ def test_knob_codes(torch_cuda, dtype):
                 else:
                     assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_X_FORM, f) == -4
             assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_X_FORM, 2) == -1
+            for f in (0, 1):
+                if f in xyforms(N, dtype):
+                    p.xy_form = f
+                    assert p.xy_form == f
+                else:
+                    assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_XY_FORM, f) == -4
+            assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_XY_FORM, 2) == -1
             assert lib.poisson_plan_set_knob(p.handle, 7, 0) == -1
             assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, 3) == -1
             assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, -1) == -1
@@ -106,6 +120,7 @@ def test_tuning_is_per_shape(torch_cuda):
     for dtype in ("f32", "f64"):
         with Plan(256, 10.0, 1e-6, dtype) as a, Plan(256, 3.0, 1e-9, dtype, max_batch=2) as b:
             assert a.z_form == b.z_form and a.y_form == b.y_form and a.x_form == b.x_form
+            assert a.xy_form == b.xy_form
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -127,12 +142,13 @@ def test_forms_full_grid_n256(torch_cuda, plan_cache, dtype):
     rho = D.config_aniso4().sample()
     tol = 1e-12 if dtype == "f64" else 1e-6
     uo = osolver.solve(rho, 10.0, tol, plan=plan_cache(256, 10.0, tol))
-    combos = [(f, 0, 0) for f in forms(256, dtype)] + [(f, 1, x) for f in forms(256, dtype)
-                                                        for x in xforms(256, dtype) if dtype == "f32"]
-    for form, yform, xform in combos:
-        u = solve_form(torch_cuda, 256, 10.0, tol, dtype, rho, form, yform, xform)
-        assert rel_l2(u, uo) <= TOL[dtype], (form, yform, xform)
-        assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max(), (form, yform, xform)
+    combos = [(f, 0, 0, 0) for f in forms(256, dtype)] + [(f, 1, x, 0) for f in forms(256, dtype)
+                                                           for x in xforms(256, dtype) if dtype == "f32"]
+    combos += [(f, 0, 0, 1) for f in forms(256, dtype) if dtype == "f32"]
+    for form, yform, xform, xyform in combos:
+        u = solve_form(torch_cuda, 256, 10.0, tol, dtype, rho, form, yform, xform, xyform)
+        assert rel_l2(u, uo) <= TOL[dtype], (form, yform, xform, xyform)
+        assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max(), (form, yform, xform, xyform)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -219,7 +235,55 @@ def test_warp_forms_full_grid(torch_cuda, plan_cache, N):
     L, tol = 10.0, 1e-6
     rho = D.config_aniso4(N=N, seed=400 + N).gaussians.sample(N, L)
     uo = osolver.solve(rho, L, tol, plan=plan_cache(N, L, tol))
-    for form, yform, xform in [(0, 0, 0), (2, 0, 0), (0, 1, 0), (0, 0, 1), (2, 1, 1)]:
-        u = solve_form(torch_cuda, N, L, tol, "f32", rho, form, yform, xform)
-        assert rel_l2(u, uo) <= TOL["f32"], (form, yform, xform)
-        assert np.max(np.abs(u - uo)) <= 50 * TOL["f32"] * np.abs(uo).max(), (form, yform, xform)
+    for form, yform, xform, xyform in [(0, 0, 0, 0), (2, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (2, 1, 1, 0),
+                                       (2, 0, 0, 1), (0, 0, 0, 1)]:
+        u = solve_form(torch_cuda, N, L, tol, "f32", rho, form, yform, xform, xyform)
+        assert rel_l2(u, uo) <= TOL["f32"], (form, yform, xform, xyform)
+        assert np.max(np.abs(u - uo)) <= 50 * TOL["f32"] * np.abs(uo).max(), (form, yform, xform, xyform)
+
+
+@pytest.mark.parametrize("N,count", [(256, 1), (256, 3), (192, 2), (160, 2), (128, 3), (96, 4), (64, 1), (64, 6)])
+def test_xy_fused_equals_separate_warp_forms(torch_cuda, N, count):
+    """The fused x-y passes run the arithmetic of the separate warp-form x and y passes, so
+    a batch through them equals, bit for bit, the same batch through the separate passes.
+    Batches of several densities cycle every ring slot through several planes (the ring
+    holds at most 2N planes per density and often fewer), so this also checks the slot
+    hand-over between producers and consumers; the second fused run checks that the
+    counters return to zero after a launch."""
+    torch = torch_cuda
+    from paper_1612_01799_gb300 import Plan, solve_batched
+    L = 10.0
+    rhos = [torch.from_numpy(D.config_aniso4(N=N, seed=70 + i).gaussians.sample(N, L).astype(np.float32)).cuda()
+            for i in range(count)]
+    with Plan(N, L, 1e-6, "f32", max_batch=count) as p:
+        p.z_form = 2
+        p.y_form = 1
+        p.x_form = 1
+        p.xy_form = 0
+        ref = [torch.empty_like(r) for r in rhos]
+        solve_batched([p] * count, rhos, ref)
+        p.xy_form = 1
+        for _ in range(2):
+            outs = [torch.full_like(r, float("nan")) for r in rhos]
+            solve_batched([p] * count, rhos, outs)
+            torch.cuda.synchronize()
+            for r, o in zip(ref, outs):
+                assert torch.equal(r, o)
+        p.last_status()
+
+
+def test_xy_fused_timed_passes(torch_cuda):
+    """With the fused x-y form the timed solve reports the forward x-y kernel in the x
+    forward entry and the inverse one in the y inverse entry; the folded entries are 0."""
+    torch = torch_cuda
+    from paper_1612_01799_gb300 import Plan
+    N = 128
+    rho = torch.from_numpy(D.config_aniso4(N=N, seed=5).gaussians.sample(N, 10.0).astype(np.float32)).cuda()
+    with Plan(N, 10.0, 1e-6, "f32") as p:
+        p.xy_form = 1
+        u = torch.empty_like(rho)
+        ms = p.solve_timed(rho, u)
+        assert ms[0] > 0 and ms[2] > 0 and ms[3] > 0
+        assert ms[1] < 0.02 and ms[4] < 0.02
+        assert torch.equal(u, p.solve(rho))
+        p.last_status()
