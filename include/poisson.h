@@ -98,7 +98,11 @@ int poisson_solve(poisson_plan p, const void *rho_d, void *u_d, void *stream);
  * The same solve on host buffers: copies rho_h to the device, solves, copies u back
  * and synchronises the stream before returning.  rho_h, u_h: host pointers to N^3
  * values of the plan's dtype (pinned memory gives full copy bandwidth).  Uses the
- * plan's own device staging buffers.
+ * plan's own device staging buffers.  Where N is a multiple of 8 (N >= 16) and the x and y
+ * passes are separate launches, the copies run in 8 z-slabs on a copy stream of the plan,
+ * overlapped with the x and y passes of the neighbouring slabs (those passes transform
+ * each z-plane on its own); they start after the work already queued on `stream`.  The result is the
+ * same, bit for bit, as poisson_solve's on device copies of the buffers.
  */
 int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream);
 

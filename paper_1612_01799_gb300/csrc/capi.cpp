@@ -14,9 +14,14 @@
 
 namespace gsp {
 cudaError_t solve_f32(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *,
-                      double *);
+                      double *, int);
 cudaError_t solve_f64(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *,
-                      double *);
+                      double *, int);
+cudaError_t xy_slab_f32(const DevicePlan &, const void *, void *, int, int, cudaStream_t, bool);
+cudaError_t xy_slab_f64(const DevicePlan &, const void *, void *, int, int, cudaStream_t, bool);
+cudaError_t launch_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd) {
+    return p.dtype == POISSON_F32 ? xy_slab_f32(p, rho, u, z0, nz, s, fwd) : xy_slab_f64(p, rho, u, z0, nz, s, fwd);
+}
 cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *, int, double,
                              double, double, cudaStream_t);
 cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
@@ -58,10 +63,10 @@ bool n_supported(int N) {
 }
 
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
-                         cudaStream_t s, cudaEvent_t *ev, double *tail) {
+                         cudaStream_t s, cudaEvent_t *ev, double *tail, int skip) {
     if (count < 1 || count > p.max_batch || count > kMaxBatch) return cudaErrorInvalidValue;
-    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, count, s, ev, tail)
-                                  : solve_f64(p, rho, u, count, s, ev, tail);
+    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, count, s, ev, tail, skip)
+                                  : solve_f64(p, rho, u, count, s, ev, tail, skip);
 }
 
 // Streams that poisson_solve_batched forks independent plan groups onto (per device,
@@ -209,6 +214,11 @@ struct poisson_plan_s {
     void *stage_out = nullptr;
     cudaEvent_t ev[6] = {};
     bool have_events = false;
+    // poisson_solve_host's slab pipeline: a copy stream and one event per slab and
+    // direction, made on first use.
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t slab_ev[2 * 8 + 1] = {};
+    bool have_slab_events = false;
 };
 
 namespace gsp {
@@ -238,6 +248,9 @@ static void free_plan(poisson_plan p) {
         if (b) cudaFree(b);
     if (p->have_events)
         for (auto &e : p->ev) cudaEventDestroy(e);
+    if (p->have_slab_events)
+        for (auto &e : p->slab_ev) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     delete p;
 }
 
@@ -430,6 +443,9 @@ extern "C" int poisson_solve(poisson_plan p, const void *rho_d, void *u_d, void 
     return map_cuda(gsp::launch_solve(p->dp, in, out, 1, (cudaStream_t)stream, nullptr));
 }
 
+// Slabs of the host-buffer solve's copy / x-pass pipeline.
+constexpr int kSlabs = 8;
+
 extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream) {
     int rc = check_solve_args(p, rho_h, u_h);
     if (rc) return rc;
@@ -442,14 +458,62 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
         if ((e = cudaMalloc(&p->stage_out, n)) != cudaSuccess) return map_cuda(e);
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if ((e = cudaMemcpyAsync(p->stage_in, rho_h, n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return map_cuda(e);
     gsp::PtrArray in, out;
     one(in, p->stage_in);
     one(out, p->stage_out);
-    if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr)) != cudaSuccess) return map_cuda(e);
-    if ((e = cudaMemcpyAsync(u_h, p->stage_out, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    const int N = p->dp.N;
+    const bool fused = p->dp.xyform == 1 && p->dp.sync != nullptr;
+    if (fused || N % kSlabs != 0 || N < 2 * kSlabs) {
+        if ((e = cudaMemcpyAsync(p->stage_in, rho_h, n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return map_cuda(e);
+        if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr)) != cudaSuccess) return map_cuda(e);
+        if ((e = cudaMemcpyAsync(u_h, p->stage_out, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return map_cuda(e);
+        return map_cuda(cudaStreamSynchronize(s));
+    }
+    // Slab pipeline: the x and y passes transform each z-plane on its own (only the z pass
+    // needs the whole volume), so the copy of slab k + 1 to the device runs while the x and
+    // y forward passes transform slab k, and the copy of slab k back to the host while the
+    // y and x inverse passes make slab k + 1.  Copies on the plan's copy stream, passes on
+    // `stream`, one event per slab and direction.
+    if (!p->copy_stream && (e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return map_cuda(e);
+    if (!p->have_slab_events) {
+        for (auto &ev : p->slab_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return map_cuda(e);
+        p->have_slab_events = true;
+    }
+    cudaStream_t cs = p->copy_stream;
+    cudaEvent_t *ev_in = p->slab_ev, *ev_out = p->slab_ev + kSlabs, start = p->slab_ev[2 * kSlabs];
+    const int nzs = N / kSlabs;  // planes per slab
+    const size_t sb = (size_t)nzs * N * N * p->elem;
+    // The copies wait for the work already on `stream` (an earlier solve reading the
+    // staging buffers).
+    if ((e = cudaEventRecord(start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, start, 0)) != cudaSuccess)
+        return map_cuda(e);
+    for (int k = 0; k < kSlabs; ++k) {
+        e = cudaMemcpyAsync(static_cast<char *>(p->stage_in) + k * sb, static_cast<const char *>(rho_h) + k * sb, sb,
+                            cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[k], 0);
+        if (e == cudaSuccess) e = gsp::launch_xy_slab(p->dp, p->stage_in, p->stage_out, k * nzs, nzs, s, true);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr, nullptr, 3)) != cudaSuccess) return map_cuda(e);
+    for (int k = 0; k < kSlabs; ++k) {
+        e = gsp::launch_xy_slab(p->dp, p->stage_in, p->stage_out, k * nzs, nzs, s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out[k], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_out[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char *>(u_h) + k * sb, static_cast<char *>(p->stage_out) + k * sb, sb,
+                                cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    // `stream` waits for the last copy, so that work issued after the call is ordered
+    // after it, then the call returns once everything has finished.
+    if ((e = cudaEventRecord(start, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, start, 0)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return map_cuda(e);
     return map_cuda(cudaStreamSynchronize(s));
 }
 

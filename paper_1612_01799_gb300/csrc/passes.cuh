@@ -454,9 +454,10 @@ template <typename Real, int N> constexpr bool xwarp_form() {
 }
 
 template <typename Real, int N>
-cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s, bool fwd) {
+cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s, bool fwd,
+                   int rows = 0) {
     using T2 = Cx2<Real>;
-    const int nrows = B * N * N;
+    const int nrows = rows ? rows : B * N * N;
     if constexpr (xwarp_form<Real, N>()) {
         if (p.xform == 1) {
             const int npairs = nrows / 2;
@@ -504,22 +505,24 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
 // block form (k_col_tma), 1 the warp form (k_y_warp, ywarp_form); an absent form runs as 0.
 template <typename Real, int N> constexpr bool ywarp_form() { return std::is_same<Real, float>::value && warp_n(N); }
 
+// planes z0 .. z0 + nz - 1 of the stacked densities (nz = 0: all B N planes).
 template <typename Real, int N>
-cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
+cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 = 0, int nz = 0) {
     using T2 = Cx2<Real>;
     using TwC = typename TwOf<typename Types<Real>::CC>::T;
     constexpr int L = 2 * N;
     const int ncols = N + 1;
+    const int planes = nz ? nz : B * N;
     if constexpr (ywarp_form<Real, N>()) {
         if (p.yform == 1) {
             using Y = YWarp<N / 16>;
-            const int ntx = (ncols + Y::TC - 1) / Y::TC, nt = ntx * B * N;
+            const int ntx = (ncols + Y::TC - 1) / Y::TC, nt = ntx * planes;
             auto k = fwd ? k_y_warp<N / 16, true> : k_y_warp<N / 16, false>;
             const int smem = fwd ? Y::SMEM_F : Y::SMEM_I;
             GSP_CHECK(set_smem(k, smem));
             k<<<persistent_blocks(k, Y::NT, smem, nt), Y::NT, smem, s>>>(
                 fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1, static_cast<const float2 *>(p.tw), ntx, nt,
-                ncols, p.status);
+                ncols, p.status, z0);
             return cudaGetLastError();
         }
     }
@@ -527,18 +530,18 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd) {
     const int Px = p.Px;
     if (fwd) {
         using L0 = TmaLayout<Real, L, 0>;
-        const int ntx0 = (ncols + L0::TC - 1) / L0::TC, nt = ntx0 * B * N;
+        const int ntx0 = (ncols + L0::TC - 1) / L0::TC, nt = ntx0 * planes;
         auto k = k_col_tma<Real, L, 0>;
         GSP_CHECK(set_smem(k, L0::SMEM));
         k<<<persistent_blocks(k, tma_threads<Real, L, 0>(), L0::SMEM, nt), tma_threads<Real, L, 0>(), L0::SMEM, s>>>(
-            p.tm_y_in, static_cast<T2 *>(p.w2), twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status);
+            p.tm_y_in, static_cast<T2 *>(p.w2), twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status, z0);
     } else {
         using L2 = TmaLayout<Real, L, 2>;
-        const int ntx2 = (ncols + L2::TC - 1) / L2::TC, nt = ntx2 * B * N;
+        const int ntx2 = (ncols + L2::TC - 1) / L2::TC, nt = ntx2 * planes;
         auto k = k_col_tma<Real, L, 2>;
         GSP_CHECK(set_smem(k, L2::SMEM));
         k<<<persistent_blocks(k, tma_threads<Real, L, 2>(), L2::SMEM, nt), tma_threads<Real, L, 2>(), L2::SMEM, s>>>(
-            p.tm_yi_in, static_cast<T2 *>(p.w1), twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status);
+            p.tm_yi_in, static_cast<T2 *>(p.w1), twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status, z0);
     }
     return cudaGetLastError();
 }
@@ -584,29 +587,51 @@ cudaError_t xy_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
     return cudaErrorInvalidValue;
 }
 
+// The x and y passes of planes z0 .. z0 + nz - 1 of one density (rho and u device
+// pointers to the whole density): forward x then y, or inverse y then x, with the kernels
+// of the plan's separate x and y forms on that slab of planes only.
+template <typename Real, int N>
+cudaError_t xy_slab(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd) {
+    const long long row0 = (long long)z0 * N;
+    DevicePlan q = p;
+    q.w1 = static_cast<char *>(p.w1) + row0 * p.Px * 2 * (long long)sizeof(Real);
+    PtrArray a{}, b{};
+    a.p[0] = static_cast<const char *>(rho) + row0 * N * (long long)sizeof(Real);
+    b.p[0] = static_cast<char *>(u) + row0 * N * (long long)sizeof(Real);
+    if (fwd) {
+        GSP_CHECK((x_pass<Real, N>(q, a, b, 1, s, true, nz * N)));
+        return y_pass<Real, N>(p, 1, s, true, z0, nz);
+    }
+    GSP_CHECK((y_pass<Real, N>(p, 1, s, false, z0, nz)));
+    return x_pass<Real, N>(q, a, b, 1, s, false, nz * N);
+}
+
 // The five passes.  With the fused x-y form the forward x and y passes are one launch
 // (timed as the x forward, ev[1] and ev[2] recorded together) and so are the inverse y and
-// x passes (timed as the y inverse).
+// x passes (timed as the y inverse).  skip: bit 0 leaves out the forward x and y passes
+// (w2 already holds their output), bit 1 the inverse y and x passes (the caller runs them
+// from w3, with xy_slab); not with the fused form.
 template <typename Real, int N>
 cudaError_t solve_n(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
-                    cudaEvent_t *ev, double *tail) {
+                    cudaEvent_t *ev, double *tail, int skip) {
     const bool fused = xy_fused_on<Real, N>(p);
+    if (fused && skip) return cudaErrorInvalidValue;
     if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
     if (fused) GSP_CHECK((xy_pass<Real, N>(p, rho, u, B, s, true)));
-    else GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, true)));
+    else if (!(skip & 1)) GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, true)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
 
-    if (!fused) GSP_CHECK((y_pass<Real, N>(p, B, s, true)));
+    if (!fused && !(skip & 1)) GSP_CHECK((y_pass<Real, N>(p, B, s, true)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
 
     GSP_CHECK((z_pass<Real, N>(p, B, s, tail)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
 
     if (fused) GSP_CHECK((xy_pass<Real, N>(p, rho, u, B, s, false)));
-    else GSP_CHECK((y_pass<Real, N>(p, B, s, false)));
+    else if (!(skip & 2)) GSP_CHECK((y_pass<Real, N>(p, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
 
-    if (!fused) GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, false)));
+    if (!fused && !(skip & 2)) GSP_CHECK((x_pass<Real, N>(p, rho, u, B, s, false)));
     if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
     return cudaSuccess;
 }
@@ -701,22 +726,24 @@ cudaError_t encode_n(DevicePlan &p) {
 #define GSP_SIZE_GROUP_C(X) X(320) X(384) X(512) X(1024)
 #define GSP_DECLARE_N(EXT, Real, n)                                                                      \
     EXT template cudaError_t solve_n<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int, \
-                                              cudaStream_t, cudaEvent_t *, double *);                      \
+                                              cudaStream_t, cudaEvent_t *, double *, int);                 \
+    EXT template cudaError_t xy_slab<Real, n>(const DevicePlan &, const void *, void *, int, int,           \
+                                              cudaStream_t, bool);                                         \
     EXT template cudaError_t z_pass<Real, n>(const DevicePlan &, int, cudaStream_t, double *);             \
-    EXT template cudaError_t y_pass<Real, n>(const DevicePlan &, int, cudaStream_t, bool);                 \
+    EXT template cudaError_t y_pass<Real, n>(const DevicePlan &, int, cudaStream_t, bool, int, int);       \
     EXT template cudaError_t x_pass<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int,   \
-                                             cudaStream_t, bool);                                          \
+                                             cudaStream_t, bool, int);                                     \
     EXT template cudaError_t xy_pass<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int,  \
                                               cudaStream_t, bool);                                         \
     EXT template cudaError_t encode_n<Real, n>(DevicePlan &);
 
 template <typename Real>
 cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B,
-                           cudaStream_t s, cudaEvent_t *ev, double *tail) {
+                           cudaStream_t s, cudaEvent_t *ev, double *tail, int skip) {
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
-        return solve_n<Real, n>(p, rho, u, B, s, ev, tail);
+        return solve_n<Real, n>(p, rho, u, B, s, ev, tail, skip);
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE
         default:
@@ -790,6 +817,19 @@ cudaError_t xy_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
         if (e == cudaSuccess) e = y_pass<Real, n>(p, 1, s, false);                   \
         return e != cudaSuccess ? e : x_pass<Real, n>(p, a, a, 1, s, false);         \
     }
+        GSP_SUPPORTED_N(GSP_CASE)
+#undef GSP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Real>
+cudaError_t xy_slab_dispatch(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd) {
+    switch (p.N) {
+#define GSP_CASE(n) \
+    case n:         \
+        return xy_slab<Real, n>(p, rho, u, z0, nz, s, fwd);
         GSP_SUPPORTED_N(GSP_CASE)
 #undef GSP_CASE
         default:

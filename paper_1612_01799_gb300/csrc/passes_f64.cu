@@ -7,8 +7,11 @@ GSP_SUPPORTED_N(GSP_EXTERN_F64)
 #undef GSP_EXTERN_F64
 
 cudaError_t solve_f64(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
-                     cudaEvent_t *ev, double *tail) {
-    return solve_dispatch<double>(p, rho, u, B, s, ev, tail);
+                     cudaEvent_t *ev, double *tail, int skip) {
+    return solve_dispatch<double>(p, rho, u, B, s, ev, tail, skip);
+}
+cudaError_t xy_slab_f64(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd) {
+    return xy_slab_dispatch<double>(p, rho, u, z0, nz, s, fwd);
 }
 cudaError_t symbol_table_f64(const DevicePlan &p, const double *dA, const double *dw, int nterms,
                              double C0, double C2, double scale, cudaStream_t s) {

@@ -130,7 +130,7 @@ template <typename Real, int L, int KIND>
 __global__ void __launch_bounds__(tma_threads<Real, L, KIND>(), min_blocks_for<tma_threads<Real, L, KIND>(), FftCfg<L>::E>())
 k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
           const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
-          int ncols, long long out_row, long long out_outer, int *__restrict__ status) {
+          int ncols, long long out_row, long long out_outer, int *__restrict__ status, int z0) {
     using C = typename Types<Real>::CC;
     using Lay = TmaLayout<Real, L, KIND>;
     using Rs = typename FftCfg<L>::Rs;
@@ -151,7 +151,7 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
     }
     __syncthreads();
     auto issue = [&](int t) {
-        const int tx = t % ntx, outer = t / ntx;
+        const int tx = t % ntx, outer = z0 + t / ntx;
         mbar_arrive_expect_tx(bar, Lay::IN_BYTES);
 #pragma unroll
         for (int c = 0; c < Lay::NCP; ++c)
@@ -161,7 +161,7 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
     if (threadIdx.x == 0 && t < ntiles) issue(t);
     uint32_t phase = 0;
     for (; t < ntiles; t += gridDim.x) {
-        const int tx = t % ntx, outer = t / ntx;
+        const int tx = t % ntx, outer = z0 + t / ntx;
         const int col = tx * TC + W * g;
         const bool valid = col < ncols;
         const bool ok = mbar_wait(bar, phase, status);

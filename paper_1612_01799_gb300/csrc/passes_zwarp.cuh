@@ -506,7 +506,7 @@ __device__ __forceinline__ void yw_inv(CV *v, const ZwLane &zl, unsigned char *x
 template <int E1, bool FWD>
 __global__ void __launch_bounds__(YWarp<E1>::NT, 2)
 k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
-         const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status) {
+         const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status, int z0) {
     using Y = YWarp<E1>;
     constexpr int NW = Y::NW, N = Y::N, H = Y::H;
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -526,7 +526,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     for (int i = threadIdx.x; i < E1 * 32; i += Y::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
     auto issue_in = [&](int t) {
-        const int tx = t % ntx, zz = t / ntx;
+        const int tx = t % ntx, zz = z0 + t / ntx;
         mbar_arrive_expect_tx(bar, (FWD ? 1 : 2) * N * 128);
         tma_load_3d(inb, &tin, bar, tx * Y::TC, 0, zz);
         if (!FWD) tma_load_3d(inb + N * 128, &tin, bar, tx * Y::TC, N, zz);
@@ -555,7 +555,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
-        const int tx = t % ntx, zz = t / ntx;
+        const int tx = t % ntx, zz = z0 + t / ntx;
         const bool valid = tx * Y::TC + 2 * g < ncols;
         const bool more = t + (int)gridDim.x < ntiles;
         CV v[16];

@@ -82,9 +82,15 @@ cudaError_t encode_tma_maps(DevicePlan &p);
 // The five passes of `count` solves (1 <= count <= p.max_batch) of the plan's geometry on
 // `s`: rho[b] -> u[b].  ev: null, or 6 events recorded before pass 1, between the passes
 // and after pass 5.  tail: null, or 2 count zeroed doubles that receive, per density, the
-// padded spectrum's energy in the outer |k|_inf shell and its total energy.
+// padded spectrum's energy in the outer |k|_inf shell and its total energy.  skip: bit 0
+// leaves out the forward x and y passes, bit 1 the inverse y and x passes (the caller runs
+// them with launch_xy_slab); not with the fused x-y form.
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
-                         cudaStream_t s, cudaEvent_t *ev, double *tail = nullptr);
+                         cudaStream_t s, cudaEvent_t *ev, double *tail = nullptr, int skip = 0);
+
+// The x and y passes (forward: x then y; inverse: y then x) of planes z0 .. z0 + nz - 1 of
+// one density, in the plan's separate forms: rho, u device pointers to the whole density.
+cudaError_t launch_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd);
 
 // Forms of the z pass that exist for (N, dtype), as a bit mask over DevicePlan::zform:
 // bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;

@@ -156,3 +156,25 @@ def test_device_errors_are_codes(torch_cuda):
         assert lib.poisson_solve(p.handle, None, None, None) == -1
         h = ctypes.c_void_p()
         assert lib.poisson_plan_create(ctypes.byref(h), 64, 8.0, 1e-300, 2) == -1
+
+
+@pytest.mark.parametrize("N,dtype,xyform", [(256, "f32", 0), (256, "f32", 1), (48, "f32", 0), (80, "f64", 0),
+                                            (128, "f64", 0), (8, "f32", 0)])
+def test_host_solve_slab_pipeline(torch_cuda, N, dtype, xyform):
+    """poisson_solve_host on pinned buffers: the slab pipeline (copies of 8 z-slabs
+    overlapped with the x passes; N a multiple of 8, N >= 16, separate x and y passes) and
+    the plain path (N = 8, or the fused x-y form) give the device solve's bits."""
+    from paper_1612_01799_gb300 import Plan
+    torch = torch_cuda
+    L = 10.0
+    with Plan(N, L, 1e-6 if dtype == "f32" else 1e-12, dtype) as p:
+        if xyform:
+            p.z_form, p.y_form, p.x_form, p.xy_form = 2, 1, 1, 1
+        rho = torch.from_numpy(D.config_aniso4(N=N, seed=60 + N).gaussians.sample(N, L).astype(p.np_dtype))
+        rho_pinned = rho.pin_memory()
+        out = torch.full_like(rho_pinned, float("nan")).pin_memory()
+        ref = p.solve(rho.cuda()).cpu()
+        for _ in range(2):
+            p.solve_host(rho_pinned, out)
+            assert torch.equal(out, ref)
+        p.last_status()
