@@ -194,7 +194,8 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       2 = one warp per column pair: an E1-point DFT (N = 16 E1) and a 16-point DFT in
  *           registers, a radix-2 step between lane pairs and one warp-local
  *           shared-memory exchange per direction (POISSON_F32, N = 64, 96, 128, 160,
- *           192, 256).
+ *           192, 256); at N = 512 one warp per column, two 32-point DFTs in registers
+ *           and one warp-local exchange per direction (POISSON_F32).
  *   POISSON_KNOB_Y_FORM  form of the two y passes (Sec. 2, the zero-padded transforms
  *       along the middle axis): 0 = a column pair spread over the threads of a block;
  *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, the same N).

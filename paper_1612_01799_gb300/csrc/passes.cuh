@@ -400,7 +400,9 @@ inline constexpr bool warp_n(int N) {
     return N == 256 || N == 192 || N == 160 || N == 128 || N == 96 || N == 64;
 }
 template <typename Real, int N> constexpr bool zwarp_form() { return std::is_same<Real, float>::value && warp_n(N); }
-inline bool zwarp_available(int N) { return warp_n(N); }
+// The N = 512 warp form of the z pass (k_z_w512: one warp per column, unpacked).
+template <typename Real, int N> constexpr bool zw512_form() { return std::is_same<Real, float>::value && N == ZW512::N; }
+inline bool zwarp_available(int N) { return warp_n(N) || N == ZW512::N; }
 
 // The fused z pass (K3) of B densities in the form p.zform selects: the length-2N
 // transforms (0), the split into even and odd length-N transforms (1, where
@@ -424,6 +426,18 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
             GSP_CHECK(set_smem(k, Z::SMEM));
             k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s>>>(
                 p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status,
+                tail);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (zw512_form<Real, N>()) {
+        if (p.zform == 2) {
+            using Z = ZW512;
+            const int ntx5 = (ncols + Z::TC - 1) / Z::TC, nt5 = ntx5 * L * B;
+            auto k = tail ? k_z_w512<true> : k_z_w512<false>;
+            GSP_CHECK(set_smem(k, Z::SMEM));
+            k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt5), Z::NT, Z::SMEM, s>>>(
+                p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx5, nt5, ncols, p.status,
                 tail);
             return cudaGetLastError();
         }
@@ -712,6 +726,17 @@ cudaError_t encode_n(DevicePlan &p) {
         GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
                             (cuuint64_t)(N + 1) * srow, ZWarp<N / 16>::TC, 1, ZWarp<N / 16>::SYM_RPC,
                             CU_TENSOR_MAP_SWIZZLE_64B));
+    }
+    if constexpr (zw512_form<Real, N>()) {
+        // 8 columns x 1 ky x 256 z-rows of w2 and w3 (64-byte swizzle); the symbol octant
+        // read with its innermost index as kz (the table is symmetric in its three indices):
+        // 256 kz x 1 ky x 8 kx per box.
+        GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZW512::TC, 1, N / 2,
+                            CU_TENSOR_MAP_SWIZZLE_64B));
+        GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZW512::TC, 1, N / 2,
+                            CU_TENSOR_MAP_SWIZZLE_64B));
+        GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
+                            (cuuint64_t)(N + 1) * srow, ZW512::SYM_BOX, 1, ZW512::TC));
     }
     return cudaSuccess;
 }

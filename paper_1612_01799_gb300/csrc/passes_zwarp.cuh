@@ -970,3 +970,278 @@ k_x_warp2_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__r
 }
 
 }  // namespace gsp
+
+namespace gsp {
+
+// ---- K3, warp form at N = 512 (FP32) -------------------------------------------------------
+// The fused z pass of k_z_warp for L = 2N = 1024, where a packed column pair would need 32
+// CV values (128 registers) per lane: one warp per column, unpacked complex values (CF),
+// L = 32 x 32.  Lane q holds x[q + 32 r] of its column (r < 16 nonzero) in register r:
+//   F1  A_q[k1] = sum_{r<16} x[q + 32 r] W_32^{r k1}   pruned 32-point DFT in registers
+//       (two 16-point DFTs of the inputs and of the inputs times W_32^r): register j holds
+//       k1 = kappa(j) = 2j (j < 16) or 2(j - 16) + 1
+//   F2  B_q[k1] = A_q[k1] W_1024^{q k1}                (shared table T[k1][q])
+//   F3  transpose through the warp's own 8 KB of shared memory: lane l gathers B_q[l], q < 32,
+//       slot (q, k1) at byte 256 k1 + 8 (q ^ (k1 & 15)) (both directions conflict free)
+//   F4  X[l + 32 k2] = sum_q B_q[l] W_32^{q k2}        32-point DFT in registers
+// then the product with G(kx, |ky|, |kz|) at kz = l + 32 k2 (folded to kz <= N), and the
+// adjoint of each step in reverse order, which returns z = q + 32 r to the lanes and
+// registers the inputs came from; rows r < 16 are kept (Sec. 2: the convolution with the
+// G-tensor on the zero-padded grid and the crop).
+//
+// A CTA of 8 warps owns a tile of 8 consecutive columns kx at one ky.  Shared memory:
+//   B   32 KB: the input tile (512 z-rows x 64 B, two TMA boxes of 256 rows, 64-byte
+//       swizzle), then the tile's symbol lines (three boxes of 256 kz x 8 kx: the octant
+//       table is symmetric in (kx, ky, kz), so with kz as its innermost index each column's
+//       kz values lie contiguous), then the next tile's input;
+//   XO  64 KB: the warps' 8 KB exchange regions; the first 32 KB is also the output tile
+//       in the TMA store's 64-byte swizzle, written after a block barrier that ends every
+//       warp's exchange reads;
+//   T   8 KB: W_1024^{q k1} as T[k1][q].
+struct ZW512 {
+    static constexpr int N = 512, L = 1024, TC = 8, NW = 8, NT = 256;
+    static constexpr int IN_BYTES = N * TC * 8;                  // two 16 KB boxes
+    static constexpr int SYM_BOX = 256, SYM_NB = 3;              // kz boxes 0, 256, 512
+    static constexpr int SYM_BYTES = SYM_NB * SYM_BOX * TC * 4;  // 24 KB
+    static constexpr int OFF_B = 0, OFF_XO = 32768, OFF_T = OFF_XO + 65536, OFF_BAR = OFF_T + 8192;
+    static constexpr int SMEM = 1024 + OFF_BAR + 64;
+    static_assert(IN_BYTES == 32768 && SYM_BYTES <= 32768, "input and symbol share B");
+};
+
+// exp(-2 pi i r / 32) for r < 16.
+__host__ __device__ constexpr float w32c(int r) {
+    constexpr float c1 = 0.98078528040323044913f, c2 = 0.92387953251128675613f, c3 = 0.83146961230254523708f;
+    constexpr float s1 = 0.19509032201612826785f, s2 = 0.38268343236508977173f, s3 = 0.55557023301960222474f;
+    constexpr float c4 = 0.70710678118654752440f;
+    return r == 0 ? 1.f : r == 1 ? c1 : r == 2 ? c2 : r == 3 ? c3 : r == 4 ? c4 : r == 5 ? s3 : r == 6 ? s2
+         : r == 7 ? s1 : r == 8 ? 0.f : r == 9 ? -s1 : r == 10 ? -s2 : r == 11 ? -s3 : r == 12 ? -c4
+         : r == 13 ? -c3 : r == 14 ? -c2 : -c1;
+}
+__host__ __device__ constexpr float w32s(int r) {
+    constexpr float c1 = 0.98078528040323044913f, c2 = 0.92387953251128675613f, c3 = 0.83146961230254523708f;
+    constexpr float s1 = 0.19509032201612826785f, s2 = 0.38268343236508977173f, s3 = 0.55557023301960222474f;
+    constexpr float c4 = 0.70710678118654752440f;
+    return r == 0 ? 0.f : r == 1 ? -s1 : r == 2 ? -s2 : r == 3 ? -s3 : r == 4 ? -c4 : r == 5 ? -c3 : r == 6 ? -c2
+         : r == 7 ? -c1 : r == 8 ? -1.f : r == 9 ? -c1 : r == 10 ? -c2 : r == 11 ? -c3 : r == 12 ? -c4
+         : r == 13 ? -s3 : r == 14 ? -s2 : -s1;
+}
+
+// 32-point DFT of v in natural order, X_k = sum_n v_n exp(D 2 pi i n k / 32).
+template <int D> __device__ __forceinline__ void dft32(CF *v) {
+    CF e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft<16, D>(e);
+    dft<16, D>(o);
+    float cs[16], sn[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) cs[k] = w32c(k), sn[k] = w32s(k);
+    combine2<D, 16>(e, o, v, cs, sn);
+}
+// F1: v[0..15] inputs (v[16..31] ignored) -> v[m] = A[2m], v[16 + m] = A[2m + 1].
+__device__ __forceinline__ void w512_f1(CF *v) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[16 + r] = r == 0 ? v[0] : r == 8 ? add_rot<-1>(czero<CF>(), v[8]) : cmulk<-1>(v[r], w32c(r), w32s(r));
+    dft<16, -1>(v);
+    dft<16, -1>(v + 16);
+}
+// Adjoint of F1, outputs r < 16 in v[0..15].
+__device__ __forceinline__ void w512_f1_adj(CF *v) {
+    dft<16, 1>(v);
+    dft<16, 1>(v + 16);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const CF o = r == 0 ? v[16] : r == 8 ? add_rot<1>(czero<CF>(), v[24]) : cmulk<1>(v[16 + r], w32c(r), w32s(r));
+        v[r] = cadd(v[r], o);
+    }
+}
+__host__ __device__ constexpr int w512_kappa(int j) { return j < 16 ? 2 * j : 2 * (j - 16) + 1; }
+
+// Byte offset of row z, column c (8 bytes) in a tile of 64-byte rows with the 64-byte swizzle.
+__device__ __forceinline__ int sw64(int z, int c) { return z * 64 + ((((c >> 1) ^ (z >> 1)) & 3) << 4) + ((c & 1) << 3); }
+
+__device__ __forceinline__ void sts2(uint32_t a, CF x) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x.re), "f"(x.im) : "memory");
+}
+__device__ __forceinline__ CF lds2(uint32_t a) {
+    float2 f;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(f.x), "=f"(f.y) : "r"(a) : "memory");
+    return {f.x, f.y};
+}
+
+// Tile t = (tx, ky, b): tx the 8-column block, consecutive tiles take ky and its mirror
+// 2N - ky (same symbol lines), b the density.  With TAIL the forward spectrum's shell and
+// total energies are added to tail[2 b], tail[2 b + 1] (as in k_z_warp).
+template <bool TAIL>
+__global__ void __launch_bounds__(ZW512::NT, 2)
+k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
+         const __grid_constant__ CUtensorMap tout, const float2 *__restrict__ tw, int ntx, int ntiles,
+         int ncols, int *__restrict__ status, double *__restrict__ tail) {
+    using Z = ZW512;
+    constexpr int L = Z::L, N = Z::N, NW = Z::NW;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    unsigned char *Bb = base + Z::OFF_B;
+    unsigned char *xo = base + Z::OFF_XO;
+    float2 *T = reinterpret_cast<float2 *>(base + Z::OFF_T);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Z::OFF_BAR);  // input, symbol, XO free
+    int *cnt = reinterpret_cast<int *>(bar + 3);                       // input, symbol, output
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init(bar + 2, 1);
+        cnt[0] = cnt[1] = cnt[2] = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < 1024; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    __syncthreads();
+
+    auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
+    auto issue_in = [&](int t) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), b = t / (ntx * L);
+        mbar_arrive_expect_tx(bar, Z::IN_BYTES);
+        tma_load_3d(Bb, &tin, bar, tx * Z::TC, ky, b * N);
+        tma_load_3d(Bb + Z::IN_BYTES / 2, &tin, bar, tx * Z::TC, ky, b * N + N / 2);
+    };
+    auto issue_sym = [&](int t) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L);
+        const int kya = ky <= N ? ky : L - ky;
+        mbar_arrive_expect_tx(bar + 1, Z::SYM_BYTES);
+#pragma unroll
+        for (int c = 0; c < Z::SYM_NB; ++c)
+            tma_load_3d(Bb + c * Z::SYM_BOX * Z::TC * 4, &tsym, bar + 1, c * Z::SYM_BOX, kya, tx * Z::TC);
+    };
+    // Arrival of this warp on counter c; true on the lane-0 thread of the tile's last warp.
+    auto last_arrival = [&](int c) {
+        __syncwarp();
+        bool last = false;
+        if (q == 0) {
+            __threadfence_block();
+            last = atomicAdd(cnt + c, 1) % NW == NW - 1;
+            if (last) {
+                __threadfence_block();
+                fence_proxy_async();
+            }
+        }
+        return last;
+    };
+    if (threadIdx.x == 0) {
+        mbar_arrive(bar + 2);  // XO starts free
+        if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
+    }
+
+    const uint32_t xw = smem_addr(xo) + 8192 * g;           // this warp's exchange region
+    const uint32_t aw = xw + 8 * q;                          // writer (lane q) base
+    const uint32_t ar = xw + 256 * q + 8 * (q & 15);         // reader (lane l = q) base
+    // Symbol value at folded kz for reader lane q and register k2.
+    auto sym_at = [&](int k2) {
+        int kz = q + 32 * k2;
+        if (kz > N) kz = L - kz;
+        return *reinterpret_cast<const float *>(Bb + (kz >> 8) * (Z::SYM_BOX * Z::TC * 4) + 1024 * g + 4 * (kz & 255));
+    };
+    bool stored = false;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
+        const int kya = ky <= N ? ky : L - ky;
+        const int col = tx * Z::TC + g;
+        const bool valid = col < ncols;
+        CF v[32];
+        // A wait that gives up marks the thread; the block leaves together at its barrier
+        // below (no thread may return while others still wait there).
+        bool bad = !mbar_wait(bar, ph, status);
+        if (valid && !bad) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const float2 f = *reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g));
+                v[r] = {f.x, f.y};
+            }
+        }
+        if (last_arrival(0)) issue_sym(t);
+        if (valid) {
+            w512_f1(v);
+#pragma unroll
+            for (int j = 1; j < 32; ++j) v[j] = twmul<-1>(v[j], T[w512_kappa(j) * 32 + q]);
+        }
+        if (!bad) bad = !mbar_wait(bar + 2, ph, status);  // the previous tile's store has read XO
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int k1 = w512_kappa(j);
+                sts2((aw ^ (8 * (k1 & 15))) + 256 * k1, v[j]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int p = 0; p < 32; ++p) v[p] = lds2(ar ^ (8 * p));
+            dft32<-1>(v);  // v[k2] = X[q + 32 k2]
+        }
+        if constexpr (TAIL) {
+            constexpr int SHELL = N - N / 8;
+            float eshell = 0.f, etot = 0.f;
+            if (valid) {
+                const float w0 = (col == 0 || col == N) ? 1.f : 2.f;
+#pragma unroll
+                for (int k2 = 0; k2 < 32; ++k2) {
+                    int kz = q + 32 * k2;
+                    if (kz > N) kz = L - kz;
+                    const float en = v[k2].re * v[k2].re + v[k2].im * v[k2].im;
+                    etot += w0 * en;
+                    if (kz >= SHELL || kya >= SHELL || col >= SHELL) eshell += w0 * en;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                eshell += __shfl_xor_sync(0xffffffffu, eshell, o);
+                etot += __shfl_xor_sync(0xffffffffu, etot, o);
+            }
+            if (valid && q == 0) {
+                atomicAdd(tail + 2 * bb, (double)eshell);
+                atomicAdd(tail + 2 * bb + 1, (double)etot);
+            }
+        }
+        if (!bad) bad = !mbar_wait(bar + 1, ph, status);
+        if (valid) {
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) v[k2] = cscale(v[k2], sym_at(k2));
+        }
+        if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
+        if (valid) {
+            dft32<1>(v);  // v[p] = B_p[q] (adjoint of F4)
+#pragma unroll
+            for (int p = 0; p < 32; ++p) sts2(ar ^ (8 * p), v[p]);
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int k1 = w512_kappa(j);
+                v[j] = lds2((aw ^ (8 * (k1 & 15))) + 256 * k1);
+            }
+#pragma unroll
+            for (int j = 1; j < 32; ++j) v[j] = twmul<1>(v[j], T[w512_kappa(j) * 32 + q]);
+            w512_f1_adj(v);
+        }
+        // Every warp's exchange reads are done: XO takes the output tile.
+        if (__syncthreads_or(bad)) break;
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                *reinterpret_cast<float2 *>(xo + sw64(q + 32 * r, g)) = make_float2(v[r].re, v[r].im);
+        }
+        fence_proxy_async();
+        if (last_arrival(2)) {
+            tma_store_3d(&tout, xo, tx * Z::TC, ky, bb * N);
+            tma_store_3d(&tout, xo + Z::IN_BYTES / 2, tx * Z::TC, ky, bb * N + N / 2);
+            bulk_commit();
+            bulk_wait_read0();
+            stored = true;
+            mbar_arrive(bar + 2);
+        }
+    }
+    if (stored) bulk_wait0();
+}
+
+}  // namespace gsp

@@ -42,7 +42,7 @@ struct DevicePlan {
     int *status = nullptr;  // device status word (bit 0: a bounded wait timed out)
     double *tail = nullptr; // 2 max_batch doubles: spectral-tail sums of a checked solve
     // z pass form: 0 length-2N transforms, 1 even/odd length-N split, 2 warp form (one
-    // warp per column pair, FP32, N = 64 ... 256)
+    // warp per column pair, FP32, N = 64 ... 256; one warp per column at N = 512)
     int zform = 0;
     // y pass form: 0 block form (a column pair spread over a block), 1 warp form (FP32,
     // N = 64 ... 256)
@@ -94,7 +94,7 @@ cudaError_t launch_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0
 
 // Forms of the z pass that exist for (N, dtype), as a bit mask over DevicePlan::zform:
 // bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;
-// bit 2 for FP32 at N = 64, 96, 128, 160, 192, 256.
+// bit 2 for FP32 at N = 64, 96, 128, 160, 192, 256 and 512.
 int z_forms(int N, int dtype);
 
 // Forms of the x passes that exist for (N, dtype), as a bit mask over DevicePlan::xform:

@@ -18,7 +18,7 @@ WARP_N = (64, 96, 128, 160, 192, 256)
 
 
 def forms(N, dtype):
-    return [0] + ([1] if N in SPLIT_N else []) + ([2] if dtype == "f32" and N in WARP_N else [])
+    return [0] + ([1] if N in SPLIT_N else []) + ([2] if dtype == "f32" and (N in WARP_N or N == 512) else [])
 
 
 def yforms(N, dtype):
@@ -215,17 +215,44 @@ def test_warp_form_batched(torch_cuda, N, yform, xform):
         p.last_status()
 
 
-@pytest.mark.parametrize("xform", [0, 1])
-def test_x_forms_sampled_n512(torch_cuda, xform):
-    """N = 512 (the padded 1024^3 grid) in both x forms, FP32: output lines against the
-    oracle's real-space evaluation of the discrete convolution."""
+@pytest.mark.parametrize("zform,xform", [(0, 0), (0, 1), (2, 1), (2, 0)])
+def test_forms_sampled_n512(torch_cuda, zform, xform):
+    """N = 512 (the padded 1024^3 grid), FP32, the z pass in its block form (0) and its
+    warp form (2, one warp per column, 1024 = 32 x 32) with both x forms: output lines
+    against the oracle's real-space evaluation of the discrete convolution.  The lines
+    cross every z, so each crosses all 16 output registers of the warp form."""
     N, L, tol = 512, 10.0, 1e-6
     rho = D.config_aniso4(N=N, seed=512).gaussians.sample(N, L)
-    lines = [(0, 0), (N // 2, N // 2 - 1), (N - 1, N - 1), (N // 3, 2 * N // 3)]
+    lines = [(0, 0), (N // 2, N // 2 - 1), (N - 1, N - 1), (N // 3, 2 * N // 3), (7, 505)]
     ref = direct.sample_lines(rho, gtensor.make_plan(N, L, tol), lines)
-    u = solve_form(torch_cuda, N, L, tol, "f32", rho, 0, None, xform)
+    u = solve_form(torch_cuda, N, L, tol, "f32", rho, zform, None, xform)
     got = np.stack([u[z, y] for z, y in lines])
     assert rel_l2(got, ref) <= TOL["f32"]
+
+
+def test_w512_tail_matches_block_form(torch_cuda):
+    """The checked solve at N = 512 in the z warp form: the same potential as its unchecked
+    solve and the same eta as the block form (both sum the same forward spectrum; they
+    differ only by FP32 rounding of the transforms)."""
+    torch = torch_cuda
+    from paper_1612_01799_gb300 import Plan, _lib
+    lib = _lib.load()
+    N, L = 512, 6.0
+    rho = torch.from_numpy(D.config_aniso4(N=N, seed=33).gaussians.sample(N, L).astype(np.float32)).cuda()
+    etas = {}
+    with Plan(N, L, 1e-6, "f32") as p:
+        for form in (0, 2):
+            p.z_form = form
+            u1 = p.solve(rho)
+            u2 = torch.empty_like(rho)
+            eta = ctypes.c_double()
+            assert lib.poisson_solve_checked(p.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(u2.data_ptr()),
+                                             ctypes.byref(eta), None) == 0
+            torch.cuda.synchronize()
+            assert torch.equal(u1, u2)
+            etas[form] = eta.value
+        p.last_status()
+    assert etas[2] == pytest.approx(etas[0], rel=1e-3)
 
 
 @pytest.mark.parametrize("N", [64, 96, 128, 160, 192])
