@@ -198,7 +198,8 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *           and one warp-local exchange per direction (POISSON_F32).
  *   POISSON_KNOB_Y_FORM  form of the two y passes (Sec. 2, the zero-padded transforms
  *       along the middle axis): 0 = a column pair spread over the threads of a block;
- *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, the same N).
+ *       1 = one warp per column pair, as form 2 of the z pass (POISSON_F32, the same N;
+ *       at N = 512 one warp per column).
  *   POISSON_KNOB_X_FORM  form of the two x passes (Sec. 2, the real transforms along the
  *       first axis and the crop): 0 = a tile of rows staged in shared memory; 1 = one
  *       half-warp (N = 64 ... 256 as for the z pass) or warp (N = 512) per pair of rows,

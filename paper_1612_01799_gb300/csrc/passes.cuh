@@ -518,6 +518,7 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
 // The y passes (K2 forward, K4 inverse) of B densities in the form p.yform selects: 0 the
 // block form (k_col_tma), 1 the warp form (k_y_warp, ywarp_form); an absent form runs as 0.
 template <typename Real, int N> constexpr bool ywarp_form() { return std::is_same<Real, float>::value && warp_n(N); }
+template <typename Real, int N> constexpr bool yw512_form() { return std::is_same<Real, float>::value && N == ZW512::N; }
 
 // planes z0 .. z0 + nz - 1 of the stacked densities (nz = 0: all B N planes).
 template <typename Real, int N>
@@ -527,6 +528,18 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 
     constexpr int L = 2 * N;
     const int ncols = N + 1;
     const int planes = nz ? nz : B * N;
+    if constexpr (yw512_form<Real, N>()) {
+        if (p.yform == 1) {
+            using Z = ZW512;
+            const int ntx = (ncols + Z::TC - 1) / Z::TC, nt = ntx * planes;
+            auto k = fwd ? k_y_w512<true> : k_y_w512<false>;
+            GSP_CHECK(set_smem(k, Z::SMEM));
+            k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s>>>(
+                fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1, static_cast<const float2 *>(p.tw), ntx, nt,
+                ncols, p.status, z0);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (ywarp_form<Real, N>()) {
         if (p.yform == 1) {
             using Y = YWarp<N / 16>;
@@ -725,6 +738,15 @@ cudaError_t encode_n(DevicePlan &p) {
                             CU_TENSOR_MAP_SWIZZLE_128B));
         GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
                             (cuuint64_t)(N + 1) * srow, ZWarp<N / 16>::TC, 1, ZWarp<N / 16>::SYM_RPC,
+                            CU_TENSOR_MAP_SWIZZLE_64B));
+    }
+    if constexpr (yw512_form<Real, N>()) {
+        // 8 columns x 256 rows of y or ky x 1 plane of w1, w2, w3 (64-byte swizzle).
+        GSP_CHECK(encode_3d(&p.tm_yw1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, ZW512::TC, 256, 1,
+                            CU_TENSOR_MAP_SWIZZLE_64B));
+        GSP_CHECK(encode_3d(&p.tm_yw2, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZW512::TC, 256, 1,
+                            CU_TENSOR_MAP_SWIZZLE_64B));
+        GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZW512::TC, 256, 1,
                             CU_TENSOR_MAP_SWIZZLE_64B));
     }
     if constexpr (zw512_form<Real, N>()) {

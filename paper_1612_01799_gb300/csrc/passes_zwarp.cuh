@@ -1245,3 +1245,183 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
 }
 
 }  // namespace gsp
+
+namespace gsp {
+
+// ---- K2 / K4, warp form at N = 512 (FP32) --------------------------------------------------
+// The y passes with the transform halves of k_z_w512: the forward half (F1..F4) alone for
+// the y forward (N input rows, all 2N rows kept) and the adjoint half alone for the y
+// inverse (2N input rows, rows y < N kept), one warp per column, a tile of 8 columns kx of
+// one plane.  Shared memory (104 KB, two CTAs per SM):
+//   y forward: B holds the 512 input rows (prefetched for the next tile as soon as every
+//     warp has read them); XO holds the exchange regions, then the 1024-row output tile,
+//     written after a block barrier and freed for the next tile once the store has read it;
+//   y inverse: the 1024 input rows arrive split, rows < 512 in B and rows >= 512 in the
+//     upper half of XO; a block barrier after the input reads frees B for the next tile's
+//     first half and the upper exchange regions; a second one after the exchange frees the
+//     upper half of XO for the next tile's second half while the outputs (rows < 512) go to
+//     the lower half.
+template <bool FWD>
+__global__ void __launch_bounds__(ZW512::NT, 2)
+k_y_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+         const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status, int z0) {
+    using Z = ZW512;
+    constexpr int N = Z::N, NW = Z::NW, HALF = 16384;  // one 256-row box of 64-byte rows
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    unsigned char *Bb = base + Z::OFF_B;
+    unsigned char *xo = base + Z::OFF_XO;
+    float2 *T = reinterpret_cast<float2 *>(base + Z::OFF_T);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Z::OFF_BAR);  // input, XO (lower half) free
+    int *cnt = reinterpret_cast<int *>(bar + 2);                       // input read, outputs written
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        cnt[0] = cnt[1] = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < 1024; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    __syncthreads();
+
+    // Loads of tile t: forward, rows 0..511 into B; inverse, rows 0..511 into B (first)
+    // and rows 512..1023 into the upper half of XO (second), on one barrier phase.
+    auto issue_first = [&](int t) {
+        const int tx = t % ntx, zz = z0 + t / ntx;
+        mbar_arrive_expect_tx(bar, FWD ? 2 * HALF : 4 * HALF);
+        tma_load_3d(Bb, &tin, bar, tx * Z::TC, 0, zz);
+        tma_load_3d(Bb + HALF, &tin, bar, tx * Z::TC, 256, zz);
+    };
+    auto issue_second = [&](int t) {
+        const int tx = t % ntx, zz = z0 + t / ntx;
+        tma_load_3d(xo + 2 * HALF, &tin, bar, tx * Z::TC, 512, zz);
+        tma_load_3d(xo + 3 * HALF, &tin, bar, tx * Z::TC, 768, zz);
+    };
+    auto last_arrival = [&](int c) {
+        __syncwarp();
+        bool last = false;
+        if (q == 0) {
+            __threadfence_block();
+            last = atomicAdd(cnt + c, 1) % NW == NW - 1;
+            if (last) {
+                __threadfence_block();
+                fence_proxy_async();
+            }
+        }
+        return last;
+    };
+    if (threadIdx.x == 0) {
+        mbar_arrive(bar + 1);  // XO starts free
+        if ((int)blockIdx.x < ntiles) {
+            issue_first(blockIdx.x);
+            if (!FWD) issue_second(blockIdx.x);
+        }
+    }
+    const uint32_t xw = smem_addr(xo) + 8192 * g;
+    const uint32_t aw = xw + 8 * q;
+    const uint32_t ar = xw + 256 * q + 8 * (q & 15);
+    bool stored = false;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        const int tx = t % ntx, zz = z0 + t / ntx;
+        const bool valid = tx * Z::TC + g < ncols;
+        const bool more = t + (int)gridDim.x < ntiles;
+        CF v[32];
+        bool bad = !mbar_wait(bar, ph, status);
+        if constexpr (FWD) {
+            if (valid && !bad) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const float2 f = *reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g));
+                    v[r] = {f.x, f.y};
+                }
+            }
+            if (last_arrival(0) && more) issue_first(t + gridDim.x);
+            if (valid) {
+                w512_f1(v);
+#pragma unroll
+                for (int j = 1; j < 32; ++j) v[j] = twmul<-1>(v[j], T[w512_kappa(j) * 32 + q]);
+            }
+            if (!bad) bad = !mbar_wait(bar + 1, ph, status);  // the previous tile's store has read XO
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int k1 = w512_kappa(j);
+                    sts2((aw ^ (8 * (k1 & 15))) + 256 * k1, v[j]);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int p = 0; p < 32; ++p) v[p] = lds2(ar ^ (8 * p));
+                dft32<-1>(v);  // v[k2] = X[q + 32 k2]
+            }
+            if (__syncthreads_or(bad)) break;  // every warp's exchange reads are done
+            if (valid) {
+#pragma unroll
+                for (int k2 = 0; k2 < 32; ++k2)
+                    *reinterpret_cast<float2 *>(xo + sw64(q + 32 * k2, g)) = make_float2(v[k2].re, v[k2].im);
+            }
+            fence_proxy_async();
+            if (last_arrival(1)) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) tma_store_3d(&tout, xo + c * HALF, tx * Z::TC, 256 * c, zz);
+                bulk_commit();
+                bulk_wait_read0();
+                stored = true;
+                mbar_arrive(bar + 1);
+            }
+        } else {
+            if (valid && !bad) {
+#pragma unroll
+                for (int k2 = 0; k2 < 32; ++k2) {
+                    const int row = q + 32 * k2;
+                    const unsigned char *src = k2 < 16 ? Bb + sw64(row, g) : xo + 2 * HALF + sw64(row - 512, g);
+                    const float2 f = *reinterpret_cast<const float2 *>(src);
+                    v[k2] = {f.x, f.y};
+                }
+            }
+            if (__syncthreads_or(bad)) break;  // every warp has read its input rows
+            if (threadIdx.x == 0 && more) {
+                fence_proxy_async();
+                issue_first(t + gridDim.x);  // B is free
+            }
+            if (valid) dft32<1>(v);  // v[p] = B_p[q]
+            if (!bad) bad = !mbar_wait(bar + 1, ph, status);  // the previous tile's store has read XO
+            if (valid) {
+#pragma unroll
+                for (int p = 0; p < 32; ++p) sts2(ar ^ (8 * p), v[p]);
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int k1 = w512_kappa(j);
+                    v[j] = lds2((aw ^ (8 * (k1 & 15))) + 256 * k1);
+                }
+#pragma unroll
+                for (int j = 1; j < 32; ++j) v[j] = twmul<1>(v[j], T[w512_kappa(j) * 32 + q]);
+                w512_f1_adj(v);
+            }
+            if (__syncthreads_or(bad)) break;  // every warp's exchange reads are done
+            if (threadIdx.x == 0 && more) {
+                fence_proxy_async();
+                issue_second(t + gridDim.x);  // the upper half of XO is free
+            }
+            if (valid) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r)
+                    *reinterpret_cast<float2 *>(xo + sw64(q + 32 * r, g)) = make_float2(v[r].re, v[r].im);
+            }
+            fence_proxy_async();
+            if (last_arrival(1)) {
+                tma_store_3d(&tout, xo, tx * Z::TC, 0, zz);
+                tma_store_3d(&tout, xo + HALF, tx * Z::TC, 256, zz);
+                bulk_commit();
+                bulk_wait_read0();
+                stored = true;
+                mbar_arrive(bar + 1);
+            }
+        }
+    }
+    if (stored) bulk_wait0();
+}
+
+}  // namespace gsp

@@ -45,7 +45,7 @@ struct DevicePlan {
     // warp per column pair, FP32, N = 64 ... 256; one warp per column at N = 512)
     int zform = 0;
     // y pass form: 0 block form (a column pair spread over a block), 1 warp form (FP32,
-    // N = 64 ... 256)
+    // N = 64 ... 256: a warp per column pair; N = 512: a warp per column)
     int yform = 0;
     // x pass form: 0 block form (a tile of rows staged in shared memory), 1 warp form (a
     // half-warp or warp per row pair, FP32, N = 64 ... 256 and 512)
@@ -61,7 +61,7 @@ struct DevicePlan {
     // symbol, w3 out; 128- and 64-byte swizzled boxes), encoded where that form exists.
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
     CUtensorMap tm_zw_in, tm_zw_sym, tm_zw_out;
-    CUtensorMap tm_yw1, tm_yw2, tm_yw3;  // warp-form y passes: N-row boxes of w1, w2, w3
+    CUtensorMap tm_yw1, tm_yw2, tm_yw3;  // warp-form y passes: boxes of N rows (256 at N = 512) of w1, w2, w3
     CUtensorMap tm_rf;                   // fused forward x-y pass: N-row boxes of its ring in w3
 };
 
@@ -105,7 +105,7 @@ int x_forms(int N, int dtype);
 cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s);
 
 // Forms of the y passes that exist for (N, dtype), as a bit mask over DevicePlan::yform:
-// bit 0 always; bit 1 for FP32 at N = 64, 96, 128, 160, 192, 256.
+// bit 0 always; bit 1 for FP32 at N = 64, 96, 128, 160, 192, 256 and 512.
 int y_forms(int N, int dtype);
 
 // The two y passes alone, one density, in the form p.yform selects (for timing the forms).

@@ -159,7 +159,7 @@ def test_device_errors_are_codes(torch_cuda):
 
 
 @pytest.mark.parametrize("N,dtype,xyform", [(256, "f32", 0), (256, "f32", 1), (48, "f32", 0), (80, "f64", 0),
-                                            (128, "f64", 0), (8, "f32", 0)])
+                                            (128, "f64", 0), (8, "f32", 0), (512, "f32", 0)])
 def test_host_solve_slab_pipeline(torch_cuda, N, dtype, xyform):
     """poisson_solve_host on pinned buffers: the slab pipeline (copies of 8 z-slabs
     overlapped with the x passes; N a multiple of 8, N >= 16, separate x and y passes) and

@@ -22,7 +22,7 @@ def forms(N, dtype):
 
 
 def yforms(N, dtype):
-    return [0] + ([1] if dtype == "f32" and N in WARP_N else [])
+    return [0] + ([1] if dtype == "f32" and (N in WARP_N or N == 512) else [])
 
 
 def xforms(N, dtype):
@@ -215,17 +215,17 @@ def test_warp_form_batched(torch_cuda, N, yform, xform):
         p.last_status()
 
 
-@pytest.mark.parametrize("zform,xform", [(0, 0), (0, 1), (2, 1), (2, 0)])
-def test_forms_sampled_n512(torch_cuda, zform, xform):
-    """N = 512 (the padded 1024^3 grid), FP32, the z pass in its block form (0) and its
-    warp form (2, one warp per column, 1024 = 32 x 32) with both x forms: output lines
+@pytest.mark.parametrize("zform,yform,xform", [(0, 0, 0), (0, 0, 1), (2, 1, 1), (2, 0, 0), (0, 1, 0)])
+def test_forms_sampled_n512(torch_cuda, zform, yform, xform):
+    """N = 512 (the padded 1024^3 grid), FP32, the z and y passes in their block forms and
+    their warp forms (one warp per column, 1024 = 32 x 32) with both x forms: output lines
     against the oracle's real-space evaluation of the discrete convolution.  The lines
-    cross every z, so each crosses all 16 output registers of the warp form."""
+    cross every z, so each crosses all 16 output registers of the z warp form."""
     N, L, tol = 512, 10.0, 1e-6
     rho = D.config_aniso4(N=N, seed=512).gaussians.sample(N, L)
     lines = [(0, 0), (N // 2, N // 2 - 1), (N - 1, N - 1), (N // 3, 2 * N // 3), (7, 505)]
     ref = direct.sample_lines(rho, gtensor.make_plan(N, L, tol), lines)
-    u = solve_form(torch_cuda, N, L, tol, "f32", rho, zform, None, xform)
+    u = solve_form(torch_cuda, N, L, tol, "f32", rho, zform, yform, xform)
     got = np.stack([u[z, y] for z, y in lines])
     assert rel_l2(got, ref) <= TOL["f32"]
 
