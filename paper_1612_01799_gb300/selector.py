@@ -13,7 +13,7 @@ Pipeline for a density:
      training data; if the estimate exceeds tol, move to the next candidate and solve again.
 
 The plain method (start at the smallest candidate and refine with the same check) is the
-fallback and the judge of what the network saves.
+fallback, and the yardstick for what the network saves.
 """
 import ctypes
 import json
