@@ -736,9 +736,10 @@ cudaError_t encode_n(DevicePlan &p) {
                             CU_TENSOR_MAP_SWIZZLE_128B));
         GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp<N / 16>::TC, 1, N,
                             CU_TENSOR_MAP_SWIZZLE_128B));
+        // The symbol octant read with its innermost index as kz (symmetric table): boxes of
+        // 128 kz x 1 ky x 16 kx.
         GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
-                            (cuuint64_t)(N + 1) * srow, ZWarp<N / 16>::TC, 1, ZWarp<N / 16>::SYM_RPC,
-                            CU_TENSOR_MAP_SWIZZLE_64B));
+                            (cuuint64_t)(N + 1) * srow, ZWarp<N / 16>::SYM_KZB, 1, ZWarp<N / 16>::TC));
     }
     if constexpr (yw512_form<Real, N>()) {
         // 8 columns x 256 rows of y or ky x 1 plane of w1, w2, w3 (64-byte swizzle).

@@ -37,7 +37,10 @@
 //
 // Shared memory (one CTA = one tile of 16 columns x 1 ky x the N input rows, 8 warps):
 //   B   32 KB: the TMA input tile (256 rows x 128 B, 128-byte swizzle), then the tile's
-//       symbol rows (272 x 64 B, 64-byte swizzle), then the next tile's input;
+//       symbol lines (boxes of 128 kz x 16 kx, kz innermost: the octant table is
+//       symmetric in (kx, ky, kz) up to the FP64 rounding of its tabulated sums, so read
+//       with its innermost index as kz each column's kz values lie contiguous and the
+//       lanes read consecutive floats), then the next tile's input;
 //   XO  64 KB: 512 rows of 128 B; warp g owns the 16-byte chunk g ^ (row & 7) of every row,
 //       for its exchange slots (all 512 rows) and for its outputs (rows z < 256), so the
 //       first 32 KB is the output tile in the TMA store's 128-byte swizzle;
@@ -58,18 +61,17 @@ namespace gsp {
 
 template <int E1> struct ZWarp {
     static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N, TC = 16, NW = 8, NT = 256;
-    static constexpr int SYM_NCP = (N + 1 + 255) / 256;                              // symbol TMA copies
-    static constexpr int SYM_RPC = ((N + 1 + SYM_NCP - 1) / SYM_NCP + 7) / 8 * 8;    // rows per copy
+    // Symbol lines: boxes of SYM_KZB kz values (innermost) x 1 ky x TC kx; kz <= N.
+    static constexpr int SYM_KZB = 128, SYM_NCP = (N + 1 + SYM_KZB - 1) / SYM_KZB;
     static constexpr int IN_BYTES = N * TC * 8;
-    static constexpr int SYM_BYTES = SYM_NCP * SYM_RPC * TC * 4;
+    static constexpr int SYM_BYTES = SYM_NCP * SYM_KZB * TC * 4;
     static constexpr int B_BYTES = IN_BYTES > SYM_BYTES ? IN_BYTES : SYM_BYTES;
     static constexpr int OFF_B = 0, OFF_XO = (B_BYTES + 1023) / 1024 * 1024, OFF_T = OFF_XO + 65536;
     static constexpr int OFF_BAR = OFF_T + E1 * 32 * 8;
     static constexpr int SMEM = 1024 + OFF_BAR + 64;  // 1 KB alignment slack
     static_assert(E1 == 16 || E1 == 12 || E1 == 10 || E1 == 8 || E1 == 6 || E1 == 4,
                   "first stage: a pruned DFT of E1 / 2 inputs");
-    static_assert(SYM_NCP * SYM_RPC >= N + 1 && SYM_RPC <= 256, "symbol rows fit the TMA boxes");
-    static_assert((SYM_RPC * TC * 4) % 512 == 0, "64-byte-swizzled copies start 512-byte aligned");
+    static_assert(SYM_BYTES <= IN_BYTES, "the symbol lines fit the input buffer");
 };
 
 // CV times the scalar twiddle w = (re, im) (D < 0) or its conjugate (D > 0).
@@ -305,7 +307,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         mbar_arrive_expect_tx(bar + 1, Z::SYM_BYTES);
 #pragma unroll
         for (int c = 0; c < Z::SYM_NCP; ++c)
-            tma_load_3d(Bb + c * Z::SYM_RPC * Z::TC * 4, &tsym, bar + 1, tx * Z::TC, kya, c * Z::SYM_RPC);
+            tma_load_3d(Bb + c * Z::SYM_KZB * Z::TC * 4, &tsym, bar + 1, c * Z::SYM_KZB, kya, tx * Z::TC);
     };
     // Arrival of this warp on counter c; true on the lane-0 thread of the tile's last warp.
     auto last_arrival = [&](int c) {
@@ -329,10 +331,10 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     const ZwLane zl = zw_lane<E1>(tw, smem_addr(xo), g, q);
     // Input/output rows q + 32 r of this warp's 16-byte chunk.
     const int io = zw_sw128(q, g);
-    // Symbol rows: reader q holds kz = kb + 2 E1 k2 (k2 < 8) and 2N - kb - 2 E1 k2 (k2 >= 8).
+    // Symbol: reader q holds kz = kb + 2 E1 k2 (k2 < 8) and 2N - kb - 2 E1 k2 (k2 >= 8); its
+    // columns 2g and 2g + 1 have kz lines SYM_KZB floats apart in every box.
     const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
-    const int sym_lo = 64 * kb + ((8 * g) ^ (((kb >> 1) & 3) << 4));
-    const int sym_hi = 64 * (L - kb) + ((8 * g) ^ ((((L - kb) >> 1) & 3) << 4));
+    const unsigned char *symg = Bb + 2 * g * Z::SYM_KZB * 4;
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
@@ -387,15 +389,10 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid && zl.rd) {
 #pragma unroll
             for (int k2 = 0; k2 < 16; ++k2) {
-                int off;
-                if constexpr ((2 * E1) % 8 == 0) {  // (kz >> 1) & 3 is the lane's own
-                    off = k2 < 8 ? sym_lo + 128 * E1 * k2 : sym_hi - 128 * E1 * k2;
-                } else {
-                    const int kz = k2 < 8 ? kb + 2 * E1 * k2 : L - kb - 2 * E1 * k2;
-                    const int A = 64 * kz + 8 * g;
-                    off = A ^ (((A >> 7) & 3) << 4);
-                }
-                v[k2] = cscale2(v[k2], *reinterpret_cast<const float2 *>(Bb + off));
+                const int kz = k2 < 8 ? kb + 2 * E1 * k2 : L - kb - 2 * E1 * k2;
+                const unsigned char *sp = symg + (kz >> 7) * (Z::SYM_KZB * Z::TC * 4) + 4 * (kz & (Z::SYM_KZB - 1));
+                v[k2] = cscale2(v[k2], f2(*reinterpret_cast<const float *>(sp),
+                                          *reinterpret_cast<const float *>(sp + Z::SYM_KZB * 4)));
             }
         }
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
@@ -992,8 +989,9 @@ namespace gsp {
 // A CTA of 8 warps owns a tile of 8 consecutive columns kx at one ky.  Shared memory:
 //   B   32 KB: the input tile (512 z-rows x 64 B, two TMA boxes of 256 rows, 64-byte
 //       swizzle), then the tile's symbol lines (three boxes of 256 kz x 8 kx: the octant
-//       table is symmetric in (kx, ky, kz), so with kz as its innermost index each column's
-//       kz values lie contiguous), then the next tile's input;
+//       table is symmetric in (kx, ky, kz) up to the FP64 rounding of its tabulated sums,
+//       so with kz as its innermost index each column's kz values lie contiguous), then the
+//       next tile's input;
 //   XO  64 KB: the warps' 8 KB exchange regions; the first 32 KB is also the output tile
 //       in the TMA store's 64-byte swizzle, written after a block barrier that ends every
 //       warp's exchange reads;
