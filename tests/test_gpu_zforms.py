@@ -314,3 +314,22 @@ def test_xy_fused_timed_passes(torch_cuda):
         assert ms[1] < 0.02 and ms[4] < 0.02
         assert torch.equal(u, p.solve(rho))
         p.last_status()
+
+
+def test_w512_batched(torch_cuda):
+    """Two densities at N = 512 through one grouped launch sequence in the N = 512 warp forms
+    of the z and y passes: each equals its single solve bit for bit (the kernels take the
+    density from the tile index)."""
+    torch = torch_cuda
+    from paper_1612_01799_gb300 import Plan, solve_batched
+    N, L = 512, 10.0
+    rhos = [torch.from_numpy(D.config_aniso4(N=N, seed=80 + i).gaussians.sample(N, L).astype(np.float32)).cuda()
+            for i in range(2)]
+    with Plan(N, L, 1e-6, "f32", max_batch=2) as p:
+        p.z_form, p.y_form, p.x_form = 2, 1, 1
+        outs = [torch.empty_like(r) for r in rhos]
+        solve_batched([p, p], rhos, outs)
+        torch.cuda.synchronize()
+        for r, o in zip(rhos, outs):
+            assert torch.equal(p.solve(r), o)
+        p.last_status()
