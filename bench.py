@@ -228,11 +228,26 @@ def workload_config(N, dtype):
 
 
 def time_solves(torch, plan, rho_t, out_t, steps, warmup, flush, hold_s=0.0):
-    """Per-step event times (ms) of whole solves, and per-pass times from the same steps.
-    Untimed warm-up: at least `warmup` solves, continued for hold_s seconds so that the
-    clock sampler records the GPU under this load right up to the timed steps."""
+    """Per-step device times (ms) of whole solves and per-pass times, L2 flushed before
+    every solve.  A step is one replay of a CUDA graph holding one poisson_solve (its five
+    kernels, no host launches inside the timed span), timed with CUDA events on the
+    replaying stream.  Each step is followed by one poisson_solve_timed (events between the
+    passes) for the per-pass breakdown and the roofline's kernel times.  Untimed warm-up: at
+    least `warmup` solves, continued for hold_s seconds so that the clock sampler records
+    the GPU under this load right up to the timed steps."""
+    cur = torch.cuda.current_stream()
+    s = torch.cuda.Stream()
+    s.wait_stream(cur)
+    with torch.cuda.stream(s):
+        plan.solve(rho_t, out=out_t, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.solve(rho_t, out=out_t, stream=s)
     t0, i = time.perf_counter(), 0
     while i < warmup or time.perf_counter() - t0 < hold_s:
+        flush.zero_()
+        g.replay()
         flush.zero_()
         plan.solve_timed(rho_t, out_t)
         i += 1
@@ -240,9 +255,15 @@ def time_solves(torch, plan, rho_t, out_t, steps, warmup, flush, hold_s=0.0):
     totals, passes = [], []
     for _ in range(steps):
         flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        g.replay()
+        e1.record(cur)
+        flush.zero_()
         ms = plan.solve_timed(rho_t, out_t)  # events on the launching stream, synchronised
+        totals.append(e0.elapsed_time(e1))
         passes.append(ms)
-        totals.append(sum(ms))
+    del g
     return totals, passes
 
 
@@ -444,6 +465,9 @@ def run_ours(args):
             "e2e": {"value": aggregate_rate(world, N, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": N ** 3 * 4, "d2h_bytes_per_step": N ** 3 * 4},
             "gpu_launches": len(rows32) * r32["steps"],
+            "step": "one replay of a CUDA graph holding one poisson_solve (its kernels, nothing else), "
+                    "CUDA events around it on the replaying stream; per-pass times from a "
+                    "poisson_solve_timed after each step (events between the passes)",
             "tuning": {"z_pass_f32": Z_FORMS[r32["z_form"]],
                        "z_pass_f64": Z_FORMS[results["f64"]["z_form"]],
                        "y_passes_f32": Y_FORMS[r32["y_form"]], "y_passes_f64": Y_FORMS[results["f64"]["y_form"]],

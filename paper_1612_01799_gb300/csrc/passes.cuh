@@ -139,6 +139,7 @@ k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     static_assert((N * N) % TR == 0, "row tiles stay inside one density");
     extern __shared__ __align__(16) unsigned char smraw[];
+    griddep_wait();
     C *sm = reinterpret_cast<C *>(smraw);  // (N + 1) x SP
     const int t = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * TR;
@@ -275,6 +276,7 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
     using T2 = Cx2<Real>;
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     extern __shared__ __align__(16) unsigned char smraw[];
+    griddep_wait();
     C *sm = reinterpret_cast<C *>(smraw);  // (N + 1) x SP
     const int t = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * TR;
@@ -369,6 +371,25 @@ template <class K> static cudaError_t set_smem(K kernel, size_t bytes) {
 
 // Blocks of a persistent kernel: as many as fit on all SMs at once.  The occupancy of
 // each kernel is queried once and cached by the kernel's address.
+// Launch with programmatic dependent launch allowed: the kernel's CTAs may become resident
+// and build their shared tables while the previous kernel on the stream finishes; every
+// pass kernel calls griddep_wait before it touches memory that kernel writes or reads.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <class K> static int persistent_blocks(K kernel, int threads, size_t smem, int ntiles) {
     struct Entry {
         const void *fn;
@@ -424,9 +445,9 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
             static_assert(Z::TC == L1::TC, "same tiles as the direct form");
             auto k = tail ? k_z_warp<N / 16, true> : k_z_warp<N / 16, false>;
             GSP_CHECK(set_smem(k, Z::SMEM));
-            k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s>>>(
-                p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status,
-                tail);
+            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s,
+                                 p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx, nt,
+                                 ncols, p.status, tail));
             return cudaGetLastError();
         }
     }
@@ -436,9 +457,9 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
             const int ntx5 = (ncols + Z::TC - 1) / Z::TC, nt5 = ntx5 * L * B;
             auto k = tail ? k_z_w512<true> : k_z_w512<false>;
             GSP_CHECK(set_smem(k, Z::SMEM));
-            k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt5), Z::NT, Z::SMEM, s>>>(
-                p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx5, nt5, ncols, p.status,
-                tail);
+            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Z::NT, Z::SMEM, nt5), Z::NT, Z::SMEM, s,
+                                 p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx5, nt5,
+                                 ncols, p.status, tail));
             return cudaGetLastError();
         }
     }
@@ -447,16 +468,16 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
             auto k = tail ? k_z_split_tma<Real, L, true> : k_z_split_tma<Real, L, false>;
             constexpr int T = zsplit_threads<Real, L>();
             GSP_CHECK(set_smem(k, L1::SMEM));
-            k<<<persistent_blocks(k, T, L1::SMEM, nt), T, L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx, nt,
-                                                                      ncols, p.Px, p.status, tail);
+            GSP_CHECK(launch_pdl(k, persistent_blocks(k, T, L1::SMEM, nt), T, L1::SMEM, s,
+                                 p.tm_z_in, p.tm_z_sym, w3, twc, ntx, nt, ncols, p.Px, p.status, tail));
             return cudaGetLastError();
         }
     }
     auto k = tail ? k_z_symbol_tma<Real, L, true> : k_z_symbol_tma<Real, L, false>;
     constexpr int T = tma_threads<Real, L, 1>();
     GSP_CHECK(set_smem(k, L1::SMEM));
-    k<<<persistent_blocks(k, T, L1::SMEM, nt), T, L1::SMEM, s>>>(p.tm_z_in, p.tm_z_sym, w3, twc, ntx, nt, ncols,
-                                                              p.Px, p.status, tail);
+    GSP_CHECK(launch_pdl(k, persistent_blocks(k, T, L1::SMEM, nt), T, L1::SMEM, s,
+                         p.tm_z_in, p.tm_z_sym, w3, twc, ntx, nt, ncols, p.Px, p.status, tail));
     return cudaGetLastError();
 }
 
@@ -480,23 +501,26 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
                 GSP_CHECK(set_smem(k_x_warp2_fwd<N>, XWarp2::SMEM));
                 GSP_CHECK(set_smem(k_x_warp2_inv<N>, XWarp2::SMEM));
                 const int nw = (npairs + XWarp2::NW - 1) / XWarp2::NW;
+                constexpr int NT2 = XWarp2::NT, SM2 = XWarp2::SMEM;
                 if (fwd)
-                    k_x_warp2_fwd<N><<<persistent_blocks(k_x_warp2_fwd<N>, XWarp2::NT, XWarp2::SMEM, nw), XWarp2::NT,
-                                       XWarp2::SMEM, s>>>(rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px);
+                    GSP_CHECK(launch_pdl(k_x_warp2_fwd<N>, persistent_blocks(k_x_warp2_fwd<N>, NT2, SM2, nw), NT2, SM2,
+                                         s, rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px));
                 else
-                    k_x_warp2_inv<N><<<persistent_blocks(k_x_warp2_inv<N>, XWarp2::NT, XWarp2::SMEM, nw), XWarp2::NT,
-                                       XWarp2::SMEM, s>>>(static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
+                    GSP_CHECK(launch_pdl(k_x_warp2_inv<N>, persistent_blocks(k_x_warp2_inv<N>, NT2, SM2, nw), NT2, SM2,
+                                         s, static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px));
             } else {
                 using X = XWarp<N>;
                 GSP_CHECK(set_smem(k_x_warp_fwd<N>, X::SMEM));
                 GSP_CHECK(set_smem(k_x_warp_inv<N>, X::SMEM));
                 const int nw = (npairs + 15) / 16;
                 if (fwd)
-                    k_x_warp_fwd<N><<<persistent_blocks(k_x_warp_fwd<N>, X::NT, X::SMEM, nw), X::NT, X::SMEM, s>>>(
-                        rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px);
+                    GSP_CHECK(launch_pdl(k_x_warp_fwd<N>,
+                                         persistent_blocks(k_x_warp_fwd<N>, X::NT, X::SMEM, nw), X::NT, X::SMEM, s,
+                                         rho, static_cast<float2 *>(p.w1), tw, npairs, p.Px));
                 else
-                    k_x_warp_inv<N><<<persistent_blocks(k_x_warp_inv<N>, X::NT, X::SMEM, nw), X::NT, X::SMEM, s>>>(
-                        static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px);
+                    GSP_CHECK(launch_pdl(k_x_warp_inv<N>,
+                                         persistent_blocks(k_x_warp_inv<N>, X::NT, X::SMEM, nw), X::NT, X::SMEM, s,
+                                         static_cast<const float2 *>(p.w1), u, tw, npairs, p.Px));
             }
             return cudaGetLastError();
         }
@@ -507,10 +531,12 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
     const T2 *tw = static_cast<const T2 *>(p.tw);
     if (fwd) {
         GSP_CHECK(set_smem(k_x_forward<Real, N>, smem_row));
-        k_x_forward<Real, N><<<grow, TR * PX1, smem_row, s>>>(rho, static_cast<T2 *>(p.w1), tw, nrows, p.Px);
+        GSP_CHECK(launch_pdl(k_x_forward<Real, N>, grow, TR * PX1, smem_row, s,
+                             rho, static_cast<T2 *>(p.w1), tw, nrows, p.Px));
     } else {
         GSP_CHECK(set_smem(k_x_inverse<Real, N>, smem_row));
-        k_x_inverse<Real, N><<<grow, TR * PX1, smem_row, s>>>(static_cast<const T2 *>(p.w1), u, tw, nrows, p.Px);
+        GSP_CHECK(launch_pdl(k_x_inverse<Real, N>, grow, TR * PX1, smem_row, s,
+                             static_cast<const T2 *>(p.w1), u, tw, nrows, p.Px));
     }
     return cudaGetLastError();
 }
@@ -534,9 +560,9 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 
             const int ntx = (ncols + Z::TC - 1) / Z::TC, nt = ntx * planes;
             auto k = fwd ? k_y_w512<true> : k_y_w512<false>;
             GSP_CHECK(set_smem(k, Z::SMEM));
-            k<<<persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s>>>(
-                fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1, static_cast<const float2 *>(p.tw), ntx, nt,
-                ncols, p.status, z0);
+            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s,
+                                 fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1,
+                                 static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status, z0));
             return cudaGetLastError();
         }
     }
@@ -547,9 +573,9 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 
             auto k = fwd ? k_y_warp<N / 16, true> : k_y_warp<N / 16, false>;
             const int smem = fwd ? Y::SMEM_F : Y::SMEM_I;
             GSP_CHECK(set_smem(k, smem));
-            k<<<persistent_blocks(k, Y::NT, smem, nt), Y::NT, smem, s>>>(
-                fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1, static_cast<const float2 *>(p.tw), ntx, nt,
-                ncols, p.status, z0);
+            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Y::NT, smem, nt), Y::NT, smem, s,
+                                 fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1,
+                                 static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status, z0));
             return cudaGetLastError();
         }
     }
@@ -560,15 +586,17 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 
         const int ntx0 = (ncols + L0::TC - 1) / L0::TC, nt = ntx0 * planes;
         auto k = k_col_tma<Real, L, 0>;
         GSP_CHECK(set_smem(k, L0::SMEM));
-        k<<<persistent_blocks(k, tma_threads<Real, L, 0>(), L0::SMEM, nt), tma_threads<Real, L, 0>(), L0::SMEM, s>>>(
-            p.tm_y_in, static_cast<T2 *>(p.w2), twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status, z0);
+        constexpr int NTC = tma_threads<Real, L, 0>();
+        GSP_CHECK(launch_pdl(k, persistent_blocks(k, NTC, L0::SMEM, nt), NTC, L0::SMEM, s,
+                             p.tm_y_in, static_cast<T2 *>(p.w2), twc, ntx0, nt, ncols, Px, (long long)L * Px, p.status, z0));
     } else {
         using L2 = TmaLayout<Real, L, 2>;
         const int ntx2 = (ncols + L2::TC - 1) / L2::TC, nt = ntx2 * planes;
         auto k = k_col_tma<Real, L, 2>;
         GSP_CHECK(set_smem(k, L2::SMEM));
-        k<<<persistent_blocks(k, tma_threads<Real, L, 2>(), L2::SMEM, nt), tma_threads<Real, L, 2>(), L2::SMEM, s>>>(
-            p.tm_yi_in, static_cast<T2 *>(p.w1), twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status, z0);
+        constexpr int NTC = tma_threads<Real, L, 2>();
+        GSP_CHECK(launch_pdl(k, persistent_blocks(k, NTC, L2::SMEM, nt), NTC, L2::SMEM, s,
+                             p.tm_yi_in, static_cast<T2 *>(p.w1), twc, ntx2, nt, ncols, Px, (long long)N * Px, p.status, z0));
     }
     return cudaGetLastError();
 }
@@ -604,11 +632,12 @@ cudaError_t xy_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u,
         const XYOrder ord{P, D, fwd ? X::NX : X::NY, fwd ? X::NY : X::NX};
         const float2 *tw = static_cast<const float2 *>(p.tw);
         if (fwd)
-            k_xy_fwd<N / 16><<<G, X::NT, smem, s>>>(rho, static_cast<float2 *>(p.w3), p.tm_rf, p.tm_yw2, tw, ord, R,
-                                                    p.Px, p.sync, p.status);
+            GSP_CHECK(launch_pdl(k_xy_fwd<N / 16>, G, X::NT, smem, s,
+                                 rho, static_cast<float2 *>(p.w3), p.tm_rf, p.tm_yw2, tw, ord, R, p.Px, p.sync,
+                                 p.status));
         else
-            k_yx_inv<N / 16><<<G, X::NT, smem, s>>>(p.tm_yw3, static_cast<float2 *>(p.w2), u, tw, ord, R, p.Px,
-                                                    p.sync, p.status);
+            GSP_CHECK(launch_pdl(k_yx_inv<N / 16>, G, X::NT, smem, s,
+                                 p.tm_yw3, static_cast<float2 *>(p.w2), u, tw, ord, R, p.Px, p.sync, p.status));
         return cudaGetLastError();
     }
     return cudaErrorInvalidValue;

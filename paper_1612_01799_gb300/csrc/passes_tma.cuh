@@ -138,6 +138,7 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
     constexpr int E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P, R0 = FirstRadix<Rs>::v;
     constexpr int TCU = Lay::ROWB / 8;  // box width in 8-byte units
     extern __shared__ __align__(128) unsigned char smraw[];
+    griddep_wait();
     unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
     unsigned char *inb = base;
     C *xb = reinterpret_cast<C *>(base + Lay::OFF_XB);
@@ -212,6 +213,7 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
     constexpr int RL = LastRadix<Rs>::v, R0 = FirstRadix<Rs>::v;
     constexpr int TCU = Lay::ROWB / 8;
     extern __shared__ __align__(128) unsigned char smraw[];
+    griddep_wait();
     unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
     unsigned char *inb = base;
     C *xb = reinterpret_cast<C *>(base + Lay::OFF_XB);
@@ -384,6 +386,7 @@ k_z_split_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ C
     static_assert(R0 % 2 == 0, "the A + B exchange splits the first radix's outputs in halves");
     static_assert(NT <= 1024, "threads of one CTA");
     extern __shared__ __align__(128) unsigned char smraw[];
+    griddep_wait();
     unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
     unsigned char *inb = base;
     C *xb = reinterpret_cast<C *>(base + Lay::OFF_XB);

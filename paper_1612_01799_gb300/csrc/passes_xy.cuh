@@ -119,6 +119,7 @@ k_xy_fwd(const PtrArray rho, float2 *__restrict__ ring, const __grid_constant__ 
     using X = XYWarp<E1>;
     constexpr int N = X::N, H = X::H, NX = X::NX, NY = X::NY;
     extern __shared__ __align__(1024) unsigned char smraw[];
+    griddep_wait();  // the previous kernel has finished (and reset the counter block)
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *inb = base + X::F_IN, *xb = base + X::F_XB;
     float2 *T = reinterpret_cast<float2 *>(base + X::F_T);
@@ -208,6 +209,7 @@ k_yx_inv(const __grid_constant__ CUtensorMap tin, float2 *__restrict__ ring, con
     using X = XYWarp<E1>;
     constexpr int N = X::N, H = X::H, NX = X::NX, NY = X::NY, NN = N * N;
     extern __shared__ __align__(1024) unsigned char smraw[];
+    griddep_wait();  // the previous kernel has finished (and reset the counter block)
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *xb = base + X::I_XB;
     float2 *T = reinterpret_cast<float2 *>(base + X::I_T);

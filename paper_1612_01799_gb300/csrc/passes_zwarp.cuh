@@ -294,6 +294,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     }
     for (int i = threadIdx.x; i < E1 * 32; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
 
     auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
     auto issue_in = [&](int t) {
@@ -522,6 +523,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     }
     for (int i = threadIdx.x; i < E1 * 32; i += Y::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
     auto issue_in = [&](int t) {
         const int tx = t % ntx, zz = z0 + t / ntx;
         mbar_arrive_expect_tx(bar, (FWD ? 1 : 2) * N * 128);
@@ -696,6 +698,7 @@ k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restr
     float2 *T2 = reinterpret_cast<float2 *>(smraw + X::OFF_T2);
     xw_tables<N>(T, T2, tw);
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
     const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
     const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
     const int stride = gridDim.x * (X::NT / 16);
@@ -796,6 +799,7 @@ k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__re
     float2 *T2 = reinterpret_cast<float2 *>(smraw + X::OFF_T2);
     xw_tables<N>(T, T2, tw);
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
     const int lane = threadIdx.x & 31, hw = threadIdx.x >> 4, qq = lane & 15;
     const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
     const int stride = gridDim.x * (X::NT / 16);
@@ -838,6 +842,7 @@ k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__rest
     for (int i = threadIdx.x; i < 512; i += XWarp2::NT) T[i] = tw[2 * (i & 31) * (i >> 5)];
     for (int i = threadIdx.x; i <= N / 2; i += XWarp2::NT) T2[i] = tw[i];
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
     const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
     const ZwLane zl = zw_lane<16>(tw, smem_addr(xo), g, q, 2);
     const int stride = gridDim.x * XWarp2::NW;
@@ -912,6 +917,7 @@ k_x_warp2_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__r
     for (int i = threadIdx.x; i < 512; i += XWarp2::NT) T[i] = tw[2 * (i & 31) * (i >> 5)];
     for (int i = threadIdx.x; i <= N / 2; i += XWarp2::NT) T2[i] = tw[i];
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
     const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
     const ZwLane zl = zw_lane<16>(tw, smem_addr(xo), g, q, 2);
     const int stride = gridDim.x * XWarp2::NW;
@@ -1098,6 +1104,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     }
     for (int i = threadIdx.x; i < 1024; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
 
     auto ky_of = [&](int by) { return (by & 1) ? L - ((by + 1) >> 1) : (by >> 1); };
     auto issue_in = [&](int t) {
@@ -1282,6 +1289,7 @@ k_y_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     }
     for (int i = threadIdx.x; i < 1024; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
     __syncthreads();
+    griddep_wait();  // the previous pass has finished: its outputs are readable
 
     // Loads of tile t: forward, rows 0..511 into B; inverse, rows 0..511 into B (first)
     // and rows 512..1023 into the upper half of XO (second), on one barrier phase.

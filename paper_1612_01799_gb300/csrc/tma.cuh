@@ -77,6 +77,13 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
 
 namespace gsp {
 
+// Wait until the kernel launched before this one on the stream has completed and its memory
+// operations are visible.  Pass kernels are launched with programmatic dependent launch, so
+// their CTAs may start (and build their shared tables) while the previous pass finishes;
+// each calls this before its first access to memory that pass writes or reads.  A no-op
+// for a kernel launched without that attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Plain arrival (count 1) on an mbarrier.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
