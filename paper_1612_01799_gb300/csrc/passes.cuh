@@ -21,6 +21,7 @@
 // with packed FP32x2 arithmetic (type CV); the row passes and the FP64 path use one
 // complex value per slot.
 #pragma once
+#include <mutex>
 #include <type_traits>
 
 #include "fft_core.cuh"
@@ -393,23 +394,28 @@ static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
 template <class K> static int persistent_blocks(K kernel, int threads, size_t smem, int ntiles) {
     struct Entry {
         const void *fn;
-        int blocks;
+        int dev, blocks;
     };
     static Entry cache[64];
     static int n = 0;
+    static std::mutex mu;  // plans may launch from several host threads
     const void *fn = reinterpret_cast<const void *>(kernel);
-    int blocks = 0;
-    for (int i = 0; i < n; ++i)
-        if (cache[i].fn == fn) blocks = cache[i].blocks;
+    int dev = 0, blocks = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int i = 0; i < n; ++i)
+            if (cache[i].fn == fn && cache[i].dev == dev) blocks = cache[i].blocks;
+    }
     if (blocks == 0) {
-        int dev = 0, sms = 1, per_sm = 1;
-        cudaGetDevice(&dev);
+        int sms = 1, per_sm = 1;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         blocks = per_sm * (sms > 0 ? sms : 1);
-        if (n < 64) cache[n++] = Entry{fn, blocks};
+        std::lock_guard<std::mutex> lock(mu);
+        if (n < 64) cache[n++] = Entry{fn, dev, blocks};
     }
     return blocks < ntiles ? blocks : ntiles;
 }
