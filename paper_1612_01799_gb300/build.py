@@ -17,7 +17,7 @@ BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["capi.cpp", "setup.cpp", "passes_f32.cu", "passes_f64.cu",
            "passes_f32_a.cu", "passes_f32_b.cu", "passes_f32_c.cu",
            "passes_f64_a.cu", "passes_f64_b.cu", "passes_f64_c.cu",
-           "noalloc.cu", "reduce.cu", "sample.cu", "selector.cu", "selftest.cu"]
+           "noalloc.cu", "reduce.cu", "sample.cu", "selector.cu", "selftest.cu", "setup_device.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -283,7 +283,9 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     if (!gsp::n_supported(N)) return POISSON_ERR_UNSUPPORTED;
     poisson_plan p = new (std::nothrow) poisson_plan_s();
     if (!p) return POISSON_ERR_ALLOC;
-    int rc = gsp::build_host_tables(N, L, tol, p->ht);
+    // The Gaussian sum, delta, eps and the near-zone constants on the host; the per-axis
+    // table A_j(k) below on the device.
+    int rc = gsp::build_host_scalars(N, L, tol, p->ht);
     if (rc != POISSON_OK) {
         delete p;
         return rc;
@@ -309,10 +311,10 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     p->ws_bytes = w1_bytes + 2 * w2_bytes;  // for max_batch densities
     p->table_bytes = sym_bytes + tw_bytes + twc_bytes;
 
-    double *dA = nullptr, *dw = nullptr;
+    double *dA = nullptr, *dw = nullptr, *dtau = nullptr, *dgl = nullptr;
     auto fail = [&](cudaError_t err) {
-        if (dA) cudaFree(dA);
-        if (dw) cudaFree(dw);
+        for (double *b : {dA, dw, dtau, dgl})
+            if (b) cudaFree(b);
         free_plan(p);
         return map_cuda(err);
     };
@@ -363,11 +365,23 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
 
     // Symbol octant on the device, in FP64, from the per-axis factors.
     const int nterms = (int)p->ht.tau.size();
-    if ((e = cudaMalloc(&dA, p->ht.A.size() * sizeof(double))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&dw, p->ht.w.size() * sizeof(double))) != cudaSuccess) return fail(e);
-    if ((e = cudaMemcpy(dA, p->ht.A.data(), p->ht.A.size() * sizeof(double),
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
+    const size_t nA = (size_t)nterms * K;
+    if ((e = cudaMalloc(&dA, nA * sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&dtau, (size_t)nterms * sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&dgl, 32 * sizeof(double))) != cudaSuccess) return fail(e);
+    {
+        double gl[32];
+        gsp::gauss_legendre16(gl, gl + 16);
+        if ((e = cudaMemcpy(dgl, gl, sizeof gl, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    }
+    if ((e = cudaMemcpy(dtau, p->ht.tau.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
         return fail(e);
+    if ((e = gsp::launch_axis_table(dtau, dgl, nterms, N, dA, 0)) != cudaSuccess) return fail(e);
+    p->ht.A.resize(nA);  // the plan keeps the table for poisson_plan_axis_table
+    if ((e = cudaMemcpy(p->ht.A.data(), dA, nA * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMalloc(&dw, p->ht.w.size() * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(dw, p->ht.w.data(), p->ht.w.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
@@ -379,7 +393,9 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
     cudaFree(dA);
     cudaFree(dw);
-    dA = dw = nullptr;
+    cudaFree(dtau);
+    cudaFree(dgl);
+    dA = dw = dtau = dgl = nullptr;
     if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
     *out = p;
     return POISSON_OK;

@@ -51,10 +51,12 @@ bool build_gauss_sum(double eps, double delta, double r_max, std::vector<double>
     r[0] = delta;
     r[nfit - 1] = r_max;
     const double norm = 1.0 / (2.0 * std::pow(kPi, 1.5));
-    for (int m = 2; m < 4000; ++m) {
+    // The sum and its error for h = 2/m.
+    auto candidate = [&](int m, std::vector<double> &tt, std::vector<double> &ww) {
         const double hh = 2.0 / m;
         const long j0 = (long)std::floor(s_lo / hh), j1 = (long)std::ceil(s_hi / hh);
-        std::vector<double> tt, ww;
+        tt.clear();
+        ww.clear();
         for (long j = j0; j <= j1; ++j) {
             double s = (double)j * hh;
             tt.push_back(std::exp(s));
@@ -69,13 +71,26 @@ bool build_gauss_sum(double eps, double delta, double r_max, std::vector<double>
             }
             e = std::max(e, std::fabs(4.0 * kPi * r[i] * acc - 1.0));
         }
-        if (e <= eps) {
-            tau.swap(tt);
-            w.swap(ww);
-            h = hh;
-            err = e;
-            return true;
-        }
+        return e;
+    };
+    // The first m (smallest, i.e. the largest step) whose error is <= eps, found by
+    // evaluating batches of consecutive m on the host's threads: the same m as a scan.
+    const int batch = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    for (int m0 = 2; m0 < 4000; m0 += batch) {
+        const int nb = std::min(batch, 4000 - m0);
+        std::vector<std::vector<double>> tt(nb), ww(nb);
+        std::vector<double> e(nb);
+        std::vector<std::thread> th;
+        for (int b = 0; b < nb; ++b) th.emplace_back([&, b]() { e[b] = candidate(m0 + b, tt[b], ww[b]); });
+        for (auto &x : th) x.join();
+        for (int b = 0; b < nb; ++b)
+            if (e[b] <= eps) {
+                tau.swap(tt[b]);
+                w.swap(ww[b]);
+                h = 2.0 / (m0 + b);
+                err = e[b];
+                return true;
+            }
     }
     return false;
 }
@@ -140,7 +155,7 @@ void build_axis_table(const std::vector<double> &tau, int N, std::vector<double>
     const int order = 16;
     std::vector<double> gx, gw;
     gauss_legendre(order, gx, gw);
-    const int P = std::max(16, (N + 1) / 2);
+    const int P = axis_table_panels(N);
     const int T = P * order;
     std::vector<double> t(T), wt(T);
     for (int p = 0; p < P; ++p) {
@@ -228,7 +243,22 @@ void near_zone_constants(const std::vector<double> &tau, const std::vector<doubl
     C2 = (0.25 * std::pow(delta, 4) - 4.0 * kPi * s4) / 6.0;
 }
 
+int axis_table_panels(int N) { return std::max(16, (N + 1) / 2); }
+
+void gauss_legendre16(double *x, double *w) {
+    std::vector<double> gx, gw;
+    gauss_legendre(16, gx, gw);
+    for (int i = 0; i < 16; ++i) x[i] = gx[i], w[i] = gw[i];
+}
+
 int build_host_tables(int N, double L, double tol, HostTables &o) {
+    const int rc = build_host_scalars(N, L, tol, o);
+    if (rc != POISSON_OK) return rc;
+    build_axis_table(o.tau, N, o.A);
+    return POISSON_OK;
+}
+
+int build_host_scalars(int N, double L, double tol, HostTables &o) {
     if (N < 4 || N > 1024 || (N & 1) || !(L > 0.0) || !(tol > 0.0) || !std::isfinite(L) ||
         !std::isfinite(tol))
         return POISSON_ERR_ARG;
@@ -242,7 +272,6 @@ int build_host_tables(int N, double L, double tol, HostTables &o) {
     o.r_max = 2.0 * std::sqrt(3.0);
     if (!build_gauss_sum(o.eps, o.delta, o.r_max, o.tau, o.w, o.h, o.gs_err))
         return POISSON_ERR_NUMERIC;
-    build_axis_table(o.tau, N, o.A);
     near_zone_constants(o.tau, o.w, o.delta, o.C0, o.C2);
     return POISSON_OK;
 }

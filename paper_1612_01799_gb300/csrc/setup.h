@@ -34,6 +34,12 @@ bool build_gauss_sum(double eps, double delta, double r_max, std::vector<double>
 // A[j*(N+1)+k] = 2 int_0^2 exp(-tau_j^2 t^2) cos(pi k t / 2) dt, k = 0..N.
 void build_axis_table(const std::vector<double> &tau, int N, std::vector<double> &A);
 
+// Panels of the composite Gauss-Legendre rule of the axis table: max(16, (N + 1) / 2).
+int axis_table_panels(int N);
+
+// The 16-point Gauss-Legendre nodes x[16] and weights w[16] on [-1, 1].
+void gauss_legendre16(double *x, double *w);
+
 // C0 and C2 of I_delta = C0 rho + C2 Laplace(rho).
 void near_zone_constants(const std::vector<double> &tau, const std::vector<double> &w,
                          double delta, double &C0, double &C2);
@@ -41,6 +47,10 @@ void near_zone_constants(const std::vector<double> &tau, const std::vector<doubl
 // Everything above for the cube [-L, L]^3 with N points per axis.  Returns 0 or a
 // POISSON_ERR_* code.
 int build_host_tables(int N, double L, double tol, HostTables &out);
+
+// The same without the axis table (out.A left empty), for a setup that builds the table
+// on the device.
+int build_host_scalars(int N, double L, double tol, HostTables &out);
 
 // tw[e] = exp(-2 pi i e / n), e in [0, n), as (re, im) pairs, accurate to FP64 rounding.
 void twiddles(int n, std::vector<double> &re_im);

@@ -129,6 +129,11 @@ cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s);
 // (the test hook of poisson_selftest_wait).
 cudaError_t launch_wait_selftest(const DevicePlan &p, long long polls, cudaStream_t s);
 
+// The per-axis factors A_j(k), k = 0..N, of the S Gaussian-sum terms dtau into dA (S x (N+1),
+// FP64, on the device) by the host setup's rule; dgl: the 16-point Gauss-Legendre nodes
+// then weights.
+cudaError_t launch_axis_table(const double *dtau, const double *dgl, int S, int N, double *dA, cudaStream_t s);
+
 // Fill p.sym from the per-axis factors (FP64, on the device):
 // sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
