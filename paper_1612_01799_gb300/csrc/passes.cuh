@@ -341,21 +341,30 @@ template <typename Real>
 __global__ void k_symbol_table(Real *__restrict__ sym, const double *__restrict__ A,
                                const double *__restrict__ w, int nterms, int N, int Ps, double C0,
                                double C2, double scale) {
+    // Block (b, c) with b <= c computes, for every a <= b, the entry at (kx, ky, kz) =
+    // (a, b, c) and writes it to all six permutations: the symbol is symmetric in its
+    // three indices, so each value is summed once (about a sixth of the terms) and the
+    // table is exactly symmetric.  Entries kz >= ky >= kx keep this sum order:
+    // (w_j A_j(ky) A_j(kz)) A_j(kx).
     extern __shared__ double cj[];
-    const int ky = blockIdx.x, kz = blockIdx.y, K = N + 1;
+    const int b = blockIdx.x, c = blockIdx.y, K = N + 1;
+    if (b > c) return;
     for (int j = threadIdx.x; j < nterms; j += blockDim.x)
-        cj[j] = w[j] * A[(long long)j * K + ky] * A[(long long)j * K + kz];
+        cj[j] = w[j] * A[(long long)j * K + b] * A[(long long)j * K + c];
     __syncthreads();
     const double hp2 = 0.25 * 3.141592653589793238462643383279502884 * 3.141592653589793238462643383279502884;
-    for (int kx = threadIdx.x; kx < Ps; kx += blockDim.x) {
-        double g = 0.0;
-        if (kx < K) {
-            double s = 0.0;
-            for (int j = 0; j < nterms; ++j) s += cj[j] * A[(long long)j * K + kx];
-            const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
-            g = scale * (s + C0 - C2 * hp2 * k2);
-        }
-        sym[((long long)kz * K + ky) * Ps + kx] = (Real)g;
+    for (int a = threadIdx.x; a <= b; a += blockDim.x) {
+        double sum = 0.0;
+        for (int j = 0; j < nterms; ++j) sum += cj[j] * A[(long long)j * K + a];
+        const double k2 = (double)a * a + (double)b * b + (double)c * c;
+        const Real g = (Real)(scale * (sum + C0 - C2 * hp2 * k2));
+        auto put = [&](int z, int y, int x) { sym[((long long)z * K + y) * Ps + x] = g; };
+        put(c, b, a);
+        put(c, a, b);
+        put(b, c, a);
+        put(b, a, c);
+        put(a, c, b);
+        put(a, b, c);
     }
 }
 
@@ -949,6 +958,8 @@ template <typename Real>
 cudaError_t symbol_table(const DevicePlan &p, const double *dA, const double *dw, int nterms,
                          double C0, double C2, double scale, cudaStream_t s) {
     const int K = p.N + 1;
+    // Padding columns kx > N hold zeros (the kernel writes the octant entries only).
+    GSP_CHECK(cudaMemsetAsync(p.sym, 0, (size_t)K * K * p.Ps * sizeof(Real), s));
     k_symbol_table<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
         static_cast<Real *>(p.sym), dA, dw, nterms, p.N, p.Ps, C0, C2, scale);
     return cudaGetLastError();

@@ -38,9 +38,9 @@
 // Shared memory (one CTA = one tile of 16 columns x 1 ky x the N input rows, 8 warps):
 //   B   32 KB: the TMA input tile (256 rows x 128 B, 128-byte swizzle), then the tile's
 //       symbol lines (boxes of 128 kz x 16 kx, kz innermost: the octant table is
-//       symmetric in (kx, ky, kz) up to the FP64 rounding of its tabulated sums, so read
-//       with its innermost index as kz each column's kz values lie contiguous and the
-//       lanes read consecutive floats), then the next tile's input;
+//       symmetric in (kx, ky, kz), so read with its innermost index as kz each column's kz
+//       values lie contiguous and the lanes read consecutive floats), then the next
+//       tile's input;
 //   XO  64 KB: 512 rows of 128 B; warp g owns the 16-byte chunk g ^ (row & 7) of every row,
 //       for its exchange slots (all 512 rows) and for its outputs (rows z < 256), so the
 //       first 32 KB is the output tile in the TMA store's 128-byte swizzle;
@@ -995,9 +995,8 @@ namespace gsp {
 // A CTA of 8 warps owns a tile of 8 consecutive columns kx at one ky.  Shared memory:
 //   B   32 KB: the input tile (512 z-rows x 64 B, two TMA boxes of 256 rows, 64-byte
 //       swizzle), then the tile's symbol lines (three boxes of 256 kz x 8 kx: the octant
-//       table is symmetric in (kx, ky, kz) up to the FP64 rounding of its tabulated sums,
-//       so with kz as its innermost index each column's kz values lie contiguous), then the
-//       next tile's input;
+//       table is symmetric in (kx, ky, kz), so with kz as its innermost index each column's
+//       kz values lie contiguous), then the next tile's input;
 //   XO  64 KB: the warps' 8 KB exchange regions; the first 32 KB is also the output tile
 //       in the TMA store's 64-byte swizzle, written after a block barrier that ends every
 //       warp's exchange reads;
