@@ -105,19 +105,21 @@ def test_config2_full_size(torch_cuda, plan_cache, dtype):
     assert rel_l2(u, uo) <= TOL[dtype]
 
 
-def test_config3_full_size_sampled(torch_cuda):
-    """Bump plus 8 Gaussians, [-6,6]^3, N = 512 (padded 1024^3), FP32: sampled output lines
-    against the oracle's real-space evaluation of the same discrete convolution."""
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_config3_full_size_sampled(torch_cuda, dtype):
+    """Bump plus 8 Gaussians, [-6,6]^3, N = 512 (padded 1024^3), FP32 and FP64: sampled
+    output lines against the oracle's real-space evaluation of the same discrete
+    convolution."""
     from oracle import gtensor
     w = D.config_bump8()
     rho = w.sample()
-    tol = 1e-6
-    u = gpu_solve(torch_cuda, 512, 6.0, tol, "f32", rho)
+    tol = 1e-6 if dtype == "f32" else 1e-12
+    u = gpu_solve(torch_cuda, 512, 6.0, tol, dtype, rho)
     p = gtensor.make_plan(512, 6.0, tol)
     lines = [(0, 0), (255, 256), (256, 100), (511, 511), (100, 400), (256, 255)]
     ref = direct.sample_lines(rho, p, lines)
     got = np.stack([u[z, y] for z, y in lines])
-    assert rel_l2(got, ref) <= TOL["f32"]
+    assert rel_l2(got, ref) <= TOL[dtype]
 
 
 def test_solve_variants_agree(torch_cuda):
