@@ -314,29 +314,36 @@ def run_batched(torch, dev, steps, warmup, seed=4):
 
 
 def run_large(torch, dev, flush, steps, warmup, peak, N=512):
-    """Config 3, the large single solve (padded 1024^3), FP32: per-pass times against the
-    HBM roofline.  Reported next to the headline, not as it."""
+    """Config 3, the large single solve (padded 1024^3), FP32 with FP64 beside it: per-pass
+    times against the HBM roofline.  Reported next to the headline, not as it."""
     import numpy as np
     from paper_1612_01799_gb300 import Plan
     from paper_1612_01799_gb300 import densities as D
     wl = D.config_bump8(N=N)
-    rho = torch.from_numpy(wl.sample(np.float32)).to(dev)
-    with Plan(N, wl.L, TOL32, "f32") as plan:
-        out = torch.empty_like(rho)
-        totals, passes = time_solves(torch, plan, rho, out, steps, warmup, flush)
-        plan.last_status()
-        forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form],
-                 "xy": XY_FORMS[plan.xy_form]}
-        xyform = plan.xy_form
-    ms = statistics.mean(totals)
-    per = [statistics.mean(p[i] for p in passes) for i in range(5)]
-    rows = pass_table(N, 4, per, xyform, [None] * 5)
-    return {"value": N ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "dtype": "f32",
-            "passes": [{"pass": n, "ms": t, "GB_s": b / (t * 1e-3) / 1e9,
-                        "frac": b / (t * 1e-3) / 1e9 / peak} for n, _, t, b in rows],
-            "forms": forms,
-            "workload": "config_large: (1-r^2/16)^4 on r<4 plus 8 Gaussians (widths U[0.3,1], seed 3), box "
-                        "[-6,6]^3, N=512 per axis, padded 1024^3, FP32, L2 flushed between steps"}
+    sample = wl.sample()
+
+    def one(dtype, tol, nsteps):
+        rho = torch.from_numpy(sample.astype(np.float32 if dtype == "f32" else np.float64)).to(dev)
+        with Plan(N, wl.L, tol, dtype) as plan:
+            out = torch.empty_like(rho)
+            totals, passes = time_solves(torch, plan, rho, out, nsteps, warmup, flush)
+            plan.last_status()
+            forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form],
+                     "xy": XY_FORMS[plan.xy_form]}
+            xyform = plan.xy_form
+        ms = statistics.mean(totals)
+        per = [statistics.mean(p[i] for p in passes) for i in range(5)]
+        rows = pass_table(N, 4 if dtype == "f32" else 8, per, xyform, [None] * 5)
+        return {"value": N ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": nsteps, "dtype": dtype,
+                "passes": [{"pass": n, "ms": t, "GB_s": b / (t * 1e-3) / 1e9,
+                            "frac": b / (t * 1e-3) / 1e9 / peak} for n, _, t, b in rows],
+                "forms": forms}
+
+    r = one("f32", TOL32, steps)
+    r["f64"] = one("f64", TOL64, 3)
+    r["workload"] = ("config_large: (1-r^2/16)^4 on r<4 plus 8 Gaussians (widths U[0.3,1], seed 3), box "
+                     "[-6,6]^3, N=512 per axis, padded 1024^3, FP32 (FP64 beside it), L2 flushed between steps")
+    return r
 
 
 def run_selector(n_train=384, n_test=128, epochs=3000):
