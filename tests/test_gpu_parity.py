@@ -208,3 +208,39 @@ def test_max_size_closed_form(torch_cuda, dtype):
     x = D.axis(N, L)
     ref = np.stack([exact.gaussian_iso(np.sqrt(x ** 2 + x[y] ** 2 + x[z] ** 2), 1.0) for z, y in lines])
     assert rel_l2(got, ref) <= (1e-5 if dtype == "f32" else 1e-10)
+
+
+@pytest.mark.parametrize("N,dtype,forms", [(64, "f64", None), (64, "f32", (2, 1, 1)), (256, "f32", (2, 1, 1)),
+                                           (256, "f32", (0, 0, 0)), (512, "f32", (2, 1, 1))])
+def test_degenerate_inputs_and_invariants(torch_cuda, N, dtype, forms):
+    """A zero density gives exactly zero; an empty batch does nothing; the solve is linear
+    (to rounding); and the same sample array on a box twice as large gives four times the
+    potential to the method's accuracy (the scaled problem differs only in delta, which
+    follows the box, and so in the Gaussian-sum fit; the result carries lambda^2)."""
+    import ctypes
+    torch = torch_cuda
+    from paper_1612_01799_gb300 import Plan, _lib, solve_batched
+    lib = _lib.load()
+    L = 10.0
+    tol = 1e-6 if dtype == "f32" else 1e-12
+    eps = 2e-6 if dtype == "f32" else 1e-13      # rounding of one solve
+    eps_method = 1e-5 if dtype == "f32" else 1e-11
+    r1 = D.config_aniso4(N=N, seed=91).gaussians.sample(N, L)
+    r2 = D.config_aniso4(N=N, seed=92).gaussians.sample(N, L)
+    with Plan(N, L, tol, dtype) as p, Plan(N, 2 * L, tol, dtype) as q:
+        if forms:
+            p.z_form, p.y_form, p.x_form = forms
+            q.z_form, q.y_form, q.x_form = forms
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=p.np_dtype)).cuda()
+        z = p.solve(t(np.zeros((N, N, N))))
+        assert int(torch.count_nonzero(z)) == 0
+        assert lib.poisson_solve_batched(0, None, None, None, None) == 0
+        assert solve_batched([], [], []) in (None, [], ())
+        u1, u2 = p.solve(t(r1)), p.solve(t(r2))
+        u12 = p.solve(t(2.0 * r1 - 3.0 * r2))
+        comb = 2.0 * u1.double() - 3.0 * u2.double()
+        assert float((u12.double() - comb).norm() / comb.norm()) <= 10 * eps
+        uq = q.solve(t(r1))
+        assert float((uq.double() - 4.0 * u1.double()).norm() / (4.0 * u1.double()).norm()) <= eps_method
+        p.last_status()
+        q.last_status()
