@@ -503,6 +503,13 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
     cudaEvent_t *ev_in = p->slab_ev, *ev_out = p->slab_ev + kSlabs, start = p->slab_ev[2 * kSlabs];
     const int nzs = N / kSlabs;  // planes per slab
     const size_t sb = (size_t)nzs * N * N * p->elem;
+    // On an error part of the pipeline may already be queued: wait for both streams so
+    // that no copy into or out of the staging buffers outlives the call.
+    auto fail = [&](cudaError_t err) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(s);
+        return map_cuda(err);
+    };
     // The copies wait for the work already on `stream` (an earlier solve reading the
     // staging buffers).
     if ((e = cudaEventRecord(start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, start, 0)) != cudaSuccess)
@@ -513,9 +520,9 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
         if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[k], 0);
         if (e == cudaSuccess) e = gsp::launch_xy_slab(p->dp, p->stage_in, p->stage_out, k * nzs, nzs, s, true);
-        if (e != cudaSuccess) return map_cuda(e);
+        if (e != cudaSuccess) return fail(e);
     }
-    if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr, nullptr, 3)) != cudaSuccess) return map_cuda(e);
+    if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr, nullptr, 3)) != cudaSuccess) return fail(e);
     for (int k = 0; k < kSlabs; ++k) {
         e = gsp::launch_xy_slab(p->dp, p->stage_in, p->stage_out, k * nzs, nzs, s, false);
         if (e == cudaSuccess) e = cudaEventRecord(ev_out[k], s);
@@ -523,13 +530,13 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(static_cast<char *>(u_h) + k * sb, static_cast<char *>(p->stage_out) + k * sb, sb,
                                 cudaMemcpyDeviceToHost, cs);
-        if (e != cudaSuccess) return map_cuda(e);
+        if (e != cudaSuccess) return fail(e);
     }
     // `stream` waits for the last copy, so that work issued after the call is ordered
     // after it, then the call returns once everything has finished.
     if ((e = cudaEventRecord(start, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, start, 0)) != cudaSuccess)
-        return map_cuda(e);
-    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return map_cuda(e);
+        return fail(e);
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return fail(e);
     return map_cuda(cudaStreamSynchronize(s));
 }
 
