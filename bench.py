@@ -42,7 +42,8 @@ KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_in
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; a
 # source change makes the figure stale and it is reported as null.
-NCU_TRAFFIC = {("b8ef0809a9b45413", "k_z_warp", 256): 368998400 + 234200320}
+NCU_TRAFFIC = {("7c983fbf0ef7272a", "k_z_warp", 256): 368725504 + 233974016,
+               ("7c983fbf0ef7272a", "k_z_w512", 512): 3154690048 + 2136481408}
 
 
 def kernel_source_hash():
@@ -442,8 +443,10 @@ def run_ours(args):
         r32 = results["f32"]
         names = list(KERNEL_NAMES)
         names[2] = Z_KERNELS[r32["z_form"]]
+        if r32["z_form"] == 2 and N == 512:
+            names[2] = "k_z_w512"
         if r32["y_form"] == 1:
-            names[1], names[3] = "k_y_warp<fwd>", "k_y_warp<inv>"
+            names[1], names[3] = ("k_y_w512<fwd>", "k_y_w512<inv>") if N == 512 else ("k_y_warp<fwd>", "k_y_warp<inv>")
         if r32["x_form"] == 1:
             names[0], names[4] = "k_x_warp_fwd", "k_x_warp_inv"
         rows32 = pass_table(N, 4, r32["per_pass"], r32["xy_form"], names)

@@ -730,15 +730,16 @@ inline TensorMapEncodeFn tensor_map_encoder() {
 inline cudaError_t encode_3d(CUtensorMap *m, CUtensorMapDataType dt, void *base, cuuint64_t d0,
                              cuuint64_t d1, cuuint64_t d2, cuuint64_t s1, cuuint64_t s2, cuuint32_t b0,
                              cuuint32_t b1, cuuint32_t b2,
-                             CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE) {
+                             CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CUtensorMapL2promotion l2 = CU_TENSOR_MAP_L2_PROMOTION_L2_256B) {
     TensorMapEncodeFn enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[3] = {d0, d1, d2};
     const cuuint64_t strides[2] = {s1, s2};
     const cuuint32_t box[3] = {b0, b1, b2};
     const cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, l2,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -798,8 +799,9 @@ cudaError_t encode_n(DevicePlan &p) {
         // 8 columns x 1 ky x 256 z-rows of w2 and w3 (64-byte swizzle); the symbol octant
         // read with its innermost index as kz (the table is symmetric in its three indices):
         // 256 kz x 1 ky x 8 kx per box.
+        // Rows of a box are 64 bytes: promote L2 fills to 64 B, not 256 B.
         GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZW512::TC, 1, N / 2,
-                            CU_TENSOR_MAP_SWIZZLE_64B));
+                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_64B));
         GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZW512::TC, 1, N / 2,
                             CU_TENSOR_MAP_SWIZZLE_64B));
         GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,
