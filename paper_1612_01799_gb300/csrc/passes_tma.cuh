@@ -116,8 +116,11 @@ __device__ __forceinline__ CD scale_sym_sm(CD x, const double *s) { return cscal
 // Blocks per SM requested from the compiler: a register budget of 64 per thread for E <= 8
 // values per thread, 128 otherwise.
 template <int T, int E> __host__ __device__ constexpr int min_blocks_for() {
+    // Bounded by the SM's 65536 registers, 2048 threads and 32 resident blocks.
     const int regs = E <= 8 ? 64 : 128;
-    return 65536 / (T * regs) > 0 ? 65536 / (T * regs) : 1;
+    const int by_regs = 65536 / (T * regs), by_threads = 2048 / T;
+    const int b = by_regs < by_threads ? by_regs : by_threads;
+    return b > 32 ? 32 : b > 0 ? b : 1;
 }
 
 // ---- K2 / K4 -----------------------------------------------------------------------------
@@ -135,9 +138,9 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
     using Lay = TmaLayout<Real, L, KIND>;
     using Rs = typename FftCfg<L>::Rs;
     constexpr bool FWD = KIND == 0;
-    constexpr int E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P, R0 = FirstRadix<Rs>::v;
+    constexpr int E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, R0 = FirstRadix<Rs>::v;
     constexpr int TCU = Lay::ROWB / 8;  // box width in 8-byte units
-    extern __shared__ __align__(128) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
     unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
     unsigned char *inb = base;
@@ -212,7 +215,7 @@ k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ 
     constexpr int N = L / 2, E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P;
     constexpr int RL = LastRadix<Rs>::v, R0 = FirstRadix<Rs>::v;
     constexpr int TCU = Lay::ROWB / 8;
-    extern __shared__ __align__(128) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
     unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
     unsigned char *inb = base;
@@ -385,7 +388,7 @@ k_z_split_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ C
     constexpr int NT = zsplit_threads<Real, L>();
     static_assert(R0 % 2 == 0, "the A + B exchange splits the first radix's outputs in halves");
     static_assert(NT <= 1024, "threads of one CTA");
-    extern __shared__ __align__(128) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
     unsigned char *base = smraw + ((128 - (smem_addr(smraw) & 127)) & 127);
     unsigned char *inb = base;

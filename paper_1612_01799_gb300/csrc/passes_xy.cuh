@@ -118,7 +118,7 @@ k_xy_fwd(const PtrArray rho, float2 *__restrict__ ring, const __grid_constant__ 
          int *__restrict__ sync, int *__restrict__ status) {
     using X = XYWarp<E1>;
     constexpr int N = X::N, H = X::H, NX = X::NX, NY = X::NY;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();  // the previous kernel has finished (and reset the counter block)
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *inb = base + X::F_IN, *xb = base + X::F_XB;
@@ -208,7 +208,7 @@ k_yx_inv(const __grid_constant__ CUtensorMap tin, float2 *__restrict__ ring, con
          int *__restrict__ status) {
     using X = XYWarp<E1>;
     constexpr int N = X::N, H = X::H, NX = X::NX, NY = X::NY, NN = N * N;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();  // the previous kernel has finished (and reset the counter block)
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *xb = base + X::I_XB;

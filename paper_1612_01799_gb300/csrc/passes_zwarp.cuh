@@ -276,14 +276,14 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
          int ncols, int *__restrict__ status, double *__restrict__ tail) {
     using Z = ZWarp<E1>;
     constexpr int L = Z::L, N = Z::N, NW = Z::NW, H = Z::H;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *Bb = base + Z::OFF_B;
     unsigned char *xo = base + Z::OFF_XO;
     float2 *T = reinterpret_cast<float2 *>(base + Z::OFF_T);
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + Z::OFF_BAR);  // input, symbol, XO free
     int *cnt = reinterpret_cast<int *>(bar + 3);                       // input, symbol, output
-    const int g = threadIdx.x >> 5, q = threadIdx.x & 31, s = q >> 4, qp = q & 15;
+    const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -507,7 +507,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
          const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status, int z0) {
     using Y = YWarp<E1>;
     constexpr int NW = Y::NW, N = Y::N, H = Y::H;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *inb = base + (FWD ? Y::F_IN : Y::I_XB);
     unsigned char *xb = base + (FWD ? Y::F_XB : Y::I_XB);
@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(XWarp2::NT, 2)
 k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restrict__ tw, int npairs, int Px) {
     static_assert(N == XWarp2::N, "one warp per row pair: 512 = 16 x 2 x 16");
     constexpr long long NN = (long long)N * N;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *xo = base + XWarp2::OFF_XO;
     float2 *T = reinterpret_cast<float2 *>(base + XWarp2::OFF_T);
@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(XWarp2::NT, 2)
 k_x_warp2_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__restrict__ tw, int npairs, int Px) {
     static_assert(N == XWarp2::N, "one warp per row pair: 512 = 16 x 2 x 16");
     constexpr long long NN = (long long)N * N;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *xo = base + XWarp2::OFF_XO;
     float2 *T = reinterpret_cast<float2 *>(base + XWarp2::OFF_T);
@@ -1085,7 +1085,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
          int ncols, int *__restrict__ status, double *__restrict__ tail) {
     using Z = ZW512;
     constexpr int L = Z::L, N = Z::N, NW = Z::NW;
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *Bb = base + Z::OFF_B;
     unsigned char *xo = base + Z::OFF_XO;
@@ -1270,8 +1270,8 @@ __global__ void __launch_bounds__(ZW512::NT, 2)
 k_y_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
          const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status, int z0) {
     using Z = ZW512;
-    constexpr int N = Z::N, NW = Z::NW, HALF = 16384;  // one 256-row box of 64-byte rows
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    constexpr int NW = Z::NW, HALF = 16384;  // one 256-row box of 64-byte rows
+    extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *Bb = base + Z::OFF_B;
     unsigned char *xo = base + Z::OFF_XO;
