@@ -210,6 +210,16 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       ring of plane slots that stays in L2, so the x spectrum never goes to device
  *       memory; the bodies are the warp forms; POISSON_F32, N = 64, 96, 128, 160, 192,
  *       256).
+ *   POISSON_KNOB_CORRECTION  where the near-field correction I_delta = C0 rho +
+ *       C2 Laplace(rho) of Sec. 2 enters: 0 (the default) = in the symbol at every padded
+ *       frequency, C0 - C2 |kappa|^2 (the Laplacian of the 2N-periodic series);
+ *       1 = the paper's order, Laplace(rho) of the N-periodic series from an unpadded N^3
+ *       transform pair; the plan gets it from the same padded transforms by placing
+ *       8 (C0 - C2 |kappa|^2) at the frequencies whose three indices are all even (the
+ *       N-point DFT is the padded DFT at even frequencies) and nothing elsewhere.  The two
+ *       differ by terms of order C2 |kappa|^2 at high frequencies.  Setting it recomputes
+ *       the plan's symbol table on its device (a temporary device allocation and a
+ *       synchronisation) and is not timed; every dtype and N, every kernel form.
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that
@@ -220,6 +230,7 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
 #define POISSON_KNOB_Y_FORM 1
 #define POISSON_KNOB_X_FORM 2
 #define POISSON_KNOB_XY_FORM 3
+#define POISSON_KNOB_CORRECTION 4
 int poisson_plan_get_knob(poisson_plan p, int knob, int *value);
 int poisson_plan_set_knob(poisson_plan p, int knob, int value);
 

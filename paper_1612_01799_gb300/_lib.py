@@ -68,6 +68,7 @@ KNOB_Z_FORM = 0
 KNOB_Y_FORM = 1
 KNOB_X_FORM = 2
 KNOB_XY_FORM = 3
+KNOB_CORRECTION = 4
 
 
 def load():

@@ -169,6 +169,23 @@ class Plan:
     def xy_form(self, value):
         _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_XY_FORM, int(value)), "poisson_plan_set_knob")
 
+    @property
+    def correction(self):
+        """Where the near-field correction enters: "fused" (C0 - C2 |kappa|^2 at every
+        padded frequency) or "literal" (C0 rho + C2 Laplace(rho) of the N-periodic series,
+        the paper's unpadded transform pair, placed at the all-even padded frequencies)."""
+        v = ctypes.c_int()
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_CORRECTION, ctypes.byref(v)),
+                   "poisson_plan_get_knob")
+        return ("fused", "literal")[v.value]
+
+    @correction.setter
+    def correction(self, value):
+        code = {"fused": 0, "literal": 1}.get(value)
+        if code is None:
+            raise ValueError("correction must be 'fused' or 'literal'")
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_CORRECTION, code), "poisson_plan_set_knob")
+
     def gauss_sum(self):
         n = self.info()["n_terms"]
         tau, w = np.empty(n), np.empty(n)

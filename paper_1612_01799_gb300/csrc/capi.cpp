@@ -23,9 +23,9 @@ cudaError_t launch_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0
     return p.dtype == POISSON_F32 ? xy_slab_f32(p, rho, u, z0, nz, s, fwd) : xy_slab_f64(p, rho, u, z0, nz, s, fwd);
 }
 cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *, int, double,
-                             double, double, cudaStream_t);
+                             double, double, int, cudaStream_t);
 cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
-                             double, double, cudaStream_t);
+                             double, double, int, cudaStream_t);
 cudaError_t encode_maps_f32(DevicePlan &);
 cudaError_t encode_maps_f64(DevicePlan &);
 cudaError_t z_pass_f32(const DevicePlan &, cudaStream_t);
@@ -98,9 +98,10 @@ static cudaError_t fork_pool(int dev, ForkPool **out) {
 }
 
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
-                                int nterms, double C0, double C2, double scale, cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? symbol_table_f32(p, dA, dw, nterms, C0, C2, scale, s)
-                                  : symbol_table_f64(p, dA, dw, nterms, C0, C2, scale, s);
+                                int nterms, double C0, double C2, double scale, int literal,
+                                cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? symbol_table_f32(p, dA, dw, nterms, C0, C2, scale, literal, s)
+                                  : symbol_table_f64(p, dA, dw, nterms, C0, C2, scale, literal, s);
 }
 
 // ---- autotuning of kernel variants --------------------------------------------------------
@@ -207,6 +208,7 @@ struct poisson_plan_s {
     gsp::HostTables ht;
     gsp::DevicePlan dp;
     int device = 0;
+    int correction = 0;      // POISSON_KNOB_CORRECTION: 0 fused, 1 the unpadded transform pair
     size_t elem = 0;         // bytes per real value
     size_t ws_bytes = 0;
     size_t table_bytes = 0;
@@ -387,7 +389,7 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
         return fail(e);
     const double M = 2.0 * N;
     const double scale = p->ht.lambda * p->ht.lambda / (M * M * M);
-    if ((e = gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0)) !=
+    if ((e = gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0, 0)) !=
         cudaSuccess)
         return fail(e);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
@@ -407,12 +409,46 @@ extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
     else if (knob == POISSON_KNOB_Y_FORM) *value = p->dp.yform;
     else if (knob == POISSON_KNOB_X_FORM) *value = p->dp.xform;
     else if (knob == POISSON_KNOB_XY_FORM) *value = p->dp.xyform;
+    else if (knob == POISSON_KNOB_CORRECTION) *value = p->correction;
     else return POISSON_ERR_ARG;
     return POISSON_OK;
 }
 
+// Recompute the plan's symbol octant from its kept per-axis factors with the correction
+// placed as `literal` says (0 fused, 1 the unpadded transform pair), on the plan's device.
+static int rebuild_symbol(poisson_plan p, int literal) {
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return map_cuda(e);
+    if ((e = cudaSetDevice(p->device)) != cudaSuccess) return map_cuda(e);
+    const int nterms = (int)p->ht.tau.size(), K = p->dp.N + 1;
+    double *dA = nullptr, *dw = nullptr;
+    e = cudaMalloc(&dA, (size_t)nterms * K * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dw, (size_t)nterms * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dA, p->ht.A.data(), (size_t)nterms * K * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dw, p->ht.w.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice);
+    const double M = 2.0 * p->dp.N;
+    if (e == cudaSuccess)
+        e = gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2,
+                                     p->ht.lambda * p->ht.lambda / (M * M * M), literal, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(dA);
+    cudaFree(dw);
+    cudaSetDevice(prev);
+    return map_cuda(e);
+}
+
 extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     if (!p) return POISSON_ERR_ARG;
+    if (knob == POISSON_KNOB_CORRECTION) {
+        if (value != 0 && value != 1) return POISSON_ERR_ARG;
+        if (value == p->correction) return POISSON_OK;
+        const int rc = rebuild_symbol(p, value);
+        if (rc == POISSON_OK) p->correction = value;
+        return rc;
+    }
     int forms, *field;
     if (knob == POISSON_KNOB_Z_FORM) {
         forms = gsp::z_forms(p->dp.N, p->dp.dtype);

@@ -281,7 +281,7 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
     }
     if (e) return map_cuda(e);
     const double M = 2.0 * N;
-    if ((e = gsp::launch_symbol_table(dp, dA, dw, S, C0, C2, L * L / (M * M * M), s)))
+    if ((e = gsp::launch_symbol_table(dp, dA, dw, S, C0, C2, L * L / (M * M * M), 0, s)))
         return map_cuda(e);
     // The host arrays are reused by the next setup: wait for the copies and the table.
     if ((e = cudaStreamSynchronize(s))) return map_cuda(e);

@@ -337,10 +337,19 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
 // ---- symbol octant (setup, FP64 arithmetic) ---------------------------------------------
 // sym[(kz * (N+1) + ky) * Ps + kx] for kx, ky, kz <= N; the pitch Ps (a multiple of 4)
 // keeps the two-column loads of the FP32 z pass aligned.
+//
+// The near-field correction I_delta = C0 rho + C2 Laplace(rho) (Sec. 2) is placed in one of
+// two ways.  literal = 0 (fused): C0 - C2 |kappa|^2 at every padded frequency, the
+// Laplacian of the 2N-periodic series.  literal = 1 (the paper's order, where Laplace(rho)
+// comes from an unpadded N^3 transform pair): the N-point DFT of rho is the padded DFT at
+// even frequencies and kappa of N-point frequency k equals kappa of padded frequency 2k,
+// so 8 (C0 - C2 |kappa|^2) at frequencies whose three indices are all even, 0 elsewhere,
+// gives C0 rho + C2 Laplace_N(rho) on the kept N^3 points after the padded inverse (the 8
+// turns its 1 / (2N)^3 into the unpadded 1 / N^3).
 template <typename Real>
 __global__ void k_symbol_table(Real *__restrict__ sym, const double *__restrict__ A,
                                const double *__restrict__ w, int nterms, int N, int Ps, double C0,
-                               double C2, double scale) {
+                               double C2, double scale, int literal) {
     // Block (b, c) with b <= c computes, for every a <= b, the entry at (kx, ky, kz) =
     // (a, b, c) and writes it to all six permutations: the symbol is symmetric in its
     // three indices, so each value is summed once (about a sixth of the terms) and the
@@ -357,7 +366,10 @@ __global__ void k_symbol_table(Real *__restrict__ sym, const double *__restrict_
         double sum = 0.0;
         for (int j = 0; j < nterms; ++j) sum += cj[j] * A[(long long)j * K + a];
         const double k2 = (double)a * a + (double)b * b + (double)c * c;
-        const Real g = (Real)(scale * (sum + C0 - C2 * hp2 * k2));
+        double v;
+        if (!literal) v = sum + C0 - C2 * hp2 * k2;
+        else v = ((a | b | c) & 1) ? sum : sum + 8.0 * (C0 - C2 * hp2 * k2);
+        const Real g = (Real)(scale * v);
         auto put = [&](int z, int y, int x) { sym[((long long)z * K + y) * Ps + x] = g; };
         put(c, b, a);
         put(c, a, b);
@@ -958,12 +970,12 @@ cudaError_t encode_dispatch(DevicePlan &p) {
 
 template <typename Real>
 cudaError_t symbol_table(const DevicePlan &p, const double *dA, const double *dw, int nterms,
-                         double C0, double C2, double scale, cudaStream_t s) {
+                         double C0, double C2, double scale, int literal, cudaStream_t s) {
     const int K = p.N + 1;
     // Padding columns kx > N hold zeros (the kernel writes the octant entries only).
     GSP_CHECK(cudaMemsetAsync(p.sym, 0, (size_t)K * K * p.Ps * sizeof(Real), s));
     k_symbol_table<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
-        static_cast<Real *>(p.sym), dA, dw, nterms, p.N, p.Ps, C0, C2, scale);
+        static_cast<Real *>(p.sym), dA, dw, nterms, p.N, p.Ps, C0, C2, scale, literal);
     return cudaGetLastError();
 }
 

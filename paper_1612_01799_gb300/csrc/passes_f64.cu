@@ -14,8 +14,8 @@ cudaError_t xy_slab_f64(const DevicePlan &p, const void *rho, void *u, int z0, i
     return xy_slab_dispatch<double>(p, rho, u, z0, nz, s, fwd);
 }
 cudaError_t symbol_table_f64(const DevicePlan &p, const double *dA, const double *dw, int nterms,
-                             double C0, double C2, double scale, cudaStream_t s) {
-    return symbol_table<double>(p, dA, dw, nterms, C0, C2, scale, s);
+                             double C0, double C2, double scale, int literal, cudaStream_t s) {
+    return symbol_table<double>(p, dA, dw, nterms, C0, C2, scale, literal, s);
 }
 cudaError_t encode_maps_f64(DevicePlan &p) { return encode_dispatch<double>(p); }
 cudaError_t z_pass_f64(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<double>(p, s); }

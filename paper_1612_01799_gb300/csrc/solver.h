@@ -135,8 +135,11 @@ cudaError_t launch_wait_selftest(const DevicePlan &p, long long polls, cudaStrea
 cudaError_t launch_axis_table(const double *dtau, const double *dgl, int S, int N, double *dA, cudaStream_t s);
 
 // Fill p.sym from the per-axis factors (FP64, on the device):
-// sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2).
+// sym = scale * (sum_j w_j A_j(kx) A_j(ky) A_j(kz) + C0 - C2 (pi/2)^2 |k|^2) (literal = 0),
+// or with 8 (C0 - C2 (pi/2)^2 |k|^2) at all-even (kx, ky, kz) only (literal = 1: the
+// correction of the unpadded N^3 transform pair).
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
-                                int nterms, double C0, double C2, double scale, cudaStream_t s);
+                                int nterms, double C0, double C2, double scale, int literal,
+                                cudaStream_t s);
 
 }  // namespace gsp

@@ -25,6 +25,14 @@ def test_header_and_binding_agree():
     assert declared_functions() == sorted(_lib.SIGNATURES)
 
 
+def test_knob_codes_match_the_header():
+    with open(_lib.HEADER) as f:
+        defs = dict(re.findall(r"#define POISSON_(KNOB_[A-Z_]+)\s+(\d+)", f.read()))
+    assert defs, "no knob codes in the header"
+    for name, code in defs.items():
+        assert getattr(_lib, name) == int(code), name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
