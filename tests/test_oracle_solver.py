@@ -1,16 +1,13 @@
 """Pins of the oracle's solve: closed-form potentials, the paper's printed errors,
 brute-force real-space sums, invariants, and planted mistakes that the pins must catch."""
-import json
 import math
-import os
 
 import numpy as np
 import pytest
 
 from oracle import direct, exact, gtensor, solver
 from paper_1612_01799_gb300 import densities as D
-
-HERE = os.path.dirname(os.path.abspath(__file__))
+from paper_cases import load_cases, paper_case
 
 
 def rel_l2(a, b):
@@ -163,40 +160,17 @@ def test_polynomial_bump_closed_form(plan_cache):
     assert errs[1] < 1e-5
 
 
-def _paper_case(case, N):
-    L = 2.0
-    r = radius(N, L)
-    if case["density"] == "gaussian":
-        return D.gaussian_iso(N, L, case["sigma"]), exact.gaussian_iso(r, case["sigma"])
-    if case["density"] == "two_gaussians":
-        d = np.array(case["d"])
-        rho = D.paper_two_gaussians(N, [-L] * 3, [L] * 3, d=d, s1=case["sigma1"], s2=case["sigma2"])
-        ue = 0.5 * (exact.gaussian_iso(radius(N, L, d), case["sigma1"])
-                    + exact.gaussian_iso(radius(N, L, -d), case["sigma2"]))
-        return rho, ue
-    x = D.axis(N, L)
-    if case["density"] == "aniso":
-        sg = case["sigma"]
-        return D.paper_aniso(N, L, sg), exact.aniso_exp(x[None, None, :], x[None, :, None],
-                                                        x[:, None, None], (0, 0, 0), sg)
-    if case["density"] == "oscillating":
-        return (D.paper_oscillating(N, L, case["sigma"], case["omega"]),
-                exact.oscillating(r, case["sigma"], case["omega"]))
-    raise KeyError(case["density"])
-
-
 @pytest.mark.parametrize("N", [16, 32, 64])
 def test_paper_tables_order_of_magnitude(N, plan_cache, symbol_cache):
     """Tables 1, 3, 5, 7 (box [-2,2]^3): E = max|u - u*| / max|u*| (eq. error_infty).  The
     oracle's cell-centred grid differs from the paper's linspace grid, so the pin is the
     order of magnitude: within a factor 5 of the printed value, or below 1e-14 where the
     paper is at its rounding floor."""
-    with open(os.path.join(HERE, "golden", "paper_tables.json")) as f:
-        cases = json.load(f)["cases"]
+    cases = load_cases()
     p = plan_cache(N, 2.0, 1e-12)
     G = symbol_cache(N, 2.0, 1e-12)
     for case in cases:
-        rho, ue = _paper_case(case, N)
+        rho, ue = paper_case(case, N)
         E = rel_inf(solver.solve(rho, 2.0, 1e-12, plan=p, G=G), ue)
         ref = case["E"][str(N)]
         if ref < 1e-14:
