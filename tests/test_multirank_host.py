@@ -83,3 +83,8 @@ def test_reference_arm_runs_on_rank_zero_only():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    sys.path.insert(0, ROOT)
+    import bench
+    # the same workload, metric and direction as the CUDA arm's line
+    assert line["config"] == bench.workload_config(16, "f32")
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"]
