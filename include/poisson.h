@@ -346,6 +346,8 @@ int poisson_select_n(poisson_selector s, const float *sample32_d, int count, dou
  * parameters) also computes the tables on the host, copies them into the array and
  * synchronises `stream`.  Make those set-up calls before any stream capture.  Later calls
  * with the same parameters only launch the five solve kernels, stream ordered.
+ * The near-field correction is the fused placement (POISSON_KNOB_CORRECTION = 0); the
+ * kernel forms are the block forms (knob value 0 of each form knob).
  * All calls share the array and it keeps the last call's contents; nothing in it needs
  * to start at zero (each pass writes every element the next one reads).  Calls that
  * overlap on the GPU (on different streams, or from different threads) race on the
