@@ -19,6 +19,8 @@ The oracle takes the method's steps in the paper's order, slowly and in FP64:
 * ``direct``     -- the same discrete convolution evaluated in real space one output
   line at a time, for sampled outputs of grids too large for the FFT oracle and for
   brute force on tiny grids.
+* ``box``        -- the same steps on a general rectangular box with n_q points per axis
+  (Sec. 2 standardised form: lambda, l_q and the per-axis G-tensor factors).
 * ``exact``      -- closed-form potentials of the paper's test densities (Sec. 5) and of
   Gaussian sums, used to pin the oracle to something other than itself.
 
@@ -26,4 +28,4 @@ Readings of points the paper leaves open (grid offset, delta's units, the GS ran
 the GS construction, epsilon from the tolerance, the normalisation) are stated in the
 module that uses them.
 """
-from . import direct, exact, gauss_sum, gtensor, solver  # noqa: F401
+from . import box, direct, exact, gauss_sum, gtensor, solver  # noqa: F401

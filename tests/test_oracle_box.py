@@ -1,0 +1,112 @@
+"""Pins of the oracle on general rectangular boxes (Sec. 2 standardised form): the cube
+as a special case, invariance under a permutation of the axes, closed-form potentials with
+different point counts per axis, the paper's Tables 2 and 6, and planted mistakes."""
+import dataclasses
+import json
+import math
+import os
+
+import numpy as np
+
+from oracle import box, exact, gtensor, solver
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rel_inf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def coords(plan):
+    x, y, z = (box.axis(plan, q) for q in range(3))
+    return x[None, None, :], y[None, :, None], z[:, None, None]
+
+
+def gaussian_case(plan, sigma, c):
+    x, y, z = coords(plan)
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    rho = np.exp(-r ** 2 / (2 * sigma ** 2)) / ((2 * math.pi) ** 1.5 * sigma ** 3)
+    return rho, exact.gaussian_iso(r, sigma)
+
+
+def aniso_case(plan, s, c=(0.0, 0.0, 0.0)):
+    """-Laplace of exp(-sum (x_q - c_q)^2 / s_q^2) (Sec. 5.4) and that exact solution."""
+    X = [xq - cq for xq, cq in zip(coords(plan), c)]
+    E = np.exp(-sum(X[q] ** 2 / s[q] ** 2 for q in range(3)))
+    P = sum(4 * X[q] ** 2 / s[q] ** 4 - 2 / s[q] ** 2 for q in range(3))
+    return -P * E, E
+
+
+def test_cube_reduces_to_cube_plan():
+    N, L = 12, 4.0
+    pb = box.make_box_plan(N, [-L] * 3, [L] * 3, 1e-10)
+    pc = gtensor.make_plan(N, L, 1e-10)
+    assert pb.lam == pc.lam and pb.delta == pc.delta and np.array_equal(pb.gs.tau, pc.gs.tau)
+    assert np.array_equal(box.box_symbol(pb), gtensor.symbol(pc))
+    rho = np.random.default_rng(3).uniform(-1, 1, (N, N, N))
+    assert np.array_equal(box.solve_box(rho, pb), solver.solve(rho, L, 1e-10, plan=pc))
+
+
+def test_axis_permutation():
+    """Exchanging the x and z extents (and point counts) transposes the potential."""
+    lo, hi, n = (-2.0, -3.0, -1.0), (2.0, 1.5, 4.0), (8, 10, 12)
+    p1 = box.make_box_plan(n, lo, hi, 1e-10)
+    p2 = box.make_box_plan(n[::-1], lo[::-1], hi[::-1], 1e-10)
+    rho = np.random.default_rng(4).uniform(-1, 1, (n[2], n[1], n[0]))
+    u1 = box.solve_box(rho, p1)
+    u2 = box.solve_box(np.ascontiguousarray(rho.transpose(2, 1, 0)), p2)
+    assert rel_inf(u2.transpose(2, 1, 0), u1) < 1e-13
+
+
+def test_closed_form_with_different_counts_per_axis():
+    """Table 6's box and density with n_q per axis: refining an axis lowers the error, and
+    refining x (sigma_x = 0.1, the narrowest) lowers it most, which a mix-up of the axes'
+    tables or lengths would reverse."""
+    def err(n):
+        p = box.make_box_plan(n, (-2, -4, -6), (2, 4, 6), 1e-12)
+        rho, ue = aniso_case(p, (0.10, 0.20, 0.30))
+        return rel_inf(box.solve_box(rho, p), ue)
+    e32, e64 = err((32, 32, 32)), err((64, 64, 64))
+    assert err((32, 64, 96)) < e32
+    assert err((64, 128, 192)) < e64 < 2e-4
+    assert err((64, 32, 32)) < 0.6 * err((32, 64, 64))
+
+
+def test_paper_rectangular_tables():
+    """Tables 2 and 6: within a factor 5 of the printed E while the paper is above 1e-8;
+    at or below the paper's floor where it has stopped converging."""
+    with open(os.path.join(HERE, "golden", "paper_tables_box.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        for ns, ref in case["E"].items():
+            n = int(ns)
+            p = box.make_box_plan(n, case["lo"], case["hi"], 1e-12)
+            if case["density"] == "gaussian":
+                c = [0.5 * (a + b) for a, b in zip(case["lo"], case["hi"])]
+                rho, ue = gaussian_case(p, case["sigma"], c)
+            else:
+                rho, ue = aniso_case(p, case["sigma"])
+            E = rel_inf(box.solve_box(rho, p), ue)
+            if ref > 1e-8:
+                assert abs(math.log10(E / ref)) <= math.log10(5.0), (case["table"], n, E, ref)
+            else:
+                assert E <= ref, (case["table"], n, E, ref)
+
+
+def test_planted_swapped_half_lengths_are_caught():
+    """Per-axis factors built with the x and z half-lengths exchanged must fail a pin."""
+    p = box.make_box_plan((64, 128, 192), (-2, -4, -6), (2, 4, 6), 1e-12)
+    rho, ue = aniso_case(p, (0.10, 0.20, 0.30))
+    assert rel_inf(box.solve_box(rho, p), ue) < 2e-4
+    lw = p.l[::-1]
+    bad = dataclasses.replace(p, A=tuple(lq * gtensor.a_table(p.gs.tau * lq, m) for lq, m in zip(lw, p.n)))
+    assert rel_inf(box.solve_box(rho, bad), ue) > 1e-2
+
+
+def test_planted_cube_factor_on_every_axis_is_caught():
+    """Dropping the per-axis scaling (the cube's factor A_j on every axis) must fail a pin."""
+    p = box.make_box_plan((64, 128, 192), (-2, -4, -6), (2, 4, 6), 1e-12)
+    rho, ue = aniso_case(p, (0.10, 0.20, 0.30))
+    assert rel_inf(box.solve_box(rho, p), ue) < 2e-4
+    bad = dataclasses.replace(p, A=tuple(gtensor.a_table(p.gs.tau, m) for m in p.n))
+    assert rel_inf(box.solve_box(rho, bad), ue) > 1e-2
