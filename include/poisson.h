@@ -77,6 +77,20 @@ int poisson_plan_create(poisson_plan *out, int N, double L, double tol, int dtyp
 int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, int dtype,
                                 int max_batch);
 
+/*
+ * A plan for the rectangular box [-Lx, Lx] x [-Ly, Ly] x [-Lz, Lz] with N points on every
+ * axis (spacings 2 Lx / N, 2 Ly / N, 2 Lz / N; a box off the origin gives the same grid
+ * values, the potential depending only on the offsets between points).  Sec. 2's
+ * standardised form: lambda = max_q L_q, scaled half-lengths l_q = L_q / lambda, one
+ * G-tensor factor per axis, l_q A_j(tau_j l_q, k), kappa_q = pi k / (2 l_q) in the
+ * correction, the Gaussian sum fitted on [delta, 2 |l|], delta = max(min_q 2 L_q / (50 N),
+ * 1e-3) below min_q l_q (else POISSON_ERR_ARG).  The symbol is not symmetric in its three
+ * indices, so the z pass runs in its block forms (POISSON_KNOB_Z_FORM 0 or 1; 2 is
+ * POISSON_ERR_UNSUPPORTED).  poisson_plan_axis_table returns the x axis's factors.  Other
+ * arguments, errors and use as for poisson_plan_create (one density per solve).
+ */
+int poisson_plan_create_box(poisson_plan *out, int N, double Lx, double Ly, double Lz, double tol, int dtype);
+
 /* Free a plan and its device memory.  NULL is accepted.  The caller must make sure no
  * solve on the plan is still running (synchronise its stream first). */
 int poisson_plan_destroy(poisson_plan p);

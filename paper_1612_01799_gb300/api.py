@@ -26,19 +26,30 @@ def supported_n(N):
 
 
 class Plan:
-    """A solve plan for the cube [-L, L]^3 with N cell-centred points per axis
-    (setup phase: Gaussian sum, G-tensor factors, near-zone constants, symbol table)."""
+    """A solve plan for the cube [-L, L]^3, or with L = (Lx, Ly, Lz) the box
+    [-Lx, Lx] x [-Ly, Ly] x [-Lz, Lz], with N cell-centred points per axis (setup phase:
+    Gaussian sum, G-tensor factors, near-zone constants, symbol table)."""
 
     def __init__(self, N, L, tol, dtype="f32", max_batch=1):
         if dtype not in DTYPES:
             raise ValueError("dtype must be 'f32' or 'f64'")
-        self.N, self.L, self.tol, self.dtype = int(N), float(L), float(tol), dtype
+        self.N, self.tol, self.dtype = int(N), float(tol), dtype
         self.max_batch = int(max_batch)
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
-        _lib.check(self._lib.poisson_plan_create_batched(ctypes.byref(self._h), self.N, self.L,
-                                                         self.tol, DTYPES[dtype], self.max_batch),
-                   "poisson_plan_create_batched")
+        if np.ndim(L):
+            self.box = tuple(float(v) for v in L)
+            if len(self.box) != 3 or self.max_batch != 1:
+                raise ValueError("a box takes three half-lengths and one density per solve")
+            self.L = max(self.box)
+            _lib.check(self._lib.poisson_plan_create_box(ctypes.byref(self._h), self.N, *self.box, self.tol,
+                                                         DTYPES[dtype]), "poisson_plan_create_box")
+        else:
+            self.box = None
+            self.L = float(L)
+            _lib.check(self._lib.poisson_plan_create_batched(ctypes.byref(self._h), self.N, self.L,
+                                                             self.tol, DTYPES[dtype], self.max_batch),
+                       "poisson_plan_create_batched")
 
     @property
     def handle(self):

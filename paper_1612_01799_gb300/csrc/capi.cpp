@@ -26,6 +26,10 @@ cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *,
                              double, double, int, cudaStream_t);
 cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
                              double, double, int, cudaStream_t);
+cudaError_t symbol_table_box_f32(const DevicePlan &, const double *, const double *, int, double, double, double,
+                                 const double *, int, cudaStream_t);
+cudaError_t symbol_table_box_f64(const DevicePlan &, const double *, const double *, int, double, double, double,
+                                 const double *, int, cudaStream_t);
 cudaError_t encode_maps_f32(DevicePlan &);
 cudaError_t encode_maps_f64(DevicePlan &);
 cudaError_t z_pass_f32(const DevicePlan &, cudaStream_t);
@@ -97,6 +101,12 @@ static cudaError_t fork_pool(int dev, ForkPool **out) {
     return cudaSuccess;
 }
 
+cudaError_t launch_symbol_table_box(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
+                                    double C0, double C2, double scale, const double *l, int literal,
+                                    cudaStream_t s) {
+    return p.dtype == POISSON_F32 ? symbol_table_box_f32(p, dA3, dw, nterms, C0, C2, scale, l, literal, s)
+                                  : symbol_table_box_f64(p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
+}
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
                                 int nterms, double C0, double C2, double scale, int literal,
                                 cudaStream_t s) {
@@ -275,8 +285,22 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     return poisson_plan_create_batched(out, N, L, tol, dtype, 1);
 }
 
+static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3, double tol, int dtype,
+                            int max_batch);
+
 extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, int dtype,
                                            int max_batch) {
+    return plan_create_impl(out, N, L, nullptr, tol, dtype, max_batch);
+}
+
+extern "C" int poisson_plan_create_box(poisson_plan *out, int N, double Lx, double Ly, double Lz, double tol,
+                                       int dtype) {
+    const double L3[3] = {Lx, Ly, Lz};
+    return plan_create_impl(out, N, 0.0, L3, tol, dtype, 1);
+}
+
+static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3, double tol, int dtype,
+                            int max_batch) {
     if (!out) return POISSON_ERR_ARG;
     *out = nullptr;
     if (dtype != POISSON_F32 && dtype != POISSON_F64) return POISSON_ERR_ARG;
@@ -287,7 +311,7 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     if (!p) return POISSON_ERR_ALLOC;
     // The Gaussian sum, delta, eps and the near-zone constants on the host; the per-axis
     // table A_j(k) below on the device.
-    int rc = gsp::build_host_scalars(N, L, tol, p->ht);
+    int rc = L3 ? gsp::build_host_scalars_box(N, L3, tol, p->ht) : gsp::build_host_scalars(N, L, tol, p->ht);
     if (rc != POISSON_OK) {
         delete p;
         return rc;
@@ -365,10 +389,12 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     }
     if (e != cudaSuccess) return fail(e);
 
-    // Symbol octant on the device, in FP64, from the per-axis factors.
+    // Symbol octant on the device, in FP64, from the per-axis factors (a box: one table per
+    // axis, l_q A_j(tau_j l_q), Sec. 2).
     const int nterms = (int)p->ht.tau.size();
     const size_t nA = (size_t)nterms * K;
-    if ((e = cudaMalloc(&dA, nA * sizeof(double))) != cudaSuccess) return fail(e);
+    const bool box = p->ht.box;
+    if ((e = cudaMalloc(&dA, (box ? 3 : 1) * nA * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&dtau, (size_t)nterms * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&dgl, 32 * sizeof(double))) != cudaSuccess) return fail(e);
     {
@@ -376,22 +402,41 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
         gsp::gauss_legendre16(gl, gl + 16);
         if ((e = cudaMemcpy(dgl, gl, sizeof gl, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     }
-    if ((e = cudaMemcpy(dtau, p->ht.tau.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-        return fail(e);
-    if ((e = gsp::launch_axis_table(dtau, dgl, nterms, N, dA, 0)) != cudaSuccess) return fail(e);
-    p->ht.A.resize(nA);  // the plan keeps the table for poisson_plan_axis_table
-    if ((e = cudaMemcpy(p->ht.A.data(), dA, nA * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return fail(e);
+    if (!box) {
+        if ((e = cudaMemcpy(dtau, p->ht.tau.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return fail(e);
+        if ((e = gsp::launch_axis_table(dtau, dgl, nterms, N, dA, 0)) != cudaSuccess) return fail(e);
+        p->ht.A.resize(nA);  // the plan keeps the table for poisson_plan_axis_table
+        if ((e = cudaMemcpy(p->ht.A.data(), dA, nA * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return fail(e);
+    } else {
+        std::vector<double> taul(nterms);
+        p->ht.A3.resize(3 * nA);
+        for (int q = 0; q < 3; ++q) {
+            for (int j = 0; j < nterms; ++j) taul[j] = p->ht.tau[j] * p->ht.l[q];
+            if ((e = cudaMemcpy(dtau, taul.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return fail(e);
+            if ((e = gsp::launch_axis_table(dtau, dgl, nterms, N, dA + q * nA, 0)) != cudaSuccess) return fail(e);
+            if ((e = cudaMemcpy(p->ht.A3.data() + q * nA, dA + q * nA, nA * sizeof(double),
+                                cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return fail(e);
+            for (size_t i = 0; i < nA; ++i) p->ht.A3[q * nA + i] *= p->ht.l[q];
+        }
+        if ((e = cudaMemcpy(dA, p->ht.A3.data(), 3 * nA * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+        p->ht.A.assign(p->ht.A3.begin(), p->ht.A3.begin() + nA);  // the x axis
+    }
     if ((e = cudaMalloc(&dw, p->ht.w.size() * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(dw, p->ht.w.data(), p->ht.w.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
     const double M = 2.0 * N;
     const double scale = p->ht.lambda * p->ht.lambda / (M * M * M);
-    if ((e = gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0, 0)) !=
-        cudaSuccess)
-        return fail(e);
+    e = box ? gsp::launch_symbol_table_box(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, p->ht.l, 0, 0)
+            : gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0, 0);
+    if (e != cudaSuccess) return fail(e);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
     cudaFree(dA);
     cudaFree(dw);
@@ -399,6 +444,8 @@ extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, d
     cudaFree(dgl);
     dA = dw = dtau = dgl = nullptr;
     if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
+    // The z warp forms read the symbol with kz innermost through the cube's symmetry.
+    if (box && p->dp.zform == 2) p->dp.zform = 0;
     *out = p;
     return POISSON_OK;
 }
@@ -421,18 +468,19 @@ static int rebuild_symbol(poisson_plan p, int literal) {
     cudaError_t e = cudaGetDevice(&prev);
     if (e != cudaSuccess) return map_cuda(e);
     if ((e = cudaSetDevice(p->device)) != cudaSuccess) return map_cuda(e);
-    const int nterms = (int)p->ht.tau.size(), K = p->dp.N + 1;
+    const int nterms = (int)p->ht.tau.size();
+    const std::vector<double> &A = p->ht.box ? p->ht.A3 : p->ht.A;  // one table or the box's three
     double *dA = nullptr, *dw = nullptr;
-    e = cudaMalloc(&dA, (size_t)nterms * K * sizeof(double));
+    e = cudaMalloc(&dA, A.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&dw, (size_t)nterms * sizeof(double));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(dA, p->ht.A.data(), (size_t)nterms * K * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(dw, p->ht.w.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice);
-    const double M = 2.0 * p->dp.N;
+    const double M = 2.0 * p->dp.N, scale = p->ht.lambda * p->ht.lambda / (M * M * M);
     if (e == cudaSuccess)
-        e = gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2,
-                                     p->ht.lambda * p->ht.lambda / (M * M * M), literal, 0);
+        e = p->ht.box ? gsp::launch_symbol_table_box(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, p->ht.l,
+                                                     literal, 0)
+                      : gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, literal, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(dA);
     cudaFree(dw);
@@ -467,6 +515,7 @@ extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     }
     if (value < 0 || value > (knob == POISSON_KNOB_Z_FORM ? 2 : 1)) return POISSON_ERR_ARG;
     if (!(forms >> value & 1)) return POISSON_ERR_UNSUPPORTED;
+    if (p->ht.box && knob == POISSON_KNOB_Z_FORM && value == 2) return POISSON_ERR_UNSUPPORTED;
     *field = value;
     return POISSON_OK;
 }

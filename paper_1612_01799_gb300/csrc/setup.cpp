@@ -276,6 +276,37 @@ int build_host_scalars(int N, double L, double tol, HostTables &o) {
     return POISSON_OK;
 }
 
+int build_host_scalars_box(int N, const double *L3, double tol, HostTables &o) {
+    if (N < 4 || N > 1024 || (N & 1) || !L3 || !(tol > 0.0) || !std::isfinite(tol))
+        return POISSON_ERR_ARG;
+    double lam = 0.0, lmin = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        if (!(L3[q] > 0.0) || !std::isfinite(L3[q])) return POISSON_ERR_ARG;
+        lam = std::max(lam, L3[q]);
+    }
+    o.N = N;
+    o.L = lam;
+    o.tol = tol;
+    o.lambda = lam;
+    o.box = true;
+    double l2 = 0.0;
+    lmin = 1.0;
+    for (int q = 0; q < 3; ++q) {
+        o.l[q] = L3[q] / lam;
+        l2 += o.l[q] * o.l[q];
+        lmin = std::min(lmin, o.l[q]);
+    }
+    // Sec. 3: min_q (b_q - a_q) / (50 n_q), at least 1e-3, used as is in the scaled box.
+    o.delta = std::max(2.0 * std::min({L3[0], L3[1], L3[2]}) / (50.0 * N), 1e-3);
+    if (!(o.delta < lmin)) return POISSON_ERR_ARG;  // Sec. 3: delta < min_q l_q
+    o.eps = eps_for_tol(tol);
+    o.r_max = 2.0 * std::sqrt(l2);
+    if (!build_gauss_sum(o.eps, o.delta, o.r_max, o.tau, o.w, o.h, o.gs_err))
+        return POISSON_ERR_NUMERIC;
+    near_zone_constants(o.tau, o.w, o.delta, o.C0, o.C2);
+    return POISSON_OK;
+}
+
 void twiddles(int n, std::vector<double> &re_im) {
     re_im.resize(2 * (size_t)n);
     const long double two_pi = 2.0L * std::acos(-1.0L);

@@ -15,8 +15,13 @@ struct HostTables {
     double h = 0;        // sinc-quadrature step
     double gs_err = 0;   // measured max relative error of U_GS on the fit grid
     std::vector<double> tau, w;   // Gaussian sum, S+1 terms
-    std::vector<double> A;        // (S+1) x (N+1): A_j(k), row-major
+    std::vector<double> A;        // (S+1) x (N+1): A_j(k), row-major (the x axis of a box)
     double C0 = 0, C2 = 0;        // near-zone Taylor constants
+    // Box [-L_x, L_x] x [-L_y, L_y] x [-L_z, L_z] (Sec. 2 standardised form): half-lengths
+    // l_q = L_q / lambda of the scaled box; all 1 for the cube.
+    bool box = false;
+    double l[3] = {1.0, 1.0, 1.0};
+    std::vector<double> A3;       // box: the three axes' tables l_q A_j(tau_j l_q), x, y, z
 };
 
 // eps = clamp(tol/10, 1e-14, 1e-7).
@@ -51,6 +56,11 @@ int build_host_tables(int N, double L, double tol, HostTables &out);
 // The same without the axis table (out.A left empty), for a setup that builds the table
 // on the device.
 int build_host_scalars(int N, double L, double tol, HostTables &out);
+
+// The scalars for the box [-L3[0], L3[0]] x [-L3[1], L3[1]] x [-L3[2], L3[2]] with N points
+// per axis: lambda = max_q L_q, l_q = L_q / lambda, delta = max(min_q 2 L_q / (50 N), 1e-3)
+// below min_q l_q, the Gaussian sum fitted on [delta, 2 |l|].
+int build_host_scalars_box(int N, const double *L3, double tol, HostTables &out);
 
 // tw[e] = exp(-2 pi i e / n), e in [0, n), as (re, im) pairs, accurate to FP64 rounding.
 void twiddles(int n, std::vector<double> &re_im);

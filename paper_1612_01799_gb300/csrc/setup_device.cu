@@ -1,4 +1,5 @@
-// Plan setup on the device: the per-axis factors of the G-tensor (Sec. 2),
+// Plan setup on the device: the per-axis factors of the G-tensor (Sec. 2) and the symbol
+// table of a rectangular box.  The per-axis factors (Sec. 2),
 //   A_j(k) = 2 int_0^2 exp(-tau_j^2 t^2) cos(kappa_k t) dt,  kappa_k = pi k / 2,  k = 0..N,
 // by the rule of the host setup (build_axis_table): the full-line closed form
 // (sqrt(pi) / tau) exp(-kappa^2 / (4 tau^2)) for tau >= 3, where the Gaussian is below
@@ -62,7 +63,58 @@ __global__ void k_axis_table(const double *__restrict__ tau, const double *__res
     }
     A[(size_t)j * K + k] = 2.0 * (acc + comp);
 }
+
+// The symbol of a box [-l_1, l_1] x [-l_2, l_2] x [-l_3, l_3] (Sec. 2 standardised form):
+// sum_j w_j Ax_j(kx) Ay_j(ky) Az_j(kz) with the per-axis factors of each axis, and kappa_q =
+// pi k_q / (2 l_q) in the correction (il2[q] = 1 / l_q^2); `literal` as in k_symbol_table.
+// The table is no longer symmetric: block (ky, kz) computes its whole kx line,
+// sym[(kz * (N+1) + ky) * Ps + kx].
+template <typename Real>
+__global__ void k_symbol_box(Real *__restrict__ sym, const double *__restrict__ Ax, const double *__restrict__ Ay,
+                             const double *__restrict__ Az, const double *__restrict__ w, int nterms, int N,
+                             int Ps, double C0, double C2, double scale, double il2x, double il2y, double il2z,
+                             int literal) {
+    extern __shared__ double cj[];
+    const int b = blockIdx.x, c = blockIdx.y, K = N + 1;
+    for (int j = threadIdx.x; j < nterms; j += blockDim.x)
+        cj[j] = w[j] * Ay[(long long)j * K + b] * Az[(long long)j * K + c];
+    __syncthreads();
+    const double hp2 = 0.25 * 3.141592653589793238462643383279502884 * 3.141592653589793238462643383279502884;
+    for (int a = threadIdx.x; a <= N; a += blockDim.x) {
+        double sum = 0.0;
+        for (int j = 0; j < nterms; ++j) sum += cj[j] * Ax[(long long)j * K + a];
+        const double k2 = (double)a * a * il2x + (double)b * b * il2y + (double)c * c * il2z;
+        double v;
+        if (!literal) v = sum + C0 - C2 * hp2 * k2;
+        else v = ((a | b | c) & 1) ? sum : sum + 8.0 * (C0 - C2 * hp2 * k2);
+        sym[((long long)c * K + b) * Ps + a] = (Real)(scale * v);
+    }
+}
+
+template <typename Real>
+cudaError_t symbol_table_box(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
+                             double C0, double C2, double scale, const double *l, int literal, cudaStream_t s) {
+    const int K = p.N + 1;
+    const size_t tab = (size_t)nterms * K;
+    cudaError_t e = cudaMemsetAsync(p.sym, 0, (size_t)K * K * p.Ps * sizeof(Real), s);
+    if (e != cudaSuccess) return e;
+    k_symbol_box<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
+        static_cast<Real *>(p.sym), dA3, dA3 + tab, dA3 + 2 * tab, dw, nterms, p.N, p.Ps, C0, C2, scale,
+        1.0 / (l[0] * l[0]), 1.0 / (l[1] * l[1]), 1.0 / (l[2] * l[2]), literal);
+    return cudaGetLastError();
+}
 }  // namespace
+
+cudaError_t symbol_table_box_f32(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
+                                 double C0, double C2, double scale, const double *l, int literal,
+                                 cudaStream_t s) {
+    return symbol_table_box<float>(p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
+}
+cudaError_t symbol_table_box_f64(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
+                                 double C0, double C2, double scale, const double *l, int literal,
+                                 cudaStream_t s) {
+    return symbol_table_box<double>(p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
+}
 
 cudaError_t launch_axis_table(const double *dtau, const double *dgl, int S, int N, double *dA, cudaStream_t s) {
     const int P = axis_table_panels(N);

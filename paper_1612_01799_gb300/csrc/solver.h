@@ -141,5 +141,10 @@ cudaError_t launch_axis_table(const double *dtau, const double *dgl, int S, int 
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
                                 int nterms, double C0, double C2, double scale, int literal,
                                 cudaStream_t s);
+// The same for a box: dA3 holds the x, y and z tables one after the other, l the scaled
+// half-lengths; the table is not symmetric.
+cudaError_t launch_symbol_table_box(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
+                                    double C0, double C2, double scale, const double *l, int literal,
+                                    cudaStream_t s);
 
 }  // namespace gsp
