@@ -85,8 +85,9 @@ int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, 
  * G-tensor factor per axis, l_q A_j(tau_j l_q, k), kappa_q = pi k / (2 l_q) in the
  * correction, the Gaussian sum fitted on [delta, 2 |l|], delta = max(min_q 2 L_q / (50 N),
  * 1e-3) below min_q l_q (else POISSON_ERR_ARG).  The symbol is not symmetric in its three
- * indices, so the z pass runs in its block forms (POISSON_KNOB_Z_FORM 0 or 1; 2 is
- * POISSON_ERR_UNSUPPORTED).  poisson_plan_axis_table returns the x axis's factors.  Other
+ * indices, so the plan also keeps a copy with kz innermost for the z warp forms (the
+ * table's memory counts twice in poisson_plan_info).  poisson_plan_axis_table returns the
+ * x axis's factors.  Other
  * arguments, errors and use as for poisson_plan_create (one density per solve).
  */
 int poisson_plan_create_box(poisson_plan *out, int N, double Lx, double Ly, double Lz, double tol, int dtype);

@@ -254,7 +254,7 @@ static int map_cuda(cudaError_t e) {
 static void free_plan(poisson_plan p) {
     if (!p) return;
     void *twc = p->dp.twc != p->dp.tw ? p->dp.twc : nullptr;
-    void *bufs[] = {p->dp.sym, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->dp.status,
+    void *bufs[] = {p->dp.sym, p->dp.symT, p->dp.tw, twc, p->dp.w1, p->dp.w2, p->dp.w3, p->dp.status,
                     p->dp.tail, p->dp.sync, p->stage_in, p->stage_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -345,6 +345,10 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
         return map_cuda(err);
     };
     if ((e = cudaMalloc(&p->dp.sym, sym_bytes)) != cudaSuccess) return fail(e);
+    if (p->ht.box) {
+        if ((e = cudaMalloc(&p->dp.symT, sym_bytes)) != cudaSuccess) return fail(e);
+        p->table_bytes += sym_bytes;
+    }
     if ((e = cudaMalloc(&p->dp.tw, tw_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.w1, w1_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.w2, w2_bytes)) != cudaSuccess) return fail(e);
@@ -367,7 +371,20 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
         if ((e = cudaMalloc(&p->dp.sync, sync_bytes)) != cudaSuccess) return fail(e);
         if ((e = cudaMemset(p->dp.sync, 0, sync_bytes)) != cudaSuccess) return fail(e);
     }
-    if ((e = gsp::encode_tma_maps(p->dp)) != cudaSuccess) return fail(e);
+    if (p->ht.box) {
+        // The z warp forms read the symbol with kz innermost, which for the cube is the table
+        // itself (it is symmetric); a box's map covers its transposed copy instead.
+        void *natural = p->dp.sym;
+        p->dp.sym = p->dp.symT;
+        e = gsp::encode_tma_maps(p->dp);
+        const CUtensorMap zw_sym = p->dp.tm_zw_sym;
+        p->dp.sym = natural;
+        if (e == cudaSuccess) e = gsp::encode_tma_maps(p->dp);
+        p->dp.tm_zw_sym = zw_sym;
+        if (e != cudaSuccess) return fail(e);
+    } else if ((e = gsp::encode_tma_maps(p->dp)) != cudaSuccess) {
+        return fail(e);
+    }
     gsp::ForkPool *pool = nullptr;
     if ((e = gsp::fork_pool(p->device, &pool)) != cudaSuccess) return fail(e);
 
@@ -444,8 +461,6 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
     cudaFree(dgl);
     dA = dw = dtau = dgl = nullptr;
     if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
-    // The z warp forms read the symbol with kz innermost through the cube's symmetry.
-    if (box && p->dp.zform == 2) p->dp.zform = 0;
     *out = p;
     return POISSON_OK;
 }
@@ -515,7 +530,6 @@ extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
     }
     if (value < 0 || value > (knob == POISSON_KNOB_Z_FORM ? 2 : 1)) return POISSON_ERR_ARG;
     if (!(forms >> value & 1)) return POISSON_ERR_UNSUPPORTED;
-    if (p->ht.box && knob == POISSON_KNOB_Z_FORM && value == 2) return POISSON_ERR_UNSUPPORTED;
     *field = value;
     return POISSON_OK;
 }

@@ -68,9 +68,10 @@ __global__ void k_axis_table(const double *__restrict__ tau, const double *__res
 // sum_j w_j Ax_j(kx) Ay_j(ky) Az_j(kz) with the per-axis factors of each axis, and kappa_q =
 // pi k_q / (2 l_q) in the correction (il2[q] = 1 / l_q^2); `literal` as in k_symbol_table.
 // The table is no longer symmetric: block (ky, kz) computes its whole kx line,
-// sym[(kz * (N+1) + ky) * Ps + kx].
+// sym[(kz * (N+1) + ky) * Ps + kx], and writes it transposed, symT[(kx * (N+1) + ky) * Ps +
+// kz], for the z warp forms, which read the table with kz innermost.
 template <typename Real>
-__global__ void k_symbol_box(Real *__restrict__ sym, const double *__restrict__ Ax, const double *__restrict__ Ay,
+__global__ void k_symbol_box(Real *__restrict__ sym, Real *__restrict__ symT, const double *__restrict__ Ax, const double *__restrict__ Ay,
                              const double *__restrict__ Az, const double *__restrict__ w, int nterms, int N,
                              int Ps, double C0, double C2, double scale, double il2x, double il2y, double il2z,
                              int literal) {
@@ -88,6 +89,7 @@ __global__ void k_symbol_box(Real *__restrict__ sym, const double *__restrict__ 
         if (!literal) v = sum + C0 - C2 * hp2 * k2;
         else v = ((a | b | c) & 1) ? sum : sum + 8.0 * (C0 - C2 * hp2 * k2);
         sym[((long long)c * K + b) * Ps + a] = (Real)(scale * v);
+        symT[((long long)a * K + b) * Ps + c] = (Real)(scale * v);
     }
 }
 
@@ -98,8 +100,10 @@ cudaError_t symbol_table_box(const DevicePlan &p, const double *dA3, const doubl
     const size_t tab = (size_t)nterms * K;
     cudaError_t e = cudaMemsetAsync(p.sym, 0, (size_t)K * K * p.Ps * sizeof(Real), s);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.symT, 0, (size_t)K * K * p.Ps * sizeof(Real), s);
+    if (e != cudaSuccess) return e;
     k_symbol_box<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
-        static_cast<Real *>(p.sym), dA3, dA3 + tab, dA3 + 2 * tab, dw, nterms, p.N, p.Ps, C0, C2, scale,
+        static_cast<Real *>(p.sym), static_cast<Real *>(p.symT), dA3, dA3 + tab, dA3 + 2 * tab, dw, nterms, p.N, p.Ps, C0, C2, scale,
         1.0 / (l[0] * l[0]), 1.0 / (l[1] * l[1]), 1.0 / (l[2] * l[2]), literal);
     return cudaGetLastError();
 }

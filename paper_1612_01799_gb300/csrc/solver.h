@@ -34,6 +34,7 @@ struct DevicePlan {
     int Px = 0;
     int Ps = 0;
     void *sym = nullptr;
+    void *symT = nullptr;  // a box plan's symbol with kz innermost, read by the z warp forms
     void *tw = nullptr;
     void *twc = nullptr;
     void *w1 = nullptr;

@@ -72,25 +72,69 @@ def test_box_f64_matches_oracle(torch_cuda, N, geom):
     rho, _ = (t2_case if geom is T2 else t6_case)(op)
     uo = obox.solve_box(rho, op)
     with Plan(N, half(*geom), 1e-12, "f64") as p:
-        assert p.z_form != 2
         assert rel_l2(gpu(torch_cuda, p, rho), uo) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("N", [64, 80, 128])
+@pytest.mark.parametrize("N", [64, 80, 128, 256])
 def test_box_f32_every_form(torch_cuda, N):
-    from paper_1612_01799_gb300 import Plan, _lib
+    """Every z form, the warp forms reading the box symbol's kz-innermost copy."""
+    from paper_1612_01799_gb300 import Plan
     op = obox.make_box_plan(N, T6[0], T6[1], 1e-6)
     rho, _ = t6_case(op)
     uo = obox.solve_box(rho, op)
-    lib = _lib.load()
+    warp = (64, 96, 128, 160, 192, 256)
     with Plan(N, half(*T6), 1e-6, "f32") as p:
-        assert lib.poisson_plan_set_knob(p.handle, _lib.KNOB_Z_FORM, 2) == -4
-        zf = [0] + ([1] if N in (16, 80, 256, 320, 384) else [])
-        yf = [0] + ([1] if N in (64, 96, 128, 160, 192, 256) else [])
+        zf = [0] + ([1] if N in (16, 80, 256, 320, 384) else []) + ([2] if N in warp else [])
+        yf = [0] + ([1] if N in warp else [])
         for z in zf:
             for y in yf:
                 p.z_form, p.y_form, p.x_form = z, y, y
                 assert rel_l2(gpu(torch_cuda, p, rho), uo) <= TOL["f32"], (z, y)
+
+
+def test_box_literal_correction_and_warp_form(torch_cuda):
+    """The literal correction on a box (all-even frequencies, per-axis kappa) and the z warp
+    form reading the rebuilt transposed copy give the same potential as the block form."""
+    from paper_1612_01799_gb300 import Plan
+    N = 64
+    rho = np.random.default_rng(6).uniform(-1, 1, (N, N, N))
+    with Plan(N, half(*T2), 1e-6, "f32") as p:
+        p.correction = "literal"
+        p.z_form = 0
+        u0 = gpu(torch_cuda, p, rho)
+        p.z_form = 2
+        u2 = gpu(torch_cuda, p, rho)
+        assert rel_l2(u2, u0) < 1e-6
+
+
+def folded_literal(rho, plan):
+    """The literal correction of a box placed at the all-even padded frequencies (as pinned
+    for the cube in test_literal_fold.py), per-axis kappa = pi k / (2 l_q)."""
+    import scipy.fft as sfft
+    from oracle.gtensor import signed_freq
+    nx, ny, nz = plan.n
+    ks = [signed_freq(m) for m in (nx, ny, nz)]
+    kap2 = [(0.5 * math.pi * k / lq) ** 2 for k, lq in zip(ks, plan.l)]
+    ev = [k % 2 == 0 for k in ks]
+    E = ev[2][:, None, None] & ev[1][None, :, None] & ev[0][None, None, :]
+    K2 = kap2[2][:, None, None] + kap2[1][None, :, None] + kap2[0][None, None, :]
+    G = obox.box_symbol(plan, correction=False) + np.where(E, 8.0 * (plan.C0 - plan.C2 * K2), 0.0)
+    spec = sfft.fftn(rho, s=(2 * nz, 2 * ny, 2 * nx)) * G
+    return plan.lam ** 2 * sfft.ifftn(spec).real[:nz, :ny, :nx]
+
+
+def test_box_literal_f64(torch_cuda):
+    from paper_1612_01799_gb300 import Plan
+    N, tol = 32, 1e-10
+    op = obox.make_box_plan(N, T2[0], T2[1], tol)
+    rng = np.random.default_rng(8)
+    checker = np.fromfunction(lambda i, j, l: (-1.0) ** (i + j + l), (N, N, N))
+    with Plan(N, half(*T2), tol, "f64") as p:
+        p.correction = "literal"
+        for rho in (rng.uniform(-1, 1, (N, N, N)), checker):
+            u = gpu(torch_cuda, p, rho)
+            assert rel_l2(u, folded_literal(rho, op)) <= TOL["f64"]
+            assert rel_l2(u, obox.solve_box(rho, op)) > 2e-11   # the placements differ by 2e-10 and 1e-8
 
 
 def test_cube_shaped_box_equals_cube_plan(torch_cuda):
