@@ -29,3 +29,18 @@ extern "C" void shim_twiddles(int n, double *out) {
     gsp::twiddles(n, v);
     std::memcpy(out, v.data(), v.size() * sizeof(double));
 }
+
+// Box scalars: out = {lambda, l_x, l_y, l_z, delta, eps, C0, C2, r_max}.
+extern "C" int shim_box_scalars(int N, const double *L3, double tol, int cap_terms, int *n_terms, double *tau,
+                                double *w, double *out) {
+    gsp::HostTables t;
+    int rc = gsp::build_host_scalars_box(N, L3, tol, t);
+    if (rc) return rc;
+    *n_terms = (int)t.tau.size();
+    if ((int)t.tau.size() > cap_terms) return -100;
+    std::copy(t.tau.begin(), t.tau.end(), tau);
+    std::copy(t.w.begin(), t.w.end(), w);
+    const double v[9] = {t.lambda, t.l[0], t.l[1], t.l[2], t.delta, t.eps, t.C0, t.C2, t.r_max};
+    std::copy(v, v + 9, out);
+    return 0;
+}

@@ -65,6 +65,19 @@ def test_plan_create_rejects_bad_arguments(lib):
     assert lib.poisson_plan_create(ctypes.byref(h), 4, 1000.0, 1e-6, 0) == -1    # delta >= 1
 
 
+def test_box_plan_create_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p(1234)
+    assert lib.poisson_plan_create_box(None, 32, 1.0, 2.0, 3.0, 1e-12, 1) == -1
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 33, 1.0, 2.0, 3.0, 1e-12, 1) == -1   # odd N
+    assert h.value is None
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 100, 1.0, 2.0, 3.0, 1e-12, 0) == -4  # no FFT plan
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 32, 1.0, -2.0, 3.0, 1e-12, 0) == -1  # L_q <= 0
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 32, 1.0, float("inf"), 3.0, 1e-12, 0) == -1
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 32, 1.0, 2.0, 3.0, 0.0, 0) == -1     # tol <= 0
+    # Sec. 3 side condition: delta (at least 1e-3) must lie below the flattest l_q = 1e-4
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 4, 0.001, 10.0, 10.0, 1e-6, 0) == -1
+
+
 def test_null_plan_calls_are_errors(lib):
     assert lib.poisson_plan_destroy(None) == 0
     assert lib.poisson_solve(None, None, None, None) == -1

@@ -24,6 +24,8 @@ def shim(tmp_path_factory):
     lib.shim_host_tables.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), P, P, P, P]
     lib.shim_twiddles.argtypes = [ctypes.c_int, P]
+    lib.shim_box_scalars.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), P, P, P]
     return lib
 
 
@@ -68,3 +70,28 @@ def test_twiddles_exact(shim):
             assert abs(z[e] - ref) <= 1.2e-16
         # numpy evaluates 2 pi e / n in double: its own error reaches ~1e-15
         assert np.max(np.abs(z - np.exp(-2j * np.pi * np.arange(n) / n))) <= 4e-15
+
+
+@pytest.mark.parametrize("N,L3,tol", [(32, (2.5, 2.75, 3.0), 1e-12), (64, (2.0, 4.0, 6.0), 1e-6),
+                                      (48, (4.0, 4.0, 4.0), 1e-10)])
+def test_box_scalars_match_oracle(shim, N, L3, tol):
+    """Box plans (Sec. 2 standardised form): lambda, l_q, delta, the Gaussian sum on
+    [delta, 2 |l|] and the near-zone constants against the oracle's box plan."""
+    from oracle import box
+    P = ctypes.POINTER(ctypes.c_double)
+    cap = 1000
+    n = ctypes.c_int()
+    tau, w, out = np.zeros(cap), np.zeros(cap), np.zeros(9)
+    L = np.array(L3, dtype=np.float64)
+    assert shim.shim_box_scalars(N, L.ctypes.data_as(P), tol, cap, ctypes.byref(n), tau.ctypes.data_as(P),
+                                 w.ctypes.data_as(P), out.ctypes.data_as(P)) == 0
+    k = n.value
+    po = box.make_box_plan(N, [-v for v in L3], list(L3), tol)
+    assert out[0] == po.lam and tuple(out[1:4]) == pytest.approx(po.l, rel=1e-15)
+    assert out[4] == pytest.approx(po.delta, rel=1e-15) and out[5] == po.eps
+    assert k == len(po.gs.tau)
+    assert np.max(np.abs(tau[:k] / po.gs.tau - 1)) <= 1e-14
+    assert np.max(np.abs(w[:k] / po.gs.w - 1)) <= 1e-14
+    assert out[6] == pytest.approx(po.C0, rel=1e-12)
+    assert out[7] == pytest.approx(po.C2, rel=1e-10)
+    assert out[8] == pytest.approx(po.gs.r_max, rel=1e-15)
