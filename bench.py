@@ -206,7 +206,7 @@ def run_reference(args):
     ms = 1e3 * statistics.mean(times)
     value = N ** 3 / (ms / 1e3)
     cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
-    sample = ("one full FP64 oracle solve per step of the N=%d workload (scipy FFT of the "
+    sample = ("one full FP64 oracle solve per step of the N=%d workload (the oracle's own FFT of the "
               "padded %d^3 grid, symbol product, inverse FFT, crop); setup untimed" % (N, 2 * N))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -13,6 +13,8 @@ The oracle takes the method's steps in the paper's order, slowly and in FP64:
 * ``gtensor``    -- the per-axis factors of the G-tensor by adaptive Gauss-Kronrod
   quadrature (Sec. 2, G-tensor formula), the Taylor near-field constants C0 and C2
   (Sec. 2, correction integral I_delta) and the full padded symbol.
+* ``fft``        -- the oracle's own FP64 mixed-radix Cooley-Tukey FFT (fft.c), used by
+  every transform below; no library FFT is called.
 * ``solver``     -- zero padding to (2N)^3, forward FFT, product with the symbol,
   inverse FFT, crop to N^3 (Sec. 2 and Sec. 3), with the correction either folded into
   the symbol or applied the paper's literal way through an N^3 FFT pair.
@@ -20,7 +22,8 @@ The oracle takes the method's steps in the paper's order, slowly and in FP64:
   line at a time, for sampled outputs of grids too large for the FFT oracle and for
   brute force on tiny grids.
 * ``box``        -- the same steps on a general rectangular box with n_q points per axis
-  (Sec. 2 standardised form: lambda, l_q and the per-axis G-tensor factors).
+  (Sec. 2 standardised form: lambda, l_q and the per-axis G-tensor factors), with the
+  correction folded into the symbol or in the paper's literal order.
 * ``exact``      -- closed-form potentials of the paper's test densities (Sec. 5) and of
   Gaussian sums, used to pin the oracle to something other than itself.
 
@@ -28,4 +31,4 @@ Readings of points the paper leaves open (grid offset, delta's units, the GS ran
 the GS construction, epsilon from the tolerance, the normalisation) are stated in the
 module that uses them.
 """
-from . import box, direct, exact, gauss_sum, gtensor, solver  # noqa: F401
+from . import box, direct, exact, fft, gauss_sum, gtensor, solver  # noqa: F401

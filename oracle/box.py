@@ -18,11 +18,10 @@ the cube [-L, L]^3 every step reduces to gtensor.make_plan / gtensor.symbol / so
 """
 from dataclasses import dataclass
 import math
-import os
 
 import numpy as np
-import scipy.fft as sfft
 
+from . import fft
 from .gauss_sum import GaussSum, eps_from_tol, gauss_sum, near_zone_delta
 from .gtensor import a_table, correction_constants, signed_freq
 
@@ -82,16 +81,44 @@ def box_symbol(plan: BoxPlan, correction: bool = True) -> np.ndarray:
     return G
 
 
-def solve_box(rho: np.ndarray, plan: BoxPlan, G: np.ndarray = None) -> np.ndarray:
-    """Potential of rho (shape (n_z, n_y, n_x), FP64, cell-centred grid of the box)."""
+def solve_box(rho: np.ndarray, plan: BoxPlan, G: np.ndarray = None,
+              correction: bool = True) -> np.ndarray:
+    """Potential of rho (shape (n_z, n_y, n_x), FP64, cell-centred grid of the box), the
+    correction folded into the padded symbol (or left out: correction=False)."""
     rho = np.asarray(rho, dtype=np.float64)
     nx, ny, nz = plan.n
     if rho.shape != (nz, ny, nx):
         raise ValueError("rho must have shape (n_z, n_y, n_x)")
     if G is None:
-        G = box_symbol(plan)
-    workers = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
-    spec = sfft.fftn(rho, s=(2 * nz, 2 * ny, 2 * nx), workers=workers)
+        G = box_symbol(plan, correction=correction)
+    spec = fft.fftn(rho, s=(2 * nz, 2 * ny, 2 * nx))
     spec *= G
-    u = sfft.ifftn(spec, workers=workers)
+    u = fft.ifftn(spec, overwrite=True)
     return plan.lam ** 2 * np.ascontiguousarray(u.real[:nz, :ny, :nx])
+
+
+def spectral_laplacian_box(rho: np.ndarray, plan: BoxPlan) -> np.ndarray:
+    """Laplacian, in the scaled coordinates, of the finite Fourier series of rho on the
+    unpadded grid (Sec. 2, last paragraph): axis q has n_q points over the period 2 l_q,
+    so DFT index k of that axis has kappa_q = 2 pi k_s / (2 l_q) = pi k_s / l_q with k_s
+    the signed frequency; one forward and one inverse n_x n_y n_z transform."""
+    rho = np.asarray(rho, dtype=np.float64)
+    kap2 = []
+    for m, lq in zip(plan.n, plan.l):
+        idx = np.arange(m)
+        ks = np.where(idx < (m + 1) // 2, idx, idx - m).astype(np.float64)
+        kap2.append((math.pi * ks / lq) ** 2)
+    lap = kap2[2][:, None, None] + kap2[1][None, :, None] + kap2[0][None, None, :]
+    spec = fft.fftn(rho)
+    spec *= -lap
+    return np.ascontiguousarray(fft.ifftn(spec, overwrite=True).real)
+
+
+def solve_box_literal(rho: np.ndarray, plan: BoxPlan) -> np.ndarray:
+    """The paper's literal order on a box (Sec. 2): I_1 by the padded transform with the
+    Gaussian-sum G-tensor alone, then I_delta = C0 rho + C2 Laplace(rho) with the
+    Laplacian from the unpadded transform pair; u = lambda^2 (I_1 + I_delta)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    i1 = solve_box(rho, plan, correction=False) / plan.lam ** 2
+    i_delta = plan.C0 * rho + plan.C2 * spectral_laplacian_box(rho, plan)
+    return plan.lam ** 2 * (i1 + i_delta)

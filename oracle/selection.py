@@ -1,6 +1,7 @@
 """Oracle for the grid-selection pieces (TEST INFRASTRUCTURE ONLY).
 
-Plain FP64 numpy definitions that the tests hold the GPU kernels to:
+Plain FP64 definitions (transforms by the oracle's own FFT) that the tests hold the GPU
+kernels to:
 
 * ``spectral_tail``  -- eta = sqrt(E_shell / E_total) of the zero-padded (2N)^3 DFT of the
   density, E_shell the energy where max(|kx|, |ky|, |kz|) >= N - N/8 (signed frequencies of
@@ -17,13 +18,15 @@ import math
 
 import numpy as np
 
+from . import fft
+
 H = 64
 
 
 def spectral_tail(rho):
     N = rho.shape[0]
     M = 2 * N
-    F = np.fft.fftn(np.asarray(rho, np.float64), s=(M, M, M))
+    F = fft.fftn(np.asarray(rho, np.float64), s=(M, M, M))
     e = np.abs(F) ** 2
     k = np.abs(np.where(np.arange(M) < N, np.arange(M), np.arange(M) - M))
     kinf = np.maximum(np.maximum(k[:, None, None], k[None, :, None]), k[None, None, :])
@@ -33,9 +36,10 @@ def spectral_tail(rho):
 
 def features32(sample):
     s = np.asarray(sample, np.float64).reshape(32, 32, 32)
-    F = np.fft.fftn(s)
+    F = fft.fftn(s)
     p = np.abs(F) ** 2
-    k = np.fft.fftfreq(32, d=1.0 / 32)
+    idx = np.arange(32)
+    k = np.where(idx < 16, idx, idx - 32).astype(np.float64)   # signed frequency
     kr = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
     b = np.minimum((kr / (16 * math.sqrt(3.0)) * 64).astype(int), 63)
     pw = np.bincount(b.ravel(), weights=p.ravel(), minlength=64)

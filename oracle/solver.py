@@ -7,23 +7,17 @@ length per axis; I_delta is the near-zone Taylor correction.
 Normalisation (not printed in the paper; derived from Sec. 2).  On the padded period-4
 scaled box the Fourier coefficients are rho_hat_k = DFT(P)_k / (2N)^3, where P is the
 density zero padded to (2N)^3 with the data at indices 0..N-1 per axis, and
-I_1(x_m) = sum_k rho_hat_k G_k exp(i kappa.(x_m - x_0)).  So, with numpy's unnormalised
-forward and 1/(2N)^3-normalised inverse transforms,
+I_1(x_m) = sum_k rho_hat_k G_k exp(i kappa.(x_m - x_0)).  So, with the unnormalised
+forward and 1/(2N)^3-normalised inverse transforms (the oracle's own FFT, ``fft``),
 
     u = lambda^2 * Re(IFFT(G_tot * FFT(P)))[0:N, 0:N, 0:N].
 
 Arrays are indexed [z, y, x] (x fastest), the layout of the library's buffers.
 """
-import os
-
 import numpy as np
-import scipy.fft as sfft
 
+from . import fft
 from .gtensor import OraclePlan, make_plan, symbol
-
-
-def _workers():
-    return int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
 
 
 def solve(rho: np.ndarray, L: float, tol: float, plan: OraclePlan = None,
@@ -39,9 +33,9 @@ def solve(rho: np.ndarray, L: float, tol: float, plan: OraclePlan = None,
     M = 2 * N
     if G is None:
         G = symbol(plan, correction=correction)
-    spec = sfft.fftn(rho, s=(M, M, M), workers=_workers())
+    spec = fft.fftn(rho, s=(M, M, M))
     spec *= G
-    u = sfft.ifftn(spec, workers=_workers())
+    u = fft.ifftn(spec, overwrite=True)
     return plan.lam ** 2 * np.ascontiguousarray(u.real[:N, :N, :N])
 
 
@@ -50,12 +44,13 @@ def spectral_laplacian(rho: np.ndarray, L: float) -> np.ndarray:
     scaled coordinates, by one forward and one inverse N^3 FFT (Sec. 2, last paragraph;
     Sec. 3 counts this FFT pair)."""
     N = rho.shape[0]
-    k = np.fft.fftfreq(N, d=1.0 / N)          # integer frequencies, -N/2 .. N/2-1
+    idx = np.arange(N)
+    k = np.where(idx < (N + 1) // 2, idx, idx - N)   # signed frequency of DFT index idx
     kap2 = (np.pi * k) ** 2                    # period 2: kappa = 2 pi k / 2
     lap = kap2[:, None, None] + kap2[None, :, None] + kap2[None, None, :]
-    spec = sfft.fftn(rho, workers=_workers())
+    spec = fft.fftn(rho)
     spec *= -lap
-    return np.ascontiguousarray(sfft.ifftn(spec, workers=_workers()).real)
+    return np.ascontiguousarray(fft.ifftn(spec, overwrite=True).real)
 
 
 def solve_literal_correction(rho: np.ndarray, L: float, tol: float,

@@ -107,23 +107,9 @@ def test_box_literal_correction_and_warp_form(torch_cuda):
         assert rel_l2(u2, u0) < 1e-6
 
 
-def folded_literal(rho, plan):
-    """The literal correction of a box placed at the all-even padded frequencies (as pinned
-    for the cube in test_literal_fold.py), per-axis kappa = pi k / (2 l_q)."""
-    import scipy.fft as sfft
-    from oracle.gtensor import signed_freq
-    nx, ny, nz = plan.n
-    ks = [signed_freq(m) for m in (nx, ny, nz)]
-    kap2 = [(0.5 * math.pi * k / lq) ** 2 for k, lq in zip(ks, plan.l)]
-    ev = [k % 2 == 0 for k in ks]
-    E = ev[2][:, None, None] & ev[1][None, :, None] & ev[0][None, None, :]
-    K2 = kap2[2][:, None, None] + kap2[1][None, :, None] + kap2[0][None, None, :]
-    G = obox.box_symbol(plan, correction=False) + np.where(E, 8.0 * (plan.C0 - plan.C2 * K2), 0.0)
-    spec = sfft.fftn(rho, s=(2 * nz, 2 * ny, 2 * nx)) * G
-    return plan.lam ** 2 * sfft.ifftn(spec).real[:nz, :ny, :nx]
-
-
 def test_box_literal_f64(torch_cuda):
+    """The literal correction on a box against the oracle's literal box solve (the Gaussian-sum
+    convolution plus C0 rho + C2 Laplace(rho) from its own unpadded transform pair)."""
     from paper_1612_01799_gb300 import Plan
     N, tol = 32, 1e-10
     op = obox.make_box_plan(N, T2[0], T2[1], tol)
@@ -133,7 +119,7 @@ def test_box_literal_f64(torch_cuda):
         p.correction = "literal"
         for rho in (rng.uniform(-1, 1, (N, N, N)), checker):
             u = gpu(torch_cuda, p, rho)
-            assert rel_l2(u, folded_literal(rho, op)) <= TOL["f64"]
+            assert rel_l2(u, obox.solve_box_literal(rho, op)) <= TOL["f64"]
             assert rel_l2(u, obox.solve_box(rho, op)) > 2e-11   # the placements differ by 2e-10 and 1e-8
 
 

@@ -6,11 +6,12 @@ Gaussian-sum symbol, gives the same potential on the kept N^3 points.  These CPU
 the oracle's spectral Laplacian to plane waves and the folding to the oracle's literal
 solve, and check that the two correction placements differ enough for the GPU parity
 tests to tell them apart."""
+import math
+
 import numpy as np
 import pytest
-import scipy.fft as sfft
 
-from oracle import gtensor, solver
+from oracle import box as obox, fft, gtensor, solver
 
 
 def rel_l2(a, b):
@@ -27,8 +28,8 @@ def folded_solve(rho, plan, factor=8.0):
     even = k % 2 == 0
     E = even[:, None, None] & even[None, :, None] & even[None, None, :]
     G = gtensor.symbol(plan, correction=False) + np.where(E, factor * (plan.C0 - plan.C2 * K2), 0.0)
-    spec = sfft.fftn(rho, s=(M, M, M)) * G
-    return plan.lam ** 2 * sfft.ifftn(spec).real[:N, :N, :N]
+    spec = fft.fftn(rho, s=(M, M, M)) * G
+    return plan.lam ** 2 * fft.ifftn(spec).real[:N, :N, :N]
 
 
 def densities(N, seed=1):
@@ -76,3 +77,30 @@ def test_planted_missing_factor_8_is_caught():
     rho = densities(N)["noise"]
     lit = solver.solve_literal_correction(rho, L, 1e-10, plan=plan)
     assert rel_l2(folded_solve(rho, plan, factor=1.0), lit) > 1e-9
+
+
+def folded_box_solve(rho, plan, factor=8.0):
+    """The same reading on a box: 8 (C0 - C2 |kappa|^2) at the padded frequencies whose three
+    indices are all even, kappa_q = pi k / (2 l_q) per axis."""
+    nx, ny, nz = plan.n
+    ks = [gtensor.signed_freq(m) for m in (nx, ny, nz)]
+    kap2 = [(0.5 * math.pi * k / lq) ** 2 for k, lq in zip(ks, plan.l)]
+    ev = [k % 2 == 0 for k in ks]
+    E = ev[2][:, None, None] & ev[1][None, :, None] & ev[0][None, None, :]
+    K2 = kap2[2][:, None, None] + kap2[1][None, :, None] + kap2[0][None, None, :]
+    G = obox.box_symbol(plan, correction=False) + np.where(E, factor * (plan.C0 - plan.C2 * K2), 0.0)
+    spec = fft.fftn(rho, s=(2 * nz, 2 * ny, 2 * nx)) * G
+    return plan.lam ** 2 * fft.ifftn(spec).real[:nz, :ny, :nx]
+
+
+@pytest.mark.parametrize("n", [(8, 8, 8), (8, 10, 12), (12, 9, 16)])
+def test_box_folded_symbol_equals_box_literal_transform_pair(n):
+    """On the box of Table 2 with n_q per axis: the folded placement against the oracle's
+    literal box solve (its own unpadded transform pair with kappa_q = pi k / l_q)."""
+    plan = obox.make_box_plan(n, (-3.0, -2.0, -1.0), (2.0, 3.5, 5.0), 1e-10)
+    rng = np.random.default_rng(12)
+    checker = np.fromfunction(lambda i, j, l: (-1.0) ** (i + j + l), (n[2], n[1], n[0]))
+    for rho in (rng.uniform(-1, 1, (n[2], n[1], n[0])), checker):
+        lit = obox.solve_box_literal(rho, plan)
+        assert rel_l2(folded_box_solve(rho, plan), lit) < 1e-14
+        assert rel_l2(folded_box_solve(rho, plan, factor=1.0), lit) > 1e-10

@@ -110,3 +110,44 @@ def test_planted_cube_factor_on_every_axis_is_caught():
     assert rel_inf(box.solve_box(rho, p), ue) < 2e-4
     bad = dataclasses.replace(p, A=tuple(gtensor.a_table(p.gs.tau, m) for m in p.n))
     assert rel_inf(box.solve_box(rho, bad), ue) > 1e-2
+
+
+def test_box_spectral_laplacian_plane_waves():
+    """cos(pi k x'_q / l_q) on axis q (n_q points over the scaled period 2 l_q) is an
+    eigenfunction of the unpadded spectral Laplacian with eigenvalue -(pi k / l_q)^2."""
+    p = box.make_box_plan((8, 10, 12), (-2.0, -4.0, -6.0), (2.0, 4.0, 6.0), 1e-10)
+    shape = (12, 10, 8)
+    for q in range(3):
+        xs = (box.axis(p, q) - 0.5 * (p.lo[q] + p.hi[q])) / p.lam     # scaled coordinate
+        for k in range(0, (p.n[q] - 1) // 2 + 1):
+            f = np.cos(math.pi * k * xs / p.l[q])
+            sh = [1, 1, 1]
+            sh[2 - q] = p.n[q]
+            F = np.broadcast_to(f.reshape(sh), shape).copy()
+            lam2 = (math.pi * k / p.l[q]) ** 2
+            np.testing.assert_allclose(box.spectral_laplacian_box(F, p), -lam2 * F,
+                                       atol=1e-11 * max(1.0, lam2))
+
+
+def test_box_literal_reduces_to_cube_literal():
+    N, L = 10, 4.0
+    pb = box.make_box_plan(N, [-L] * 3, [L] * 3, 1e-10)
+    rho = np.random.default_rng(9).uniform(-1, 1, (N, N, N))
+    ub = box.solve_box_literal(rho, pb)
+    uc = solver.solve_literal_correction(rho, L, 1e-10, plan=gtensor.make_plan(N, L, 1e-10))
+    assert rel_inf(ub, uc) < 1e-14
+
+
+def test_box_literal_closed_form_and_placement_gap():
+    """Table 6's box with different n_q: the literal order meets the closed form as the
+    folded one does, and for a noise density the two placements differ far above the FP64
+    parity tolerance (the GPU parity tests can tell them apart)."""
+    p = box.make_box_plan((64, 128, 192), (-2, -4, -6), (2, 4, 6), 1e-12)
+    rho, ue = aniso_case(p, (0.10, 0.20, 0.30))
+    e_lit = rel_inf(box.solve_box_literal(rho, p), ue)
+    e_fold = rel_inf(box.solve_box(rho, p), ue)
+    assert e_lit < 2e-4 and 0.5 < e_lit / e_fold < 2.0
+    q = box.make_box_plan((12, 16, 20), (-3.0, -2.0, -1.0), (2.0, 3.5, 5.0), 1e-10)
+    noise = np.random.default_rng(10).uniform(-1, 1, (20, 16, 12))
+    lit, fold = box.solve_box_literal(noise, q), box.solve_box(noise, q)
+    assert np.linalg.norm(lit - fold) / np.linalg.norm(lit) > 1e-10
