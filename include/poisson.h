@@ -344,34 +344,54 @@ int poisson_select_n(poisson_selector s, const float *sample32_d, int count, dou
 
 /*
  * A solve that allocates nothing.  The paper has no counterpart: this entry point exists
- * for callers that cannot allocate device memory when they solve, for example code that
- * issues work while a stream is captured in global capture mode (cudaMalloc is not
- * allowed then), a real-time loop that must not enter an allocator, or a process whose
- * device memory is reserved by a framework's caching allocator.  It needs no plan: the
- * symbol table, the twiddles and the workspace live in one static device array of
- * POISSON_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit, and
- * the host-side setup uses fixed static host arrays.  No cudaMalloc, cudaFree or other
- * allocating routine is called.
+ * for callers that may not allocate device memory when they solve, for example a
+ * real-time loop that must not enter an allocator (an allocation can take unbounded
+ * time), or a process whose device memory is reserved by a framework's caching allocator
+ * (a cudaMalloc there fails, or forces the framework to give memory back).  It needs no
+ * plan: the symbol table, the twiddles, the workspace and a status word live in one static
+ * device array of POISSON_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * until exit, and the host-side setup uses fixed static host arrays.  No cudaMalloc,
+ * cudaFree or other allocating routine is called.
  *   N, L, tol, dtype  as for poisson_plan_create, with N <= POISSON_NOALLOC_MAX_N;
  *                     a larger N returns POISSON_ERR_UNSUPPORTED.
  *   rho_d, u_d        device pointers to N^3 values of dtype (u_d may equal rho_d).
  *   stream            cudaStream_t as void*.
- * The first call on a device looks up the array's device address; the first call with a
- * given (N, L, tol, dtype) on a device (and the next one after a call with other
- * parameters) also computes the tables on the host, copies them into the array and
- * synchronises `stream`.  Make those set-up calls before any stream capture.  Later calls
- * with the same parameters only launch the five solve kernels, stream ordered.
+ * The first call on a device looks up the array's device address and clears its status
+ * word; the first call with a given (N, L, tol, dtype) on a device (and the next one after
+ * a call with other parameters) also computes the tables on the host, copies them into the
+ * array and synchronises `stream`.  Make those set-up calls before any stream capture.
+ * Later calls with the same parameters only launch the five solve kernels, stream ordered.
  * The near-field correction is the fused placement (POISSON_KNOB_CORRECTION = 0); the
  * kernel forms are the block forms (knob value 0 of each form knob).
- * All calls share the array and it keeps the last call's contents; nothing in it needs
- * to start at zero (each pass writes every element the next one reads).  Calls that
- * overlap on the GPU (on different streams, or from different threads) race on the
- * array; serialise them.
+ * All calls share the array and it keeps the last call's contents.  Only the status word
+ * must start at zero (the first call on a device clears it, poisson_noalloc_last_status
+ * clears it after reading); the tables and workspace need no clearing, since each pass
+ * writes every element the next one reads.  Calls that overlap on the GPU (on different
+ * streams, or from different threads) race on the array; serialise them.
+ * A bounded device-side wait that gives up during such a solve sets the status word, and
+ * the returned code (launch errors only) cannot show it: read it with
+ * poisson_noalloc_last_status after the solve.
  */
 #define POISSON_NOALLOC_MAX_N 64
 #define POISSON_NOALLOC_SCRATCH_BYTES (32u << 20)
 int poisson_solve_noalloc(int N, double L, double tol, int dtype, const void *rho_d, void *u_d,
                           void *stream);
+
+/*
+ * The status word of the allocation-free solves on the current device: POISSON_OK, or
+ * POISSON_ERR_TIMEOUT if a bounded device-side wait of one of them gave up since the last
+ * read (its result is then undefined).  A non-zero word is cleared.  Synchronises `stream`
+ * (order it after the solves it reports on).  Allocates nothing.
+ */
+int poisson_noalloc_last_status(void *stream);
+
+/*
+ * Test hook: one bounded device-side wait that nothing completes, on the allocation-free
+ * solves' status word, giving up after `polls` polls (1 <= polls <= 2^24, else
+ * POISSON_ERR_ARG) so that poisson_noalloc_last_status then reports POISSON_ERR_TIMEOUT.
+ * No fault, trap or hang.  Allocates nothing.
+ */
+int poisson_noalloc_selftest_wait(long long polls, void *stream);
 
 #ifdef __cplusplus
 }

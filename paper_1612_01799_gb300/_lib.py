@@ -41,6 +41,8 @@ SIGNATURES = {
     "poisson_strerror": (ctypes.c_char_p, [c_int]),
     "poisson_last_cuda_error": (ctypes.c_char_p, []),
     "poisson_solve_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p]),
+    "poisson_noalloc_last_status": (c_int, [c_void_p]),
+    "poisson_noalloc_selftest_wait": (c_int, [ctypes.c_longlong, c_void_p]),
     "poisson_sample_gaussians": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p]),
     "poisson_gaussian_potential": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p,
                                            c_void_p]),

@@ -1,16 +1,19 @@
 // poisson_solve_noalloc: a small-grid solve that allocates nothing.
 //
-// Who needs it: code that must solve while it cannot allocate device memory, for example
-// work issued while a stream is being captured in global capture mode (cudaMalloc is not
-// permitted then), a real-time loop that must not enter an allocator, or a process whose
-// device memory is already reserved by a framework's caching allocator.  A plan
-// (poisson_plan_create) allocates its tables and workspace; this entry point instead
-// keeps everything, symbol table, twiddles and the three workspace buffers, in one
-// file-scope static device array, and its host-side setup uses fixed static host arrays.
-// It calls no cudaMalloc, cudaFree, malloc/new or other allocating routine.
+// Who needs it: code that must solve while it may not allocate device memory, for example
+// a real-time loop that must not enter an allocator (an allocation can take unbounded
+// time), or a process whose device memory is already reserved by a framework's caching
+// allocator (a cudaMalloc there fails or forces the framework to release its cache).  A
+// plan (poisson_plan_create) allocates its tables and workspace; this entry point instead
+// keeps everything, symbol table, twiddles, the three workspace buffers and its status
+// word, in one file-scope static device array, and its host-side setup uses fixed static
+// host arrays.  It calls no cudaMalloc, cudaFree, malloc/new or other allocating routine.
 //
 // The array is allocated with the module: every GPU that loads this library holds its
 // POISSON_NOALLOC_SCRATCH_BYTES until the process exits.  All calls share it.
+// Layout: the status word in the first 256 bytes (a fixed place, so that a set-up for other
+// parameters does not clear a timeout not yet read), then the tables and the workspace of
+// the current parameters.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,6 +32,7 @@ constexpr int kMaxPanels = (kMaxN + 1) / 2 > 16 ? (kMaxN + 1) / 2 : 16;
 constexpr int kMaxNodes = kOrder * kMaxPanels;
 constexpr int kMaxDevices = 64;
 constexpr int kNfit = 4096;
+constexpr size_t kStatusBytes = 256;  // the status word's slot at the start of the array
 const double kPi = 3.141592653589793238462643383279502884;
 
 // The scratch of every call: symbol octant, twiddles, setup inputs and the workspace.
@@ -241,7 +245,7 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
     const size_t K = (size_t)N + 1;
     const int Px = gsp::pitch_for(N);
     const int Ps = gsp::sym_pitch_for(N);
-    size_t off = 0;
+    size_t off = kStatusBytes;
     auto take = [&](size_t bytes) {
         unsigned char *p = st.base + off;
         off = align256(off + bytes);
@@ -260,12 +264,15 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
     dp.w1 = take((size_t)N * N * Px * cx);
     dp.w2 = take((size_t)N * 2 * N * Px * cx);
     dp.w3 = take((size_t)N * 2 * N * Px * cx);
-    dp.status = reinterpret_cast<int *>(take(sizeof(int)));
+    dp.status = reinterpret_cast<int *>(st.base);
     if (off > kScratchBytes) return POISSON_ERR_UNSUPPORTED;
     if (gsp::encode_tma_maps(dp) != cudaSuccess) return POISSON_ERR_CUDA;
 
     cudaError_t e;
-    // Workspace padding columns and the status word start at zero.
+    // The workspace is cleared when the parameters change, so that no value left by a solve
+    // of another size sits in its padding columns.  Nothing reads those columns, and every
+    // element a pass reads was written by the pass before it in the same call, so no result
+    // depends on this clearing.
     if ((e = cudaMemsetAsync(dp.w1, 0, (size_t)(st.base + off - (unsigned char *)dp.w1), s)))
         return map_cuda(e);
     if ((e = cudaMemcpyAsync(dA, h_A, (size_t)S * K * sizeof(double), cudaMemcpyHostToDevice, s)))
@@ -294,6 +301,28 @@ int setup(DeviceState &st, int N, double L, double tol, int dtype, cudaStream_t 
     return POISSON_OK;
 }
 
+// The array's device address on the current device (looked up once per device, with that
+// device current), or an error.  Called with g_mutex held.
+int device_state(DeviceState *&out, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (dev < 0 || dev >= kMaxDevices) return POISSON_ERR_UNSUPPORTED;
+    DeviceState &st = g_state[dev];
+    if (!st.have_addr) {
+        void *ptr = nullptr;
+        if ((e = cudaGetSymbolAddress(&ptr, g_scratch)) != cudaSuccess) return map_cuda(e);
+        // The status word must start at zero; it is cleared here once per device and then
+        // only by poisson_noalloc_last_status.
+        if ((e = cudaMemsetAsync(ptr, 0, kStatusBytes, s)) != cudaSuccess) return map_cuda(e);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+        st.base = static_cast<unsigned char *>(ptr);
+        st.have_addr = true;
+    }
+    out = &st;
+    return POISSON_OK;
+}
+
 }  // namespace
 
 extern "C" int poisson_solve_noalloc(int N, double L, double tol, int dtype, const void *rho_d,
@@ -303,28 +332,50 @@ extern "C" int poisson_solve_noalloc(int N, double L, double tol, int dtype, con
     if (N < 4 || (N & 1) || !(L > 0.0) || !(tol > 0.0) || !std::isfinite(L) || !std::isfinite(tol))
         return POISSON_ERR_ARG;
     if (N > kMaxN || !gsp::n_supported(N)) return POISSON_ERR_UNSUPPORTED;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return map_cuda(e);
-    if (dev < 0 || dev >= kMaxDevices) return POISSON_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_mutex);
-    DeviceState &st = g_state[dev];
-    if (!st.have_addr) {
-        // Once per device, with that device current: the device address of the array.
-        void *ptr = nullptr;
-        if ((e = cudaGetSymbolAddress(&ptr, g_scratch)) != cudaSuccess) return map_cuda(e);
-        st.base = static_cast<unsigned char *>(ptr);
-        st.have_addr = true;
-    }
-    if (!st.have_tables || st.N != N || st.L != L || st.tol != tol || st.dtype != dtype) {
-        st.have_tables = false;
-        int rc = setup(st, N, L, tol, dtype, s);
+    DeviceState *st = nullptr;
+    int rc = device_state(st, s);
+    if (rc) return rc;
+    if (!st->have_tables || st->N != N || st->L != L || st->tol != tol || st->dtype != dtype) {
+        st->have_tables = false;
+        rc = setup(*st, N, L, tol, dtype, s);
         if (rc) return rc;
     }
     gsp::PtrArray in, out;
     in.p[0] = rho_d;
     out.p[0] = u_d;
     for (int i = 1; i < gsp::kMaxBatch; ++i) in.p[i] = out.p[i] = nullptr;
-    return map_cuda(gsp::launch_solve(st.dp, in, out, 1, s, nullptr));
+    return map_cuda(gsp::launch_solve(st->dp, in, out, 1, s, nullptr));
+}
+
+extern "C" int poisson_noalloc_last_status(void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    DeviceState *st = nullptr;
+    int rc = device_state(st, s);
+    if (rc) return rc;
+    static int h_status;  // static: the read allocates nothing; g_mutex serialises its use
+    h_status = 0;
+    cudaError_t e = cudaMemcpyAsync(&h_status, st->base, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (h_status == 0) return POISSON_OK;
+    const int h = h_status;
+    e = cudaMemsetAsync(st->base, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return map_cuda(e);
+    return (h & gsp::kStatusTimeoutBit) ? POISSON_ERR_TIMEOUT : POISSON_ERR_CUDA;
+}
+
+extern "C" int poisson_noalloc_selftest_wait(long long polls, void *stream) {
+    if (polls < 1 || polls > (1ll << 24)) return POISSON_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    DeviceState *st = nullptr;
+    int rc = device_state(st, s);
+    if (rc) return rc;
+    static gsp::DevicePlan probe;  // only its status pointer is used
+    probe.status = reinterpret_cast<int *>(st->base);
+    return map_cuda(gsp::launch_wait_selftest(probe, polls, s));
 }
