@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Throughput of the free-space Poisson solve: grid points per second per solve (N^3 / solve
 time) on the 4-anisotropic-Gaussian workload (box [-10, 10]^3, N = 256, padded 512^3),
-FP32 split-precision path, with the FP64 path, the per-pass HBM roofline, an end-to-end
-figure through the C-ABI on host buffers, and the FP64 CPU oracle as a reported baseline.
+FP32 split-precision path, with the FP64 path, the rel-L2 and rel-l-infinity error of both
+against the FP64 oracle, the per-pass HBM roofline, an end-to-end figure through the C-ABI
+on host buffers, and the FP64 CPU oracle as a reported baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -53,29 +54,47 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+# Algorithmic bytes per grid point of each pass in FP32 (the per-unit figures of the five-pass
+# design with the middle pass fused and the zero halves pruned, (N+1) taken as N): x forward
+# reads rho (4) and writes the Hermitian half spectrum (8); y forward reads it (8) and writes
+# the y-padded spectrum (16); the fused z pass reads and writes that (16 + 16); the inverse
+# passes mirror the forward ones.  FP64 doubles every figure.  The z pass's symbol octant is
+# this implementation's choice, not algorithmic traffic, and is reported on its own.
+BYTES_PER_POINT_F32 = [12, 24, 32, 24, 12]
+
+
 def pass_bytes(N, s):
-    """Algorithmic DRAM bytes of each pass (each operand read or written once), s = bytes
-    per real value.  Complex workspace rows hold the N+1 Hermitian x frequencies."""
-    K = N + 1
-    c = 2 * s
-    return [N ** 3 * s + N * N * K * c,                 # x forward: rho in, w1 out
-            N * N * K * c + 2 * N * N * K * c,          # y forward: w1 in, w2 out
-            2 * (2 * N * N * K * c) + K ** 3 * s,       # z fused: w2 in, w3 out, symbol octant
-            2 * N * N * K * c + N * N * K * c,          # y inverse: w3 in, w1 out
-            N * N * K * c + N ** 3 * s]                 # x inverse: w1 in, u out
+    """Algorithmic DRAM bytes of each pass of one solve, s = bytes per real value."""
+    return [b * (s // 4) * N ** 3 for b in BYTES_PER_POINT_F32]
+
+
+def symbol_bytes(N, s):
+    """Bytes of the symbol octant the z pass reads (N+1)^3 reals: implementation traffic."""
+    return (N + 1) ** 3 * s
 
 
 def pass_table(N, s, per_pass, xyform, names):
     """(pass, kernel, ms, algorithmic bytes) of the launches of one solve.  With the fused
-    x-y form the forward x and y passes are one kernel (rho in, w2 out: w1 stays in L2) and
-    so are the inverse y and x passes (w3 in, u out); their times sit in entries 0 and 3."""
+    x-y form the forward x and y passes are one kernel (rho in, y-padded spectrum out: the x
+    spectrum stays in L2) and so are the inverse y and x passes; their times sit in entries 0
+    and 3."""
     b = pass_bytes(N, s)
     if not xyform:
         return [(PASSES[i], names[i], per_pass[i], b[i]) for i in range(5)]
-    K, c = N + 1, 2 * s
-    return [("xy_forward", "k_xy_fwd", per_pass[0], N ** 3 * s + 2 * N * N * K * c),
+    w1 = 8 * (s // 4) * N ** 3     # one write or one read of the x spectrum
+    return [("xy_forward", "k_xy_fwd", per_pass[0], b[0] + b[1] - 2 * w1),
             (PASSES[2], names[2], per_pass[2], b[2]),
-            ("yx_inverse", "k_yx_inv", per_pass[3], 2 * N * N * K * c + N ** 3 * s)]
+            ("yx_inverse", "k_yx_inv", per_pass[3], b[3] + b[4] - 2 * w1)]
+
+
+def errors(u, ref):
+    """rel-L2 and rel-l-infinity (the paper's E, Sec. 5) of u against ref, FP64."""
+    import numpy as np
+    u = np.asarray(u, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    d = u - ref
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "rel_linf": float(np.abs(d).max() / np.abs(ref).max())}
 
 
 def load_peaks():
@@ -168,28 +187,36 @@ def aggregate_rate(world, N, seconds):
     return world * N ** 3 / seconds
 
 
-def cpu_oracle_baseline(N, steps=1):
-    """The oracle as it stands on the host cores: setup once (untimed, as for the GPU plan),
-    then `steps` full solves of the same workload.  Returns (pts/s, cores, seconds)."""
-    from oracle import gtensor, solver as osolver
-    from paper_1612_01799_gb300 import densities as D
-    w = D.config_aniso4(N=N)
-    rho = w.sample()
-    plan = gtensor.make_plan(N, w.L, TOL32)
+def oracle_reference(rho, N, L, tol):
+    """The oracle as it stands on the host cores: setup untimed (as for the GPU plan), then one
+    full FP64 solve of the workload, timed.  Returns (potential, pts/s, cores, seconds)."""
+    from oracle import fft, gtensor, solver as osolver
+    plan = gtensor.make_plan(N, L, tol)
     G = gtensor.symbol(plan)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        osolver.solve(rho, w.L, TOL32, plan=plan, G=G)
+    u = osolver.solve(rho, L, tol, plan=plan, G=G)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
-    return steps * N ** 3 / dt, cores, dt
+    return u, N ** 3 / dt, fft.threads(), dt
+
+
+def oracle_lines(rho, N, L, tol, lines):
+    """Sampled output lines u[z, y, :] of the oracle's real-space evaluation of the same
+    discrete convolution (for grids whose FFT oracle would hold 17 GB)."""
+    from oracle import direct, gtensor
+    return direct.sample_lines(rho, gtensor.make_plan(N, L, tol), lines)
+
+
+# Output lines (z, y) of the N = 512 accuracy sample: both tile edges of the column passes,
+# the box faces and the interior, 8 distinct z planes.
+LINES_512 = [(0, 0), (0, 511), (7, 8), (7, 300), (64, 63), (64, 64), (255, 256), (255, 100),
+             (256, 255), (256, 17), (300, 1), (300, 400), (448, 447), (448, 0), (511, 511), (511, 256)]
 
 
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import gtensor, solver as osolver
+    from oracle import fft, gtensor, solver as osolver
     from paper_1612_01799_gb300 import densities as D
     N = args.N
     w = D.config_aniso4(N=N)
@@ -205,7 +232,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = N ** 3 / (ms / 1e3)
-    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+    cores = fft.threads()
     sample = ("one full FP64 oracle solve per step of the N=%d workload (the oracle's own FFT of the "
               "padded %d^3 grid, symbol product, inverse FFT, crop); setup untimed" % (N, 2 * N))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -331,13 +358,18 @@ def run_large(torch, dev, flush, steps, warmup, peak, N=512):
             forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form],
                      "xy": XY_FORMS[plan.xy_form]}
             xyform = plan.xy_form
+            u = out.view(N, N, N)
+            got = np.stack([u[z, y, :].cpu().numpy() for z, y in LINES_512])
+        err = errors(got, oracle_lines(sample, N, wl.L, tol, LINES_512))
+        err["vs"] = ("FP64 oracle (real-space evaluation of the same discrete convolution) on %d "
+                     "output lines of %d points" % (len(LINES_512), N))
         ms = statistics.mean(totals)
         per = [statistics.mean(p[i] for p in passes) for i in range(5)]
         rows = pass_table(N, 4 if dtype == "f32" else 8, per, xyform, [None] * 5)
         return {"value": N ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": nsteps, "dtype": dtype,
                 "passes": [{"pass": n, "ms": t, "GB_s": b / (t * 1e-3) / 1e9,
                             "frac": b / (t * 1e-3) / 1e9 / peak} for n, _, t, b in rows],
-                "forms": forms}
+                "forms": forms, "accuracy": err}
 
     r = one("f32", TOL32, steps)
     r["f64"] = one("f64", TOL64, 3)
@@ -456,19 +488,36 @@ def run_ours(args):
         r64 = results["f64"]
         rows64 = pass_table(N, 8, r64["per_pass"], r64["xy_form"], [None] * 5)
         gbs64 = [b / (t * 1e-3) / 1e9 for _, _, t, b in rows64]
+        # Accuracy of the timed outputs against the FP64 oracle on the whole grid; the oracle's
+        # solve with the FP32 plan's tolerance is also the CPU baseline (timed, setup untimed).
+        acc, cpu = {}, None
+        if not args.no_accuracy and world == 1:
+            for dtype, tol in (("f32", TOL32), ("f64", TOL64)):
+                ref, v, cores, dt = oracle_reference(rho64, N, L_BOX, tol)
+                acc[dtype] = errors(results[dtype]["out"].cpu().numpy(), ref)
+                acc[dtype]["vs"] = "FP64 oracle, whole %d^3 grid, plan tolerance %g" % (N, tol)
+                if dtype == "f32":
+                    cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": "1 full FP64 oracle solve of the same N=%d workload (its own "
+                                     "FFT of the padded %d^3 grid, symbol product, inverse, crop; "
+                                     "setup untimed), %.1f s" % (N, 2 * N, dt)}
+                del ref
         line = {
             "metric": METRIC, "value": aggregate_rate(world, N, r32["ms"] * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(N, "f32"),
+            "accuracy": acc.get("f32"),
             "roofline": {"bound": "hbm", "achieved": gbs[dom], "peak": peak, "unit": "GB/s",
                          "frac": gbs[dom] / peak, "traffic": traffic,
                          "kernel": rows32[dom][1], "algorithmic_bytes": rows32[dom][3],
+                         "bytes_per_point": rows32[dom][3] / N ** 3,
+                         "symbol_bytes": symbol_bytes(N, 4) if rows32[dom][0] == PASSES[2] else 0,
                          "peak_source": peak_kind},
             "passes": [{"pass": n, "kernel": k, "ms": t, "GB_s": gbs[i], "frac": gbs[i] / peak}
                        for i, (n, k, t, _) in enumerate(rows32)],
             "f64": {"value": aggregate_rate(world, N, r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
-                    "steps": r64["steps"],
+                    "steps": r64["steps"], "accuracy": acc.get("f64"),
                     "passes": [{"pass": n, "ms": t, "GB_s": gbs64[i], "frac": gbs64[i] / peak}
                                for i, (n, _, t, _) in enumerate(rows64)]},
             "e2e": {"value": aggregate_rate(world, N, e2e_s), "unit": UNIT,
@@ -493,11 +542,8 @@ def run_ours(args):
             line["batched"] = run_batched(torch, dev, max(3, args.steps // 2), args.warmup)
         if not args.no_selector and world == 1:
             line["selector"] = run_selector()
-        if not args.no_cpu_baseline and world == 1:
-            v, cores, dt = cpu_oracle_baseline(N, steps=args.cpu_steps)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": "%d full FP64 oracle solve(s) of the same N=%d workload "
-                                              "(setup untimed), %.1f s" % (args.cpu_steps, N, dt)}
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     for r in results.values():
         r["plan"].close()
@@ -513,8 +559,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
-    ap.add_argument("--cpu-steps", type=int, default=4)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the oracle solves (accuracy figures and the CPU baseline)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the N=512 single-solve section")
     ap.add_argument("--no-selector", action="store_true")

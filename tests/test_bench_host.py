@@ -10,19 +10,27 @@ if ROOT not in sys.path:
 
 def test_pass_bytes_sum():
     import bench
-    N, s = 256, 4
-    K = N + 1
-    b = bench.pass_bytes(N, s)
-    # Every operand read or written once: rho and u (s N^3 each), w1 twice each way
-    # (2s N^2 K per touch), w2 and w3 (4s N^2 K per touch, three touches each), the symbol
-    # octant (s K^3) once.
-    assert sum(b) == 2 * s * N ** 3 + 4 * (2 * s * N * N * K) + 4 * (4 * s * N * N * K) + s * K ** 3
+    N = 256
+    # Per grid point in FP32: rho and u (4 B each), the x spectrum written and read twice
+    # each way (8 B per touch), the y-padded spectrum written and read twice each way
+    # (16 B per touch): 104 B; FP64 doubles it.  The symbol octant is not algorithmic.
+    assert sum(bench.pass_bytes(N, 4)) == 104 * N ** 3
+    assert sum(bench.pass_bytes(N, 8)) == 208 * N ** 3
+    assert bench.pass_bytes(N, 4)[2] == 32 * N ** 3
+    assert bench.symbol_bytes(N, 4) == 4 * (N + 1) ** 3
+
+
+def test_errors_are_relative_l2_and_linf():
+    import numpy as np
+    import bench
+    ref = np.array([3.0, -4.0, 0.0])
+    e = bench.errors(ref + np.array([0.0, 0.0, 0.5]), ref)
+    assert abs(e["rel_l2"] - 0.1) < 1e-15 and abs(e["rel_linf"] - 0.125) < 1e-15
 
 
 def test_pass_table_fused_drops_w1():
     import bench
     N, s = 192, 4
-    K = N + 1
     per = [0.1, 0.2, 0.3, 0.4, 0.5]
     names = ["a", "b", "c", "d", "e"]
     sep = bench.pass_table(N, s, per, 0, names)
@@ -30,7 +38,7 @@ def test_pass_table_fused_drops_w1():
     fused = bench.pass_table(N, s, per, 1, names)
     assert [r[1] for r in fused] == ["k_xy_fwd", "c", "k_yx_inv"]
     assert [r[2] for r in fused] == [0.1, 0.3, 0.4]
-    w1 = 2 * s * N * N * K  # one write or one read of w1
+    w1 = 2 * s * N ** 3     # one write or one read of the x spectrum (N^3 complex)
     b = bench.pass_bytes(N, s)
     assert fused[0][3] == b[0] + b[1] - 2 * w1
     assert fused[2][3] == b[3] + b[4] - 2 * w1
