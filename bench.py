@@ -35,6 +35,8 @@ PASSES = ["x_forward", "y_forward", "z_fwd_symbol_inv", "y_inverse", "x_inverse"
 Z_FORMS = ["direct", "split", "warp"]
 Y_FORMS = ["block", "warp"]
 XY_FORMS = ["separate", "fused"]
+# arithmetic of a plan: FP32; FP64 on the FP64 pipe; double-float (FP32 pairs, 48-bit significand)
+ARITH_NAMES = {"f32": "fp32", "f64": "fp64", "df": "double-float (FP32 pairs, 48-bit significand)"}
 Z_KERNELS = ["k_z_symbol", "k_z_split", "k_z_warp"]
 # forms of the x and y passes: "block" (tiles staged in shared memory, columns or rows spread
 # over a block) and "warp" (one warp or half-warp per column or row pair)
@@ -356,7 +358,7 @@ def run_large(torch, dev, flush, steps, warmup, peak, N=512):
             totals, passes = time_solves(torch, plan, rho, out, nsteps, warmup, flush)
             plan.last_status()
             forms = {"z": Z_FORMS[plan.z_form], "y": Y_FORMS[plan.y_form], "x": Y_FORMS[plan.x_form],
-                     "xy": XY_FORMS[plan.xy_form]}
+                     "xy": XY_FORMS[plan.xy_form], "arith": ARITH_NAMES[plan.arith]}
             xyform = plan.xy_form
             u = out.view(N, N, N)
             got = np.stack([u[z, y, :].cpu().numpy() for z, y in LINES_512])
@@ -452,7 +454,7 @@ def run_ours(args):
         ms = max_over_ranks(torch, statistics.mean(totals), dev)
         per_pass = [statistics.mean(p[i] for p in passes) for i in range(5)]
         results[dtype] = {"ms": ms, "per_pass": per_pass, "steps": steps, "z_form": plan.z_form, "y_form": plan.y_form, "x_form": plan.x_form,
-                          "xy_form": plan.xy_form,
+                          "xy_form": plan.xy_form, "arith": plan.arith,
                           "clocks": sampler.summary() if sampler else None, "plan": plan,
                           "rho": rho_t, "out": out_t}
 
@@ -517,7 +519,7 @@ def run_ours(args):
             "passes": [{"pass": n, "kernel": k, "ms": t, "GB_s": gbs[i], "frac": gbs[i] / peak}
                        for i, (n, k, t, _) in enumerate(rows32)],
             "f64": {"value": aggregate_rate(world, N, r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
-                    "steps": r64["steps"], "accuracy": acc.get("f64"),
+                    "steps": r64["steps"], "accuracy": acc.get("f64"), "arith": ARITH_NAMES[r64["arith"]],
                     "passes": [{"pass": n, "ms": t, "GB_s": gbs64[i], "frac": gbs64[i] / peak}
                                for i, (n, _, t, _) in enumerate(rows64)]},
             "e2e": {"value": aggregate_rate(world, N, e2e_s), "unit": UNIT,

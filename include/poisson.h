@@ -66,6 +66,13 @@ enum {
  *         the maximum relative error of U_GS on [delta, 2 sqrt(3)] (Sec. 2 and 3).
  *   dtype POISSON_F32 or POISSON_F64.
  * The plan owns its device memory; poisson_plan_destroy() frees it.
+ * Kernel forms (the POISSON_KNOB_*_FORM knobs) are chosen by timing them on the first plan
+ * of each (device, N, dtype) in the process.  If the environment variable
+ * POISSON_TUNE_CACHE names a file, the choices persist across processes: the file is read
+ * at the first plan creation, a shape found there (for a device of the same name) is not
+ * timed again, and every new choice is appended (first line "gspoisson-tune 1", then one
+ * line "N dtype zform yform xform xyform device-name" per choice).  Unreadable or invalid
+ * lines are ignored; a missing or unwritable file only disables the persistence.
  */
 int poisson_plan_create(poisson_plan *out, int N, double L, double tol, int dtype);
 
@@ -235,6 +242,18 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
  *       differ by terms of order C2 |kappa|^2 at high frequencies.  Setting it recomputes
  *       the plan's symbol table on its device (a temporary device allocation and a
  *       synchronisation) and is not timed; every dtype and N, every kernel form.
+ *   POISSON_KNOB_ARITH  arithmetic of a POISSON_F64 plan: 0 = FP64 (the FP64 pipe);
+ *       1 = double-float, each real an unevaluated sum hi + lo of two FP32 numbers (a
+ *       48-bit significand, unit roundoff 2^-48 = 3.6e-15) computed on the FP32 pipe, with
+ *       the workspace, twiddles and symbol table in that format and rho and u still FP64
+ *       (converted where the x passes read and write them).  The forms of both are the
+ *       block forms (knob value 0 or 1 of the z knob).  Timed at plan creation like the
+ *       forms (the faster is kept); setting it rebuilds the plan's twiddles and symbol
+ *       table on its device (temporary device memory, a synchronisation).  POISSON_F32
+ *       plans have only 0.  The FP32 exponent range limits double-float to values of
+ *       magnitude above about 1e-38 relative to the density's scale: smaller entries
+ *       (deep in the symbol's decay) flush to zero, which is far below the FP64 path's
+ *       1e-12 accuracy bar.
  * poisson_plan_get_knob stores the plan's current value in *value.
  * poisson_plan_set_knob selects a variant for this plan only (no other plan changes):
  * POISSON_ERR_ARG for an unknown knob or value, POISSON_ERR_UNSUPPORTED for a variant that
@@ -246,6 +265,7 @@ int poisson_plan_info(poisson_plan p, double *delta, double *eps, int *n_terms, 
 #define POISSON_KNOB_X_FORM 2
 #define POISSON_KNOB_XY_FORM 3
 #define POISSON_KNOB_CORRECTION 4
+#define POISSON_KNOB_ARITH 5
 int poisson_plan_get_knob(poisson_plan p, int knob, int *value);
 int poisson_plan_set_knob(poisson_plan p, int knob, int value);
 

@@ -72,6 +72,7 @@ KNOB_Y_FORM = 1
 KNOB_X_FORM = 2
 KNOB_XY_FORM = 3
 KNOB_CORRECTION = 4
+KNOB_ARITH = 5
 
 
 def load():

@@ -181,6 +181,25 @@ class Plan:
         _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_XY_FORM, int(value)), "poisson_plan_set_knob")
 
     @property
+    def arith(self):
+        """Arithmetic of the solve: "f32" for an FP32 plan; for an FP64 plan "f64" (the FP64
+        pipe) or "df" (double-float: pairs of FP32 numbers on the FP32 pipe, 48-bit
+        significand), chosen by timing at plan creation."""
+        if self.dtype == "f32":
+            return "f32"
+        v = ctypes.c_int()
+        _lib.check(self._lib.poisson_plan_get_knob(self._h, _lib.KNOB_ARITH, ctypes.byref(v)),
+                   "poisson_plan_get_knob")
+        return ("f64", "df")[v.value]
+
+    @arith.setter
+    def arith(self, value):
+        code = {"f64": 0, "df": 1}.get(value)
+        if code is None or self.dtype != "f64":
+            raise ValueError("arith of an FP64 plan is 'f64' or 'df'")
+        _lib.check(self._lib.poisson_plan_set_knob(self._h, _lib.KNOB_ARITH, code), "poisson_plan_set_knob")
+
+    @property
     def correction(self):
         """Where the near-field correction enters: "fused" (C0 - C2 |kappa|^2 at every
         padded frequency) or "literal" (C0 rho + C2 Laplace(rho) of the N-periodic series,

@@ -14,9 +14,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libgspoisson.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["capi.cpp", "setup.cpp", "passes_f32.cu", "passes_f64.cu",
+SOURCES = ["capi.cpp", "setup.cpp", "passes_f32.cu", "passes_f64.cu", "passes_df.cu",
            "passes_f32_a.cu", "passes_f32_b.cu", "passes_f32_c.cu",
            "passes_f64_a.cu", "passes_f64_b.cu", "passes_f64_c.cu",
+           "passes_df_1.cu", "passes_df_2.cu", "passes_df_3.cu", "passes_df_4.cu", "passes_df_5.cu",
+           "passes_df_6.cu", "passes_df_7.cu", "passes_df_8.cu", "passes_df_9.cu",
            "noalloc.cu", "reduce.cu", "sample.cu", "selector.cu", "selftest.cu", "setup_device.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -3,9 +3,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/poisson.h"
@@ -13,50 +16,38 @@
 #include "solver.h"
 
 namespace gsp {
-cudaError_t solve_f32(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *,
-                      double *, int);
-cudaError_t solve_f64(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *,
-                      double *, int);
-cudaError_t xy_slab_f32(const DevicePlan &, const void *, void *, int, int, cudaStream_t, bool);
-cudaError_t xy_slab_f64(const DevicePlan &, const void *, void *, int, int, cudaStream_t, bool);
+// Per arithmetic (FP32, FP64, double-float) entry points of the pass code.
+#define GSP_ARITH_DECL(sfx)                                                                                        \
+    cudaError_t solve_##sfx(const DevicePlan &, const PtrArray &, const PtrArray &, int, cudaStream_t, cudaEvent_t *, \
+                            double *, int);                                                                        \
+    cudaError_t xy_slab_##sfx(const DevicePlan &, const void *, void *, int, int, cudaStream_t, bool);            \
+    cudaError_t symbol_table_##sfx(const DevicePlan &, const double *, const double *, int, double, double, double, \
+                                   int, cudaStream_t);                                                             \
+    cudaError_t symbol_table_box_##sfx(const DevicePlan &, const double *, const double *, int, double, double,    \
+                                       double, const double *, int, cudaStream_t);                                 \
+    cudaError_t encode_maps_##sfx(DevicePlan &);                                                                   \
+    cudaError_t z_pass_##sfx(const DevicePlan &, cudaStream_t);                                                    \
+    cudaError_t y_passes_##sfx(const DevicePlan &, cudaStream_t);                                                  \
+    cudaError_t x_passes_##sfx(const DevicePlan &, cudaStream_t);                                                  \
+    cudaError_t xy_passes_##sfx(const DevicePlan &, cudaStream_t);
+GSP_ARITH_DECL(f32)
+GSP_ARITH_DECL(f64)
+GSP_ARITH_DECL(df)
+#undef GSP_ARITH_DECL
+
+// The entry point of `name` for p's arithmetic.
+#define GSP_BY_ARITH(p, name, ...)                                                                 \
+    ((p).dtype == POISSON_F32 ? name##_f32(__VA_ARGS__)                                            \
+                              : (p).arith ? name##_df(__VA_ARGS__) : name##_f64(__VA_ARGS__))
+
 cudaError_t launch_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd) {
-    return p.dtype == POISSON_F32 ? xy_slab_f32(p, rho, u, z0, nz, s, fwd) : xy_slab_f64(p, rho, u, z0, nz, s, fwd);
+    return GSP_BY_ARITH(p, xy_slab, p, rho, u, z0, nz, s, fwd);
 }
-cudaError_t symbol_table_f32(const DevicePlan &, const double *, const double *, int, double,
-                             double, double, int, cudaStream_t);
-cudaError_t symbol_table_f64(const DevicePlan &, const double *, const double *, int, double,
-                             double, double, int, cudaStream_t);
-cudaError_t symbol_table_box_f32(const DevicePlan &, const double *, const double *, int, double, double, double,
-                                 const double *, int, cudaStream_t);
-cudaError_t symbol_table_box_f64(const DevicePlan &, const double *, const double *, int, double, double, double,
-                                 const double *, int, cudaStream_t);
-cudaError_t encode_maps_f32(DevicePlan &);
-cudaError_t encode_maps_f64(DevicePlan &);
-cudaError_t z_pass_f32(const DevicePlan &, cudaStream_t);
-cudaError_t z_pass_f64(const DevicePlan &, cudaStream_t);
-cudaError_t y_passes_f32(const DevicePlan &, cudaStream_t);
-cudaError_t y_passes_f64(const DevicePlan &, cudaStream_t);
-cudaError_t x_passes_f32(const DevicePlan &, cudaStream_t);
-cudaError_t x_passes_f64(const DevicePlan &, cudaStream_t);
-cudaError_t xy_passes_f32(const DevicePlan &, cudaStream_t);
-cudaError_t xy_passes_f64(const DevicePlan &, cudaStream_t);
-cudaError_t launch_xy_passes(const DevicePlan &p, cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? xy_passes_f32(p, s) : xy_passes_f64(p, s);
-}
-cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? x_passes_f32(p, s) : x_passes_f64(p, s);
-}
-cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? y_passes_f32(p, s) : y_passes_f64(p, s);
-}
-
-cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? z_pass_f32(p, s) : z_pass_f64(p, s);
-}
-
-cudaError_t encode_tma_maps(DevicePlan &p) {
-    return p.dtype == POISSON_F32 ? encode_maps_f32(p) : encode_maps_f64(p);
-}
+cudaError_t launch_xy_passes(const DevicePlan &p, cudaStream_t s) { return GSP_BY_ARITH(p, xy_passes, p, s); }
+cudaError_t launch_x_passes(const DevicePlan &p, cudaStream_t s) { return GSP_BY_ARITH(p, x_passes, p, s); }
+cudaError_t launch_y_passes(const DevicePlan &p, cudaStream_t s) { return GSP_BY_ARITH(p, y_passes, p, s); }
+cudaError_t launch_z_pass(const DevicePlan &p, cudaStream_t s) { return GSP_BY_ARITH(p, z_pass, p, s); }
+cudaError_t encode_tma_maps(DevicePlan &p) { return GSP_BY_ARITH(p, encode_maps, p); }
 
 static const int kSupportedN[] = {4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 1024};
 
@@ -69,8 +60,7 @@ bool n_supported(int N) {
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
                          cudaStream_t s, cudaEvent_t *ev, double *tail, int skip) {
     if (count < 1 || count > p.max_batch || count > kMaxBatch) return cudaErrorInvalidValue;
-    return p.dtype == POISSON_F32 ? solve_f32(p, rho, u, count, s, ev, tail, skip)
-                                  : solve_f64(p, rho, u, count, s, ev, tail, skip);
+    return GSP_BY_ARITH(p, solve, p, rho, u, count, s, ev, tail, skip);
 }
 
 // Streams that poisson_solve_batched forks independent plan groups onto (per device,
@@ -104,23 +94,127 @@ static cudaError_t fork_pool(int dev, ForkPool **out) {
 cudaError_t launch_symbol_table_box(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
                                     double C0, double C2, double scale, const double *l, int literal,
                                     cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? symbol_table_box_f32(p, dA3, dw, nterms, C0, C2, scale, l, literal, s)
-                                  : symbol_table_box_f64(p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
+    return GSP_BY_ARITH(p, symbol_table_box, p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
 }
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
                                 int nterms, double C0, double C2, double scale, int literal,
                                 cudaStream_t s) {
-    return p.dtype == POISSON_F32 ? symbol_table_f32(p, dA, dw, nterms, C0, C2, scale, literal, s)
-                                  : symbol_table_f64(p, dA, dw, nterms, C0, C2, scale, literal, s);
+    return GSP_BY_ARITH(p, symbol_table, p, dA, dw, nterms, C0, C2, scale, literal, s);
 }
 
 // ---- autotuning of kernel variants --------------------------------------------------------
-// Decisions per (device, N, dtype), made by the first plan of that shape and reused.
+// Decisions per (device, N, dtype), made by the first plan of that shape and reused.  With
+// the environment variable POISSON_TUNE_CACHE naming a file, decisions also persist across
+// processes: the file is read once, and each new decision is appended to it.  Lines are
+//   <N> <dtype> <zform> <yform> <xform> <xyform> <arith> <device name>
+// after a first line "gspoisson-tune 1"; a decision read from the file applies to every
+// device of that name, and lines that do not parse, or name a form that does not exist
+// for their shape, are ignored.
 struct TuneEntry {
-    int dev, N, dtype, zform, yform, xform, xyform;
+    int dev, N, dtype, zform, yform, xform, xyform, arith;
 };
 static std::vector<TuneEntry> g_tune;
 static std::mutex g_tune_mutex;
+
+struct FileTune {
+    std::string name;
+    int N, dtype, zform, yform, xform, xyform, arith;
+};
+static std::vector<FileTune> g_file_tune;
+static bool g_file_tune_read = false;
+static const char *kTuneHeader = "gspoisson-tune 1";
+
+static std::string device_name(int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return std::string();
+    return std::string(prop.name);
+}
+
+static bool forms_valid(int N, int dtype, int arith, int zf, int yf, int xf, int xyf) {
+    return zf >= 0 && zf < 3 && (z_forms(N, dtype, arith) >> zf & 1) && yf >= 0 && yf < 2 &&
+           (y_forms(N, dtype) >> yf & 1) && xf >= 0 && xf < 2 && (x_forms(N, dtype) >> xf & 1) &&
+           xyf >= 0 && xyf < 2 && (xy_forms(N, dtype) >> xyf & 1);
+}
+
+// Called with g_tune_mutex held.
+static void read_tune_file() {
+    if (g_file_tune_read) return;
+    g_file_tune_read = true;
+    const char *path = std::getenv("POISSON_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    bool header = false;
+    while (std::fgets(line, sizeof line, f)) {
+        line[strcspn(line, "\r\n")] = 0;
+        if (!header) {
+            header = std::strcmp(line, kTuneHeader) == 0;
+            if (!header) break;
+            continue;
+        }
+        FileTune t;
+        int used = 0;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %n", &t.N, &t.dtype, &t.zform, &t.yform, &t.xform, &t.xyform,
+                        &t.arith, &used) != 7 ||
+            used <= 0 || !line[used])
+            continue;
+        t.name = line + used;
+        if (!n_supported(t.N) || (t.dtype != POISSON_F32 && t.dtype != POISSON_F64)) continue;
+        if (t.arith != 0 && (t.arith != 1 || t.dtype != POISSON_F64)) continue;
+        if (!forms_valid(t.N, t.dtype, t.arith, t.zform, t.yform, t.xform, t.xyform)) continue;
+        g_file_tune.push_back(t);
+    }
+    std::fclose(f);
+}
+
+// Called with g_tune_mutex held.
+static void append_tune_file(const TuneEntry &t, const std::string &name) {
+    const char *path = std::getenv("POISSON_TUNE_CACHE");
+    if (!path || !*path || name.empty()) return;
+    FILE *f = std::fopen(path, "r");
+    bool fresh = true;
+    if (f) {
+        fresh = std::fgetc(f) == EOF;
+        std::fclose(f);
+    }
+    f = std::fopen(path, "a");
+    if (!f) return;
+    if (fresh) std::fprintf(f, "%s\n", kTuneHeader);
+    std::fprintf(f, "%d %d %d %d %d %d %d %s\n", t.N, t.dtype, t.zform, t.yform, t.xform, t.xyform, t.arith,
+                 name.c_str());
+    std::fclose(f);
+}
+
+// A decision for p's shape on device dev, from this process or the cache file: true and
+// p's forms set, or false.  Called with g_tune_mutex held.
+static bool lookup_tune(DevicePlan &p, int dev) {
+    for (const TuneEntry &t : g_tune)
+        if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
+            p.zform = t.zform;
+            p.yform = t.yform;
+            p.xform = t.xform;
+            p.xyform = t.xyform;
+            p.arith = t.arith;
+            return true;
+        }
+    read_tune_file();
+    if (g_file_tune.empty()) return false;
+    const std::string name = device_name(dev);
+    for (const FileTune &t : g_file_tune)
+        if (t.N == p.N && t.dtype == p.dtype && t.name == name) {
+            // A plan without the counter block cannot run the fused x-y form.
+            const int xyf = p.sync ? t.xyform : 0;
+            g_tune.push_back(TuneEntry{dev, p.N, p.dtype, t.zform, t.yform, t.xform, t.xyform, t.arith});
+            p.zform = t.zform;
+            p.yform = t.yform;
+            p.xform = t.xform;
+            p.xyform = xyf;
+            p.arith = t.arith;
+            return true;
+        }
+    return false;
+}
 
 // Mean time (ms) of `reps` runs of `run` (one density) after one warm-up run.
 template <class Run>
@@ -160,36 +254,41 @@ static cudaError_t pick_form(int forms, int *field, Run &&run, cudaStream_t s, c
     return cudaSuccess;
 }
 
-// Choose p.zform, p.yform, p.xform and p.xyform: the cached decision for this shape, else
-// the fastest forms that exist, timed on p's zeroed workspace.  The z pass writes only w3,
-// the y passes w2 and w1, the x passes (timed with w2 as density and output) w1 and w2, the
-// x-y passes all three, and every solve writes each of them before reading it.  The x-y
-// form is timed last, against the separate passes in the y and x forms just chosen.
+// Choose p.arith (FP64 plans), p.zform, p.yform, p.xform and p.xyform: the cached decision
+// for this shape, else the fastest forms that exist, timed on p's zeroed workspace.  An FP64
+// plan first times its passes (block forms) in FP64 and in double-float arithmetic and keeps
+// the faster; timing needs no valid tables, so the caller builds the twiddles and the symbol
+// afterwards, in the chosen arithmetic's format.  The z pass writes only w3, the y passes w2
+// and w1, the x passes (timed with w2 as density and output) w1 and w2, the x-y passes all
+// three, and every solve writes each of them before reading it.  The x-y form is timed last,
+// against the separate passes in the y and x forms just chosen.
 static cudaError_t autotune(DevicePlan &p, int dev) {
     p.zform = 0;
     p.yform = 0;
     p.xform = 0;
     p.xyform = 0;
+    p.arith = 0;
     const int zf = z_forms(p.N, p.dtype), yf = y_forms(p.N, p.dtype), xf = x_forms(p.N, p.dtype);
     const int xyf = p.sync ? xy_forms(p.N, p.dtype) : 1;
-    if (zf == 1 && yf == 1 && xf == 1 && xyf == 1) return cudaSuccess;
+    const int af = p.dtype == POISSON_F64 ? 3 : 1;
+    if (zf == 1 && yf == 1 && xf == 1 && xyf == 1 && af == 1) return cudaSuccess;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        for (const TuneEntry &t : g_tune)
-            if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
-                p.zform = t.zform;
-                p.yform = t.yform;
-                p.xform = t.xform;
-                p.xyform = t.xyform;
-                return cudaSuccess;
-            }
+        if (lookup_tune(p, dev)) return cudaSuccess;
     }
     cudaStream_t s = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    if (e == cudaSuccess) e = pick_form(zf, &p.zform, [&] { return launch_z_pass(p, s); }, s, a, b);
+    if (e == cudaSuccess && af != 1)
+        e = pick_form(af, &p.arith, [&] {
+            cudaError_t r = launch_x_passes(p, s);
+            if (r == cudaSuccess) r = launch_y_passes(p, s);
+            return r == cudaSuccess ? launch_z_pass(p, s) : r;
+        }, s, a, b);
+    if (e == cudaSuccess)
+        e = pick_form(z_forms(p.N, p.dtype, p.arith), &p.zform, [&] { return launch_z_pass(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(yf, &p.yform, [&] { return launch_y_passes(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(xf, &p.xform, [&] { return launch_x_passes(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(xyf, &p.xyform, [&] { return launch_xy_passes(p, s); }, s, a, b);
@@ -197,7 +296,7 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
     if (b) cudaEventDestroy(b);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) {
-        p.zform = p.yform = p.xform = p.xyform = 0;
+        p.zform = p.yform = p.xform = p.xyform = p.arith = 0;
         return e;
     }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -207,9 +306,12 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
             p.yform = t.yform;
             p.xform = t.xform;
             p.xyform = t.xyform;
+            p.arith = t.arith;
             return cudaSuccess;
         }
-    g_tune.push_back(TuneEntry{dev, p.N, p.dtype, p.zform, p.yform, p.xform, p.xyform});
+    const TuneEntry mine{dev, p.N, p.dtype, p.zform, p.yform, p.xform, p.xyform, p.arith};
+    g_tune.push_back(mine);
+    append_tune_file(mine, device_name(dev));
     return cudaSuccess;
 }
 }  // namespace gsp
@@ -297,6 +399,36 @@ extern "C" int poisson_plan_create_box(poisson_plan *out, int N, double Lx, doub
                                        int dtype) {
     const double L3[3] = {Lx, Ly, Lz};
     return plan_create_impl(out, N, 0.0, L3, tol, dtype, 1);
+}
+
+// Twiddles W_{2N}^e from FP64 (long double arithmetic) into the plan's tables, in its
+// arithmetic's format: FP32 rounded once (and the column passes' (re, re, im, im) copy), FP64,
+// or double-float (re.hi, re.lo, im.hi, im.lo) split from the FP64 value.
+static cudaError_t upload_twiddles(poisson_plan p) {
+    const int N = p->dp.N;
+    std::vector<double> tw;
+    gsp::twiddles(2 * N, tw);
+    const size_t n = (size_t)2 * N;
+    cudaError_t e;
+    if (p->dp.dtype == POISSON_F32) {
+        std::vector<float> twf(tw.begin(), tw.end());
+        e = cudaMemcpy(p->dp.tw, twf.data(), n * 2 * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        std::vector<float> tw4(n * 4);
+        for (size_t i = 0; i < n; ++i) {
+            tw4[4 * i] = tw4[4 * i + 1] = (float)tw[2 * i];
+            tw4[4 * i + 2] = tw4[4 * i + 3] = (float)tw[2 * i + 1];
+        }
+        return cudaMemcpy(p->dp.twc, tw4.data(), n * 4 * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (!p->dp.arith) return cudaMemcpy(p->dp.tw, tw.data(), n * 2 * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float> twd(n * 4);
+    for (size_t i = 0; i < 2 * n; ++i) {
+        const float hi = (float)tw[i];
+        twd[2 * i] = hi;
+        twd[2 * i + 1] = (float)(tw[i] - (double)hi);
+    }
+    return cudaMemcpy(p->dp.tw, twd.data(), n * 4 * sizeof(float), cudaMemcpyHostToDevice);
 }
 
 static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3, double tol, int dtype,
@@ -388,23 +520,12 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
     gsp::ForkPool *pool = nullptr;
     if ((e = gsp::fork_pool(p->device, &pool)) != cudaSuccess) return fail(e);
 
-    // Twiddles W_{2N}^e from FP64 (long double arithmetic), rounded once to the dtype.
-    std::vector<double> tw;
-    gsp::twiddles(2 * N, tw);
-    if (dtype == POISSON_F32) {
-        std::vector<float> twf(tw.begin(), tw.end());
-        e = cudaMemcpy(p->dp.tw, twf.data(), tw_bytes, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return fail(e);
-        std::vector<float> tw4((size_t)2 * N * 4);
-        for (size_t i = 0; i < (size_t)2 * N; ++i) {
-            tw4[4 * i] = tw4[4 * i + 1] = (float)tw[2 * i];
-            tw4[4 * i + 2] = tw4[4 * i + 3] = (float)tw[2 * i + 1];
-        }
-        e = cudaMemcpy(p->dp.twc, tw4.data(), twc_bytes, cudaMemcpyHostToDevice);
-    } else {
-        e = cudaMemcpy(p->dp.tw, tw.data(), tw_bytes, cudaMemcpyHostToDevice);
-    }
-    if (e != cudaSuccess) return fail(e);
+    // The arithmetic and kernel forms, timed on the zeroed workspace (the tables below are
+    // built in the chosen arithmetic's format).
+    if ((e = cudaMemset(p->dp.sym, 0, sym_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(p->dp.tw, 0, tw_bytes)) != cudaSuccess) return fail(e);
+    if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
+    if ((e = upload_twiddles(p)) != cudaSuccess) return fail(e);
 
     // Symbol octant on the device, in FP64, from the per-axis factors (a box: one table per
     // axis, l_q A_j(tau_j l_q), Sec. 2).
@@ -460,7 +581,6 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
     cudaFree(dtau);
     cudaFree(dgl);
     dA = dw = dtau = dgl = nullptr;
-    if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
     *out = p;
     return POISSON_OK;
 }
@@ -472,6 +592,7 @@ extern "C" int poisson_plan_get_knob(poisson_plan p, int knob, int *value) {
     else if (knob == POISSON_KNOB_X_FORM) *value = p->dp.xform;
     else if (knob == POISSON_KNOB_XY_FORM) *value = p->dp.xyform;
     else if (knob == POISSON_KNOB_CORRECTION) *value = p->correction;
+    else if (knob == POISSON_KNOB_ARITH) *value = p->dp.arith;
     else return POISSON_ERR_ARG;
     return POISSON_OK;
 }
@@ -512,9 +633,35 @@ extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
         if (rc == POISSON_OK) p->correction = value;
         return rc;
     }
+    if (knob == POISSON_KNOB_ARITH) {
+        if (value != 0 && value != 1) return POISSON_ERR_ARG;
+        if (value == 1 && p->dp.dtype != POISSON_F64) return POISSON_ERR_UNSUPPORTED;
+        if (value == p->dp.arith) return POISSON_OK;
+        // The twiddles and the symbol change format with the arithmetic; the workspace
+        // needs nothing (every solve writes each buffer before reading it).
+        const int prev = p->dp.arith, prev_z = p->dp.zform;
+        p->dp.arith = value;
+        if (!(gsp::z_forms(p->dp.N, p->dp.dtype, value) >> p->dp.zform & 1)) p->dp.zform = 0;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(p->device);
+        if (e == cudaSuccess) e = upload_twiddles(p);
+        cudaSetDevice(dev);
+        int rc = map_cuda(e);
+        if (rc == POISSON_OK) rc = rebuild_symbol(p, p->correction);
+        if (rc != POISSON_OK) {
+            p->dp.arith = prev;
+            p->dp.zform = prev_z;
+            cudaSetDevice(p->device);
+            upload_twiddles(p);
+            cudaSetDevice(dev);
+            rebuild_symbol(p, p->correction);
+        }
+        return rc;
+    }
     int forms, *field;
     if (knob == POISSON_KNOB_Z_FORM) {
-        forms = gsp::z_forms(p->dp.N, p->dp.dtype);
+        forms = gsp::z_forms(p->dp.N, p->dp.dtype, p->dp.arith);
         field = &p->dp.zform;
     } else if (knob == POISSON_KNOB_Y_FORM) {
         forms = gsp::y_forms(p->dp.N, p->dp.dtype);

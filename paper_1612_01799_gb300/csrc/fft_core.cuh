@@ -18,7 +18,9 @@
 //       imaginary parts in another, so that the packed FP32x2 instructions of sm_100+
 //       (__fadd2_rn, __fmul2_rn, __ffma2_rn) do two columns' arithmetic per instruction
 //       and a product with +-i is a swap of the two registers,
-//   CD  one FP64 complex value.
+//   CD  one FP64 complex value,
+//   CDF one complex value in double-float arithmetic (type DF below: each real an
+//       unevaluated sum hi + lo of two FP32 numbers), the FP32-pipe stand-in for CD.
 //
 // Pruning.  Stage 0 reads rows j + r L/R with j < L/R, so rows >= L/2 are exactly
 // r >= R/2 when R is even: with prune_in those inputs are zero and never loaded (the zero
@@ -43,10 +45,54 @@ struct CV {
     float2 re, im;
 };
 
+// ---- double-float reals ------------------------------------------------------------------
+// A real number held as hi + lo, two FP32 values with |lo| <= ulp(hi) / 2: a 48-bit
+// significand (unit roundoff 2^-48, about 3.6e-15) with FP32's exponent range, computed on
+// the FP32 pipe.  Sums use Knuth's two-sum, which yields the exact rounding error of an
+// FP32 addition; products use the exact product of an FP32 multiplication that the fused
+// multiply-add gives (fma(a, b, -ab) = the error of ab); both end with a fast two-sum that
+// renormalises (hi, lo).  The error of a sum is at most about 2^-47 (|a| + |b|), of a
+// product 2^-47 |ab| (the lo-lo term is dropped), which is the norm-wise error model of an
+// FFT in FP64.  The _rn intrinsics keep the compiler from contracting or reassociating the
+// error terms.
+struct DF {
+    float hi, lo;
+    DF() = default;
+    __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}
+    // The nearest double-float to d (exact for |d| in FP32's normal range to 48 bits).
+    __host__ __device__ constexpr DF(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+__host__ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ DF df_fast_two_sum(float s, float e) {  // needs |s| >= |e| or s = 0
+    const float h = __fadd_rn(s, e);
+    return DF(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    return df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+struct CDF {
+    DF re, im;
+};
+
 template <typename C> struct CxReal;
 template <> struct CxReal<CF> { using T = float; };
 template <> struct CxReal<CD> { using T = double; };
 template <> struct CxReal<CV> { using T = float; };
+template <> struct CxReal<CDF> { using T = DF; };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -60,6 +106,7 @@ template <typename C> __device__ __forceinline__ C czero();
 template <> __device__ __forceinline__ CF czero<CF>() { return {0.f, 0.f}; }
 template <> __device__ __forceinline__ CD czero<CD>() { return {0.0, 0.0}; }
 template <> __device__ __forceinline__ CV czero<CV>() { return {f2(0.f, 0.f), f2(0.f, 0.f)}; }
+template <> __device__ __forceinline__ CDF czero<CDF>() { return {DF(0.f, 0.f), DF(0.f, 0.f)}; }
 
 __device__ __forceinline__ CF cadd(CF a, CF b) { return {a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ CF csub(CF a, CF b) { return {a.re - b.re, a.im - b.im}; }
@@ -67,10 +114,13 @@ __device__ __forceinline__ CD cadd(CD a, CD b) { return {a.re + b.re, a.im + b.i
 __device__ __forceinline__ CD csub(CD a, CD b) { return {a.re - b.re, a.im - b.im}; }
 __device__ __forceinline__ CV cadd(CV a, CV b) { return {f2add(a.re, b.re), f2add(a.im, b.im)}; }
 __device__ __forceinline__ CV csub(CV a, CV b) { return {f2sub(a.re, b.re), f2sub(a.im, b.im)}; }
+__device__ __forceinline__ CDF cadd(CDF a, CDF b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ CDF csub(CDF a, CDF b) { return {a.re - b.re, a.im - b.im}; }
 
 __device__ __forceinline__ CF cscale(CF a, float s) { return {a.re * s, a.im * s}; }
 __device__ __forceinline__ CD cscale(CD a, double s) { return {a.re * s, a.im * s}; }
 __device__ __forceinline__ CV cscale(CV a, float s) { return {f2mul(a.re, f2(s, s)), f2mul(a.im, f2(s, s))}; }
+__device__ __forceinline__ CDF cscale(CDF a, DF s) { return {a.re * s, a.im * s}; }
 // Lane-wise real scale (CV: one factor per column).
 __device__ __forceinline__ CV cscale2(CV a, float2 s) { return {f2mul(a.re, s), f2mul(a.im, s)}; }
 
@@ -83,6 +133,9 @@ template <int D> __device__ __forceinline__ CD add_rot(CD a, CD b) {
 }
 template <int D> __device__ __forceinline__ CV add_rot(CV a, CV b) {
     return D > 0 ? CV{f2sub(a.re, b.im), f2add(a.im, b.re)} : CV{f2add(a.re, b.im), f2sub(a.im, b.re)};
+}
+template <int D> __device__ __forceinline__ CDF add_rot(CDF a, CDF b) {
+    return D > 0 ? CDF{a.re - b.im, a.im + b.re} : CDF{a.re + b.im, a.im - b.re};
 }
 // a - i D b
 template <int D, typename C> __device__ __forceinline__ C sub_rot(C a, C b) { return add_rot<-D>(a, b); }
@@ -97,6 +150,10 @@ template <int D> __device__ __forceinline__ CD cmulk(CD a, double cr, double ci)
     const double s = D < 0 ? ci : -ci;
     return {a.re * cr - a.im * s, a.re * s + a.im * cr};
 }
+template <int D> __device__ __forceinline__ CDF cmulk(CDF a, DF cr, DF ci) {
+    const DF s = D < 0 ? ci : -ci;
+    return {a.re * cr - a.im * s, a.re * s + a.im * cr};
+}
 template <int D> __device__ __forceinline__ CV cmulk(CV a, float cr, float ci) {
     const float s = D < 0 ? ci : -ci;
     const float2 R = f2(cr, cr), S = f2(s, s), NS = f2(-s, -s);
@@ -109,6 +166,7 @@ template <typename C> struct TwOf;
 template <> struct TwOf<CF> { using T = float2; };
 template <> struct TwOf<CD> { using T = double2; };
 template <> struct TwOf<CV> { using T = float4; };
+template <> struct TwOf<CDF> { using T = float4; };  // (re.hi, re.lo, im.hi, im.lo)
 
 // a times w (D < 0) or conj(w) (D > 0).
 template <int D> __device__ __forceinline__ CF twmul(CF a, float2 w) {
@@ -118,6 +176,11 @@ template <int D> __device__ __forceinline__ CF twmul(CF a, float2 w) {
 template <int D> __device__ __forceinline__ CD twmul(CD a, double2 w) {
     const double s = D < 0 ? w.y : -w.y;
     return {a.re * w.x - a.im * s, a.re * s + a.im * w.x};
+}
+template <int D> __device__ __forceinline__ CDF twmul(CDF a, float4 w) {
+    const DF wr(w.x, w.y), wi(w.z, w.w);
+    const DF s = D < 0 ? wi : -wi;
+    return {a.re * wr - a.im * s, a.re * s + a.im * wr};
 }
 template <int D> __device__ __forceinline__ CV twmul(CV a, float4 w) {
     const float2 R = f2(w.x, w.y), I = f2(w.z, w.w);

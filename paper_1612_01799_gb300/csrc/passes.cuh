@@ -72,6 +72,12 @@ template <> struct Types<double> {
     using CC = CD;
     static constexpr int W = 1;
 };
+// Double-float arithmetic (the FP64 path on the FP32 pipe): one complex value per slot.
+template <> struct Types<DF> {
+    using CS = CDF;
+    using CC = CDF;
+    static constexpr int W = 1;
+};
 
 // Columns per CTA of a column pass: 128-byte row segments (16 FP32 or 8 FP64 complex),
 // halved until the block has <= 1024 threads and <= 128 KB of shared memory.
@@ -106,6 +112,12 @@ __device__ __forceinline__ CD ld_cc(const double2 *p) {
     return {f.x, f.y};
 }
 __device__ __forceinline__ void st_cc(double2 *p, CD x) { *p = make_double2(x.re, x.im); }
+// Double-float workspace values: float4 (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ CDF ld_cc(const float4 *p) {
+    const float4 f = __ldg(p);
+    return {DF(f.x, f.y), DF(f.z, f.w)};
+}
+__device__ __forceinline__ void st_cc(float4 *p, CDF x) { *p = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo); }
 __device__ __forceinline__ CF ld_cs(const float2 *p) {
     const float2 f = *p;
     return {f.x, f.y};
@@ -119,8 +131,40 @@ __device__ __forceinline__ CV scale_sym(CV x, const float *s) {
     return cscale2(x, __ldg(reinterpret_cast<const float2 *>(s)));
 }
 __device__ __forceinline__ CD scale_sym(CD x, const double *s) { return cscale(x, __ldg(s)); }
+__device__ __forceinline__ CDF scale_sym(CDF x, const DF *s) {
+    const float2 f = __ldg(reinterpret_cast<const float2 *>(s));
+    return cscale(x, DF(f.x, f.y));
+}
 
-template <typename Real> using Cx2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+// Storage of one complex workspace value (Cx2) and of a pair of consecutive real samples of
+// the caller's density or potential (Ext2) for each arithmetic.  Double-float keeps its
+// workspace in its own format and converts from and to FP64 only where the x passes read
+// rho and write u.
+template <typename Real> struct Store;
+template <> struct Store<float> {
+    using Ws = float2;
+    using Ext = float2;
+};
+template <> struct Store<double> {
+    using Ws = double2;
+    using Ext = double2;
+};
+template <> struct Store<DF> {
+    using Ws = float4;
+    using Ext = double2;
+};
+template <typename Real> using Cx2 = typename Store<Real>::Ws;
+template <typename Real> using Ext2 = typename Store<Real>::Ext;
+
+__device__ __forceinline__ void st_ws(float2 *p, CF x) { *p = make_float2(x.re, x.im); }
+__device__ __forceinline__ void st_ws(double2 *p, CD x) { *p = make_double2(x.re, x.im); }
+__device__ __forceinline__ void st_ws(float4 *p, CDF x) { *p = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo); }
+__device__ __forceinline__ CF ws_c(float2 f) { return {f.x, f.y}; }
+__device__ __forceinline__ CD ws_c(double2 f) { return {f.x, f.y}; }
+__device__ __forceinline__ CDF ws_c(float4 f) { return {DF(f.x, f.y), DF(f.z, f.w)}; }
+__device__ __forceinline__ float2 c_ext(CF x) { return make_float2(x.re, x.im); }
+__device__ __forceinline__ double2 c_ext(CD x) { return make_double2(x.re, x.im); }
+__device__ __forceinline__ double2 c_ext(CDF x) { return make_double2(df_to_double(x.re), df_to_double(x.im)); }
 
 }  // namespace gsp
 #include "passes_tma.cuh"
@@ -137,6 +181,7 @@ k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__
             int nrows, int Px) {
     using C = typename Types<Real>::CS;
     using T2 = Cx2<Real>;
+    using X2 = Ext2<Real>;
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     static_assert((N * N) % TR == 0, "row tiles stay inside one density");
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -147,10 +192,10 @@ k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__
     const int nr = (int)min((long long)TR, (long long)nrows - r0);
     const int b = (int)(r0 / (N * N));
     // The tile is nr consecutive rows of N reals: contiguous N/2-pair chunks.
-    const T2 *src = reinterpret_cast<const T2 *>(rho.p[b]) + (r0 - (long long)b * N * N) * (N / 2);
+    const X2 *src = reinterpret_cast<const X2 *>(rho.p[b]) + (r0 - (long long)b * N * N) * (N / 2);
     for (int e = t; e < nr * (N / 2); e += NT) {
         const int r = e / (N / 2), m = e - r * (N / 2);
-        const T2 f = __ldg(src + e);
+        const X2 f = __ldg(src + e);
         sm[m * SP + r] = C{f.x, f.y};
     }
     __syncthreads();
@@ -187,8 +232,7 @@ k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__
     T2 *dst = out + r0 * Px;
     for (int e = t; e < nr * (N + 1); e += NT) {
         const int r = e / (N + 1), k = e - r * (N + 1);
-        const C x = sm[k * SP + r];
-        dst[(long long)r * Px + k] = T2{x.re, x.im};
+        st_ws(dst + (long long)r * Px + k, sm[k * SP + r]);
     }
 }
 
@@ -275,6 +319,7 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
             int nrows, int Px) {
     using C = typename Types<Real>::CS;
     using T2 = Cx2<Real>;
+    using X2 = Ext2<Real>;
     constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
@@ -296,7 +341,7 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const int e = t + (i0 + i) * NT;
-            if (i0 + i < NI && e < nr * (N + 1)) sm[(e % (N + 1)) * SP + e / (N + 1)] = C{f[i].x, f[i].y};
+            if (i0 + i < NI && e < nr * (N + 1)) sm[(e % (N + 1)) * SP + e / (N + 1)] = ws_c(f[i]);
         }
     }
     __syncthreads();
@@ -326,11 +371,10 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
         [&](int row, C x) { sm[row * SP + c] = x; });
     __syncthreads();
     const int b = (int)(r0 / (N * N));
-    T2 *dst = reinterpret_cast<T2 *>(const_cast<void *>(u.p[b])) + (r0 - (long long)b * N * N) * (N / 2);
+    X2 *dst = reinterpret_cast<X2 *>(const_cast<void *>(u.p[b])) + (r0 - (long long)b * N * N) * (N / 2);
     for (int e = t; e < nr * (N / 2); e += NT) {
         const int r = e / (N / 2), m = e - r * (N / 2);
-        const C x = sm[m * SP + r];
-        dst[e] = T2{x.re, x.im};
+        dst[e] = c_ext(sm[m * SP + r]);
     }
 }
 
@@ -490,7 +534,7 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
             return cudaGetLastError();
         }
     }
-    if constexpr (zsplit_available<L>()) {
+    if constexpr (zsplit_available<L>() && !std::is_same<Real, DF>::value) {
         if (p.zform == 1) {
             auto k = tail ? k_z_split_tma<Real, L, true> : k_z_split_tma<Real, L, false>;
             constexpr int T = zsplit_threads<Real, L>();
@@ -830,6 +874,17 @@ cudaError_t encode_n(DevicePlan &p) {
 #define GSP_SIZE_GROUP_A(X) X(4) X(8) X(16) X(32) X(48) X(64) X(80) X(96)
 #define GSP_SIZE_GROUP_B(X) X(128) X(160) X(192) X(256)
 #define GSP_SIZE_GROUP_C(X) X(320) X(384) X(512) X(1024)
+// Double-float instantiations compile several times slower (their butterflies are long
+// straight-line FP32 sequences), so they spread over more units, one to three sizes each.
+#define GSP_DF_GROUP_1(X) X(4) X(8) X(16)
+#define GSP_DF_GROUP_2(X) X(32) X(48)
+#define GSP_DF_GROUP_3(X) X(64) X(80)
+#define GSP_DF_GROUP_4(X) X(96) X(128)
+#define GSP_DF_GROUP_5(X) X(160) X(192)
+#define GSP_DF_GROUP_6(X) X(256)
+#define GSP_DF_GROUP_7(X) X(320) X(384)
+#define GSP_DF_GROUP_8(X) X(512)
+#define GSP_DF_GROUP_9(X) X(1024)
 #define GSP_DECLARE_N(EXT, Real, n)                                                                      \
     EXT template cudaError_t solve_n<Real, n>(const DevicePlan &, const PtrArray &, const PtrArray &, int, \
                                               cudaStream_t, cudaEvent_t *, double *, int);                 \

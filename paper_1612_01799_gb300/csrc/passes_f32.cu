@@ -26,7 +26,7 @@ int xy_sync_ints() { return kSyncInts; }
 int xy_forms(int N, int dtype) { return 1 | (dtype == 0 && warp_n(N) ? 2 : 0); }
 int x_forms(int N, int dtype) { return 1 | (dtype == 0 && (warp_n(N) || N == XWarp2::N) ? 2 : 0); }
 int y_forms(int N, int dtype) { return 1 | (dtype == 0 && (warp_n(N) || N == ZW512::N) ? 2 : 0); }
-int z_forms(int N, int dtype) {
-    return 1 | (zsplit_dispatch(N) ? 2 : 0) | (dtype == 0 && zwarp_available(N) ? 4 : 0);
+int z_forms(int N, int dtype, int arith) {
+    return 1 | (zsplit_dispatch(N) && !arith ? 2 : 0) | (dtype == 0 && zwarp_available(N) ? 4 : 0);
 }
 }  // namespace gsp

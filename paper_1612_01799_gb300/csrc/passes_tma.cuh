@@ -108,10 +108,15 @@ template <> __device__ __forceinline__ CD ld_sm_cc<CD>(const unsigned char *p) {
     const double2 f = *reinterpret_cast<const double2 *>(p);
     return {f.x, f.y};
 }
+template <> __device__ __forceinline__ CDF ld_sm_cc<CDF>(const unsigned char *p) {
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    return {DF(f.x, f.y), DF(f.z, f.w)};
+}
 __device__ __forceinline__ CV scale_sym_sm(CV x, const float *s) {
     return cscale2(x, *reinterpret_cast<const float2 *>(s));
 }
 __device__ __forceinline__ CD scale_sym_sm(CD x, const double *s) { return cscale(x, *s); }
+__device__ __forceinline__ CDF scale_sym_sm(CDF x, const DF *s) { return cscale(x, *s); }
 
 // Blocks per SM requested from the compiler: a register budget of 64 per thread for E <= 8
 // values per thread, 128 otherwise.
@@ -198,6 +203,7 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
 // padding not at all).
 __device__ __forceinline__ float2 cenergy(CV x) { return f2fma(x.re, x.re, f2mul(x.im, x.im)); }
 __device__ __forceinline__ float cenergy(CD x) { return (float)(x.re * x.re + x.im * x.im); }
+__device__ __forceinline__ float cenergy(CDF x) { return x.re.hi * x.re.hi + x.im.hi * x.im.hi; }
 
 // With TAIL, the forward spectrum's energy in the outer shell max(|kx|,|ky|,|kz|) >= 7N/8
 // and its total energy are added (FP32 per thread, FP64 per tile) to tail[2 b], tail[2 b + 1]

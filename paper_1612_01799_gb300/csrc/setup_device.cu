@@ -14,6 +14,7 @@
 // from sincos every kReseed panels.
 #include <cuda_runtime.h>
 
+#include "fft_core.cuh"
 #include "setup.h"
 #include "solver.h"
 
@@ -118,6 +119,11 @@ cudaError_t symbol_table_box_f64(const DevicePlan &p, const double *dA3, const d
                                  double C0, double C2, double scale, const double *l, int literal,
                                  cudaStream_t s) {
     return symbol_table_box<double>(p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
+}
+cudaError_t symbol_table_box_df(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
+                                double C0, double C2, double scale, const double *l, int literal,
+                                cudaStream_t s) {
+    return symbol_table_box<DF>(p, dA3, dw, nterms, C0, C2, scale, l, literal, s);
 }
 
 cudaError_t launch_axis_table(const double *dtau, const double *dgl, int S, int N, double *dA, cudaStream_t s) {

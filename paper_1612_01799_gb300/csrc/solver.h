@@ -31,6 +31,10 @@ struct DevicePlan {
     int N = 0;
     int max_batch = 1;
     int dtype = 0;  // POISSON_F32 / POISSON_F64
+    // Arithmetic of an FP64 plan: 0 FP64 (the FP64 pipe), 1 double-float (pairs of FP32 on
+    // the FP32 pipe; workspace, twiddles and symbol then hold (hi, lo) float pairs, and rho
+    // and u stay FP64).  Always 0 for FP32 plans.
+    int arith = 0;
     int Px = 0;
     int Ps = 0;
     void *sym = nullptr;
@@ -93,10 +97,10 @@ cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArra
 // one density, in the plan's separate forms: rho, u device pointers to the whole density.
 cudaError_t launch_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd);
 
-// Forms of the z pass that exist for (N, dtype), as a bit mask over DevicePlan::zform:
-// bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one;
-// bit 2 for FP32 at N = 64, 96, 128, 160, 192, 256 and 512.
-int z_forms(int N, int dtype);
+// Forms of the z pass that exist for (N, dtype, arith), as a bit mask over DevicePlan::zform:
+// bit 0 always; bit 1 where the length-N schedule has fewer stages than the length-2N one
+// (not in double-float arithmetic); bit 2 for FP32 at N = 64, 96, 128, 160, 192, 256 and 512.
+int z_forms(int N, int dtype, int arith = 0);
 
 // Forms of the x passes that exist for (N, dtype), as a bit mask over DevicePlan::xform:
 // bit 0 always; bit 1 for FP32 at N = 64, 96, 128, 160, 192, 256 and 512.

@@ -17,8 +17,11 @@ SPLIT_N = (16, 80, 256, 320, 384)
 WARP_N = (64, 96, 128, 160, 192, 256)
 
 
-def forms(N, dtype):
-    return [0] + ([1] if N in SPLIT_N else []) + ([2] if dtype == "f32" and (N in WARP_N or N == 512) else [])
+def forms(N, dtype, arith=None):
+    """z forms of (N, dtype); an FP64 plan's split form exists in FP64 arithmetic only, so
+    with arith None (whichever the plan chose) it is left out for FP64."""
+    split = N in SPLIT_N and (dtype == "f32" or arith == "f64")
+    return [0] + ([1] if split else []) + ([2] if dtype == "f32" and (N in WARP_N or N == 512) else [])
 
 
 def yforms(N, dtype):
@@ -50,7 +53,9 @@ def rel_l2(a, b):
 def solve_form(torch, N, L, tol, dtype, rho, form, yform=None, xform=None, xyform=0):
     from paper_1612_01799_gb300 import Plan
     with Plan(N, L, tol, dtype) as p:
-        assert p.z_form in forms(N, dtype)
+        assert p.z_form in forms(N, dtype, p.arith)
+        if dtype == "f64" and form == 1:
+            p.arith = "f64"             # the split form exists in FP64 arithmetic only
         assert p.y_form in yforms(N, dtype)
         assert p.x_form in xforms(N, dtype)
         assert p.xy_form in xyforms(N, dtype)
@@ -77,7 +82,10 @@ def test_knob_codes(torch_cuda, dtype):
     lib = _lib.load()
     for N in (4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512):
         with Plan(N, 4.0, 1e-6, dtype) as p:
-            have = forms(N, dtype)
+            assert p.z_form in forms(N, dtype, p.arith)
+            if dtype == "f64":
+                p.arith = "f64" if N % 2 == 0 and (N // 2) % 2 == 0 else "df"
+            have = forms(N, dtype, p.arith)
             assert p.z_form in have
             for f in (0, 1, 2):
                 if f in have:
@@ -130,7 +138,7 @@ def test_forms_full_grid_small(torch_cuda, plan_cache, N, dtype):
     tol = 1e-12 if dtype == "f64" else 1e-6
     rho = D.config_aniso4(N=N, seed=200 + N).gaussians.sample(N, L)
     uo = osolver.solve(rho, L, tol, plan=plan_cache(N, L, tol))
-    for form in forms(N, dtype):
+    for form in forms(N, dtype, "f64"):
         u = solve_form(torch_cuda, N, L, tol, dtype, rho, form)
         assert rel_l2(u, uo) <= TOL[dtype], form
         assert np.max(np.abs(u - uo)) <= 50 * TOL[dtype] * np.abs(uo).max(), form
@@ -142,8 +150,8 @@ def test_forms_full_grid_n256(torch_cuda, plan_cache, dtype):
     rho = D.config_aniso4().sample()
     tol = 1e-12 if dtype == "f64" else 1e-6
     uo = osolver.solve(rho, 10.0, tol, plan=plan_cache(256, 10.0, tol))
-    combos = [(f, 0, 0, 0) for f in forms(256, dtype)] + [(f, 1, x, 0) for f in forms(256, dtype)
-                                                           for x in xforms(256, dtype) if dtype == "f32"]
+    combos = [(f, 0, 0, 0) for f in forms(256, dtype, "f64")] + [(f, 1, x, 0) for f in forms(256, dtype)
+                                                                  for x in xforms(256, dtype) if dtype == "f32"]
     combos += [(f, 0, 0, 1) for f in forms(256, dtype) if dtype == "f32"]
     for form, yform, xform, xyform in combos:
         u = solve_form(torch_cuda, 256, 10.0, tol, dtype, rho, form, yform, xform, xyform)
@@ -161,7 +169,7 @@ def test_forms_sampled_large(torch_cuda, N, dtype):
     rho = D.config_aniso4(N=N, seed=300 + N).gaussians.sample(N, L)
     lines = [(0, 0), (N // 2, N // 2 - 1), (N - 1, N - 1), (N // 3, 2 * N // 3), (N - 2, 1)]
     ref = direct.sample_lines(rho, gtensor.make_plan(N, L, tol), lines)
-    for form in forms(N, dtype):
+    for form in forms(N, dtype, "f64"):
         u = solve_form(torch_cuda, N, L, tol, dtype, rho, form)
         got = np.stack([u[z, y] for z, y in lines])
         assert rel_l2(got, ref) <= TOL[dtype], form
@@ -180,6 +188,8 @@ def test_form_tail(torch_cuda, form, N, dtype):
     L = 6.0
     rho = D.config_aniso4(N=N, seed=31).gaussians.sample(N, L)
     with Plan(N, L, 1e-6, dtype) as p:
+        if dtype == "f64":
+            p.arith = "f64"             # the split form exists in FP64 arithmetic only
         p.z_form = form
         t = torch.from_numpy(rho.astype(p.np_dtype)).cuda()
         u1 = p.solve(t)
