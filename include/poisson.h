@@ -59,7 +59,8 @@ enum {
  * G-tensor factors by quadrature, C0 and C2, the symbol table, FFT twiddles) and the
  * device workspace for solves.  Runs on the current CUDA device, synchronously.
  *   out   [out] receives the plan; *out is set to NULL on failure.
- *   N     points per axis: even, 4 <= N <= 1024, from poisson_supported_n().
+ *   N     points per axis: even, 4 <= N <= 1024, with no prime factor above 5 (so that 2N
+ *         factors into 2, 3 and 5), else POISSON_ERR_UNSUPPORTED; see poisson_supported_n().
  *   L     half-width of the cube [-L, L]^3, L > 0 and L < 25 N (the Sec. 3 condition
  *         lambda <= 25 min_q n_q that keeps delta inside the scaled box).
  *   tol   requested accuracy of the Gaussian sum: eps = clamp(tol/10, 1e-14, 1e-7) is
@@ -98,6 +99,25 @@ int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, 
  * arguments, errors and use as for poisson_plan_create (one density per solve).
  */
 int poisson_plan_create_box(poisson_plan *out, int N, double Lx, double Ly, double Lz, double tol, int dtype);
+
+/*
+ * A plan for the box [-Lx, Lx] x [-Ly, Ly] x [-Lz, Lz] with n_q points on axis q (Sec. 2's
+ * standardised form with n_1, n_2, n_3 points per axis): spacings 2 Lx / nx, 2 Ly / ny,
+ * 2 Lz / nz; each axis zero-padded to 2 n_q, so the padded period of axis q is 4 l_q and its
+ * frequency k has kappa_q = pi k / (2 l_q); the G-tensor factor of axis q is
+ * l_q A_j(tau_j l_q, k) for k = 0..n_q; delta = max(min_q 2 L_q / (50 n_q), 1e-3) (Sec. 3)
+ * below min_q l_q (else POISSON_ERR_ARG).  Densities and potentials are nz x ny x nx
+ * arrays, x fastest (index i + nx (j + ny k)).  Each n_q must be even, 4 <= n_q <= 1024,
+ * with no prime factor above 5 (else POISSON_ERR_ARG or POISSON_ERR_UNSUPPORTED).  With
+ * nx = ny = nz this is poisson_plan_create_box.  Plans whose counts differ (or whose common
+ * count has no compiled transform schedule, poisson_supported_n() == 2) run the
+ * runtime-length forms of the five passes: one form per pass (the form knobs have only
+ * value 0), the same arithmetics, no TMA staging.  poisson_plan_axis_table returns the x
+ * axis's factors (n_terms x (nx + 1)).  Other arguments, errors and use as for
+ * poisson_plan_create (one density per solve).
+ */
+int poisson_plan_create_box_n(poisson_plan *out, int nx, int ny, int nz, double Lx, double Ly, double Lz,
+                              double tol, int dtype);
 
 /* Free a plan and its device memory.  NULL is accepted.  The caller must make sure no
  * solve on the plan is still running (synchronise its stream first). */
@@ -276,7 +296,10 @@ int poisson_plan_gauss_sum(poisson_plan p, double *tau, double *w, int cap);
  * into a[cap] (cap in doubles). */
 int poisson_plan_axis_table(poisson_plan p, double *a, size_t cap);
 
-/* 1 if N is supported (even, 4..1024, with a compiled FFT plan for N and 2N), else 0. */
+/* How a plan with N points per axis runs: 1 in the compiled-length forms (a compiled
+ * transform schedule for N and 2N: N = 4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256,
+ * 320, 384, 512, 1024), 2 in the runtime-length forms (every other even N in 4..1024 with
+ * no prime factor above 5), 0 if N is not supported. */
 int poisson_supported_n(int N);
 
 /* Human-readable name of a return code. */

@@ -22,6 +22,8 @@ SIGNATURES = {
     "poisson_plan_create": (c_int, [P(c_void_p), c_int, c_double, c_double, c_int]),
     "poisson_plan_create_batched": (c_int, [P(c_void_p), c_int, c_double, c_double, c_int, c_int]),
     "poisson_plan_create_box": (c_int, [P(c_void_p), c_int, c_double, c_double, c_double, c_double, c_int]),
+    "poisson_plan_create_box_n": (c_int, [P(c_void_p), c_int, c_int, c_int, c_double, c_double, c_double, c_double,
+                                          c_int]),
     "poisson_plan_destroy": (c_int, [c_void_p]),
     "poisson_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "poisson_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -22,28 +22,37 @@ def _stream_handle(stream):
 
 
 def supported_n(N):
+    """True if plans with N points per axis can be made (compiled or runtime-length forms)."""
     return bool(_lib.load().poisson_supported_n(int(N)))
 
 
 class Plan:
     """A solve plan for the cube [-L, L]^3, or with L = (Lx, Ly, Lz) the box
-    [-Lx, Lx] x [-Ly, Ly] x [-Lz, Lz], with N cell-centred points per axis (setup phase:
-    Gaussian sum, G-tensor factors, near-zone constants, symbol table)."""
+    [-Lx, Lx] x [-Ly, Ly] x [-Lz, Lz], with N cell-centred points per axis, or with
+    N = (nx, ny, nz) a box with n_q points on axis q (setup phase: Gaussian sum, G-tensor
+    factors, near-zone constants, symbol table).  Arrays hold nz x ny x nx values, x
+    fastest."""
 
     def __init__(self, N, L, tol, dtype="f32", max_batch=1):
         if dtype not in DTYPES:
             raise ValueError("dtype must be 'f32' or 'f64'")
-        self.N, self.tol, self.dtype = int(N), float(tol), dtype
+        self.n = tuple(int(v) for v in N) if np.ndim(N) else (int(N),) * 3
+        if len(self.n) != 3:
+            raise ValueError("N is one count or three (nx, ny, nz)")
+        self.N, self.tol, self.dtype = self.n[0], float(tol), dtype
+        self.npoints = self.n[0] * self.n[1] * self.n[2]
         self.max_batch = int(max_batch)
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
+        if np.ndim(N) and not np.ndim(L):
+            L = (float(L),) * 3
         if np.ndim(L):
             self.box = tuple(float(v) for v in L)
             if len(self.box) != 3 or self.max_batch != 1:
                 raise ValueError("a box takes three half-lengths and one density per solve")
             self.L = max(self.box)
-            _lib.check(self._lib.poisson_plan_create_box(ctypes.byref(self._h), self.N, *self.box, self.tol,
-                                                         DTYPES[dtype]), "poisson_plan_create_box")
+            _lib.check(self._lib.poisson_plan_create_box_n(ctypes.byref(self._h), *self.n, *self.box, self.tol,
+                                                           DTYPES[dtype]), "poisson_plan_create_box_n")
         else:
             self.box = None
             self.L = float(L)
@@ -68,12 +77,12 @@ class Plan:
         torch = _torch()
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise TypeError("%s must be a CUDA tensor" % name)
-        if t.dtype != self.torch_dtype or t.numel() != self.N ** 3 or not t.is_contiguous():
-            raise ValueError("%s must be a contiguous %s tensor of N^3 = %d values"
-                             % (name, self.torch_dtype, self.N ** 3))
+        if t.dtype != self.torch_dtype or t.numel() != self.npoints or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor of nx ny nz = %d values"
+                             % (name, self.torch_dtype, self.npoints))
 
     def solve(self, rho, out=None, stream=None):
-        """u = U * rho on the device; rho, out: contiguous CUDA tensors of N^3 values."""
+        """u = U * rho on the device; rho, out: contiguous CUDA tensors of nx ny nz values."""
         self._check_tensor(rho, "rho")
         if out is None:
             out = _torch().empty_like(rho)
@@ -88,14 +97,14 @@ class Plan:
         torch = _torch()
         if isinstance(rho, np.ndarray):
             rho = np.ascontiguousarray(rho, dtype=self.np_dtype)
-            if rho.size != self.N ** 3:
-                raise ValueError("rho must hold N^3 values")
+            if rho.size != self.npoints:
+                raise ValueError("rho must hold nx ny nz values")
             if out is None:
                 out = np.empty_like(rho)
             pin, pout = rho.ctypes.data, out.ctypes.data
         else:
-            if rho.is_cuda or rho.dtype != self.torch_dtype or rho.numel() != self.N ** 3:
-                raise ValueError("rho must be a CPU tensor of N^3 values of the plan's dtype")
+            if rho.is_cuda or rho.dtype != self.torch_dtype or rho.numel() != self.npoints:
+                raise ValueError("rho must be a CPU tensor of nx ny nz values of the plan's dtype")
             rho = rho.contiguous()
             if out is None:
                 out = torch.empty_like(rho)

@@ -57,6 +57,34 @@ bool n_supported(int N) {
     return false;
 }
 
+bool n_any(int N) {
+    if (N < 4 || N > 1024 || (N & 1)) return false;
+    for (int f : {2, 3, 5})
+        while (N % f == 0) N /= f;
+    return N == 1;
+}
+
+AnySched any_sched(int L) {
+    AnySched s{};
+    s.L = L;
+    int m = L, n = 0;
+    for (int f : {5, 3})
+        while (m % f == 0 && n < kAnyMaxStages) {
+            s.r[n++] = f;
+            m /= f;
+        }
+    while (m % 4 == 0 && n < kAnyMaxStages) {
+        s.r[n++] = 4;
+        m /= 4;
+    }
+    if (m == 2 && n < kAnyMaxStages) {
+        s.r[n++] = 2;
+        m = 1;
+    }
+    s.nst = m == 1 ? n : 0;
+    return s;
+}
+
 cudaError_t launch_solve(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int count,
                          cudaStream_t s, cudaEvent_t *ev, double *tail, int skip) {
     if (count < 1 || count > p.max_batch || count > kMaxBatch) return cudaErrorInvalidValue;
@@ -268,11 +296,15 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
     p.xform = 0;
     p.xyform = 0;
     p.arith = 0;
-    const int zf = z_forms(p.N, p.dtype), yf = y_forms(p.N, p.dtype), xf = x_forms(p.N, p.dtype);
-    const int xyf = p.sync ? xy_forms(p.N, p.dtype) : 1;
+    // The runtime-length forms have one form per pass; only an FP64 plan's arithmetic is
+    // timed, and (their shapes being many) the choice is not cached.
+    const bool any = p.any != 0;
+    const int zf = any ? 1 : z_forms(p.N, p.dtype), yf = any ? 1 : y_forms(p.N, p.dtype);
+    const int xf = any ? 1 : x_forms(p.N, p.dtype);
+    const int xyf = p.sync && !any ? xy_forms(p.N, p.dtype) : 1;
     const int af = p.dtype == POISSON_F64 ? 3 : 1;
     if (zf == 1 && yf == 1 && xf == 1 && xyf == 1 && af == 1) return cudaSuccess;
-    {
+    if (!any) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         if (lookup_tune(p, dev)) return cudaSuccess;
     }
@@ -288,7 +320,8 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
             return r == cudaSuccess ? launch_z_pass(p, s) : r;
         }, s, a, b);
     if (e == cudaSuccess)
-        e = pick_form(z_forms(p.N, p.dtype, p.arith), &p.zform, [&] { return launch_z_pass(p, s); }, s, a, b);
+        e = pick_form(any ? 1 : z_forms(p.N, p.dtype, p.arith), &p.zform, [&] { return launch_z_pass(p, s); }, s, a,
+                      b);
     if (e == cudaSuccess) e = pick_form(yf, &p.yform, [&] { return launch_y_passes(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(xf, &p.xform, [&] { return launch_x_passes(p, s); }, s, a, b);
     if (e == cudaSuccess) e = pick_form(xyf, &p.xyform, [&] { return launch_xy_passes(p, s); }, s, a, b);
@@ -299,6 +332,7 @@ static cudaError_t autotune(DevicePlan &p, int dev) {
         p.zform = p.yform = p.xform = p.xyform = p.arith = 0;
         return e;
     }
+    if (any) return cudaSuccess;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const TuneEntry &t : g_tune)  // another thread may have decided meanwhile
         if (t.dev == dev && t.N == p.N && t.dtype == p.dtype) {
@@ -368,7 +402,7 @@ static void free_plan(poisson_plan p) {
     delete p;
 }
 
-extern "C" int poisson_supported_n(int N) { return gsp::n_supported(N) ? 1 : 0; }
+extern "C" int poisson_supported_n(int N) { return gsp::n_supported(N) ? 1 : gsp::n_any(N) ? 2 : 0; }
 
 extern "C" const char *poisson_strerror(int code) {
     switch (code) {
@@ -387,24 +421,59 @@ extern "C" int poisson_plan_create(poisson_plan *out, int N, double L, double to
     return poisson_plan_create_batched(out, N, L, tol, dtype, 1);
 }
 
-static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3, double tol, int dtype,
+static int plan_create_impl(poisson_plan *out, const int *n3, double L, const double *L3, double tol, int dtype,
                             int max_batch);
 
 extern "C" int poisson_plan_create_batched(poisson_plan *out, int N, double L, double tol, int dtype,
                                            int max_batch) {
-    return plan_create_impl(out, N, L, nullptr, tol, dtype, max_batch);
+    const int n3[3] = {N, N, N};
+    return plan_create_impl(out, n3, L, nullptr, tol, dtype, max_batch);
 }
 
 extern "C" int poisson_plan_create_box(poisson_plan *out, int N, double Lx, double Ly, double Lz, double tol,
                                        int dtype) {
+    const int n3[3] = {N, N, N};
     const double L3[3] = {Lx, Ly, Lz};
-    return plan_create_impl(out, N, 0.0, L3, tol, dtype, 1);
+    return plan_create_impl(out, n3, 0.0, L3, tol, dtype, 1);
+}
+
+extern "C" int poisson_plan_create_box_n(poisson_plan *out, int nx, int ny, int nz, double Lx, double Ly, double Lz,
+                                         double tol, int dtype) {
+    const int n3[3] = {nx, ny, nz};
+    const double L3[3] = {Lx, Ly, Lz};
+    return plan_create_impl(out, n3, 0.0, L3, tol, dtype, 1);
 }
 
 // Twiddles W_{2N}^e from FP64 (long double arithmetic) into the plan's tables, in its
 // arithmetic's format: FP32 rounded once (and the column passes' (re, re, im, im) copy), FP64,
 // or double-float (re.hi, re.lo, im.hi, im.lo) split from the FP64 value.
+static cudaError_t upload_table(void *dst, int n2, int dtype, int arith) {
+    std::vector<double> tw;
+    gsp::twiddles(n2, tw);
+    const size_t n = (size_t)n2;
+    if (dtype == POISSON_F32) {
+        std::vector<float> twf(tw.begin(), tw.end());
+        return cudaMemcpy(dst, twf.data(), n * 2 * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (!arith) return cudaMemcpy(dst, tw.data(), n * 2 * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float> twd(n * 4);
+    for (size_t i = 0; i < 2 * n; ++i) {
+        const float hi = (float)tw[i];
+        twd[2 * i] = hi;
+        twd[2 * i + 1] = (float)(tw[i] - (double)hi);
+    }
+    return cudaMemcpy(dst, twd.data(), n * 4 * sizeof(float), cudaMemcpyHostToDevice);
+}
+
 static cudaError_t upload_twiddles(poisson_plan p) {
+    if (p->dp.any) {
+        // W_{2 n_q}^e of each axis, in the arithmetic's storage.
+        for (int q = 0; q < 3; ++q) {
+            cudaError_t e = upload_table(p->dp.tw3[q], 2 * p->dp.n3[q], p->dp.dtype, p->dp.arith);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int N = p->dp.N;
     std::vector<double> tw;
     gsp::twiddles(2 * N, tw);
@@ -431,19 +500,26 @@ static cudaError_t upload_twiddles(poisson_plan p) {
     return cudaMemcpy(p->dp.tw, twd.data(), n * 4 * sizeof(float), cudaMemcpyHostToDevice);
 }
 
-static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3, double tol, int dtype,
+static int plan_create_impl(poisson_plan *out, const int *n3, double L, const double *L3, double tol, int dtype,
                             int max_batch) {
     if (!out) return POISSON_ERR_ARG;
     *out = nullptr;
     if (dtype != POISSON_F32 && dtype != POISSON_F64) return POISSON_ERR_ARG;
-    if (N < 4 || N > 1024 || (N & 1)) return POISSON_ERR_ARG;
+    for (int q = 0; q < 3; ++q)
+        if (n3[q] < 4 || n3[q] > 1024 || (n3[q] & 1)) return POISSON_ERR_ARG;
     if (max_batch < 1 || max_batch > gsp::kMaxBatch) return POISSON_ERR_ARG;
-    if (!gsp::n_supported(N)) return POISSON_ERR_UNSUPPORTED;
+    const int N = n3[0];
+    const bool cube_n = n3[1] == N && n3[2] == N;
+    // The compiled-length forms serve the sizes they were built for, the same on every axis;
+    // every other even 5-smooth count (and any mix of them) runs the runtime-length forms.
+    const bool any = !(cube_n && gsp::n_supported(N));
+    if (any && !(gsp::n_any(n3[0]) && gsp::n_any(n3[1]) && gsp::n_any(n3[2]))) return POISSON_ERR_UNSUPPORTED;
+    if (any && L3 && max_batch != 1) return POISSON_ERR_ARG;
     poisson_plan p = new (std::nothrow) poisson_plan_s();
     if (!p) return POISSON_ERR_ALLOC;
     // The Gaussian sum, delta, eps and the near-zone constants on the host; the per-axis
     // table A_j(k) below on the device.
-    int rc = L3 ? gsp::build_host_scalars_box(N, L3, tol, p->ht) : gsp::build_host_scalars(N, L, tol, p->ht);
+    int rc = L3 ? gsp::build_host_scalars_box(n3, L3, tol, p->ht) : gsp::build_host_scalars(N, L, tol, p->ht);
     if (rc != POISSON_OK) {
         delete p;
         return rc;
@@ -453,19 +529,24 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
         delete p;
         return map_cuda(e);
     }
+    const int nx = n3[0], ny = n3[1], nz = n3[2];
     p->elem = dtype == POISSON_F32 ? 4 : 8;
     p->dp.max_batch = max_batch;
     p->dp.N = N;
     p->dp.dtype = dtype;
-    p->dp.Px = gsp::pitch_for(N);
-    p->dp.Ps = gsp::sym_pitch_for(N);
+    p->dp.any = any ? 1 : 0;
+    for (int q = 0; q < 3; ++q) p->dp.n3[q] = n3[q];
+    p->dp.Px = gsp::pitch_for(nx);
+    p->dp.Ps = gsp::sym_pitch_for(nx);
     const size_t cx = 2 * p->elem;
-    const size_t K = (size_t)N + 1;
-    const size_t sym_bytes = K * K * (size_t)p->dp.Ps * p->elem;
-    const size_t tw_bytes = (size_t)2 * N * cx;
-    const size_t twc_bytes = dtype == POISSON_F32 ? (size_t)2 * N * 4 * sizeof(float) : 0;
-    const size_t w1_bytes = (size_t)max_batch * N * N * p->dp.Px * cx;
-    const size_t w2_bytes = (size_t)max_batch * N * 2 * N * p->dp.Px * cx;
+    const size_t sym_bytes = (size_t)(nz + 1) * (ny + 1) * (size_t)p->dp.Ps * p->elem;
+    // Twiddles: the compiled forms W_{2N} (and, FP32, the column passes' (re, re, im, im)
+    // copy); the runtime-length forms one table W_{2 n_q} per axis (double-float: 16 bytes
+    // per entry, as FP64).
+    const size_t tw_bytes = any ? (size_t)2 * (nx + ny + nz) * cx : (size_t)2 * N * cx;
+    const size_t twc_bytes = dtype == POISSON_F32 && !any ? (size_t)2 * N * 4 * sizeof(float) : 0;
+    const size_t w1_bytes = (size_t)max_batch * nz * ny * p->dp.Px * cx;
+    const size_t w2_bytes = (size_t)max_batch * nz * 2 * ny * p->dp.Px * cx;
     p->ws_bytes = w1_bytes + 2 * w2_bytes;  // for max_batch densities
     p->table_bytes = sym_bytes + tw_bytes + twc_bytes;
 
@@ -477,11 +558,16 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
         return map_cuda(err);
     };
     if ((e = cudaMalloc(&p->dp.sym, sym_bytes)) != cudaSuccess) return fail(e);
-    if (p->ht.box) {
+    if (p->ht.box && !any) {
         if ((e = cudaMalloc(&p->dp.symT, sym_bytes)) != cudaSuccess) return fail(e);
         p->table_bytes += sym_bytes;
     }
     if ((e = cudaMalloc(&p->dp.tw, tw_bytes)) != cudaSuccess) return fail(e);
+    if (any) {
+        p->dp.tw3[0] = p->dp.tw;
+        p->dp.tw3[1] = static_cast<char *>(p->dp.tw) + (size_t)2 * nx * cx;
+        p->dp.tw3[2] = static_cast<char *>(p->dp.tw3[1]) + (size_t)2 * ny * cx;
+    }
     if ((e = cudaMalloc(&p->dp.w1, w1_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.w2, w2_bytes)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.w3, w2_bytes)) != cudaSuccess) return fail(e);
@@ -498,12 +584,12 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
     if ((e = cudaMalloc(&p->dp.status, sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&p->dp.tail, 2 * sizeof(double) * max_batch)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->dp.status, 0, sizeof(int))) != cudaSuccess) return fail(e);
-    if (gsp::xy_forms(N, dtype) != 1) {
+    if (!any && gsp::xy_forms(N, dtype) != 1) {
         const size_t sync_bytes = sizeof(int) * (size_t)gsp::xy_sync_ints();
         if ((e = cudaMalloc(&p->dp.sync, sync_bytes)) != cudaSuccess) return fail(e);
         if ((e = cudaMemset(p->dp.sync, 0, sync_bytes)) != cudaSuccess) return fail(e);
     }
-    if (p->ht.box) {
+    if (p->ht.box && !any) {
         // The z warp forms read the symbol with kz innermost, which for the cube is the table
         // itself (it is symmetric); a box's map covers its transposed copy instead.
         void *natural = p->dp.sym;
@@ -527,12 +613,18 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
     if ((e = gsp::autotune(p->dp, p->device)) != cudaSuccess) return fail(e);
     if ((e = upload_twiddles(p)) != cudaSuccess) return fail(e);
 
-    // Symbol octant on the device, in FP64, from the per-axis factors (a box: one table per
-    // axis, l_q A_j(tau_j l_q), Sec. 2).
+    // Symbol on the device, in FP64, from the per-axis factors (a box: one table per axis,
+    // l_q A_j(tau_j l_q), Sec. 2; a runtime-length plan: n_q + 1 frequencies on axis q).
     const int nterms = (int)p->ht.tau.size();
-    const size_t nA = (size_t)nterms * K;
     const bool box = p->ht.box;
-    if ((e = cudaMalloc(&dA, (box ? 3 : 1) * nA * sizeof(double))) != cudaSuccess) return fail(e);
+    const bool three = box || any;  // one table per axis
+    size_t nA3[3], off3[3], tot = 0;
+    for (int q = 0; q < 3; ++q) {
+        nA3[q] = (size_t)nterms * (n3[q] + 1);
+        off3[q] = tot;
+        tot += three ? nA3[q] : (q == 0 ? nA3[0] : 0);
+    }
+    if ((e = cudaMalloc(&dA, tot * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&dtau, (size_t)nterms * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&dgl, 32 * sizeof(double))) != cudaSuccess) return fail(e);
     {
@@ -540,40 +632,39 @@ static int plan_create_impl(poisson_plan *out, int N, double L, const double *L3
         gsp::gauss_legendre16(gl, gl + 16);
         if ((e = cudaMemcpy(dgl, gl, sizeof gl, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     }
-    if (!box) {
+    if (!three) {
         if ((e = cudaMemcpy(dtau, p->ht.tau.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
             return fail(e);
         if ((e = gsp::launch_axis_table(dtau, dgl, nterms, N, dA, 0)) != cudaSuccess) return fail(e);
-        p->ht.A.resize(nA);  // the plan keeps the table for poisson_plan_axis_table
-        if ((e = cudaMemcpy(p->ht.A.data(), dA, nA * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        p->ht.A.resize(nA3[0]);  // the plan keeps the table for poisson_plan_axis_table
+        if ((e = cudaMemcpy(p->ht.A.data(), dA, nA3[0] * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return fail(e);
     } else {
         std::vector<double> taul(nterms);
-        p->ht.A3.resize(3 * nA);
+        p->ht.A3.resize(tot);
         for (int q = 0; q < 3; ++q) {
             for (int j = 0; j < nterms; ++j) taul[j] = p->ht.tau[j] * p->ht.l[q];
             if ((e = cudaMemcpy(dtau, taul.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice)) !=
                 cudaSuccess)
                 return fail(e);
-            if ((e = gsp::launch_axis_table(dtau, dgl, nterms, N, dA + q * nA, 0)) != cudaSuccess) return fail(e);
-            if ((e = cudaMemcpy(p->ht.A3.data() + q * nA, dA + q * nA, nA * sizeof(double),
+            if ((e = gsp::launch_axis_table(dtau, dgl, nterms, n3[q], dA + off3[q], 0)) != cudaSuccess) return fail(e);
+            if ((e = cudaMemcpy(p->ht.A3.data() + off3[q], dA + off3[q], nA3[q] * sizeof(double),
                                 cudaMemcpyDeviceToHost)) != cudaSuccess)
                 return fail(e);
-            for (size_t i = 0; i < nA; ++i) p->ht.A3[q * nA + i] *= p->ht.l[q];
+            for (size_t i = 0; i < nA3[q]; ++i) p->ht.A3[off3[q] + i] *= p->ht.l[q];
         }
-        if ((e = cudaMemcpy(dA, p->ht.A3.data(), 3 * nA * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        if ((e = cudaMemcpy(dA, p->ht.A3.data(), tot * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
             return fail(e);
-        p->ht.A.assign(p->ht.A3.begin(), p->ht.A3.begin() + nA);  // the x axis
+        p->ht.A.assign(p->ht.A3.begin(), p->ht.A3.begin() + nA3[0]);  // the x axis
     }
     if ((e = cudaMalloc(&dw, p->ht.w.size() * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(dw, p->ht.w.data(), p->ht.w.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
-    const double M = 2.0 * N;
-    const double scale = p->ht.lambda * p->ht.lambda / (M * M * M);
-    e = box ? gsp::launch_symbol_table_box(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, p->ht.l, 0, 0)
-            : gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0, 0);
+    const double scale = p->ht.lambda * p->ht.lambda / (8.0 * nx * ny * nz);
+    e = three ? gsp::launch_symbol_table_box(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, p->ht.l, 0, 0)
+              : gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, 0, 0);
     if (e != cudaSuccess) return fail(e);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
     cudaFree(dA);
@@ -605,18 +696,18 @@ static int rebuild_symbol(poisson_plan p, int literal) {
     if (e != cudaSuccess) return map_cuda(e);
     if ((e = cudaSetDevice(p->device)) != cudaSuccess) return map_cuda(e);
     const int nterms = (int)p->ht.tau.size();
-    const std::vector<double> &A = p->ht.box ? p->ht.A3 : p->ht.A;  // one table or the box's three
+    const bool three = p->ht.box || p->dp.any;
+    const std::vector<double> &A = three ? p->ht.A3 : p->ht.A;  // one table or one per axis
     double *dA = nullptr, *dw = nullptr;
     e = cudaMalloc(&dA, A.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&dw, (size_t)nterms * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(dA, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(dw, p->ht.w.data(), (size_t)nterms * sizeof(double), cudaMemcpyHostToDevice);
-    const double M = 2.0 * p->dp.N, scale = p->ht.lambda * p->ht.lambda / (M * M * M);
+    const double scale = p->ht.lambda * p->ht.lambda / (8.0 * p->dp.n3[0] * p->dp.n3[1] * p->dp.n3[2]);
     if (e == cudaSuccess)
-        e = p->ht.box ? gsp::launch_symbol_table_box(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, p->ht.l,
-                                                     literal, 0)
-                      : gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, literal, 0);
+        e = three ? gsp::launch_symbol_table_box(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, p->ht.l, literal, 0)
+                  : gsp::launch_symbol_table(p->dp, dA, dw, nterms, p->ht.C0, p->ht.C2, scale, literal, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(dA);
     cudaFree(dw);
@@ -641,7 +732,7 @@ extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
         // needs nothing (every solve writes each buffer before reading it).
         const int prev = p->dp.arith, prev_z = p->dp.zform;
         p->dp.arith = value;
-        if (!(gsp::z_forms(p->dp.N, p->dp.dtype, value) >> p->dp.zform & 1)) p->dp.zform = 0;
+        if (p->dp.any || !(gsp::z_forms(p->dp.N, p->dp.dtype, value) >> p->dp.zform & 1)) p->dp.zform = 0;
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaSetDevice(p->device);
@@ -660,14 +751,15 @@ extern "C" int poisson_plan_set_knob(poisson_plan p, int knob, int value) {
         return rc;
     }
     int forms, *field;
+    const bool any = p->dp.any != 0;  // the runtime-length forms have one form per pass
     if (knob == POISSON_KNOB_Z_FORM) {
-        forms = gsp::z_forms(p->dp.N, p->dp.dtype, p->dp.arith);
+        forms = any ? 1 : gsp::z_forms(p->dp.N, p->dp.dtype, p->dp.arith);
         field = &p->dp.zform;
     } else if (knob == POISSON_KNOB_Y_FORM) {
-        forms = gsp::y_forms(p->dp.N, p->dp.dtype);
+        forms = any ? 1 : gsp::y_forms(p->dp.N, p->dp.dtype);
         field = &p->dp.yform;
     } else if (knob == POISSON_KNOB_X_FORM) {
-        forms = gsp::x_forms(p->dp.N, p->dp.dtype);
+        forms = any ? 1 : gsp::x_forms(p->dp.N, p->dp.dtype);
         field = &p->dp.xform;
     } else if (knob == POISSON_KNOB_XY_FORM) {
         forms = p->dp.sync ? gsp::xy_forms(p->dp.N, p->dp.dtype) : 1;
@@ -711,7 +803,8 @@ constexpr int kSlabs = 8;
 extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, void *stream) {
     int rc = check_solve_args(p, rho_h, u_h);
     if (rc) return rc;
-    const size_t n = (size_t)p->dp.N * p->dp.N * p->dp.N * p->elem;
+    const int nx = p->dp.n3[0], ny = p->dp.n3[1], nz = p->dp.n3[2];
+    const size_t n = (size_t)nx * ny * nz * p->elem;
     cudaError_t e;
     if (!p->stage_in) {
         if ((e = cudaMalloc(&p->stage_in, n)) != cudaSuccess) return map_cuda(e);
@@ -723,9 +816,8 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
     gsp::PtrArray in, out;
     one(in, p->stage_in);
     one(out, p->stage_out);
-    const int N = p->dp.N;
     const bool fused = p->dp.xyform == 1 && p->dp.sync != nullptr;
-    if (fused || N % kSlabs != 0 || N < 2 * kSlabs) {
+    if (fused || nz % kSlabs != 0 || nz < 2 * kSlabs) {
         if ((e = cudaMemcpyAsync(p->stage_in, rho_h, n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return map_cuda(e);
         if ((e = gsp::launch_solve(p->dp, in, out, 1, s, nullptr)) != cudaSuccess) return map_cuda(e);
@@ -747,8 +839,8 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
     }
     cudaStream_t cs = p->copy_stream;
     cudaEvent_t *ev_in = p->slab_ev, *ev_out = p->slab_ev + kSlabs, start = p->slab_ev[2 * kSlabs];
-    const int nzs = N / kSlabs;  // planes per slab
-    const size_t sb = (size_t)nzs * N * N * p->elem;
+    const int nzs = nz / kSlabs;  // planes per slab
+    const size_t sb = (size_t)nzs * ny * nx * p->elem;
     // On an error part of the pipeline may already be queued: wait for both streams so
     // that no copy into or out of the staging buffers outlives the call.
     auto fail = [&](cudaError_t err) {

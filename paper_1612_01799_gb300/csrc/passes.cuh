@@ -166,10 +166,15 @@ __device__ __forceinline__ float2 c_ext(CF x) { return make_float2(x.re, x.im); 
 __device__ __forceinline__ double2 c_ext(CD x) { return make_double2(x.re, x.im); }
 __device__ __forceinline__ double2 c_ext(CDF x) { return make_double2(df_to_double(x.re), df_to_double(x.im)); }
 
+// Twiddle tables of the runtime-length forms: exp(-2 pi i e / (2 n_q)) in the workspace
+// storage of the arithmetic.
+template <typename Real> using AnyTw = Cx2<Real>;
+
 }  // namespace gsp
 #include "passes_tma.cuh"
 #include "passes_zwarp.cuh"
 #include "passes_xy.cuh"
+#include "passes_any.cuh"
 namespace gsp {
 
 // ---- K1: x forward (real, zero-padded to 2N) -------------------------------------------
@@ -898,9 +903,113 @@ cudaError_t encode_n(DevicePlan &p) {
                                               cudaStream_t, bool);                                         \
     EXT template cudaError_t encode_n<Real, n>(DevicePlan &);
 
+// ---- runtime-length forms: launchers ----------------------------------------------------------
+// Tiles sized so that the ping-pong pair of one CTA stays within about 64 KB of shared memory.
+template <typename Real> int any_tile(int L, int cap) {
+    const int bytes = 2 * L * (int)sizeof(typename Types<Real>::CS);
+    int t = cap;
+    while (t > 1 && t * bytes > 65536) t /= 2;
+    return t;
+}
+
+template <typename Real>
+cudaError_t any_x(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s, bool fwd,
+                  int rows = 0, void *w1 = nullptr) {
+    const int nx = p.n3[0], ny = p.n3[1], nz = p.n3[2];
+    const AnySched sc = any_sched(nx);
+    const int rows_b = ny * nz, nrows = rows ? rows : B * rows_b;
+    const int TR = any_tile<Real>(nx, 16);
+    const size_t smem = (size_t)2 * nx * TR * sizeof(typename Types<Real>::CS);
+    const AnyTw<Real> *tw = static_cast<const AnyTw<Real> *>(p.tw3[0]);
+    Cx2<Real> *ws = static_cast<Cx2<Real> *>(w1 ? w1 : p.w1);
+    const int grid = (nrows + TR - 1) / TR;
+    if (fwd) {
+        GSP_CHECK(set_smem(k_any_x_fwd<Real>, smem));
+        GSP_CHECK(launch_pdl(k_any_x_fwd<Real>, grid, 256, smem, s, rho, ws, tw, sc, rows_b, nrows, p.Px, TR));
+    } else {
+        GSP_CHECK(set_smem(k_any_x_inv<Real>, smem));
+        GSP_CHECK(launch_pdl(k_any_x_inv<Real>, grid, 256, smem, s, static_cast<const Cx2<Real> *>(ws), u, tw, sc,
+                             rows_b, nrows, p.Px, TR));
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t any_y(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 = 0, int nzs = 0) {
+    const int nx = p.n3[0], ny = p.n3[1], nz = p.n3[2], L = 2 * ny;
+    const AnySched sc = any_sched(L);
+    const int TC = any_tile<Real>(L, 16), ncols = nx + 1, ntx = (ncols + TC - 1) / TC;
+    const int planes = nzs ? nzs : B * nz;
+    const size_t smem = (size_t)2 * L * TC * sizeof(typename Types<Real>::CS);
+    const AnyTw<Real> *tw = static_cast<const AnyTw<Real> *>(p.tw3[1]);
+    const long long Px = p.Px, w1p = (long long)ny * Px, w2p = (long long)L * Px;
+    const Cx2<Real> *w1 = static_cast<const Cx2<Real> *>(p.w1), *w3 = static_cast<const Cx2<Real> *>(p.w3);
+    Cx2<Real> *w1o = static_cast<Cx2<Real> *>(p.w1), *w2 = static_cast<Cx2<Real> *>(p.w2);
+    if (fwd) {
+        GSP_CHECK(set_smem(k_any_col<Real, true>, smem));
+        GSP_CHECK(launch_pdl(k_any_col<Real, true>, ntx * planes, 256, smem, s, w1 + z0 * w1p, w2 + z0 * w2p, tw, sc,
+                             ncols, ntx, TC, Px, w1p, Px, w2p));
+    } else {
+        GSP_CHECK(set_smem(k_any_col<Real, false>, smem));
+        GSP_CHECK(launch_pdl(k_any_col<Real, false>, ntx * planes, 256, smem, s, w3 + z0 * w2p, w1o + z0 * w1p, tw, sc,
+                             ncols, ntx, TC, Px, w2p, Px, w1p));
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t any_z(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
+    const int nx = p.n3[0], ny = p.n3[1], nz = p.n3[2], L = 2 * nz;
+    const AnySched sc = any_sched(L);
+    const int TC = any_tile<Real>(L, 16), ncols = nx + 1, ntx = (ncols + TC - 1) / TC;
+    const size_t smem = (size_t)2 * L * TC * sizeof(typename Types<Real>::CS);
+    const AnyTw<Real> *tw = static_cast<const AnyTw<Real> *>(p.tw3[2]);
+    const int grid = ntx * 2 * ny * B;
+    auto k = tail ? k_any_z<Real, true> : k_any_z<Real, false>;
+    GSP_CHECK(set_smem(k, smem));
+    GSP_CHECK(launch_pdl(k, grid, 256, smem, s, static_cast<const Cx2<Real> *>(p.w2), static_cast<Cx2<Real> *>(p.w3),
+                         static_cast<const Real *>(p.sym), tw, sc, nx, ny, ntx, TC, p.Px, p.Ps, tail));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t solve_any(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B, cudaStream_t s,
+                      cudaEvent_t *ev, double *tail, int skip) {
+    if (ev) GSP_CHECK(cudaEventRecord(ev[0], s));
+    if (!(skip & 1)) GSP_CHECK(any_x<Real>(p, rho, u, B, s, true));
+    if (ev) GSP_CHECK(cudaEventRecord(ev[1], s));
+    if (!(skip & 1)) GSP_CHECK(any_y<Real>(p, B, s, true));
+    if (ev) GSP_CHECK(cudaEventRecord(ev[2], s));
+    GSP_CHECK(any_z<Real>(p, B, s, tail));
+    if (ev) GSP_CHECK(cudaEventRecord(ev[3], s));
+    if (!(skip & 2)) GSP_CHECK(any_y<Real>(p, B, s, false));
+    if (ev) GSP_CHECK(cudaEventRecord(ev[4], s));
+    if (!(skip & 2)) GSP_CHECK(any_x<Real>(p, rho, u, B, s, false));
+    if (ev) GSP_CHECK(cudaEventRecord(ev[5], s));
+    return cudaSuccess;
+}
+
+// The x and y passes of planes z0 .. z0 + nzs - 1 of one density (poisson_solve_host's slabs).
+template <typename Real>
+cudaError_t any_xy_slab(const DevicePlan &p, const void *rho, void *u, int z0, int nzs, cudaStream_t s, bool fwd) {
+    const int nx = p.n3[0], ny = p.n3[1];
+    const long long row0 = (long long)z0 * ny;
+    void *w1 = static_cast<char *>(p.w1) + row0 * p.Px * (long long)sizeof(Cx2<Real>);
+    PtrArray a{}, b{};
+    a.p[0] = static_cast<const char *>(rho) + row0 * nx * (long long)sizeof(Ext2<Real>) / 2;
+    b.p[0] = static_cast<char *>(u) + row0 * nx * (long long)sizeof(Ext2<Real>) / 2;
+    if (fwd) {
+        GSP_CHECK(any_x<Real>(p, a, b, 1, s, true, nzs * ny, w1));
+        return any_y<Real>(p, 1, s, true, z0, nzs);
+    }
+    GSP_CHECK(any_y<Real>(p, 1, s, false, z0, nzs));
+    return any_x<Real>(p, a, b, 1, s, false, nzs * ny, w1);
+}
+
 template <typename Real>
 cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, int B,
                            cudaStream_t s, cudaEvent_t *ev, double *tail, int skip) {
+    if (p.any) return solve_any<Real>(p, rho, u, B, s, ev, tail, skip);
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
@@ -914,6 +1023,7 @@ cudaError_t solve_dispatch(const DevicePlan &p, const PtrArray &rho, const PtrAr
 
 template <typename Real>
 cudaError_t z_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    if (p.any) return any_z<Real>(p, 1, s, nullptr);
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
@@ -927,6 +1037,10 @@ cudaError_t z_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
 
 template <typename Real>
 cudaError_t y_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    if (p.any) {
+        cudaError_t e = any_y<Real>(p, 1, s, true);
+        return e != cudaSuccess ? e : any_y<Real>(p, 1, s, false);
+    }
     switch (p.N) {
 #define GSP_CASE(n)                                                   \
     case n: {                                                         \
@@ -946,6 +1060,10 @@ template <typename Real>
 cudaError_t x_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
     PtrArray a{};
     a.p[0] = p.w2;
+    if (p.any) {
+        cudaError_t e = any_x<Real>(p, a, a, 1, s, true);
+        return e != cudaSuccess ? e : any_x<Real>(p, a, a, 1, s, false);
+    }
     switch (p.N) {
 #define GSP_CASE(n)                                                          \
     case n: {                                                                \
@@ -964,6 +1082,14 @@ cudaError_t x_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
 // fused w1 -> w2 (ring in w3) and w3 -> w1 (ring in w2).
 template <typename Real>
 cudaError_t xy_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
+    if (p.any) {
+        PtrArray a{};
+        a.p[0] = p.w2;
+        cudaError_t e = any_x<Real>(p, a, a, 1, s, true);
+        if (e == cudaSuccess) e = any_y<Real>(p, 1, s, true);
+        if (e == cudaSuccess) e = any_y<Real>(p, 1, s, false);
+        return e != cudaSuccess ? e : any_x<Real>(p, a, a, 1, s, false);
+    }
     switch (p.N) {
 #define GSP_CASE(n)                                                                  \
     case n: {                                                                        \
@@ -987,6 +1113,7 @@ cudaError_t xy_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
 
 template <typename Real>
 cudaError_t xy_slab_dispatch(const DevicePlan &p, const void *rho, void *u, int z0, int nz, cudaStream_t s, bool fwd) {
+    if (p.any) return any_xy_slab<Real>(p, rho, u, z0, nz, s, fwd);
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
@@ -1012,6 +1139,7 @@ inline bool zsplit_dispatch(int N) {
 
 template <typename Real>
 cudaError_t encode_dispatch(DevicePlan &p) {
+    if (p.any) return cudaSuccess;  // the runtime-length forms use no TMA descriptors
     switch (p.N) {
 #define GSP_CASE(n) \
     case n:         \
@@ -1033,5 +1161,6 @@ cudaError_t symbol_table(const DevicePlan &p, const double *dA, const double *dw
         static_cast<Real *>(p.sym), dA, dw, nterms, p.N, p.Ps, C0, C2, scale, literal);
     return cudaGetLastError();
 }
+
 
 }  // namespace gsp

@@ -203,6 +203,7 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
 // padding not at all).
 __device__ __forceinline__ float2 cenergy(CV x) { return f2fma(x.re, x.re, f2mul(x.im, x.im)); }
 __device__ __forceinline__ float cenergy(CD x) { return (float)(x.re * x.re + x.im * x.im); }
+__device__ __forceinline__ float cenergy(CF x) { return x.re * x.re + x.im * x.im; }
 __device__ __forceinline__ float cenergy(CDF x) { return x.re.hi * x.re.hi + x.im.hi * x.im.hi; }
 
 // With TAIL, the forward spectrum's energy in the outer shell max(|kx|,|ky|,|kz|) >= 7N/8

@@ -276,9 +276,11 @@ int build_host_scalars(int N, double L, double tol, HostTables &o) {
     return POISSON_OK;
 }
 
-int build_host_scalars_box(int N, const double *L3, double tol, HostTables &o) {
-    if (N < 4 || N > 1024 || (N & 1) || !L3 || !(tol > 0.0) || !std::isfinite(tol))
-        return POISSON_ERR_ARG;
+int build_host_scalars_box(const int *n3, const double *L3, double tol, HostTables &o) {
+    if (!n3 || !L3 || !(tol > 0.0) || !std::isfinite(tol)) return POISSON_ERR_ARG;
+    for (int q = 0; q < 3; ++q)
+        if (n3[q] < 4 || n3[q] > 1024 || (n3[q] & 1)) return POISSON_ERR_ARG;
+    const int N = n3[0];
     double lam = 0.0, lmin = 0.0;
     for (int q = 0; q < 3; ++q) {
         if (!(L3[q] > 0.0) || !std::isfinite(L3[q])) return POISSON_ERR_ARG;
@@ -297,7 +299,9 @@ int build_host_scalars_box(int N, const double *L3, double tol, HostTables &o) {
         lmin = std::min(lmin, o.l[q]);
     }
     // Sec. 3: min_q (b_q - a_q) / (50 n_q), at least 1e-3, used as is in the scaled box.
-    o.delta = std::max(2.0 * std::min({L3[0], L3[1], L3[2]}) / (50.0 * N), 1e-3);
+    o.delta = std::max(std::min({2.0 * L3[0] / (50.0 * n3[0]), 2.0 * L3[1] / (50.0 * n3[1]),
+                                 2.0 * L3[2] / (50.0 * n3[2])}),
+                       1e-3);
     if (!(o.delta < lmin)) return POISSON_ERR_ARG;  // Sec. 3: delta < min_q l_q
     o.eps = eps_for_tol(tol);
     o.r_max = 2.0 * std::sqrt(l2);

@@ -57,10 +57,10 @@ int build_host_tables(int N, double L, double tol, HostTables &out);
 // on the device.
 int build_host_scalars(int N, double L, double tol, HostTables &out);
 
-// The scalars for the box [-L3[0], L3[0]] x [-L3[1], L3[1]] x [-L3[2], L3[2]] with N points
-// per axis: lambda = max_q L_q, l_q = L_q / lambda, delta = max(min_q 2 L_q / (50 N), 1e-3)
-// below min_q l_q, the Gaussian sum fitted on [delta, 2 |l|].
-int build_host_scalars_box(int N, const double *L3, double tol, HostTables &out);
+// The scalars for the box [-L3[0], L3[0]] x [-L3[1], L3[1]] x [-L3[2], L3[2]] with n3[q]
+// points on axis q: lambda = max_q L_q, l_q = L_q / lambda, delta = max(min_q 2 L_q /
+// (50 n_q), 1e-3) below min_q l_q, the Gaussian sum fitted on [delta, 2 |l|].
+int build_host_scalars_box(const int *n3, const double *L3, double tol, HostTables &out);
 
 // tw[e] = exp(-2 pi i e / n), e in [0, n), as (re, im) pairs, accurate to FP64 rounding.
 void twiddles(int n, std::vector<double> &re_im);

@@ -66,46 +66,47 @@ __global__ void k_axis_table(const double *__restrict__ tau, const double *__res
 }
 
 // The symbol of a box [-l_1, l_1] x [-l_2, l_2] x [-l_3, l_3] (Sec. 2 standardised form):
-// sum_j w_j Ax_j(kx) Ay_j(ky) Az_j(kz) with the per-axis factors of each axis, and kappa_q =
-// pi k_q / (2 l_q) in the correction (il2[q] = 1 / l_q^2); `literal` as in k_symbol_table.
-// The table is no longer symmetric: block (ky, kz) computes its whole kx line,
-// sym[(kz * (N+1) + ky) * Ps + kx], and writes it transposed, symT[(kx * (N+1) + ky) * Ps +
-// kz], for the z warp forms, which read the table with kz innermost.
+// sum_j w_j Ax_j(kx) Ay_j(ky) Az_j(kz) with the per-axis factors of each axis (n_q + 1
+// frequencies on axis q), and kappa_q = pi k_q / (2 l_q) in the correction (il2[q] = 1 / l_q^2);
+// `literal` as in k_symbol_table.  The table is not symmetric: block (ky, kz) computes its
+// whole kx line, sym[(kz * Ky + ky) * Ps + kx], and, when symT is set, writes it transposed,
+// symT[(kx * Ky + ky) * Ps + kz], for the z warp forms, which read the table with kz
+// innermost (those plans have Kx = Ky = Kz).
 template <typename Real>
-__global__ void k_symbol_box(Real *__restrict__ sym, Real *__restrict__ symT, const double *__restrict__ Ax, const double *__restrict__ Ay,
-                             const double *__restrict__ Az, const double *__restrict__ w, int nterms, int N,
-                             int Ps, double C0, double C2, double scale, double il2x, double il2y, double il2z,
-                             int literal) {
+__global__ void k_symbol_box(Real *__restrict__ sym, Real *__restrict__ symT, const double *__restrict__ Ax,
+                             const double *__restrict__ Ay, const double *__restrict__ Az, const double *__restrict__ w,
+                             int nterms, int Kx, int Ky, int Ps, double C0, double C2, double scale, double il2x,
+                             double il2y, double il2z, int literal) {
     extern __shared__ double cj[];
-    const int b = blockIdx.x, c = blockIdx.y, K = N + 1;
+    const int b = blockIdx.x, c = blockIdx.y;
     for (int j = threadIdx.x; j < nterms; j += blockDim.x)
-        cj[j] = w[j] * Ay[(long long)j * K + b] * Az[(long long)j * K + c];
+        cj[j] = w[j] * Ay[(long long)j * Ky + b] * Az[(long long)j * gridDim.y + c];
     __syncthreads();
     const double hp2 = 0.25 * 3.141592653589793238462643383279502884 * 3.141592653589793238462643383279502884;
-    for (int a = threadIdx.x; a <= N; a += blockDim.x) {
+    for (int a = threadIdx.x; a < Kx; a += blockDim.x) {
         double sum = 0.0;
-        for (int j = 0; j < nterms; ++j) sum += cj[j] * Ax[(long long)j * K + a];
+        for (int j = 0; j < nterms; ++j) sum += cj[j] * Ax[(long long)j * Kx + a];
         const double k2 = (double)a * a * il2x + (double)b * b * il2y + (double)c * c * il2z;
         double v;
         if (!literal) v = sum + C0 - C2 * hp2 * k2;
         else v = ((a | b | c) & 1) ? sum : sum + 8.0 * (C0 - C2 * hp2 * k2);
-        sym[((long long)c * K + b) * Ps + a] = (Real)(scale * v);
-        symT[((long long)a * K + b) * Ps + c] = (Real)(scale * v);
+        sym[((long long)c * Ky + b) * Ps + a] = (Real)(scale * v);
+        if (symT) symT[((long long)a * Ky + b) * Ps + c] = (Real)(scale * v);
     }
 }
 
 template <typename Real>
 cudaError_t symbol_table_box(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
                              double C0, double C2, double scale, const double *l, int literal, cudaStream_t s) {
-    const int K = p.N + 1;
-    const size_t tab = (size_t)nterms * K;
-    cudaError_t e = cudaMemsetAsync(p.sym, 0, (size_t)K * K * p.Ps * sizeof(Real), s);
+    const int Kx = (p.any ? p.n3[0] : p.N) + 1, Ky = (p.any ? p.n3[1] : p.N) + 1, Kz = (p.any ? p.n3[2] : p.N) + 1;
+    const size_t bytes = (size_t)Kz * Ky * p.Ps * sizeof(Real);
+    cudaError_t e = cudaMemsetAsync(p.sym, 0, bytes, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(p.symT, 0, (size_t)K * K * p.Ps * sizeof(Real), s);
-    if (e != cudaSuccess) return e;
-    k_symbol_box<Real><<<dim3(K, K), 128, nterms * sizeof(double), s>>>(
-        static_cast<Real *>(p.sym), static_cast<Real *>(p.symT), dA3, dA3 + tab, dA3 + 2 * tab, dw, nterms, p.N, p.Ps, C0, C2, scale,
-        1.0 / (l[0] * l[0]), 1.0 / (l[1] * l[1]), 1.0 / (l[2] * l[2]), literal);
+    if (p.symT && (e = cudaMemsetAsync(p.symT, 0, bytes, s)) != cudaSuccess) return e;
+    const double *Ax = dA3, *Ay = Ax + (size_t)nterms * Kx, *Az = Ay + (size_t)nterms * Ky;
+    k_symbol_box<Real><<<dim3(Ky, Kz), 128, nterms * sizeof(double), s>>>(
+        static_cast<Real *>(p.sym), static_cast<Real *>(p.symT), Ax, Ay, Az, dw, nterms, Kx, Ky, p.Ps, C0, C2,
+        scale, 1.0 / (l[0] * l[0]), 1.0 / (l[1] * l[1]), 1.0 / (l[2] * l[2]), literal);
     return cudaGetLastError();
 }
 }  // namespace

@@ -15,6 +15,20 @@ struct PtrArray {
     const void *p[kMaxBatch];
 };
 
+// Radix schedule of a runtime-length transform (the runtime-length pass forms): length L,
+// nst stages of radices r[0..nst) in {2, 3, 4, 5}, first to last.
+constexpr int kAnyMaxStages = 16;
+struct AnySched {
+    int L;
+    int nst;
+    int r[kAnyMaxStages];
+};
+// The schedule of length L (fives, threes, fours, then a two), or nst = 0 if L has a prime
+// factor above 5.
+AnySched any_sched(int L);
+// N of the runtime-length forms: even, 4 <= N <= 1024, no prime factor above 5.
+bool n_any(int N);
+
 // Device side of a plan.  Workspace layout (complex values of the plan's dtype) for up to
 // max_batch densities b stacked along z:
 //   w1: [b][z < N][y < N][kx < Px]     after the x pass (and again after the y inverse)
@@ -35,6 +49,13 @@ struct DevicePlan {
     // the FP32 pipe; workspace, twiddles and symbol then hold (hi, lo) float pairs, and rho
     // and u stay FP64).  Always 0 for FP32 plans.
     int arith = 0;
+    // Runtime-length forms (any = 1): the points per axis n3 = (nx, ny, nz), which may
+    // differ; N = nx.  Their passes read the twiddles W_{2 n_q}^e of axis q from tw3[q]
+    // (the dtype's storage: float2, double2, or double-float float4), the symbol as
+    // [kz <= nz][ky <= ny][kx < Ps], and use no TMA descriptors and no form knobs.
+    int any = 0;
+    int n3[3] = {0, 0, 0};
+    void *tw3[3] = {nullptr, nullptr, nullptr};
     int Px = 0;
     int Ps = 0;
     void *sym = nullptr;
@@ -146,8 +167,10 @@ cudaError_t launch_axis_table(const double *dtau, const double *dgl, int S, int 
 cudaError_t launch_symbol_table(const DevicePlan &p, const double *dA, const double *dw,
                                 int nterms, double C0, double C2, double scale, int literal,
                                 cudaStream_t s);
-// The same for a box: dA3 holds the x, y and z tables one after the other, l the scaled
-// half-lengths; the table is not symmetric.
+// The same for a box: dA3 holds the x, y and z tables one after the other (n_q + 1 entries
+// per term on axis q: p.n3 for a runtime-length plan, N on every axis otherwise), l the
+// scaled half-lengths; the table is not symmetric.  p.symT, where set, also receives it with
+// kz innermost.
 cudaError_t launch_symbol_table_box(const DevicePlan &p, const double *dA3, const double *dw, int nterms,
                                     double C0, double C2, double scale, const double *l, int literal,
                                     cudaStream_t s);

@@ -30,11 +30,11 @@ extern "C" void shim_twiddles(int n, double *out) {
     std::memcpy(out, v.data(), v.size() * sizeof(double));
 }
 
-// Box scalars: out = {lambda, l_x, l_y, l_z, delta, eps, C0, C2, r_max}.
-extern "C" int shim_box_scalars(int N, const double *L3, double tol, int cap_terms, int *n_terms, double *tau,
-                                double *w, double *out) {
+// Box scalars (n3[q] points on axis q): out = {lambda, l_x, l_y, l_z, delta, eps, C0, C2, r_max}.
+extern "C" int shim_box_scalars(const int *n3, const double *L3, double tol, int cap_terms, int *n_terms,
+                                double *tau, double *w, double *out) {
     gsp::HostTables t;
-    int rc = gsp::build_host_scalars_box(N, L3, tol, t);
+    int rc = gsp::build_host_scalars_box(n3, L3, tol, t);
     if (rc) return rc;
     *n_terms = (int)t.tau.size();
     if ((int)t.tau.size() > cap_terms) return -100;

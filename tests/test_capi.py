@@ -38,11 +38,25 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def five_smooth_even(n):
+    if n < 4 or n > 1024 or n % 2:
+        return False
+    for f in (2, 3, 5):
+        while n % f == 0:
+            n //= f
+    return n == 1
+
+
 def test_supported_sizes(lib):
-    for n in (4, 8, 32, 64, 96, 128, 160, 192, 256, 512, 1024):
+    """1: compiled-length forms; 2: runtime-length forms (every other even N in 4..1024
+    with no prime factor above 5, i.e. 2N factors into 2, 3 and 5); 0: unsupported."""
+    compiled = (4, 8, 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 1024)
+    for n in compiled:
         assert lib.poisson_supported_n(n) == 1
-    for n in (0, 2, 3, 7, 33, 100, 1026, 2048, -4):
-        assert lib.poisson_supported_n(n) == 0
+    for n in range(-4, 1100):
+        if n not in compiled:
+            assert lib.poisson_supported_n(n) == (2 if five_smooth_even(n) else 0), n
+    assert sum(lib.poisson_supported_n(n) == 2 for n in range(1100)) == 51
 
 
 def test_error_strings(lib):
@@ -58,7 +72,8 @@ def test_plan_create_rejects_bad_arguments(lib):
     assert h.value is None                                                        # cleared
     assert lib.poisson_plan_create(ctypes.byref(h), 2, 8.0, 1e-12, 1) == -1
     assert lib.poisson_plan_create(ctypes.byref(h), 32, 8.0, 1e-12, 7) == -1     # dtype
-    assert lib.poisson_plan_create(ctypes.byref(h), 100, 8.0, 1e-12, 0) == -4    # no FFT plan
+    assert lib.poisson_plan_create(ctypes.byref(h), 14, 8.0, 1e-12, 0) == -4     # prime factor 7
+    assert lib.poisson_plan_create(ctypes.byref(h), 1030, 8.0, 1e-12, 0) == -1   # above 1024
     assert lib.poisson_plan_create(ctypes.byref(h), 32, -1.0, 1e-12, 0) == -1    # L <= 0
     assert lib.poisson_plan_create(ctypes.byref(h), 32, float("nan"), 1e-12, 0) == -1
     assert lib.poisson_plan_create(ctypes.byref(h), 32, 8.0, 0.0, 0) == -1       # tol <= 0
@@ -70,12 +85,26 @@ def test_box_plan_create_rejects_bad_arguments(lib):
     assert lib.poisson_plan_create_box(None, 32, 1.0, 2.0, 3.0, 1e-12, 1) == -1
     assert lib.poisson_plan_create_box(ctypes.byref(h), 33, 1.0, 2.0, 3.0, 1e-12, 1) == -1   # odd N
     assert h.value is None
-    assert lib.poisson_plan_create_box(ctypes.byref(h), 100, 1.0, 2.0, 3.0, 1e-12, 0) == -4  # no FFT plan
+    assert lib.poisson_plan_create_box(ctypes.byref(h), 44, 1.0, 2.0, 3.0, 1e-12, 0) == -4   # prime factor 11
     assert lib.poisson_plan_create_box(ctypes.byref(h), 32, 1.0, -2.0, 3.0, 1e-12, 0) == -1  # L_q <= 0
     assert lib.poisson_plan_create_box(ctypes.byref(h), 32, 1.0, float("inf"), 3.0, 1e-12, 0) == -1
     assert lib.poisson_plan_create_box(ctypes.byref(h), 32, 1.0, 2.0, 3.0, 0.0, 0) == -1     # tol <= 0
     # Sec. 3 side condition: delta (at least 1e-3) must lie below the flattest l_q = 1e-4
     assert lib.poisson_plan_create_box(ctypes.byref(h), 4, 0.001, 10.0, 10.0, 1e-6, 0) == -1
+
+
+def test_box_n_plan_create_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p(1234)
+    f = lib.poisson_plan_create_box_n
+    assert f(None, 16, 24, 32, 1.0, 2.0, 3.0, 1e-12, 1) == -1
+    assert f(ctypes.byref(h), 16, 25, 32, 1.0, 2.0, 3.0, 1e-12, 1) == -1    # odd n_y
+    assert h.value is None
+    assert f(ctypes.byref(h), 16, 24, 2, 1.0, 2.0, 3.0, 1e-12, 1) == -1     # n_z < 4
+    assert f(ctypes.byref(h), 16, 24, 2048, 1.0, 2.0, 3.0, 1e-12, 1) == -1  # n_z > 1024
+    assert f(ctypes.byref(h), 16, 28, 32, 1.0, 2.0, 3.0, 1e-12, 1) == -4    # prime factor 7
+    assert f(ctypes.byref(h), 16, 24, 32, 1.0, 0.0, 3.0, 1e-12, 1) == -1    # L_y <= 0
+    assert f(ctypes.byref(h), 16, 24, 32, 1.0, 2.0, 3.0, 1e-12, 3) == -1    # dtype
+    assert f(ctypes.byref(h), 16, 24, 32, 1.0, 2.0, 3.0, -1.0, 0) == -1     # tol <= 0
 
 
 def test_null_plan_calls_are_errors(lib):

@@ -24,7 +24,7 @@ def shim(tmp_path_factory):
     lib.shim_host_tables.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), P, P, P, P]
     lib.shim_twiddles.argtypes = [ctypes.c_int, P]
-    lib.shim_box_scalars.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
+    lib.shim_box_scalars.argtypes = [ctypes.POINTER(ctypes.c_int), P, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), P, P, P]
     return lib
 
@@ -73,20 +73,24 @@ def test_twiddles_exact(shim):
 
 
 @pytest.mark.parametrize("N,L3,tol", [(32, (2.5, 2.75, 3.0), 1e-12), (64, (2.0, 4.0, 6.0), 1e-6),
-                                      (48, (4.0, 4.0, 4.0), 1e-10)])
+                                      (48, (4.0, 4.0, 4.0), 1e-10), ((162, 162, 162), (2.0, 4.0, 6.0), 1e-12),
+                                      ((16, 64, 12), (2.0, 4.0, 6.0), 1e-10), ((100, 40, 24), (1.0, 3.0, 3.0), 1e-6)])
 def test_box_scalars_match_oracle(shim, N, L3, tol):
-    """Box plans (Sec. 2 standardised form): lambda, l_q, delta, the Gaussian sum on
-    [delta, 2 |l|] and the near-zone constants against the oracle's box plan."""
+    """Box plans (Sec. 2 standardised form, n_q points on axis q): lambda, l_q, delta (the
+    Sec. 3 heuristic's minimum over the axes), the Gaussian sum on [delta, 2 |l|] and the
+    near-zone constants against the oracle's box plan."""
     from oracle import box
     P = ctypes.POINTER(ctypes.c_double)
     cap = 1000
     n = ctypes.c_int()
     tau, w, out = np.zeros(cap), np.zeros(cap), np.zeros(9)
     L = np.array(L3, dtype=np.float64)
-    assert shim.shim_box_scalars(N, L.ctypes.data_as(P), tol, cap, ctypes.byref(n), tau.ctypes.data_as(P),
-                                 w.ctypes.data_as(P), out.ctypes.data_as(P)) == 0
+    n3 = np.array(N if np.ndim(N) else (N, N, N), dtype=np.int32)
+    assert shim.shim_box_scalars(n3.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), L.ctypes.data_as(P), tol, cap,
+                                 ctypes.byref(n), tau.ctypes.data_as(P), w.ctypes.data_as(P),
+                                 out.ctypes.data_as(P)) == 0
     k = n.value
-    po = box.make_box_plan(N, [-v for v in L3], list(L3), tol)
+    po = box.make_box_plan(tuple(int(v) for v in n3), [-v for v in L3], list(L3), tol)
     assert out[0] == po.lam and tuple(out[1:4]) == pytest.approx(po.l, rel=1e-15)
     assert out[4] == pytest.approx(po.delta, rel=1e-15) and out[5] == po.eps
     assert k == len(po.gs.tau)
