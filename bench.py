@@ -554,6 +554,72 @@ def run_ours(args):
     return 0
 
 
+def run_slab(args):
+    """One solve split over the ranks as z slabs and ky lines (two all-to-all exchanges of
+    the y-spectrum; strong scaling: the same N^3 solve on every N).  Rank 0 checks its own
+    planes against the oracle and prints the line."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1612_01799_gb300 import Plan, build, slab
+    from paper_1612_01799_gb300 import densities as D
+    build.build()
+    N = args.N
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = D.config_aniso4(N=N)
+    rho64 = wl.sample()
+    z0, z1 = slab.bounds(N, world, rank)
+    plan = Plan(N, L_BOX, TOL32, "f32")
+    stages = slab.PlanStages(torch, plan)
+    rho_slab = torch.from_numpy(np.ascontiguousarray(rho64[z0:z1]).astype(np.float32)).to(dev).reshape(-1)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return slab.slab_solve(torch, stages, rho_slab, (N, N, N), rank, world)
+
+    for _ in range(args.warmup):
+        u = step()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        u = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = max_over_ranks(torch, statistics.mean(times), dev)
+    plan.last_status()
+    if rank == 0:
+        ref, _, _, _ = oracle_reference(rho64, N, L_BOX, TOL32) if not args.no_accuracy else (None, 0, 0, 0)
+        acc = None
+        if ref is not None:
+            acc = errors(u.cpu().numpy().reshape(z1 - z0, N, N), ref[z0:z1])
+            acc["vs"] = "FP64 oracle, rank 0's planes %d..%d of the %d^3 grid" % (z0, z1 - 1, N)
+        line = {"metric": METRIC, "value": N ** 3 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_config(N, "f32"), parallelism="one solve over %d ranks: z slabs for the x "
+                               "and y passes, ky lines for the z pass, two all-to-all exchanges" % world),
+                "accuracy": acc, "gpu_launches": 5 * args.steps,
+                "step": "forward x and y on the rank's planes, exchange, z pass on its lines, exchange, "
+                        "inverse y and x; CUDA events on the rank's stream, max over ranks"}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,6 +627,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--slab", action="store_true",
+                    help="one solve split over the ranks (slab decomposition) instead of one solve per rank")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the oracle solves (accuracy figures and the CPU baseline)")
     ap.add_argument("--no-batched", action="store_true")
@@ -579,6 +647,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.slab:
+        return run_slab(args)
     return run_ours(args)
 
 

@@ -386,6 +386,42 @@ int poisson_select_n(poisson_selector s, const float *sample32_d, int count, dou
                      float *pred_out, void *stream);
 
 /*
+ * Slab decomposition of one solve over P ranks (one GPU each, one plan each; the paper has
+ * one device, this spreads its convolution).  The x and y passes work plane by plane in z and
+ * the fused z pass line by line in (kx, ky), so a rank r that owns density planes
+ * [z0_r, z0_r + nz_r) and y-spectrum lines [ky0_r, ky0_r + nky_r) solves as:
+ *   1. poisson_slab_forward: the x and y forward passes of its planes, into planes
+ *      z0_r .. of its plan's y-spectrum buffer (buffer 0 below);
+ *   2. the caller exchanges blocks: rank r sends buffer 0 [z in its planes][ky in rank s's
+ *      lines] to every rank s and receives [z in s's planes][ky in its lines] into the same
+ *      place of its own buffer 0 (an all-to-all);
+ *   3. poisson_slab_z: the fused z pass (forward, symbol, inverse) of its lines, all z, from
+ *      buffer 0 into buffer 1;
+ *   4. the reverse exchange on buffer 1: it sends [z in s's planes][ky in its lines] and
+ *      receives [z in its planes][ky in s's lines];
+ *   5. poisson_slab_inverse: the y and x inverse passes of its planes, into u.
+ * rho_slab_d / u_slab_d: device pointers to the slab's planes only (nz ny nx values of the
+ * plan's dtype, x fastest).  0 <= z0, 1 <= nz, z0 + nz <= n_z; 0 <= ky0, 1 <= nky,
+ * ky0 + nky <= 2 n_y; else POISSON_ERR_ARG.  Stream ordered, no host synchronisation.  The
+ * z pass of a slab runs in the runtime-length form on the plan's tables (any plan, any
+ * arithmetic).  Each rank's plan holds a whole workspace; the slabs divide the work, not the
+ * memory.  The plan's first density only; not with work of the plan in flight.
+ */
+int poisson_slab_forward(poisson_plan p, const void *rho_slab_d, int z0, int nz, void *stream);
+int poisson_slab_z(poisson_plan p, int ky0, int nky, void *stream);
+int poisson_slab_inverse(poisson_plan p, void *u_slab_d, int z0, int nz, void *stream);
+
+/*
+ * The plan's y-spectrum buffers for the exchanges of a slab decomposition: which = 0 the
+ * forward spectrum (the x and y passes write it, the z pass reads it), 1 the z pass's output.
+ * *ptr receives the device pointer; layout [z < n_z][ky < 2 n_y][kx < Px] of complex values
+ * (re, im of the dtype; double-float: four floats re.hi, re.lo, im.hi, im.lo); *plane_bytes
+ * the bytes of one z plane, *row_bytes of one ky row (Px complex values; only kx <= n_x
+ * matter).  Either size pointer may be NULL.
+ */
+int poisson_plan_spectrum(poisson_plan p, int which, void **ptr, size_t *plane_bytes, size_t *row_bytes);
+
+/*
  * A solve that allocates nothing.  The paper has no counterpart: this entry point exists
  * for callers that may not allocate device memory when they solve, for example a
  * real-time loop that must not enter an allocator (an allocation can take unbounded

@@ -44,6 +44,10 @@ SIGNATURES = {
     "poisson_last_cuda_error": (ctypes.c_char_p, []),
     "poisson_solve_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p]),
     "poisson_noalloc_last_status": (c_int, [c_void_p]),
+    "poisson_slab_forward": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "poisson_slab_z": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "poisson_slab_inverse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "poisson_plan_spectrum": (c_int, [c_void_p, c_int, P(c_void_p), P(ctypes.c_size_t), P(ctypes.c_size_t)]),
     "poisson_noalloc_selftest_wait": (c_int, [ctypes.c_longlong, c_void_p]),
     "poisson_sample_gaussians": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p]),
     "poisson_gaussian_potential": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p,

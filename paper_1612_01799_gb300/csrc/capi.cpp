@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -27,6 +28,7 @@ namespace gsp {
                                        double, const double *, int, cudaStream_t);                                 \
     cudaError_t encode_maps_##sfx(DevicePlan &);                                                                   \
     cudaError_t z_pass_##sfx(const DevicePlan &, cudaStream_t);                                                    \
+    cudaError_t z_lines_##sfx(const DevicePlan &, int, int, cudaStream_t);                                         \
     cudaError_t y_passes_##sfx(const DevicePlan &, cudaStream_t);                                                  \
     cudaError_t x_passes_##sfx(const DevicePlan &, cudaStream_t);                                                  \
     cudaError_t xy_passes_##sfx(const DevicePlan &, cudaStream_t);
@@ -876,6 +878,48 @@ extern "C" int poisson_solve_host(poisson_plan p, const void *rho_h, void *u_h, 
         return fail(e);
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return fail(e);
     return map_cuda(cudaStreamSynchronize(s));
+}
+
+// ---- slab decomposition of one solve ---------------------------------------------------------
+// A rank of a P-way decomposition owns planes z0 .. z0 + nz - 1 of the density for the x and
+// y passes and lines ky0 .. ky0 + nky - 1 of the y-spectrum for the z pass; between them the
+// caller moves blocks of the plan's y-spectrum buffers (poisson_plan_spectrum).
+static int slab_planes_ok(poisson_plan p, const void *ptr, int z0, int nz) {
+    if (!p || !ptr) return POISSON_ERR_ARG;
+    if (z0 < 0 || nz < 1 || z0 + nz > p->dp.n3[2]) return POISSON_ERR_ARG;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_slab_forward(poisson_plan p, const void *rho_slab_d, int z0, int nz, void *stream) {
+    int rc = slab_planes_ok(p, rho_slab_d, z0, nz);
+    if (rc) return rc;
+    // The pass code offsets a whole-density pointer by the slab's first plane.
+    const uintptr_t off = (uintptr_t)z0 * p->dp.n3[1] * p->dp.n3[0] * p->elem;
+    const void *base = reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(rho_slab_d) - off);
+    void *none = const_cast<void *>(base);
+    return map_cuda(gsp::launch_xy_slab(p->dp, base, none, z0, nz, (cudaStream_t)stream, true));
+}
+
+extern "C" int poisson_slab_z(poisson_plan p, int ky0, int nky, void *stream) {
+    if (!p || ky0 < 0 || nky < 1 || ky0 + nky > 2 * p->dp.n3[1]) return POISSON_ERR_ARG;
+    return map_cuda(GSP_BY_ARITH(p->dp, gsp::z_lines, p->dp, ky0, nky, (cudaStream_t)stream));
+}
+
+extern "C" int poisson_slab_inverse(poisson_plan p, void *u_slab_d, int z0, int nz, void *stream) {
+    int rc = slab_planes_ok(p, u_slab_d, z0, nz);
+    if (rc) return rc;
+    const uintptr_t off = (uintptr_t)z0 * p->dp.n3[1] * p->dp.n3[0] * p->elem;
+    void *base = reinterpret_cast<void *>(reinterpret_cast<uintptr_t>(u_slab_d) - off);
+    return map_cuda(gsp::launch_xy_slab(p->dp, base, base, z0, nz, (cudaStream_t)stream, false));
+}
+
+extern "C" int poisson_plan_spectrum(poisson_plan p, int which, void **ptr, size_t *plane_bytes, size_t *row_bytes) {
+    if (!p || (which != 0 && which != 1) || !ptr) return POISSON_ERR_ARG;
+    const size_t row = (size_t)p->dp.Px * 2 * p->elem;
+    *ptr = which == 0 ? p->dp.w2 : p->dp.w3;
+    if (row_bytes) *row_bytes = row;
+    if (plane_bytes) *plane_bytes = row * 2 * p->dp.n3[1];
+    return POISSON_OK;
 }
 
 extern "C" int poisson_solve_batched(int count, const poisson_plan *plans,

@@ -957,18 +957,22 @@ cudaError_t any_y(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 =
     return cudaGetLastError();
 }
 
+// The z pass of lines ky0 <= ky < ky0 + nky (nky = 0: all 2 ny lines).  Runs on the tables of
+// any plan: the compiled-length plans' symbol octant has the same layout as the box table
+// and their twiddles W_{2N} are axis z's table.
 template <typename Real>
-cudaError_t any_z(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
+cudaError_t any_z(const DevicePlan &p, int B, cudaStream_t s, double *tail, int ky0 = 0, int nky = 0) {
     const int nx = p.n3[0], ny = p.n3[1], nz = p.n3[2], L = 2 * nz;
+    if (nky == 0) nky = 2 * ny;
     const AnySched sc = any_sched(L);
     const int TC = any_tile<Real>(L, 16), ncols = nx + 1, ntx = (ncols + TC - 1) / TC;
     const size_t smem = (size_t)2 * L * TC * sizeof(typename Types<Real>::CS);
-    const AnyTw<Real> *tw = static_cast<const AnyTw<Real> *>(p.tw3[2]);
-    const int grid = ntx * 2 * ny * B;
+    const AnyTw<Real> *tw = static_cast<const AnyTw<Real> *>(p.any ? p.tw3[2] : p.tw);
+    const int grid = ntx * nky * B;
     auto k = tail ? k_any_z<Real, true> : k_any_z<Real, false>;
     GSP_CHECK(set_smem(k, smem));
     GSP_CHECK(launch_pdl(k, grid, 256, smem, s, static_cast<const Cx2<Real> *>(p.w2), static_cast<Cx2<Real> *>(p.w3),
-                         static_cast<const Real *>(p.sym), tw, sc, nx, ny, ntx, TC, p.Px, p.Ps, tail));
+                         static_cast<const Real *>(p.sym), tw, sc, nx, ny, ntx, TC, p.Px, p.Ps, tail, ky0, nky));
     return cudaGetLastError();
 }
 
@@ -1109,6 +1113,11 @@ cudaError_t xy_pass_dispatch(const DevicePlan &p, cudaStream_t s) {
         default:
             return cudaErrorInvalidValue;
     }
+}
+
+template <typename Real>
+cudaError_t z_lines_dispatch(const DevicePlan &p, int ky0, int nky, cudaStream_t s) {
+    return any_z<Real>(p, 1, s, nullptr, ky0, nky);
 }
 
 template <typename Real>

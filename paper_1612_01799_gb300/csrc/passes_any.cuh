@@ -196,18 +196,20 @@ __global__ void k_any_col(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restric
 // z < nz), product with the symbol at (|kx|, |ky|, |kz|), inverse, z < nz stored.  With TAIL
 // the forward spectrum's energy in the outer shell (|k_q| >= n_q - n_q / 8 on some axis) and
 // its total energy go to tail[2 b], tail[2 b + 1].
+// The tiles cover the lines ky0 <= ky < ky0 + nky (all of them: ky0 = 0, nky = 2 ny; a
+// rank's slab of lines in the slab decomposition of one solve).
 template <typename Real, bool TAIL>
 __global__ void k_any_z(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out, const Real *__restrict__ sym,
                         const AnyTw<Real> *__restrict__ tw, AnySched s, int nx, int ny, int ntx, int TC, int Px,
-                        int Ps, double *__restrict__ tail) {
+                        int Ps, double *__restrict__ tail, int ky0, int nky) {
     using C = typename Types<Real>::CS;
     extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
     const int Lz = s.L, nz = Lz / 2, Ly = 2 * ny, ncols = nx + 1;
     C *a = reinterpret_cast<C *>(smraw), *b = a + Lz * TC;
     const int tx = blockIdx.x % ntx;
-    const int ky = (blockIdx.x / ntx) % Ly;
-    const int bb = blockIdx.x / (ntx * Ly);
+    const int ky = ky0 + (blockIdx.x / ntx) % nky;
+    const int bb = blockIdx.x / (ntx * nky);
     const int kya = ky <= ny ? ky : Ly - ky;
     const int c0 = tx * TC;
     const long long zs = (long long)Ly * Px;  // z stride of w2 and w3

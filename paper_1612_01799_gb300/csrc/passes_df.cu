@@ -20,6 +20,9 @@ cudaError_t symbol_table_df(const DevicePlan &p, const double *dA, const double 
 }
 cudaError_t encode_maps_df(DevicePlan &p) { return encode_dispatch<DF>(p); }
 cudaError_t z_pass_df(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<DF>(p, s); }
+cudaError_t z_lines_df(const DevicePlan &p, int ky0, int nky, cudaStream_t s) {
+    return z_lines_dispatch<DF>(p, ky0, nky, s);
+}
 cudaError_t y_passes_df(const DevicePlan &p, cudaStream_t s) { return y_pass_dispatch<DF>(p, s); }
 cudaError_t x_passes_df(const DevicePlan &p, cudaStream_t s) { return x_pass_dispatch<DF>(p, s); }
 cudaError_t xy_passes_df(const DevicePlan &p, cudaStream_t s) { return xy_pass_dispatch<DF>(p, s); }

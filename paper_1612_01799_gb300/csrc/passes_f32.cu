@@ -19,6 +19,9 @@ cudaError_t symbol_table_f32(const DevicePlan &p, const double *dA, const double
 }
 cudaError_t encode_maps_f32(DevicePlan &p) { return encode_dispatch<float>(p); }
 cudaError_t z_pass_f32(const DevicePlan &p, cudaStream_t s) { return z_pass_dispatch<float>(p, s); }
+cudaError_t z_lines_f32(const DevicePlan &p, int ky0, int nky, cudaStream_t s) {
+    return z_lines_dispatch<float>(p, ky0, nky, s);
+}
 cudaError_t y_passes_f32(const DevicePlan &p, cudaStream_t s) { return y_pass_dispatch<float>(p, s); }
 cudaError_t x_passes_f32(const DevicePlan &p, cudaStream_t s) { return x_pass_dispatch<float>(p, s); }
 cudaError_t xy_passes_f32(const DevicePlan &p, cudaStream_t s) { return xy_pass_dispatch<float>(p, s); }
