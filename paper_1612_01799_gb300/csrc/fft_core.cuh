@@ -84,6 +84,23 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
     return df_fast_two_sum(p, e);
 }
 
+// a b + c d in one pass: the two leading products and their exact errors (FMA), one
+// two-sum of the products, the cross terms hi x lo accumulated in FP32, one renormalisation:
+// 19 FP32 operations instead of 25 for two products and a sum, with the same error bound
+// (the lo x lo terms dropped, about 2^-47 (|ab| + |cd|)).
+__device__ __forceinline__ DF df_sum_prod(DF a, DF b, DF c, DF d) {
+    const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
+    const float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
+    const float s = __fadd_rn(p1, p2), v = __fsub_rn(s, p1);
+    float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, v)), __fsub_rn(p2, v));
+    t = __fadd_rn(t, __fadd_rn(e1, e2));
+    t = __fmaf_rn(a.hi, b.lo, t);
+    t = __fmaf_rn(a.lo, b.hi, t);
+    t = __fmaf_rn(c.hi, d.lo, t);
+    t = __fmaf_rn(c.lo, d.hi, t);
+    return df_fast_two_sum(s, t);
+}
+
 struct CDF {
     DF re, im;
 };
@@ -152,7 +169,7 @@ template <int D> __device__ __forceinline__ CD cmulk(CD a, double cr, double ci)
 }
 template <int D> __device__ __forceinline__ CDF cmulk(CDF a, DF cr, DF ci) {
     const DF s = D < 0 ? ci : -ci;
-    return {a.re * cr - a.im * s, a.re * s + a.im * cr};
+    return {df_sum_prod(a.re, cr, a.im, -s), df_sum_prod(a.re, s, a.im, cr)};
 }
 template <int D> __device__ __forceinline__ CV cmulk(CV a, float cr, float ci) {
     const float s = D < 0 ? ci : -ci;
@@ -180,7 +197,7 @@ template <int D> __device__ __forceinline__ CD twmul(CD a, double2 w) {
 template <int D> __device__ __forceinline__ CDF twmul(CDF a, float4 w) {
     const DF wr(w.x, w.y), wi(w.z, w.w);
     const DF s = D < 0 ? wi : -wi;
-    return {a.re * wr - a.im * s, a.re * s + a.im * wr};
+    return {df_sum_prod(a.re, wr, a.im, -s), df_sum_prod(a.re, s, a.im, wr)};
 }
 template <int D> __device__ __forceinline__ CV twmul(CV a, float4 w) {
     const float2 R = f2(w.x, w.y), I = f2(w.z, w.w);

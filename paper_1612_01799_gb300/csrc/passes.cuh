@@ -59,6 +59,27 @@ GSP_FFT_CFG(1024, 16, 16, 16, 4);
 GSP_FFT_CFG(2048, 16, 16, 16, 8);
 #undef GSP_FFT_CFG
 
+// The schedule a pass uses for its arithmetic: FftCfg, except in double-float, whose
+// butterflies are about ten times longer in instructions: there the lengths that FftCfg
+// does in radix 16 (16 values per thread) run in radices 8 and 4 with 8 values per thread
+// (and 96, 384 and 768 with 12), so that a kernel's code stays within the instruction cache.
+template <typename Real, int L> struct Cfg : FftCfg<L> {};
+#define GSP_DF_CFG(LL, EE, ...)                  \
+    template <> struct Cfg<DF, LL> {             \
+        static constexpr int E = EE;             \
+        using Rs = Radices<__VA_ARGS__>;         \
+    }
+GSP_DF_CFG(16, 4, 4, 4);
+GSP_DF_CFG(96, 12, 4, 6, 4);
+GSP_DF_CFG(128, 8, 8, 4, 4);
+GSP_DF_CFG(256, 8, 8, 8, 4);
+GSP_DF_CFG(384, 12, 4, 4, 6, 4);
+GSP_DF_CFG(512, 8, 8, 8, 8);
+GSP_DF_CFG(768, 12, 4, 4, 4, 6, 2);
+GSP_DF_CFG(1024, 8, 8, 8, 4, 4);
+GSP_DF_CFG(2048, 8, 8, 8, 8, 4);
+#undef GSP_DF_CFG
+
 // Complex types per arithmetic: CS for the row passes, CC (W columns per thread) for the
 // column passes.
 template <typename Real> struct Types;
@@ -84,17 +105,17 @@ template <> struct Types<DF> {
 template <typename Real, int L> __host__ __device__ constexpr int col_tc() {
     const int W = Types<Real>::W;
     int tc = sizeof(Real) == 4 ? 16 : 8;
-    const int P = L / FftCfg<L>::E;
+    const int P = L / Cfg<Real, L>::E;
     while (tc > W && ((tc / W) * P > 1024 || tc * L * 2 * (int)sizeof(Real) > 131072)) tc /= 2;
     return tc;
 }
 template <typename Real, int L> __host__ __device__ constexpr int col_threads() {
-    return (col_tc<Real, L>() / Types<Real>::W) * (L / FftCfg<L>::E);
+    return (col_tc<Real, L>() / Types<Real>::W) * (L / Cfg<Real, L>::E);
 }
 // Rows per CTA of an x pass (shared tile (N+1) x (TR+1) complex).
 template <typename Real, int L> __host__ __device__ constexpr int row_tr() {
     int tr = sizeof(Real) == 4 ? 16 : 8;
-    const int P = L / FftCfg<L>::E;
+    const int P = L / Cfg<Real, L>::E;
     while (tr > 1 && (tr * P > 1024 || (L + 1) * (tr + 1) * 2 * (int)sizeof(Real) > 163840)) tr /= 2;
     return tr;
 }
@@ -181,13 +202,13 @@ namespace gsp {
 // Rows (y, z) of all densities are numbered b N^2 + y + N z; a CTA's TR rows never straddle
 // two densities (TR divides N^2).
 template <typename Real, int N>
-__global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
+__global__ void __launch_bounds__(row_tr<Real, N>() * (N / Cfg<Real, N>::E))
 k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__restrict__ tw,
             int nrows, int Px) {
     using C = typename Types<Real>::CS;
     using T2 = Cx2<Real>;
     using X2 = Ext2<Real>;
-    constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
+    constexpr int E = Cfg<Real, N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     static_assert((N * N) % TR == 0, "row tiles stay inside one density");
     extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
@@ -207,7 +228,7 @@ k_x_forward(const PtrArray rho, Cx2<Real> *__restrict__ out, const Cx2<Real> *__
     const int c = t % TR, q = t / TR;
     C v[E];
     constexpr RunOpt opt{false, true, false, false, true};
-    Stages<C, N, E, -1, 1, typename FftCfg<N>::Rs>::template run<opt>(
+    Stages<C, N, E, -1, 1, typename Cfg<Real, N>::Rs>::template run<opt>(
         v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
         [&](int row, C x) { sm[row * SP + c] = x; });
     __syncthreads();
@@ -250,7 +271,7 @@ k_col(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out,
       const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ncols, long long in_row,
       long long in_outer, long long out_row, long long out_outer) {
     using C = typename Types<Real>::CC;
-    constexpr int W = Types<Real>::W, E = FftCfg<L>::E, TC = col_tc<Real, L>(), NG = TC / W;
+    constexpr int W = Types<Real>::W, E = Cfg<Real, L>::E, TC = col_tc<Real, L>(), NG = TC / W;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);  // L x NG
     const int g = threadIdx.x % NG, q = threadIdx.x / NG;
@@ -260,7 +281,7 @@ k_col(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out,
     Cx2<Real> *dst = out + (long long)blockIdx.y * out_outer + col;
     C v[E];
     constexpr RunOpt opt{false, FWD, false, !FWD, false};
-    Stages<C, L, E, FWD ? -1 : 1, 1, typename FftCfg<L>::Rs>::template run<opt>(
+    Stages<C, L, E, FWD ? -1 : 1, 1, typename Cfg<Real, L>::Rs>::template run<opt>(
         v, q, g, sm, NG, tw, 1,
         [&](int row) { return valid ? ld_cc(src + row * in_row) : czero<C>(); },
         [&](int row, C x) {
@@ -275,8 +296,8 @@ k_z_symbol(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out, const 
            const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ncols, int Px,
            int Ps) {
     using C = typename Types<Real>::CC;
-    using Rs = typename FftCfg<L>::Rs;
-    constexpr int N = L / 2, W = Types<Real>::W, E = FftCfg<L>::E, TC = col_tc<Real, L>(), NG = TC / W;
+    using Rs = typename Cfg<Real, L>::Rs;
+    constexpr int N = L / 2, W = Types<Real>::W, E = Cfg<Real, L>::E, TC = col_tc<Real, L>(), NG = TC / W;
     constexpr int P = L / E;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);  // L x NG
@@ -319,13 +340,13 @@ k_z_symbol(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict__ out, const 
 
 // ---- K5: x inverse (Hermitian N+1 bins -> N real samples) -------------------------------
 template <typename Real, int N>
-__global__ void __launch_bounds__(row_tr<Real, N>() * (N / FftCfg<N>::E))
+__global__ void __launch_bounds__(row_tr<Real, N>() * (N / Cfg<Real, N>::E))
 k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> *__restrict__ tw,
             int nrows, int Px) {
     using C = typename Types<Real>::CS;
     using T2 = Cx2<Real>;
     using X2 = Ext2<Real>;
-    constexpr int E = FftCfg<N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
+    constexpr int E = Cfg<Real, N>::E, P = N / E, TR = row_tr<Real, N>(), SP = TR + 1, NT = TR * P;
     extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
     C *sm = reinterpret_cast<C *>(smraw);  // (N + 1) x SP
@@ -371,7 +392,7 @@ k_x_inverse(const Cx2<Real> *__restrict__ in, const PtrArray u, const Cx2<Real> 
     const int c = t % TR, q = t / TR;
     C v[E];
     constexpr RunOpt opt{false, false, false, true, true};
-    Stages<C, N, E, 1, 1, typename FftCfg<N>::Rs>::template run<opt>(
+    Stages<C, N, E, 1, 1, typename Cfg<Real, N>::Rs>::template run<opt>(
         v, q, c, sm, SP, tw, 2, [&](int row) { return sm[row * SP + c]; },
         [&](int row, C x) { sm[row * SP + c] = x; });
     __syncthreads();
@@ -601,7 +622,7 @@ cudaError_t x_pass(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, 
             return cudaGetLastError();
         }
     }
-    constexpr int TR = row_tr<Real, N>(), PX1 = N / FftCfg<N>::E;
+    constexpr int TR = row_tr<Real, N>(), PX1 = N / Cfg<Real, N>::E;
     const size_t smem_row = (size_t)(N + 1) * (TR + 1) * 2 * sizeof(Real);
     const dim3 grow((nrows + TR - 1) / TR);
     const T2 *tw = static_cast<const T2 *>(p.tw);

@@ -58,13 +58,13 @@ template <typename Real, int L, int KIND> __host__ __device__ constexpr int tma_
     int tc = sizeof(Real) == 4 ? 16 : 8;
     if (KIND == 2) tc /= 2;
     const int W = Types<Real>::W;
-    const int P = L / FftCfg<L>::E;
+    const int P = L / Cfg<Real, L>::E;
     const int tc_min = sizeof(Real) == 4 ? 4 : 2;
     while (tc > tc_min && ((tc / W) * P > 1024 || tma_smem<Real, L, KIND>(tc) > 232448)) tc /= 2;
     return tc;
 }
 template <typename Real, int L, int KIND> __host__ __device__ constexpr int tma_threads() {
-    return (tma_tc<Real, L, KIND>() / Types<Real>::W) * (L / FftCfg<L>::E);
+    return (tma_tc<Real, L, KIND>() / Types<Real>::W) * (L / Cfg<Real, L>::E);
 }
 
 template <typename Real, int L, int KIND> struct TmaLayout {
@@ -72,7 +72,7 @@ template <typename Real, int L, int KIND> struct TmaLayout {
     static constexpr int TC = tma_tc<Real, L, KIND>();
     static constexpr int W = Types<Real>::W;
     static constexpr int NG = TC / W;                                  // column groups (16 B each)
-    static constexpr int P = L / FftCfg<L>::E;                         // threads per group
+    static constexpr int P = L / Cfg<Real, L>::E;                      // threads per group
     static constexpr int ROWB = TC * 2 * (int)sizeof(Real);            // bytes of one tile row
     static constexpr int LIN = KIND == 2 ? L : N;                      // input rows per tile
     static constexpr int NCP = tma_ncopy(LIN, ROWB);
@@ -135,15 +135,15 @@ template <int T, int E> __host__ __device__ constexpr int min_blocks_for() {
 // column) as its q = t / NG-th thread, so the lanes of a warp cover consecutive groups of
 // the same rows and every global store of a warp is a contiguous row segment.
 template <typename Real, int L, int KIND>
-__global__ void __launch_bounds__(tma_threads<Real, L, KIND>(), min_blocks_for<tma_threads<Real, L, KIND>(), FftCfg<L>::E>())
+__global__ void __launch_bounds__(tma_threads<Real, L, KIND>(), min_blocks_for<tma_threads<Real, L, KIND>(), Cfg<Real, L>::E>())
 k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
           const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
           int ncols, long long out_row, long long out_outer, int *__restrict__ status, int z0) {
     using C = typename Types<Real>::CC;
     using Lay = TmaLayout<Real, L, KIND>;
-    using Rs = typename FftCfg<L>::Rs;
+    using Rs = typename Cfg<Real, L>::Rs;
     constexpr bool FWD = KIND == 0;
-    constexpr int E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, R0 = FirstRadix<Rs>::v;
+    constexpr int E = Cfg<Real, L>::E, W = Lay::W, TC = Lay::TC, R0 = FirstRadix<Rs>::v;
     constexpr int TCU = Lay::ROWB / 8;  // box width in 8-byte units
     extern __shared__ __align__(16) unsigned char smraw[];
     griddep_wait();
@@ -210,16 +210,16 @@ __device__ __forceinline__ float cenergy(CDF x) { return x.re.hi * x.re.hi + x.i
 // and its total energy are added (FP32 per thread, FP64 per tile) to tail[2 b], tail[2 b + 1]
 // for density b: the a-posteriori indicator of the density's resolution.
 template <typename Real, int L, bool TAIL>
-__global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_for<tma_threads<Real, L, 1>(), FftCfg<L>::E>())
+__global__ void __launch_bounds__(tma_threads<Real, L, 1>(), min_blocks_for<tma_threads<Real, L, 1>(), Cfg<Real, L>::E>())
 k_z_symbol_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
                Cx2<Real> *__restrict__ out,
                const typename TwOf<typename Types<Real>::CC>::T *__restrict__ tw, int ntx, int ntiles,
                int ncols, int Px, int *__restrict__ status, double *__restrict__ tail) {
     using C = typename Types<Real>::CC;
     using Lay = TmaLayout<Real, L, 1>;
-    using Rs = typename FftCfg<L>::Rs;
+    using Rs = typename Cfg<Real, L>::Rs;
     using Rv = Reverse<Rs>;
-    constexpr int N = L / 2, E = FftCfg<L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P;
+    constexpr int N = L / 2, E = Cfg<Real, L>::E, W = Lay::W, TC = Lay::TC, P = Lay::P;
     constexpr int RL = LastRadix<Rs>::v, R0 = FirstRadix<Rs>::v;
     constexpr int TCU = Lay::ROWB / 8;
     extern __shared__ __align__(16) unsigned char smraw[];
