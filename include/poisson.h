@@ -170,6 +170,16 @@ int poisson_solve_batched(int count, const poisson_plan *plans, const void *cons
 int poisson_solve_checked(poisson_plan p, const void *rho_d, void *u_d, double *eta, void *stream);
 
 /*
+ * count (1 <= count <= the plan's max_batch) checked solves of the plan's geometry with one
+ * launch per pass: rho_d[i] -> u_d[i] as poisson_solve_batched, eta[i] (host array of count
+ * doubles) as poisson_solve_checked for density i.  Synchronises `stream`.  The grid
+ * selector's batched refinement runs on it: the densities that chose the same N solve
+ * together, and those whose eta fails the check move to the next N together.
+ */
+int poisson_solve_checked_batched(poisson_plan p, int count, const void *const *rho_d, void *const *u_d,
+                                  double *eta, void *stream);
+
+/*
  * The final residual check: relative L2 and relative l-infinity differences of a against
  * b over n values, accumulated in FP64 on the device: rel_l2 = ||a - b||_2 / ||b||_2,
  * rel_linf = max|a - b| / max|b| (the paper's error measure E, Sec. 5, eq. error_infty).

@@ -32,6 +32,7 @@ SIGNATURES = {
     "poisson_last_status": (c_int, [c_void_p, c_void_p]),
     "poisson_selftest_wait": (c_int, [c_void_p, ctypes.c_longlong, c_void_p]),
     "poisson_solve_checked": (c_int, [c_void_p, c_void_p, c_void_p, P(c_double), c_void_p]),
+    "poisson_solve_checked_batched": (c_int, [c_void_p, c_int, P(c_void_p), P(c_void_p), P(c_double), c_void_p]),
     "poisson_compare": (c_int, [c_void_p, c_int, c_void_p, c_int, c_size_t, P(c_double), P(c_double), c_void_p]),
     "poisson_plan_info": (c_int, [c_void_p, P(c_double), P(c_double), P(c_int), P(c_double),
                                   P(c_double), P(c_size_t), P(c_size_t)]),

@@ -1017,6 +1017,28 @@ extern "C" int poisson_solve_checked(poisson_plan p, const void *rho_d, void *u_
     return POISSON_OK;
 }
 
+extern "C" int poisson_solve_checked_batched(poisson_plan p, int count, const void *const *rho_d, void *const *u_d,
+                                             double *eta, void *stream) {
+    if (!p || !rho_d || !u_d || !eta || count < 1 || count > p->dp.max_batch) return POISSON_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!rho_d[i] || !u_d[i]) return POISSON_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->dp.tail, 0, 2 * sizeof(double) * count, s)) != cudaSuccess) return map_cuda(e);
+    gsp::PtrArray in, out;
+    for (int i = 0; i < gsp::kMaxBatch; ++i) {
+        in.p[i] = i < count ? rho_d[i] : nullptr;
+        out.p[i] = i < count ? u_d[i] : nullptr;
+    }
+    if ((e = gsp::launch_solve(p->dp, in, out, count, s, nullptr, p->dp.tail)) != cudaSuccess) return map_cuda(e);
+    double h[2 * gsp::kMaxBatch];
+    if ((e = cudaMemcpyAsync(h, p->dp.tail, 2 * sizeof(double) * count, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_cuda(e);
+    for (int i = 0; i < count; ++i) eta[i] = h[2 * i + 1] > 0.0 ? std::sqrt(h[2 * i] / h[2 * i + 1]) : 0.0;
+    return POISSON_OK;
+}
+
 extern "C" int poisson_last_status(poisson_plan p, void *stream) {
     if (!p) return POISSON_ERR_ARG;
     int h = 0;

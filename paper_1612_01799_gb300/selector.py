@@ -67,9 +67,20 @@ class Workspace:
         self.idx = torch.empty(NPTS * 3, dtype=torch.int32, device="cuda")
         self.ref = torch.empty(NPTS, dtype=torch.float64, device="cuda")
         self.s32 = torch.empty(32 ** 3, dtype=torch.float32, device="cuda")
+        self.bplans = {}
+
+    def batch_plan(self, N):
+        """A plan of N whose workspace holds several densities (made on first use; about
+        10 GB of workspace per size at most)."""
+        from .api import Plan
+        if N not in self.bplans:
+            per = 40 * N ** 3 * (4 if self.dtype == "f32" else 8) // 4   # bytes of workspace per density
+            mb = int(max(1, min(16, (10 << 30) // per)))
+            self.bplans[N] = Plan(N, BOX, self.plans[N].tol, self.dtype, max_batch=mb)
+        return self.bplans[N]
 
     def close(self):
-        for p in self.plans.values():
+        for p in list(self.plans.values()) + list(self.bplans.values()):
             p.close()
 
     def sample(self, params, N, out, dtype_code):
@@ -320,27 +331,71 @@ def _solve_until_checked(ws, sel, params, start_k, tol):
         k += 1
 
 
-def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512, fixed_timed=4):
+def solve_batched_until_checked(ws, sel, params, start_ks, tol):
+    """The same refinement for many densities at once: the densities at the same candidate
+    solve together (poisson_solve_checked_batched, up to the plan's max_batch per call), and
+    those whose check fails move on together.  Returns one (N, index, solves) per density."""
+    torch = _torch()
+    code = 0 if ws.dtype == "f32" else 1
+    tdt = torch.float32 if ws.dtype == "f32" else torch.float64
+    last = len(ws.candidates) - 1
+    pending = dict(enumerate(start_ks))
+    solves = [0] * len(params)
+    out = [None] * len(params)
+    while pending:
+        groups = {}
+        for i, k in pending.items():
+            groups.setdefault(k, []).append(i)
+        pending = {}
+        for k in sorted(groups):
+            N = ws.candidates[k]
+            plan = ws.batch_plan(N)
+            members = groups[k]
+            for c0 in range(0, len(members), plan.max_batch):
+                chunk = members[c0:c0 + plan.max_batch]
+                n = len(chunk)
+                rho = torch.empty((n, N ** 3), dtype=tdt, device="cuda")
+                u = torch.empty_like(rho)
+                for j, i in enumerate(chunk):
+                    ws.sample(params[i], N, rho[j], code)
+                rp = (ctypes.c_void_p * n)(*[rho[j].data_ptr() for j in range(n)])
+                up = (ctypes.c_void_p * n)(*[u[j].data_ptr() for j in range(n)])
+                eta = (ctypes.c_double * n)()
+                _lib.check(ws.lib.poisson_solve_checked_batched(plan.handle, n, rp, up, eta, _stream()),
+                           "poisson_solve_checked_batched")
+                for j, i in enumerate(chunk):
+                    solves[i] += 1
+                    if sel.check(eta[j], tol) or k == last:
+                        out[i] = (N, k, solves[i])
+                    else:
+                        pending[i] = k + 1
+    return out
+
+
+def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512):
     """Cost and accuracy of three ways to meet `tol` on the test densities:
-    (i) a fixed N = fixed_N FP64 solve, (ii) the plain method: start at start_N and refine
-    with the a-posteriori check, (iii) the network's N, refined with the same check."""
+    (i) a fixed N = fixed_N FP64 solve of every density, (ii) the plain method: start at
+    start_N and refine with the a-posteriori check, (iii) the network's N, refined with the
+    same check.  (ii) and (iii) solve the densities at the same N together (batched checked
+    solves), so their difference is the network's; both in FP32."""
     torch = _torch()
     from .api import Plan
     params = [gaussian_params(density(i)) for i in test_indices]
     res = {}
+    # Batched plans and their workspaces exist before the timed runs.
+    for N in ws.candidates:
+        ws.batch_plan(N)
     # (iii) network + check
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, s32 = ws.features(params)
     Ns, _ = sel.select(s32, len(params), tol)
-    chosen3 = []
-    for p, n0 in zip(params, Ns):
-        chosen3.append(_solve_until_checked(ws, sel, p, ws.candidates.index(n0), tol))
+    chosen3 = solve_batched_until_checked(ws, sel, params, [ws.candidates.index(n) for n in Ns], tol)
     torch.cuda.synchronize()
     t3 = time.perf_counter() - t0
     # (ii) plain method + check
     t0 = time.perf_counter()
-    chosen2 = [_solve_until_checked(ws, sel, p, ws.candidates.index(start_N), tol) for p in params]
+    chosen2 = solve_batched_until_checked(ws, sel, params, [ws.candidates.index(start_N)] * len(params), tol)
     torch.cuda.synchronize()
     t2 = time.perf_counter() - t0
     # accuracy of the grids each strategy ended on (untimed)
@@ -350,7 +405,7 @@ def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512, fixed_ti
             out.append(ws.solve_error(p, N, seed=5000 + i)[0])
         return np.array(out)
     e3, e2 = errors(chosen3), errors(chosen2)
-    # (i) fixed N FP64: timed on the first `fixed_timed` densities, cost scaled to all
+    # (i) fixed N, FP64 plan (its timed arithmetic), every test density: timed, then its errors
     with Plan(fixed_N, BOX, 1e-12, "f64") as p64:
         rho = torch.empty(fixed_N ** 3, dtype=torch.float64, device="cuda")
         u = torch.empty_like(rho)
@@ -358,24 +413,28 @@ def gain_test(test_indices, ws, sel, tol=1e-6, start_N=64, fixed_N=512, fixed_ti
         p64.solve(rho, u)                      # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for pr in params[:fixed_timed]:
+        for pr in params:
             ws.sample(pr, fixed_N, rho, 1)
             p64.solve(rho, u)
         torch.cuda.synchronize()
-        t1 = (time.perf_counter() - t0) / fixed_timed * len(params)
+        t1 = time.perf_counter() - t0
         e1 = np.array([ws.error_at_points(pr, fixed_N, (ws.sample(pr, fixed_N, rho, 1), p64.solve(rho, u))[1],
                                           seed=5000 + i)
-                       for i, pr in zip(test_indices[:fixed_timed], params[:fixed_timed])])
+                       for i, pr in zip(test_indices, params)])
+        arith = p64.arith
+
     def summary(t, e, chosen):
-        d = {"seconds": t, "met_tol": float(np.mean(e <= tol)), "median_err": float(np.median(e))}
+        d = {"seconds": t, "met_tol": float(np.mean(e <= tol)), "median_err": float(np.median(e)),
+             "max_err": float(np.max(e))}
         if chosen is not None:
             d["mean_N"] = float(np.mean([c[0] for c in chosen]))
             d["solves_per_density"] = float(np.mean([c[2] for c in chosen]))
         return d
     res["fixed_N%d_f64" % fixed_N] = summary(t1, e1, None)
-    res["fixed_N%d_f64" % fixed_N]["timed_densities"] = fixed_timed
-    res["plain_adaptive_from_N%d_f32" % start_N] = summary(t2, e2, chosen2)
-    res["network_plus_check_f32"] = summary(t3, e3, chosen3)
+    res["fixed_N%d_f64" % fixed_N]["timed_densities"] = len(params)
+    res["fixed_N%d_f64" % fixed_N]["arith"] = arith
+    res["plain_adaptive_from_N%d_f32_batched" % start_N] = summary(t2, e2, chosen2)
+    res["network_plus_check_f32_batched"] = summary(t3, e3, chosen3)
     res["network_first_guess_kept"] = float(np.mean([c[0] == n for c, n in zip(chosen3, Ns)]))
     res["speedup_vs_fixed"] = t1 / t3
     res["speedup_vs_plain"] = t2 / t3

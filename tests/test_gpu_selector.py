@@ -166,6 +166,35 @@ def test_selector_end_to_end_small(env, tmp_path):
         for n, row in zip(Ns, pred):
             ok = [k for k in range(3) if row[k] <= goal]
             assert n == (ws.candidates[ok[0]] if ok else ws.candidates[-1])
+        # The batched refinement ends where the one-at-a-time refinement ends.
+        starts = [ws.candidates.index(n) for n in Ns]
+        batched = S.solve_batched_until_checked(ws, sel, params, starts, 1e-6)
+        single = [S._solve_until_checked(ws, sel, p, k, 1e-6) for p, k in zip(params, starts)]
+        assert batched == single
         sel.close()
     finally:
         ws.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_checked_batched_equals_checked_singles(env, dtype):
+    """poisson_solve_checked_batched: each density's potential and eta as its own checked solve."""
+    torch, lib = env
+    from paper_1612_01799_gb300 import Plan
+    N, L = 48, 4.0
+    rhos = [D.config_aniso4(N=N, seed=s).gaussians.sample(N, L) for s in (31, 32, 33)]
+    with Plan(N, L, 1e-6, dtype, max_batch=3) as p:
+        ts = [torch.from_numpy(r.astype(p.np_dtype)).cuda() for r in rhos]
+        us = [torch.empty_like(t) for t in ts]
+        rp = (ctypes.c_void_p * 3)(*[t.data_ptr() for t in ts])
+        up = (ctypes.c_void_p * 3)(*[u.data_ptr() for u in us])
+        eta = (ctypes.c_double * 3)()
+        assert lib.poisson_solve_checked_batched(p.handle, 3, rp, up, eta, None) == 0
+        assert lib.poisson_solve_checked_batched(p.handle, 4, rp, up, eta, None) == -1   # above max_batch
+        for t, u, e in zip(ts, us, eta):
+            u1 = torch.empty_like(t)
+            e1 = ctypes.c_double()
+            assert lib.poisson_solve_checked(p.handle, ptr(t), ptr(u1), ctypes.byref(e1), None) == 0
+            torch.cuda.synchronize()
+            assert torch.equal(u, u1)
+            assert e == pytest.approx(e1.value, rel=1e-12)
