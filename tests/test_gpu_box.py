@@ -149,3 +149,29 @@ def test_paper_tables_2_and_6_on_gpu(torch_cuda, N):
             assert E < 1e-12, (name, N, E)      # the paper stagnates at 3e-12 there; the method does not
         else:
             assert abs(math.log10(E / ref)) <= math.log10(5.0), (name, N, E, ref)
+
+
+def test_box_n512_warp_form_against_block_form_and_oracle(torch_cuda):
+    """N = 512 on Table 6's box: the one-warp-per-column z form (reading the box symbol's
+    kz-innermost copy through its own tensor map) against the block form, and both against
+    the oracle's box solve on the whole grid (a 1024^3 transform pair on the host)."""
+    from paper_1612_01799_gb300 import Plan
+    N = 512
+    rng = np.random.default_rng(51)
+    rho = rng.uniform(-1, 1, (N, N, N))
+    with Plan(N, half(*T6), 1e-6, "f32") as p:
+        p.z_form, p.y_form, p.x_form = 2, 1, 1
+        u2 = gpu(torch_cuda, p, rho)
+        p.z_form, p.y_form, p.x_form = 0, 0, 0
+        u0 = gpu(torch_cuda, p, rho)
+    assert rel_l2(u2, u0) < 2e-6
+    avail = 0.0
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) / 2 ** 20
+    if avail < 80:
+        pytest.skip("the N = 512 box oracle needs about 30 GB of host memory")
+    uo = obox.solve_box(rho, obox.make_box_plan(N, T6[0], T6[1], 1e-6))
+    assert rel_l2(u2, uo) <= TOL["f32"]
+    assert rel_l2(u0, uo) <= TOL["f32"]
