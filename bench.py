@@ -482,6 +482,8 @@ def run_ours(args):
             names[1], names[3] = ("k_y_w512<fwd>", "k_y_w512<inv>") if N == 512 else ("k_y_warp<fwd>", "k_y_warp<inv>")
         if r32["x_form"] == 1:
             names[0], names[4] = "k_x_warp_fwd", "k_x_warp_inv"
+        if results["f32"]["plan"]._lib.poisson_supported_n(N) == 2:   # the runtime-length forms
+            names = ["k_any_x_fwd", "k_any_col<fwd>", "k_any_z", "k_any_col<inv>", "k_any_x_inv"]
         rows32 = pass_table(N, 4, r32["per_pass"], r32["xy_form"], names)
         gbs = [b / (t * 1e-3) / 1e9 for _, _, t, b in rows32]
         dom = max(range(len(rows32)), key=lambda i: rows32[i][2])

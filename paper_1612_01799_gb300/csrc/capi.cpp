@@ -84,6 +84,11 @@ AnySched any_sched(int L) {
         m = 1;
     }
     s.nst = m == 1 ? n : 0;
+    unsigned long long ns = 1;
+    for (int st = 0; st < s.nst; ++st) {
+        s.mul[st] = ns == 1 ? 0u : (unsigned)((1ull << 32) / ns + 1);
+        ns *= (unsigned long long)s.r[st];
+    }
     return s;
 }
 

@@ -926,11 +926,16 @@ cudaError_t encode_n(DevicePlan &p) {
 
 // ---- runtime-length forms: launchers ----------------------------------------------------------
 // Tiles sized so that the ping-pong pair of one CTA stays within about 64 KB of shared memory.
-template <typename Real> int any_tile(int L, int cap) {
+template <typename Real> int any_tile(int L, int cap, int extra = 0) {
     const int bytes = 2 * L * (int)sizeof(typename Types<Real>::CS);
     int t = cap;
-    while (t > 1 && t * bytes > 65536) t /= 2;
+    while (t > 1 && (t + extra) * bytes > 65536) t /= 2;
     return t;
+}
+inline int ilog2(int t) {
+    int l = 0;
+    while ((1 << (l + 1)) <= t) ++l;
+    return l;
 }
 
 template <typename Real>
@@ -939,18 +944,18 @@ cudaError_t any_x(const DevicePlan &p, const PtrArray &rho, const PtrArray &u, i
     const int nx = p.n3[0], ny = p.n3[1], nz = p.n3[2];
     const AnySched sc = any_sched(nx);
     const int rows_b = ny * nz, nrows = rows ? rows : B * rows_b;
-    const int TR = any_tile<Real>(nx, 16);
-    const size_t smem = (size_t)2 * nx * TR * sizeof(typename Types<Real>::CS);
+    const int TR = any_tile<Real>(nx, 16, 1);  // pitch TR + 1
+    const size_t smem = (size_t)2 * nx * (TR + 1) * sizeof(typename Types<Real>::CS);
     const AnyTw<Real> *tw = static_cast<const AnyTw<Real> *>(p.tw3[0]);
     Cx2<Real> *ws = static_cast<Cx2<Real> *>(w1 ? w1 : p.w1);
     const int grid = (nrows + TR - 1) / TR;
     if (fwd) {
         GSP_CHECK(set_smem(k_any_x_fwd<Real>, smem));
-        GSP_CHECK(launch_pdl(k_any_x_fwd<Real>, grid, 256, smem, s, rho, ws, tw, sc, rows_b, nrows, p.Px, TR));
+        GSP_CHECK(launch_pdl(k_any_x_fwd<Real>, grid, 256, smem, s, rho, ws, tw, sc, rows_b, nrows, p.Px, ilog2(TR)));
     } else {
         GSP_CHECK(set_smem(k_any_x_inv<Real>, smem));
         GSP_CHECK(launch_pdl(k_any_x_inv<Real>, grid, 256, smem, s, static_cast<const Cx2<Real> *>(ws), u, tw, sc,
-                             rows_b, nrows, p.Px, TR));
+                             rows_b, nrows, p.Px, ilog2(TR)));
     }
     return cudaGetLastError();
 }
@@ -969,11 +974,11 @@ cudaError_t any_y(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 =
     if (fwd) {
         GSP_CHECK(set_smem(k_any_col<Real, true>, smem));
         GSP_CHECK(launch_pdl(k_any_col<Real, true>, ntx * planes, 256, smem, s, w1 + z0 * w1p, w2 + z0 * w2p, tw, sc,
-                             ncols, ntx, TC, Px, w1p, Px, w2p));
+                             ncols, ntx, ilog2(TC), Px, w1p, Px, w2p));
     } else {
         GSP_CHECK(set_smem(k_any_col<Real, false>, smem));
         GSP_CHECK(launch_pdl(k_any_col<Real, false>, ntx * planes, 256, smem, s, w3 + z0 * w2p, w1o + z0 * w1p, tw, sc,
-                             ncols, ntx, TC, Px, w2p, Px, w1p));
+                             ncols, ntx, ilog2(TC), Px, w2p, Px, w1p));
     }
     return cudaGetLastError();
 }
@@ -993,7 +998,7 @@ cudaError_t any_z(const DevicePlan &p, int B, cudaStream_t s, double *tail, int 
     auto k = tail ? k_any_z<Real, true> : k_any_z<Real, false>;
     GSP_CHECK(set_smem(k, smem));
     GSP_CHECK(launch_pdl(k, grid, 256, smem, s, static_cast<const Cx2<Real> *>(p.w2), static_cast<Cx2<Real> *>(p.w3),
-                         static_cast<const Real *>(p.sym), tw, sc, nx, ny, ntx, TC, p.Px, p.Ps, tail, ky0, nky));
+                         static_cast<const Real *>(p.sym), tw, sc, nx, ny, ntx, ilog2(TC), p.Px, p.Ps, tail, ky0, nky));
     return cudaGetLastError();
 }
 

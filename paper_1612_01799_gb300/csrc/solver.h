@@ -16,12 +16,15 @@ struct PtrArray {
 };
 
 // Radix schedule of a runtime-length transform (the runtime-length pass forms): length L,
-// nst stages of radices r[0..nst) in {2, 3, 4, 5}, first to last.
+// nst stages of radices r[0..nst) in {2, 3, 4, 5}, first to last; mul[st] the reciprocal
+// floor(2^32 / Ns) + 1 of the product Ns of the earlier radices (0 for the first stage), so
+// that j / Ns = umulhi(j, mul[st]) exactly for j < 4096.
 constexpr int kAnyMaxStages = 16;
 struct AnySched {
     int L;
     int nst;
     int r[kAnyMaxStages];
+    unsigned mul[kAnyMaxStages];
 };
 // The schedule of length L (fives, threes, fours, then a two), or nst = 0 if L has a prime
 // factor above 5.
