@@ -539,11 +539,11 @@ cudaError_t z_pass(const DevicePlan &p, int B, cudaStream_t s, double *tail) {
     if constexpr (zwarp_form<Real, N>()) {
         if (p.zform == 2) {
             using Z = ZWarp<N / 16>;
-            static_assert(Z::TC == L1::TC, "same tiles as the direct form");
+            const int ntxw = (ncols + Z::TC - 1) / Z::TC, ntw = ntxw * L * B;
             auto k = tail ? k_z_warp<N / 16, true> : k_z_warp<N / 16, false>;
             GSP_CHECK(set_smem(k, Z::SMEM));
-            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Z::NT, Z::SMEM, nt), Z::NT, Z::SMEM, s,
-                                 p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntx, nt,
+            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Z::NT, Z::SMEM, ntw), Z::NT, Z::SMEM, s,
+                                 p.tm_zw_in, p.tm_zw_sym, p.tm_zw_out, static_cast<const float2 *>(p.tw), ntxw, ntw,
                                  ncols, p.status, tail));
             return cudaGetLastError();
         }
@@ -859,10 +859,11 @@ cudaError_t encode_n(DevicePlan &p) {
     }
     if constexpr (zwarp_form<Real, N>()) {
         // Columns kx > N lie outside these maps: loads read zeros there, stores skip them.
+        // Boxes of 8 columns x 1 ky x N z-rows (64-byte rows, 64-byte swizzle; L2 fills of 64 B).
         GSP_CHECK(encode_3d(&p.tm_zw_in, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp<N / 16>::TC, 1, N,
-                            CU_TENSOR_MAP_SWIZZLE_128B));
+                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_64B));
         GSP_CHECK(encode_3d(&p.tm_zw_out, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, ZWarp<N / 16>::TC, 1, N,
-                            CU_TENSOR_MAP_SWIZZLE_128B));
+                            CU_TENSOR_MAP_SWIZZLE_64B));
         // The symbol octant read with its innermost index as kz (symmetric table): boxes of
         // 128 kz x 1 ky x 16 kx.
         GSP_CHECK(encode_3d(&p.tm_zw_sym, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.sym, N + 1, N + 1, N + 1, srow,

@@ -35,15 +35,15 @@
 // keep v[j], receive the partner's v[j + 4].  The upper half's difference comes out
 // negated; its F3 twiddle carries the sign (-W_32^{q'}).
 //
-// Shared memory (one CTA = one tile of 16 columns x 1 ky x the N input rows, 8 warps):
-//   B   32 KB: the TMA input tile (256 rows x 128 B, 128-byte swizzle), then the tile's
-//       symbol lines (boxes of 128 kz x 16 kx, kz innermost: the octant table is
-//       symmetric in (kx, ky, kz), so read with its innermost index as kz each column's kz
-//       values lie contiguous and the lanes read consecutive floats), then the next
-//       tile's input;
-//   XO  64 KB: 512 rows of 128 B; warp g owns the 16-byte chunk g ^ (row & 7) of every row,
-//       for its exchange slots (all 512 rows) and for its outputs (rows z < 256), so the
-//       first 32 KB is the output tile in the TMA store's 128-byte swizzle;
+// Shared memory (one CTA = one tile of 8 columns x 1 ky x the N input rows, 4 warps; four
+// CTAs per SM, so 16 warps from four independent tiles share it):
+//   B   16 KB: the TMA input tile (256 rows x 64 B, 64-byte swizzle), then the tile's
+//       symbol lines (boxes of 128 kz x 8 kx, kz innermost: the octant table is symmetric
+//       in (kx, ky, kz), so read with its innermost index as kz each column's kz values
+//       lie contiguous and the lanes read consecutive floats), then the next tile's input;
+//   XO  32 KB: 512 rows of 64 B; warp g owns the 16-byte chunk g ^ ((row >> 1) & 3) of
+//       every row, for its exchange slots (all 512 rows) and for its outputs (rows z < 256),
+//       so the first 16 KB is the output tile in the TMA store's 64-byte swizzle;
 //   T   4 KB: twiddles W_512^{q k1} as T[k1][q];
 //   three mbarriers (input, symbol, XO free) and three arrival counters.
 // The last warp to finish with B (input read, symbol read) issues the next TMA load into
@@ -51,22 +51,25 @@
 // store has read XO, frees XO for the next tile's exchange.  All waits are bounded.
 //
 // Exchange slots: reader lane l takes position p from row 16 l + (p ^ (l & 7)).  The bank
-// group (row & 7, XOR the warp) differs across the eight lanes of every quarter-warp
-// access in both directions, and both addresses are a lane constant XOR a compile-time
-// constant (bits 4-9) plus a compile-time offset.
+// group (row mod 8, with the warp's chunk) differs across the eight lanes of every
+// quarter-warp access in both directions, and both addresses are a lane constant XOR a
+// compile-time constant (bits 4-9) plus a compile-time offset.  (The y warp forms use the
+// same slots in 128-byte rows, eight warps to a row.)
 #pragma once
 #include "tma.cuh"
 
 namespace gsp {
 
 template <int E1> struct ZWarp {
-    static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N, TC = 16, NW = 8, NT = 256;
+    static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N, TC = 8, NW = 4, NT = 128, ROWB = TC * 8;
+    static constexpr int MINB = 4;  // CTAs per SM: 16 warps, 128 registers a thread
     // Symbol lines: boxes of SYM_KZB kz values (innermost) x 1 ky x TC kx; kz <= N.
     static constexpr int SYM_KZB = 128, SYM_NCP = (N + 1 + SYM_KZB - 1) / SYM_KZB;
     static constexpr int IN_BYTES = N * TC * 8;
     static constexpr int SYM_BYTES = SYM_NCP * SYM_KZB * TC * 4;
     static constexpr int B_BYTES = IN_BYTES > SYM_BYTES ? IN_BYTES : SYM_BYTES;
-    static constexpr int OFF_B = 0, OFF_XO = (B_BYTES + 1023) / 1024 * 1024, OFF_T = OFF_XO + 65536;
+    static constexpr int XO_BYTES = 512 * ROWB;  // the exchange slots (512 rows), then the output tile
+    static constexpr int OFF_B = 0, OFF_XO = (B_BYTES + 1023) / 1024 * 1024, OFF_T = OFF_XO + XO_BYTES;
     static constexpr int OFF_BAR = OFF_T + E1 * 32 * 8;
     static constexpr int SMEM = 1024 + OFF_BAR + 64;  // 1 KB alignment slack
     static_assert(E1 == 16 || E1 == 12 || E1 == 10 || E1 == 8 || E1 == 6 || E1 == 4,
@@ -152,6 +155,11 @@ template <int E1> __device__ __forceinline__ void zw_f1_adj(CV *v) {
 
 // Byte offset of row `row` of warp g in a 128-byte-swizzled region.
 __device__ __forceinline__ int zw_sw128(int row, int g) { return row * 128 + ((g ^ (row & 7)) << 4); }
+// The same in a region of RB-byte rows (RB = 128, or 64 with the TMA's 64-byte swizzle: chunk
+// g ^ ((row >> 1) & 3) of four).
+template <int RB> __device__ __forceinline__ int zw_swz(int row, int g) {
+    return RB == 128 ? zw_sw128(row, g) : row * 64 + ((g ^ ((row >> 1) & 3)) << 4);
+}
 
 // Exchange slots by shared-memory address (layout re.x, re.y, im.x, im.y).
 __device__ __forceinline__ void zw_sts(uint32_t a, CV x) {
@@ -174,7 +182,10 @@ __device__ __forceinline__ CV zw_shfl16(CV x) {
 
 
 // Per-lane constants of the warp-form transform (lane q = q' + 16 s of warp g, exchange
-// region at shared address xo with warp g owning chunk g ^ (row & 7) of its 512 rows).
+// region at shared address xo with warp g owning chunk g ^ (row & 7) of its 512 rows; with
+// RB = 64, rows of 64 bytes and chunk g ^ ((row >> 1) & 3)).  Slot row of the value
+// V[q'][k1][t] (k1 = k0 + 8 s): 256 t + 128 s + 16 k0 + (q' ^ k0); within every quarter-warp
+// access the row mod 8 differs from lane to lane, so the chunks hit distinct bank groups.
 struct ZwLane {
     float2 tw32;   // F3 twiddle sgn W_32^{q'} (sgn = -1 on the upper half-warp)
     int tkb, tnb;  // twiddle-table bases of the registers in K (k1 = kappa0 + H s) and outside
@@ -184,7 +195,7 @@ struct ZwLane {
     bool rd;       // lane q gathers after the exchange ((q & 7) < H)
 };
 // tw: W_L^e (twstride 1) or W_2L^e (twstride 2), L = 32 E1.
-template <int E1>
+template <int E1, int RB = 128>
 __device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_t xo, int g, int q, int twstride = 1) {
     constexpr int H = E1 / 2;
     const int s = q >> 4, qp = q & 15;
@@ -194,8 +205,13 @@ __device__ __forceinline__ ZwLane zw_lane(const float2 *__restrict__ tw, uint32_
     z.tkb = q + 32 * H * s;
     z.tnb = q - 32 * H * s;
     z.sg = s ? -1.f : 1.f;
-    z.aw = xo + 16384 * s + 128 * qp + 16 * (g ^ (qp & 7));
-    z.ar = xo + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
+    if (RB == 128) {
+        z.aw = xo + 16384 * s + 128 * qp + 16 * (g ^ (qp & 7));
+        z.ar = xo + 2048 * q + 128 * (q & 7) + 16 * (g ^ (q & 7));
+    } else {
+        z.aw = xo + 8192 * s + 64 * qp + 16 * (g ^ ((qp >> 1) & 3));
+        z.ar = xo + 1024 * q + 64 * (q & 7) + 16 * (g ^ ((q >> 1) & 3));
+    }
     z.rd = (q & 7) < H;
     return z;
 }
@@ -217,36 +233,45 @@ template <int E1> __device__ __forceinline__ void zw_front(CV *v, const ZwLane &
         v[M::partner(j)] = zw_twmul<-1>(csub(a, rcv), z.tw32);
     }
 }
+// Exchange slot addresses: writer slot of k0 (t = 0; t = 1 lies RB * 256 further) and reader
+// position p, for RB-byte rows.
+template <int RB> __device__ __forceinline__ uint32_t zw_wslot(const ZwLane &z, int k0) {
+    return RB == 128 ? (z.aw ^ (144 * k0)) + 2048 * k0 : (z.aw ^ (64 * k0 + 16 * ((k0 >> 1) & 3))) + 1024 * k0;
+}
+template <int RB> __device__ __forceinline__ uint32_t zw_rslot(const ZwLane &z, int p) {
+    return RB == 128 ? (z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3)
+                     : (z.ar ^ (64 * (p & 7) + 16 * ((p >> 1) & 3))) + 512 * (p >> 3);
+}
 // F5: write the values this lane holds as writer, gather its 16 as reader (reader lanes).
-template <int E1> __device__ __forceinline__ void zw_exchange(CV *v, const ZwLane &z) {
+template <int E1, int RB = 128> __device__ __forceinline__ void zw_exchange(CV *v, const ZwLane &z) {
     using M = ZwMap<E1>;
 #pragma unroll
     for (int j = 0; j < E1; ++j) {
         if (!M::inK(j)) continue;
         const int k0 = M::kappa0(j);
-        zw_sts((z.aw ^ (144 * k0)) + 2048 * k0, v[j]);
-        zw_sts((z.aw ^ (144 * k0)) + 2048 * k0 + 32768, v[M::partner(j)]);
+        zw_sts(zw_wslot<RB>(z, k0), v[j]);
+        zw_sts(zw_wslot<RB>(z, k0) + 256 * RB, v[M::partner(j)]);
     }
     __syncwarp();
     if (z.rd) {
 #pragma unroll
-        for (int p = 0; p < 16; ++p) v[p] = zw_lds((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3));
+        for (int p = 0; p < 16; ++p) v[p] = zw_lds(zw_rslot<RB>(z, p));
     }
 }
 // Adjoint of F5.
-template <int E1> __device__ __forceinline__ void zw_exchange_adj(CV *v, const ZwLane &z) {
+template <int E1, int RB = 128> __device__ __forceinline__ void zw_exchange_adj(CV *v, const ZwLane &z) {
     using M = ZwMap<E1>;
     if (z.rd) {
 #pragma unroll
-        for (int p = 0; p < 16; ++p) zw_sts((z.ar ^ (144 * (p & 7))) + 1024 * (p >> 3), v[p]);
+        for (int p = 0; p < 16; ++p) zw_sts(zw_rslot<RB>(z, p), v[p]);
     }
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < E1; ++j) {
         if (!M::inK(j)) continue;
         const int k0 = M::kappa0(j);
-        v[j] = zw_lds((z.aw ^ (144 * k0)) + 2048 * k0);
-        v[M::partner(j)] = zw_lds((z.aw ^ (144 * k0)) + 2048 * k0 + 32768);
+        v[j] = zw_lds(zw_wslot<RB>(z, k0));
+        v[M::partner(j)] = zw_lds(zw_wslot<RB>(z, k0) + 256 * RB);
     }
 }
 // Adjoints of F3 (with its twiddle), F2 and F1: the outputs r < H in v[0..H-1], odd ones
@@ -266,11 +291,11 @@ template <int E1> __device__ __forceinline__ void zw_back(CV *v, const ZwLane &z
     zw_f1_adj<E1>(v);
 }
 
-// Tile t = (tx, ky, b): tx the 16-column block, consecutive tiles take ky and its mirror
+// Tile t = (tx, ky, b): tx the 8-column block, consecutive tiles take ky and its mirror
 // 2N - ky (same symbol rows), b the density.  With TAIL the forward spectrum's shell and
 // total energies are added to tail[2 b], tail[2 b + 1] (as in k_z_symbol_tma).
 template <int E1, bool TAIL>
-__global__ void __launch_bounds__(ZWarp<E1>::NT, 2)
+__global__ void __launch_bounds__(ZWarp<E1>::NT, ZWarp<E1>::MINB)
 k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
          const __grid_constant__ CUtensorMap tout, const float2 *__restrict__ tw, int ntx, int ntiles,
          int ncols, int *__restrict__ status, double *__restrict__ tail) {
@@ -329,9 +354,10 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
 
-    const ZwLane zl = zw_lane<E1>(tw, smem_addr(xo), g, q);
+    constexpr int RB = Z::ROWB;
+    const ZwLane zl = zw_lane<E1, RB>(tw, smem_addr(xo), g, q);
     // Input/output rows q + 32 r of this warp's 16-byte chunk.
-    const int io = zw_sw128(q, g);
+    const int io = zw_swz<RB>(q, g);
     // Symbol: reader q holds kz = kb + 2 E1 k2 (k2 < 8) and 2N - kb - 2 E1 k2 (k2 >= 8); its
     // columns 2g and 2g + 1 have kz lines SYM_KZB floats apart in every box.
     const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
@@ -348,7 +374,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) {
 #pragma unroll
             for (int r = 0; r < H; ++r) {
-                const float4 f = *reinterpret_cast<const float4 *>(Bb + io + 4096 * r);
+                const float4 f = *reinterpret_cast<const float4 *>(Bb + io + 32 * RB * r);
                 v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
                 if (r & 1) v[r] = zw_sign(v[r], zl.sg);
             }
@@ -357,7 +383,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) zw_front<E1>(v, zl, T);
         if (!mbar_wait(bar + 2, ph, status)) return;  // the previous tile's store has read XO
         if (valid) {
-            zw_exchange<E1>(v, zl);
+            zw_exchange<E1, RB>(v, zl);
             if (zl.rd) dft<16, -1>(v);  // v[k2] = X[kb + 2 E1 k2]
         }
         if constexpr (TAIL) {
@@ -399,7 +425,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
         if (valid) {
             if (zl.rd) dft<16, 1>(v);
-            zw_exchange_adj<E1>(v, zl);
+            zw_exchange_adj<E1, RB>(v, zl);
             zw_back<E1>(v, zl, T);
         }
         __syncwarp();  // every lane's exchange reads are done: the slots take the outputs
@@ -408,7 +434,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             for (int r = 0; r < H; ++r) {
                 CV x = v[r];
                 if (r & 1) x = zw_sign(x, zl.sg);
-                *reinterpret_cast<float4 *>(xo + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+                *reinterpret_cast<float4 *>(xo + io + 32 * RB * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
             }
         }
         fence_proxy_async();
