@@ -1004,8 +1004,10 @@ namespace gsp {
 
 // ---- K3, warp form at N = 512 (FP32) -------------------------------------------------------
 // The fused z pass of k_z_warp for L = 2N = 1024, where a packed column pair would need 32
-// CV values (128 registers) per lane: one warp per column, unpacked complex values (CF),
-// L = 32 x 32.  Lane q holds x[q + 32 r] of its column (r < 16 nonzero) in register r:
+// CV values (128 registers) per lane: one warp per column, L = 32 x 32.  Lane q holds
+// x[q + 32 r] of its column (r < 16 nonzero) in register r.  The steps below are those of
+// the y passes (k_y_w512, on unpacked complex values CF); k_z_w512 runs the same steps on
+// packed pairs of one column's values (its own description):
 //   F1  A_q[k1] = sum_{r<16} x[q + 32 r] W_32^{r k1}   pruned 32-point DFT in registers
 //       (two 16-point DFTs of the inputs and of the inputs times W_32^r): register j holds
 //       k1 = kappa(j) = 2j (j < 16) or 2(j - 16) + 1
@@ -1026,7 +1028,7 @@ namespace gsp {
 //   XO  64 KB: the warps' 8 KB exchange regions; the first 32 KB is also the output tile
 //       in the TMA store's 64-byte swizzle, written after a block barrier that ends every
 //       warp's exchange reads;
-//   T   8 KB: W_1024^{q k1} as T[k1][q].
+//   T   8 KB: W_1024^{q k1} as T[k1][q] (k_z_w512: the pairs for k1 = 2m, 2m + 1 as one float4).
 struct ZW512 {
     static constexpr int N = 512, L = 1024, TC = 8, NW = 8, NT = 256;
     static constexpr int IN_BYTES = N * TC * 8;                  // two 16 KB boxes
@@ -1101,9 +1103,48 @@ __device__ __forceinline__ CF lds2(uint32_t a) {
     return {f.x, f.y};
 }
 
+// Shared 32-bit access by address.
+__device__ __forceinline__ void sts1(uint32_t a, float x) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(x) : "memory");
+}
+__device__ __forceinline__ float lds1(uint32_t a) {
+    float f;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(f) : "r"(a) : "memory");
+    return f;
+}
+__device__ __forceinline__ void sts2f(uint32_t a, float2 x) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x.x), "f"(x.y) : "memory");
+}
+__device__ __forceinline__ float2 lds2f(uint32_t a) {
+    float2 f;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(f.x), "=f"(f.y) : "r"(a) : "memory");
+    return f;
+}
+// The two halves of a CV pair as scalar complex values.
+__device__ __forceinline__ CF cv_lo(CV a) { return {a.re.x, a.im.x}; }
+__device__ __forceinline__ CF cv_hi(CV a) { return {a.re.y, a.im.y}; }
+__device__ __forceinline__ CV cv_pair(CF a, CF b) { return {f2(a.re, b.re), f2(a.im, b.im)}; }
+// exp(D 2 pi i r / 32) times x, r < 16 (compile-time r after unrolling).
+template <int D> __device__ __forceinline__ CF w32mul(CF x, int r) {
+    return r == 0 ? x : r == 8 ? (D < 0 ? CF{x.im, -x.re} : CF{-x.im, x.re}) : cmulk<D>(x, w32c(r), w32s(r));
+}
+
 // Tile t = (tx, ky, b): tx the 8-column block, consecutive tiles take ky and its mirror
 // 2N - ky (same symbol lines), b the density.  With TAIL the forward spectrum's shell and
 // total energies are added to tail[2 b], tail[2 b + 1] (as in k_z_warp).
+//
+// Each step runs on packed pairs of the lane's 32 values (CV u[16]), two DFT lanes of one
+// column per packed instruction:
+//   F1  u[r] = (x_r, x_r W_32^r), one packed 16-point DFT: u[m] = (A_q[2m], A_q[2m + 1]);
+//   F2  u[m] times (W_1024^{2m q}, W_1024^{(2m + 1) q}) (table T4[m][q], float4 pairs);
+//   F3  the writer stores its 32 values one float at a time into a re plane and an im
+//       plane (4 KB each), slot (q, k1) at byte 128 k1 + 4 (q ^ 2 (k1 & 15)); reader lane l
+//       loads the pair of slots (2i, l), (2i + 1, l), adjacent in each plane, so that
+//       u[i] = (B_{2i}[l], B_{2i+1}[l]) (both directions conflict free);
+//   F4  a packed 16-point DFT gives (E[k], O[k]), the DFTs of the even and odd q; then
+//       u[k] = (X[l + 32 k], X[l + 32 (k + 16)]) = (E + W_32^k O, E - W_32^k O).
+// The symbol product scales each pair by (G at kz = l + 32 k, G at 512 - l - 32 k), and the
+// adjoint steps run in reverse order.
 template <bool TAIL>
 __global__ void __launch_bounds__(ZW512::NT, 2)
 k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tsym,
@@ -1115,7 +1156,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     unsigned char *Bb = base + Z::OFF_B;
     unsigned char *xo = base + Z::OFF_XO;
-    float2 *T = reinterpret_cast<float2 *>(base + Z::OFF_T);
+    float4 *T4 = reinterpret_cast<float4 *>(base + Z::OFF_T);
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + Z::OFF_BAR);  // input, symbol, XO free
     int *cnt = reinterpret_cast<int *>(bar + 3);                       // input, symbol, output
     const int g = threadIdx.x >> 5, q = threadIdx.x & 31;
@@ -1127,7 +1168,11 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         cnt[0] = cnt[1] = cnt[2] = 0;
         fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < 1024; i += Z::NT) T[i] = tw[(i & 31) * (i >> 5)];
+    for (int i = threadIdx.x; i < 512; i += Z::NT) {
+        const int m = i >> 5, qq = i & 31;
+        const float2 w0 = tw[2 * m * qq], w1 = tw[(2 * m + 1) * qq];
+        T4[i] = make_float4(w0.x, w1.x, w0.y, w1.y);
+    }
     __syncthreads();
     griddep_wait();  // the previous pass has finished: its outputs are readable
 
@@ -1165,13 +1210,11 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
 
-    const uint32_t xw = smem_addr(xo) + 8192 * g;           // this warp's exchange region
-    const uint32_t aw = xw + 8 * q;                          // writer (lane q) base
-    const uint32_t ar = xw + 256 * q + 8 * (q & 15);         // reader (lane l = q) base
-    // Symbol value at folded kz for reader lane q and register k2.
-    auto sym_at = [&](int k2) {
-        int kz = q + 32 * k2;
-        if (kz > N) kz = L - kz;
+    const uint32_t xw = smem_addr(xo) + 8192 * g;     // this warp's exchange region (re plane, im plane)
+    const uint32_t aw = xw + 4 * q;                    // writer (lane q): slot (q, k1) at (aw ^ 8 (k1 & 15)) + 128 k1
+    const uint32_t ar = xw + 128 * q + 8 * (q & 15);   // reader (lane l = q): pair i at ar ^ 8 i
+    // Symbol value at kz <= N for this lane's column.
+    auto sym_at = [&](int kz) {
         return *reinterpret_cast<const float *>(Bb + (kz >> 8) * (Z::SYM_BOX * Z::TC * 4) + 1024 * g + 4 * (kz & 255));
     };
     bool stored = false;
@@ -1181,7 +1224,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         const int kya = ky <= N ? ky : L - ky;
         const int col = tx * Z::TC + g;
         const bool valid = col < ncols;
-        CF v[32];
+        CV u[16];
         // A wait that gives up marks the thread; the block leaves together at its barrier
         // below (no thread may return while others still wait there).
         bool bad = !mbar_wait(bar, ph, status);
@@ -1189,39 +1232,50 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
                 const float2 f = *reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g));
-                v[r] = {f.x, f.y};
+                const CF x = {f.x, f.y};
+                u[r] = cv_pair(x, w32mul<-1>(x, r));
             }
         }
         if (last_arrival(0)) issue_sym(t);
         if (valid) {
-            w512_f1(v);
+            dft<16, -1>(u);  // u[m] = (A[2m], A[2m + 1])
 #pragma unroll
-            for (int j = 1; j < 32; ++j) v[j] = twmul<-1>(v[j], T[w512_kappa(j) * 32 + q]);
+            for (int m = 0; m < 16; ++m) u[m] = twmul<-1>(u[m], T4[m * 32 + q]);
         }
         if (!bad) bad = !mbar_wait(bar + 2, ph, status);  // the previous tile's store has read XO
         if (valid) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int k1 = w512_kappa(j);
-                sts2((aw ^ (8 * (k1 & 15))) + 256 * k1, v[j]);
+            for (int m = 0; m < 16; ++m) {
+                const uint32_t sa = (aw ^ (8 * ((2 * m) & 15))) + 128 * (2 * m);
+                const uint32_t sb = (aw ^ (8 * ((2 * m + 1) & 15))) + 128 * (2 * m + 1);
+                sts1(sa, u[m].re.x);
+                sts1(sa + 4096, u[m].im.x);
+                sts1(sb, u[m].re.y);
+                sts1(sb + 4096, u[m].im.y);
             }
             __syncwarp();
 #pragma unroll
-            for (int p = 0; p < 32; ++p) v[p] = lds2(ar ^ (8 * p));
-            dft32<-1>(v);  // v[k2] = X[q + 32 k2]
+            for (int i = 0; i < 16; ++i) u[i] = {lds2f(ar ^ (8 * i)), lds2f((ar ^ (8 * i)) + 4096)};
+            dft<16, -1>(u);  // u[k] = (E[k], O[k])
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const CF e = cv_lo(u[k]), o = w32mul<-1>(cv_hi(u[k]), k);
+                u[k] = cv_pair(cadd(e, o), csub(e, o));  // (X[q + 32 k], X[q + 32 k + 512])
+            }
         }
         if constexpr (TAIL) {
             constexpr int SHELL = N - N / 8;
             float eshell = 0.f, etot = 0.f;
             if (valid) {
                 const float w0 = (col == 0 || col == N) ? 1.f : 2.f;
+                const bool cs = kya >= SHELL || col >= SHELL;
 #pragma unroll
-                for (int k2 = 0; k2 < 32; ++k2) {
-                    int kz = q + 32 * k2;
-                    if (kz > N) kz = L - kz;
-                    const float en = v[k2].re * v[k2].re + v[k2].im * v[k2].im;
-                    etot += w0 * en;
-                    if (kz >= SHELL || kya >= SHELL || col >= SHELL) eshell += w0 * en;
+                for (int k = 0; k < 16; ++k) {
+                    const int kz1 = q + 32 * k, kz2 = N - q - 32 * k;  // the second folded
+                    const float2 en = cenergy(u[k]);
+                    etot += w0 * (en.x + en.y);
+                    if (cs || kz1 >= SHELL) eshell += w0 * en.x;
+                    if (cs || kz2 >= SHELL) eshell += w0 * en.y;
                 }
             }
 #pragma unroll
@@ -1237,29 +1291,40 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (!bad) bad = !mbar_wait(bar + 1, ph, status);
         if (valid) {
 #pragma unroll
-            for (int k2 = 0; k2 < 32; ++k2) v[k2] = cscale(v[k2], sym_at(k2));
+            for (int k = 0; k < 16; ++k) u[k] = cscale2(u[k], f2(sym_at(q + 32 * k), sym_at(N - q - 32 * k)));
         }
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
         if (valid) {
-            dft32<1>(v);  // v[p] = B_p[q] (adjoint of F4)
 #pragma unroll
-            for (int p = 0; p < 32; ++p) sts2(ar ^ (8 * p), v[p]);
+            for (int k = 0; k < 16; ++k) {  // adjoint of F4's last step: (a + b, conj(W_32^k) (a - b))
+                const CF a = cv_lo(u[k]), b = cv_hi(u[k]);
+                u[k] = cv_pair(cadd(a, b), w32mul<1>(csub(a, b), k));
+            }
+            dft<16, 1>(u);  // u[i] = (B_{2i}[q], B_{2i+1}[q]) of the adjoint
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                sts2f(ar ^ (8 * i), u[i].re);
+                sts2f((ar ^ (8 * i)) + 4096, u[i].im);
+            }
             __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int k1 = w512_kappa(j);
-                v[j] = lds2((aw ^ (8 * (k1 & 15))) + 256 * k1);
+            for (int m = 0; m < 16; ++m) {
+                const uint32_t sa = (aw ^ (8 * ((2 * m) & 15))) + 128 * (2 * m);
+                const uint32_t sb = (aw ^ (8 * ((2 * m + 1) & 15))) + 128 * (2 * m + 1);
+                u[m] = {f2(lds1(sa), lds1(sb)), f2(lds1(sa + 4096), lds1(sb + 4096))};
             }
 #pragma unroll
-            for (int j = 1; j < 32; ++j) v[j] = twmul<1>(v[j], T[w512_kappa(j) * 32 + q]);
-            w512_f1_adj(v);
+            for (int m = 0; m < 16; ++m) u[m] = twmul<1>(u[m], T4[m * 32 + q]);
+            dft<16, 1>(u);  // u[r] = (a_r, b_r)
         }
         // Every warp's exchange reads are done: XO takes the output tile.
         if (__syncthreads_or(bad)) break;
         if (valid) {
 #pragma unroll
-            for (int r = 0; r < 16; ++r)
-                *reinterpret_cast<float2 *>(xo + sw64(q + 32 * r, g)) = make_float2(v[r].re, v[r].im);
+            for (int r = 0; r < 16; ++r) {
+                const CF z = cadd(cv_lo(u[r]), w32mul<1>(cv_hi(u[r]), r));  // adjoint of F1, row q + 32 r
+                *reinterpret_cast<float2 *>(xo + sw64(q + 32 * r, g)) = make_float2(z.re, z.im);
+            }
         }
         fence_proxy_async();
         if (last_arrival(2)) {
