@@ -48,8 +48,8 @@ struct CV {
 // ---- double-float reals ------------------------------------------------------------------
 // A real number held as hi + lo, two FP32 values with |lo| <= ulp(hi) / 2: a 48-bit
 // significand (unit roundoff 2^-48, about 3.6e-15) with FP32's exponent range, computed on
-// the FP32 pipe.  Sums use Knuth's two-sum, which yields the exact rounding error of an
-// FP32 addition; products use the exact product of an FP32 multiplication that the fused
+// the FP32 pipe.  Sums use a two-sum (the operands ordered by magnitude, then Dekker's fast
+// two-sum), which yields the exact rounding error of an FP32 addition; products use the exact product of an FP32 multiplication that the fused
 // multiply-add gives (fma(a, b, -ab) = the error of ab); both end with a fast two-sum that
 // renormalises (hi, lo).  The error of a sum is at most about 2^-47 (|a| + |b|), of a
 // product 2^-47 |ab| (the lo-lo term is dropped), which is the norm-wise error model of an
@@ -68,11 +68,18 @@ __device__ __forceinline__ DF df_fast_two_sum(float s, float e) {  // needs |s| 
     const float h = __fadd_rn(s, e);
     return DF(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
+// s + e = x + y exactly, s = fl(x + y): the leading parts ordered by magnitude (selects on
+// the ALU pipe), then Dekker's fast two-sum (three FP32 operations instead of the six of
+// Knuth's branch-free two-sum; both give the same exact s and e).
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const bool sw = fabsf(b) > fabsf(a);
+    const float x = sw ? b : a, y = sw ? a : b;
+    const float s = __fadd_rn(x, y);
+    return DF(s, __fsub_rn(y, __fsub_rn(s, x)));
+}
 __device__ __forceinline__ DF operator+(DF a, DF b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float v = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-    return df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+    const DF t = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
 __device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
@@ -86,14 +93,14 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
 
 // a b + c d in one pass: the two leading products and their exact errors (FMA), one
 // two-sum of the products, the cross terms hi x lo accumulated in FP32, one renormalisation:
-// 19 FP32 operations instead of 25 for two products and a sum, with the same error bound
-// (the lo x lo terms dropped, about 2^-47 (|ab| + |cd|)).
+// 16 FP32 operations and 3 selects instead of 22 and 6 for two products and a sum, with the
+// same error bound (the lo x lo terms dropped, about 2^-47 (|ab| + |cd|)).
 __device__ __forceinline__ DF df_sum_prod(DF a, DF b, DF c, DF d) {
     const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
     const float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
-    const float s = __fadd_rn(p1, p2), v = __fsub_rn(s, p1);
-    float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, v)), __fsub_rn(p2, v));
-    t = __fadd_rn(t, __fadd_rn(e1, e2));
+    const DF st = df_two_sum(p1, p2);
+    const float s = st.hi;
+    float t = __fadd_rn(st.lo, __fadd_rn(e1, e2));
     t = __fmaf_rn(a.hi, b.lo, t);
     t = __fmaf_rn(a.lo, b.hi, t);
     t = __fmaf_rn(c.hi, d.lo, t);
