@@ -665,15 +665,19 @@ cudaError_t y_pass(const DevicePlan &p, int B, cudaStream_t s, bool fwd, int z0 
     }
     if constexpr (ywarp_form<Real, N>()) {
         if (p.yform == 1) {
-            using Y = YWarp<N / 16>;
-            const int ntx = (ncols + Y::TC - 1) / Y::TC, nt = ntx * planes;
-            auto k = fwd ? k_y_warp<N / 16, true> : k_y_warp<N / 16, false>;
-            const int smem = fwd ? Y::SMEM_F : Y::SMEM_I;
-            GSP_CHECK(set_smem(k, smem));
-            GSP_CHECK(launch_pdl(k, persistent_blocks(k, Y::NT, smem, nt), Y::NT, smem, s,
-                                 fwd ? p.tm_yw1 : p.tm_yw3, fwd ? p.tm_yw2 : p.tm_yw1,
-                                 static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status, z0));
-            return cudaGetLastError();
+            // The forward and inverse kernels take tiles of different widths (16 and 8 columns).
+            auto launch = [&](auto kern, int tc, int nthreads, int smem, const CUtensorMap &tin,
+                              const CUtensorMap &tout) -> cudaError_t {
+                const int ntx = (ncols + tc - 1) / tc, nt = ntx * planes;
+                GSP_CHECK(set_smem(kern, smem));
+                GSP_CHECK(launch_pdl(kern, persistent_blocks(kern, nthreads, smem, nt), nthreads, smem, s, tin, tout,
+                                     static_cast<const float2 *>(p.tw), ntx, nt, ncols, p.status, z0));
+                return cudaGetLastError();
+            };
+            using YF = YWarp<N / 16, true>;
+            using YI = YWarp<N / 16, false>;
+            if (fwd) return launch(k_y_warp<N / 16, true>, YF::TC, YF::NT, YF::SMEM, p.tm_yw1, p.tm_yw2);
+            return launch(k_y_warp<N / 16, false>, YI::TC, YI::NT, YI::SMEM, p.tm_ywi3, p.tm_ywi1);
         }
     }
     const TwC *twc = static_cast<const TwC *>(p.twc);
@@ -847,14 +851,19 @@ cudaError_t encode_n(DevicePlan &p) {
                         L2::ROWB / 8, L2::RPC, 1));
     if constexpr (ywarp_form<Real, N>()) {
         // N-row boxes of w1, w2, w3 (16 columns x N rows of y or ky x 1 plane), 128-byte swizzle.
-        GSP_CHECK(encode_3d(&p.tm_yw1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16>::TC, N, 1,
-                            CU_TENSOR_MAP_SWIZZLE_128B));
-        GSP_CHECK(encode_3d(&p.tm_yw2, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16>::TC, N, 1,
-                            CU_TENSOR_MAP_SWIZZLE_128B));
-        GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16>::TC, N, 1,
-                            CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_yw1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16, true>::TC,
+                            N, 1, CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_yw2, U64, p.w2, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16, true>::TC,
+                            N, 1, CU_TENSOR_MAP_SWIZZLE_128B));
+        GSP_CHECK(encode_3d(&p.tm_yw3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16, true>::TC,
+                            N, 1, CU_TENSOR_MAP_SWIZZLE_128B));
+        // The warp-form y inverse: 8 columns x N rows of w3 (in) and w1 (out), 64-byte swizzle.
+        GSP_CHECK(encode_3d(&p.tm_ywi3, U64, p.w3, N + 1, L, BN, rowb, (cuuint64_t)L * rowb, YWarp<N / 16, false>::TC,
+                            N, 1, CU_TENSOR_MAP_SWIZZLE_64B));
+        GSP_CHECK(encode_3d(&p.tm_ywi1, U64, p.w1, N + 1, N, BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16, false>::TC,
+                            N, 1, CU_TENSOR_MAP_SWIZZLE_64B));
         // The fused forward pass's ring of N-row plane slots in w3.
-        GSP_CHECK(encode_3d(&p.tm_rf, U64, p.w3, N + 1, N, 2 * BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16>::TC, N,
+        GSP_CHECK(encode_3d(&p.tm_rf, U64, p.w3, N + 1, N, 2 * BN, rowb, (cuuint64_t)N * rowb, YWarp<N / 16, true>::TC, N,
                             1, CU_TENSOR_MAP_SWIZZLE_128B));
     }
     if constexpr (zwarp_form<Real, N>()) {

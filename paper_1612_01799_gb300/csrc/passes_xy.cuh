@@ -181,8 +181,8 @@ k_xy_fwd(const PtrArray rho, float2 *__restrict__ ring, const __grid_constant__ 
             if (threadIdx.x == 0) red_release_gpu(cons + slot, 1);  // the slot's tile is in shared memory
             if (ok && idx * X::TC + 2 * g < N + 1) {
                 CV v[16];
-                yw_fwd_front<E1>(v, inb, io, zl, T);
-                yw_fwd_back<E1>(v, zl, xb, kb, g);
+                yw_fwd_front<E1, 128>(v, inb, io, zl, T);
+                yw_fwd_back<E1, 128>(v, zl, xb, kb, g);
             }
             fence_proxy_async();
             __syncthreads();
@@ -253,7 +253,7 @@ k_yx_inv(const __grid_constant__ CUtensorMap tin, float2 *__restrict__ ring, con
                 const ZwLane zl = zw_lane<E1>(tw, smem_addr(xb), g, q);
                 const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
                 CV v[16];
-                yw_inv<E1>(v, zl, xb, kb, zw_sw128(q, g), g, T);
+                yw_inv<E1, 128>(v, zl, xb, kb, zw_sw128(q, g), g, T);
             }
             if (threadIdx.x == 0 && epoch > 0) counter_wait(cons + slot, epoch * NX, status);
             __syncthreads();

@@ -456,82 +456,87 @@ namespace gsp {
 // ---- K2 / K4, warp form (FP32, N = 256) -------------------------------------------------
 // The y passes with the transform halves of k_z_warp: the forward half (F1..F6) alone for
 // the y forward (N input rows, all 2N output rows kept), the adjoint half alone for the
-// y inverse (2N input rows, rows y < N kept).  Tile t = (tx, zz): 16 columns kx, plane
-// zz = b N + z.  As in k_z_warp, warp g owns the 16-byte chunk g ^ (row & 7) of each
-// 128-byte row of the exchange/output buffer, so a warp exchanges and writes its outputs
-// in its own chunks without waiting for the other warps; the last warp to finish a tile
-// issues the TMA store.
-//   y forward: a 32 KB input buffer (prefetched for the CTA's next tile as soon as every
-//     warp has read its inputs) and a 64 KB exchange/output buffer (2N rows), freed for
-//     the next tile's exchange once the store has read it;
-//   y inverse: one 64 KB buffer for the 2N input rows, the exchange and the N output rows;
-//     the next tile's load follows the store's read of it.
-template <int E1> struct YWarp {
-    static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N, TC = 16, NW = 8, NT = 256;
+// y inverse (2N input rows, rows y < N kept).  Tile t = (tx, zz): TC columns kx, plane
+// zz = b N + z.  As in k_z_warp, warp g owns one 16-byte chunk of each row of the
+// exchange/output buffer (g ^ (row & 7) in 128-byte rows, g ^ ((row >> 1) & 3) in 64-byte
+// rows), so a warp exchanges and writes its outputs in its own chunks without waiting for
+// the other warps; the last warp to finish a tile issues the TMA store.
+//   y forward: 16 columns, 8 warps, two CTAs per SM; a 32 KB input buffer (prefetched for
+//     the CTA's next tile as soon as every warp has read its inputs) and a 64 KB
+//     exchange/output buffer (2N rows of 128 B), freed for the next tile's exchange once
+//     the store has read it;
+//   y inverse: 8 columns, 4 warps, four CTAs per SM; one 32 KB buffer for the 2N input
+//     rows of 64 B, the exchange and the N output rows; the next tile's load follows the
+//     store's read of it, so four independent CTAs per SM cover each other's loads (with
+//     16-column tiles, two CTAs per SM, the pass took 80 us at N = 256 against 74).
+template <int E1, bool FWD> struct YWarp {
+    static constexpr int H = E1 / 2, N = 16 * E1, L = 2 * N;
+    static constexpr int TC = FWD ? 16 : 8, NW = TC / 2, NT = 32 * NW, RB = 8 * TC, MINB = FWD ? 2 : 4;
     static constexpr int T_BYTES = E1 * 32 * 8;
-    static constexpr int F_IN = 0, F_XB = (N * 128 + 1023) / 1024 * 1024, F_T = F_XB + 65536;
+    static constexpr int F_IN = 0, F_XB = (N * RB + 1023) / 1024 * 1024, F_T = F_XB + 512 * RB;
     static constexpr int F_BAR = F_T + T_BYTES;
-    static constexpr int I_XB = 0, I_T = 65536, I_BAR = I_T + T_BYTES;
-    static constexpr int SMEM_F = 1024 + F_BAR + 64, SMEM_I = 1024 + I_BAR + 64;
-    static_assert((N * 128) % 1024 == 0, "the second half of a 2N-row tile starts 1024-byte aligned");
+    static constexpr int I_XB = 0, I_T = 512 * RB, I_BAR = I_T + T_BYTES;
+    static constexpr int SMEM = 1024 + (FWD ? F_BAR : I_BAR) + 64;
+    static_assert((N * RB) % 1024 == 0, "the second half of a 2N-row tile starts 1024-byte aligned");
 };
 
-// y forward of warp g's column pair, first half: its N input rows from the 128-byte-swizzled
-// tile at inb (row y at inb + io + 4096 (y / 32) for lane y % 32), F1 to F3.
-template <int E1>
+// y forward of warp g's column pair, first half: its N input rows from the swizzled tile of
+// RB-byte rows at inb (row y at inb + io + 32 RB (y / 32) for lane y % 32), F1 to F3.
+template <int E1, int RB>
 __device__ __forceinline__ void yw_fwd_front(CV *v, const unsigned char *inb, int io, const ZwLane &zl, const float2 *T) {
 #pragma unroll
     for (int r = 0; r < E1 / 2; ++r) {
-        const float4 f = *reinterpret_cast<const float4 *>(inb + io + 4096 * r);
+        const float4 f = *reinterpret_cast<const float4 *>(inb + io + 32 * RB * r);
         v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
         if (r & 1) v[r] = zw_sign(v[r], zl.sg);
     }
     zw_front<E1>(v, zl, T);
 }
 // Second half: the exchange through xb, the 16-point DFTs, and the 2N spectrum rows to xb
-// (reader lane with base kb holds rows kb + 2 E1 k2, chunk g ^ (row & 7)).
-template <int E1>
+// (reader lane with base kb holds rows kb + 2 E1 k2, in warp g's chunk of each row).
+template <int E1, int RB>
 __device__ __forceinline__ void yw_fwd_back(CV *v, const ZwLane &zl, unsigned char *xb, int kb, int g) {
-    zw_exchange<E1>(v, zl);
+    zw_exchange<E1, RB>(v, zl);
     if (zl.rd) dft<16, -1>(v);  // v[k2] = X[kb + 2 E1 k2]
     __syncwarp();
     if (zl.rd) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2)
-            *reinterpret_cast<float4 *>(xb + zw_sw128(kb + 2 * E1 * k2, g)) =
+            *reinterpret_cast<float4 *>(xb + zw_swz<RB>(kb + 2 * E1 * k2, g)) =
                 make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
     }
 }
 // y inverse of warp g's column pair: the 2N spectrum rows from xb, the N kept rows back to xb
-// in the input tile's layout (row y at xb + io + 4096 (y / 32)).
-template <int E1>
+// in the input tile's layout (row y at xb + io + 32 RB (y / 32)).
+template <int E1, int RB>
 __device__ __forceinline__ void yw_inv(CV *v, const ZwLane &zl, unsigned char *xb, int kb, int io, int g,
                                        const float2 *T) {
     if (zl.rd) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
-            const float4 f = *reinterpret_cast<const float4 *>(xb + zw_sw128(kb + 2 * E1 * k2, g));
+            const float4 f = *reinterpret_cast<const float4 *>(xb + zw_swz<RB>(kb + 2 * E1 * k2, g));
             v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
         }
         dft<16, 1>(v);
     }
     __syncwarp();  // every lane has read its inputs: its chunks take exchange slots
-    zw_exchange_adj<E1>(v, zl);
+    zw_exchange_adj<E1, RB>(v, zl);
     zw_back<E1>(v, zl, T);
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < E1 / 2; ++r) {
         CV x = v[r];
         if (r & 1) x = zw_sign(x, zl.sg);
-        *reinterpret_cast<float4 *>(xb + io + 4096 * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+        *reinterpret_cast<float4 *>(xb + io + 32 * RB * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
     }
 }
 
 template <int E1, bool FWD>
-__global__ void __launch_bounds__(YWarp<E1>::NT, 2)
+__global__ void __launch_bounds__(YWarp<E1, FWD>::NT, YWarp<E1, FWD>::MINB)
 k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
          const float2 *__restrict__ tw, int ntx, int ntiles, int ncols, int *__restrict__ status, int z0) {
-    using Y = YWarp<E1>;
+    using Y = YWarp<E1, FWD>;
+    constexpr int RB = Y::RB;
     constexpr int NW = Y::NW, N = Y::N, H = Y::H;
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
@@ -552,9 +557,9 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     griddep_wait();  // the previous pass has finished: its outputs are readable
     auto issue_in = [&](int t) {
         const int tx = t % ntx, zz = z0 + t / ntx;
-        mbar_arrive_expect_tx(bar, (FWD ? 1 : 2) * N * 128);
+        mbar_arrive_expect_tx(bar, (FWD ? 1 : 2) * N * RB);
         tma_load_3d(inb, &tin, bar, tx * Y::TC, 0, zz);
-        if (!FWD) tma_load_3d(inb + N * 128, &tin, bar, tx * Y::TC, N, zz);
+        if (!FWD) tma_load_3d(inb + N * RB, &tin, bar, tx * Y::TC, N, zz);
     };
     auto last_arrival = [&](int c) {
         __syncwarp();
@@ -573,8 +578,8 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (FWD) mbar_arrive(bar + 1);  // the exchange/output buffer starts free
         if ((int)blockIdx.x < ntiles) issue_in(blockIdx.x);
     }
-    const ZwLane zl = zw_lane<E1>(tw, smem_addr(xb), g, q);
-    const int io = zw_sw128(q, g);
+    const ZwLane zl = zw_lane<E1, RB>(tw, smem_addr(xb), g, q);
+    const int io = zw_swz<RB>(q, g);
     // Rows of the 2N-point spectrum a reader holds: kb + 2 E1 k2.
     const int kb = (q & 7) + H * ((q >> 3) & 1) + E1 * (q >> 4);
     bool stored = false;
@@ -586,17 +591,17 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         CV v[16];
         if (!mbar_wait(bar, ph, status)) return;
         if constexpr (FWD) {
-            if (valid) yw_fwd_front<E1>(v, inb, io, zl, T);
+            if (valid) yw_fwd_front<E1, RB>(v, inb, io, zl, T);
             if (last_arrival(0) && more) issue_in(t + gridDim.x);
             if (!mbar_wait(bar + 1, ph, status)) return;  // the previous tile's store has read xb
-            if (valid) yw_fwd_back<E1>(v, zl, xb, kb, g);
+            if (valid) yw_fwd_back<E1, RB>(v, zl, xb, kb, g);
         } else {
-            if (valid) yw_inv<E1>(v, zl, xb, kb, io, g, T);
+            if (valid) yw_inv<E1, RB>(v, zl, xb, kb, io, g, T);
         }
         fence_proxy_async();
         if (last_arrival(1)) {
             tma_store_3d(&tout, xb, tx * Y::TC, 0, zz);
-            if (FWD) tma_store_3d(&tout, xb + N * 128, tx * Y::TC, N, zz);
+            if (FWD) tma_store_3d(&tout, xb + N * RB, tx * Y::TC, N, zz);
             bulk_commit();
             bulk_wait_read0();
             stored = true;

@@ -91,6 +91,7 @@ struct DevicePlan {
     CUtensorMap tm_y_in, tm_z_in, tm_z_sym, tm_yi_in;
     CUtensorMap tm_zw_in, tm_zw_sym, tm_zw_out;
     CUtensorMap tm_yw1, tm_yw2, tm_yw3;  // warp-form y passes: boxes of N rows (256 at N = 512) of w1, w2, w3
+    CUtensorMap tm_ywi1, tm_ywi3;        // warp-form y inverse (N <= 256): 8-column boxes of w1, w3
     CUtensorMap tm_rf;                   // fused forward x-y pass: N-row boxes of its ring in w3
 };
 
