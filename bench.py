@@ -45,8 +45,8 @@ KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_in
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; a
 # source change makes the figure stale and it is reported as null.
-NCU_TRAFFIC = {("de338054d7a4f472", "k_z_warp", 256): 358714368 + 236753152,
-               ("de338054d7a4f472", "k_z_w512", 512): 3106923776 + 2137003776}
+NCU_TRAFFIC = {("5d0ccd901c16210d", "k_z_warp", 256): 358001920 + 236691456,
+               ("5d0ccd901c16210d", "k_z_w512", 512): 3115268096 + 2137335296}
 
 
 def kernel_source_hash():
