@@ -365,6 +365,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
         const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
         const int kya = ky <= N ? ky : L - ky;
         const int col = tx * Z::TC + 2 * g;
@@ -585,6 +586,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
         const int tx = t % ntx, zz = z0 + t / ntx;
         const bool valid = tx * Y::TC + 2 * g < ncols;
         const bool more = t + (int)gridDim.x < ntiles;
@@ -737,6 +739,7 @@ k_x_warp_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__restr
     float2 f[2 * H], g[2 * H];
     if (i < npairs) xw_load<N>(rho, i, qq, f);
     for (; i < npairs; i += stride) {
+        if (i + stride >= npairs) griddep_launch();  // this half-warp's last row pair
 #pragma unroll
         for (int r = 0; r < 2 * H; ++r) g[r] = f[r];
         if (i + stride < npairs) xw_load<N>(rho, i + stride, qq, f);
@@ -835,6 +838,7 @@ k_x_warp_inv(const float2 *__restrict__ in, const PtrArray u, const float2 *__re
     const uint32_t xs = smem_addr(smraw + X::OFF_X) + 4096 * hw;
     const int stride = gridDim.x * (X::NT / 16);
     for (int i = blockIdx.x * (X::NT / 16) + hw; i < npairs; i += stride) {
+        if (i + stride >= npairs) griddep_launch();  // this half-warp's last row pair
         const float2 *s0 = in + (long long)(2 * i) * Px;
         const int b = (2 * i) / NN;
         float2 *d = reinterpret_cast<float2 *>(const_cast<void *>(u.p[b])) + (long long)(2 * i - b * NN) * (N / 2) + qq;
@@ -890,6 +894,7 @@ k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__rest
     float2 f[16];
     if (i < npairs) load(i, f);
     for (; i < npairs; i += stride) {
+        if (i + stride >= npairs) griddep_launch();  // this half-warp's last row pair
         CV v[16];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -1225,6 +1230,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
         const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
         const int kya = ky <= N ? ky : L - ky;
         const int col = tx * Z::TC + g;
@@ -1425,6 +1431,7 @@ k_y_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
+        if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
         const int tx = t % ntx, zz = z0 + t / ntx;
         const bool valid = tx * Z::TC + g < ncols;
         const bool more = t + (int)gridDim.x < ntiles;

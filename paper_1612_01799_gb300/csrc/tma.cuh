@@ -83,6 +83,10 @@ namespace gsp {
 // each calls this before its first access to memory that pass writes or reads.  A no-op
 // for a kernel launched without that attribute.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the kernel launched after this one on the stream start its CTAs early (they still
+// wait in griddep_wait until this grid has completed); every thread calls this once it has
+// begun its last piece of work, so the next pass's CTAs take the SMs this one leaves idle.
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Plain arrival (count 1) on an mbarrier.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
