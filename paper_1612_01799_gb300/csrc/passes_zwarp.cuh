@@ -458,7 +458,9 @@ namespace gsp {
 // The y passes with the transform halves of k_z_warp: the forward half (F1..F6) alone for
 // the y forward (N input rows, all 2N output rows kept), the adjoint half alone for the
 // y inverse (2N input rows, rows y < N kept).  Tile t = (tx, zz): TC columns kx, plane
-// zz = b N + z.  As in k_z_warp, warp g owns one 16-byte chunk of each row of the
+// zz = b N + z, planes in descending order: the x forward pass writes its rows in ascending
+// order and the x inverse reads them so, so each y pass starts on (or ends with) the planes
+// that L2 still holds.  As in k_z_warp, warp g owns one 16-byte chunk of each row of the
 // exchange/output buffer (g ^ (row & 7) in 128-byte rows, g ^ ((row >> 1) & 3) in 64-byte
 // rows), so a warp exchanges and writes its outputs in its own chunks without waiting for
 // the other warps; the last warp to finish a tile issues the TMA store.
@@ -557,7 +559,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     __syncthreads();
     griddep_wait();  // the previous pass has finished: its outputs are readable
     auto issue_in = [&](int t) {
-        const int tx = t % ntx, zz = z0 + t / ntx;
+        const int tx = t % ntx, zz = z0 + (ntiles / ntx - 1 - t / ntx);
         mbar_arrive_expect_tx(bar, (FWD ? 1 : 2) * N * RB);
         tma_load_3d(inb, &tin, bar, tx * Y::TC, 0, zz);
         if (!FWD) tma_load_3d(inb + N * RB, &tin, bar, tx * Y::TC, N, zz);
@@ -587,7 +589,7 @@ k_y_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
         if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
-        const int tx = t % ntx, zz = z0 + t / ntx;
+        const int tx = t % ntx, zz = z0 + (ntiles / ntx - 1 - t / ntx);
         const bool valid = tx * Y::TC + 2 * g < ncols;
         const bool more = t + (int)gridDim.x < ntiles;
         CV v[16];
