@@ -896,7 +896,6 @@ k_x_warp2_fwd(const PtrArray rho, float2 *__restrict__ out, const float2 *__rest
     float2 f[16];
     if (i < npairs) load(i, f);
     for (; i < npairs; i += stride) {
-        if (i + stride >= npairs) griddep_launch();  // this half-warp's last row pair
         CV v[16];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -1232,7 +1231,6 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
-        if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
         const int tx = t % ntx, ky = ky_of((t / ntx) % L), bb = t / (ntx * L);
         const int kya = ky <= N ? ky : L - ky;
         const int col = tx * Z::TC + g;
@@ -1433,7 +1431,6 @@ k_y_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     bool stored = false;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ph ^= 1) {
-        if (t + (int)gridDim.x >= ntiles) griddep_launch();  // this CTA's last tile
         const int tx = t % ntx, zz = z0 + t / ntx;
         const bool valid = tx * Z::TC + g < ncols;
         const bool more = t + (int)gridDim.x < ntiles;
