@@ -482,6 +482,29 @@ int poisson_noalloc_last_status(void *stream);
  */
 int poisson_noalloc_selftest_wait(long long polls, void *stream);
 
+/*
+ * The bounds-check flags of the debug build (libgspoisson_debug.so, the same sources
+ * compiled with GSP_DEBUG): in that build every shared-memory access of the pass kernels'
+ * access helpers is checked against the CTA's dynamic shared memory and the
+ * runtime-length forms check their computed row and symbol indices; an access that fails
+ * is skipped (a load yields zero; no trap) and sets a bit of a device-wide word.
+ *   flags   out: that word, bit 0 a shared-memory access out of bounds, bit 1 a global
+ *           index out of bounds (0: no violation since the last read), then cleared.
+ *   stream  synchronised before the read (order it after the solves it reports on).
+ * Returns POISSON_OK, or POISSON_ERR_UNSUPPORTED in the release build (flags set to 0),
+ * POISSON_ERR_ARG for a null flags pointer, POISSON_ERR_CUDA if the read fails.
+ */
+int poisson_debug_flags(unsigned int *flags, void *stream);
+
+/*
+ * Test hook of the debug build: one single-thread kernel evaluates the bounds checks on
+ * an address inside its dynamic shared memory (must pass), on one past its end and on the
+ * index -1 of a 10-element array (both must fail); the failing checks only set their
+ * flag bits (1 and 2), no access is made.  Read the result with poisson_debug_flags.
+ * Returns POISSON_ERR_UNSUPPORTED in the release build (nothing launched).
+ */
+int poisson_debug_selftest(void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,10 +1,15 @@
-"""ctypes binding of libgspoisson.so: signatures of include/poisson.h, nothing more."""
+"""ctypes binding of libgspoisson.so: signatures of include/poisson.h, nothing more.
+
+With POISSON_DEBUG=1 in the environment the binding loads the debug build instead
+(libgspoisson_debug.so: the same sources with bounds checks, built by
+build.build(debug=True))."""
 import ctypes
 import os
 import threading
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libgspoisson.so")
+DEBUG_LIB_PATH = os.path.join(PKG, "libgspoisson_debug.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "poisson.h")
 
 F32, F64 = 0, 1
@@ -50,6 +55,8 @@ SIGNATURES = {
     "poisson_slab_inverse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "poisson_plan_spectrum": (c_int, [c_void_p, c_int, P(c_void_p), P(ctypes.c_size_t), P(ctypes.c_size_t)]),
     "poisson_noalloc_selftest_wait": (c_int, [ctypes.c_longlong, c_void_p]),
+    "poisson_debug_flags": (c_int, [P(ctypes.c_uint), c_void_p]),
+    "poisson_debug_selftest": (c_int, [c_void_p]),
     "poisson_sample_gaussians": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p]),
     "poisson_gaussian_potential": (c_int, [c_int, c_double, c_int, P(c_double), c_int, c_void_p, c_void_p,
                                            c_void_p]),
@@ -82,15 +89,21 @@ KNOB_CORRECTION = 4
 KNOB_ARITH = 5
 
 
+def debug_requested():
+    return os.environ.get("POISSON_DEBUG", "") == "1"
+
+
 def load():
-    """Load the in-tree library.  There is no fallback: without it nothing can run."""
+    """Load the in-tree library (its debug build with POISSON_DEBUG=1).  There is no
+    fallback: without it nothing can run."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise ImportError("libgspoisson.so is not built (%s); run "
-                                  "paper_1612_01799_gb300.build.build() first" % LIB_PATH)
-            lib = ctypes.CDLL(LIB_PATH)
+            path = DEBUG_LIB_PATH if debug_requested() else LIB_PATH
+            if not os.path.exists(path):
+                raise ImportError("%s is not built; run paper_1612_01799_gb300.build.build(%s) first"
+                                  % (path, "debug=True" if debug_requested() else ""))
+            lib = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 f = getattr(lib, name)
                 f.restype = res

@@ -31,6 +31,8 @@
 
 #include <cstdint>
 
+#include "debug.cuh"
+
 namespace gsp {
 
 // ---- complex types and their arithmetic --------------------------------------------------

@@ -73,7 +73,7 @@ __device__ C *any_fft(C *a, C *b, int logT, int P, const AnySched &s, const TW *
 #pragma unroll
             for (int r = 0; r < 5; ++r) {
                 if (r < R) {
-                    x[r] = a[(j + r * LR) * P + c];
+                    x[r] = sm_ld(a + (j + r * LR) * P + c);
                     if (r > 0 && Ns > 1) x[r] = twmul<D>(x[r], __ldg(tw + r * k * tws));
                 }
             }
@@ -81,7 +81,7 @@ __device__ C *any_fft(C *a, C *b, int logT, int P, const AnySched &s, const TW *
             const int base = jh * NsR + k;
 #pragma unroll
             for (int r = 0; r < 5; ++r)
-                if (r < R) b[(base + r * Ns) * P + c] = x[r];
+                if (r < R) sm_st(b + (base + r * Ns) * P + c, x[r]);
         }
         __syncthreads();
         C *t = a;
@@ -115,11 +115,11 @@ __global__ void k_any_x_fwd(const PtrArray rho, Cx2<Real> *__restrict__ out, con
     for (int e = threadIdx.x; e < TR * n; e += blockDim.x) {
         const int r = rdiv(e, rn), m = e - r * n;
         C v = czero<C>();
-        if (r < nr && m < h) {
+        if (r < nr && m < h && dbg_index_ok(rows.row(r), rows_b)) {
             const X2 f = __ldg(reinterpret_cast<const X2 *>(rho.p[rows.density(r)]) + rows.row(r) * h + m);
             v = C{f.x, f.y};
         }
-        a[m * P + r] = v;
+        sm_st(a + m * P + r, v);
     }
     const C *y = any_fft<-1>(a, b, logTR, P, s, tw, 2);
     // X_k = Ev_k + W_{2n}^k Od_k, X_{n-k} = conj(Ev_k - W_{2n}^k Od_k), with Ev, Od the DFTs
@@ -128,7 +128,7 @@ __global__ void k_any_x_fwd(const PtrArray rho, Cx2<Real> *__restrict__ out, con
         const int r = rdiv(e, rh1), k = e - r * (h + 1);
         {
             Cx2<Real> *dst = out + (r0 + r) * Px;
-            const C ck = y[k * P + r], cn = y[(k == 0 ? 0 : n - k) * P + r];
+            const C ck = sm_ld(y + k * P + r), cn = sm_ld(y + (k == 0 ? 0 : n - k) * P + r);
             const C ev = {(Real)0.5 * (ck.re + cn.re), (Real)0.5 * (ck.im - cn.im)};
             const C od = {(Real)0.5 * (ck.im + cn.im), (Real)0.5 * (cn.re - ck.re)};
             if (k == 0) {
@@ -167,18 +167,18 @@ __global__ void k_any_x_inv(const Cx2<Real> *__restrict__ in, const PtrArray u, 
         {
             const Cx2<Real> *src = r < nr ? in + (r0 + r) * Px : nullptr;
             if (!src) {
-                a[k * P + r] = czero<C>();
-                if (k > 0 && 2 * k != n) a[(n - k) * P + r] = czero<C>();
+                sm_st(a + k * P + r, czero<C>());
+                if (k > 0 && 2 * k != n) sm_st(a + (n - k) * P + r, czero<C>());
                 continue;
             }
             const C yk = ws_c(src[k]), yn = ws_c(src[n - k]);
             if (k == 0) {
-                a[r] = C{yk.re + yn.re, yk.re - yn.re};
+                sm_st(a + r, C{yk.re + yn.re, yk.re - yn.re});
             } else {
                 const C ev = {yk.re + yn.re, yk.im - yn.im};
                 const C od = twmul<1>(C{yk.re - yn.re, yk.im + yn.im}, __ldg(tw + k));
-                a[k * P + r] = add_rot<1>(ev, od);
-                if (2 * k != n) a[(n - k) * P + r] = add_rot<1>(C{ev.re, -ev.im}, C{od.re, -od.im});
+                sm_st(a + k * P + r, add_rot<1>(ev, od));
+                if (2 * k != n) sm_st(a + (n - k) * P + r, add_rot<1>(C{ev.re, -ev.im}, C{od.re, -od.im}));
             }
         }
     }
@@ -186,8 +186,9 @@ __global__ void k_any_x_inv(const Cx2<Real> *__restrict__ in, const PtrArray u, 
     const AnyRows rows(r0, rows_b);
     for (int e = threadIdx.x; e < nr * h; e += blockDim.x) {
         const int r = rdiv(e, rh), m = e - r * h;
+        if (!dbg_index_ok(rows.row(r), rows_b)) continue;
         X2 *dst = reinterpret_cast<X2 *>(const_cast<void *>(u.p[rows.density(r)])) + rows.row(r) * h;
-        dst[m] = c_ext(y[m * P + r]);
+        dst[m] = c_ext(sm_ld(y + m * P + r));
     }
 }
 
@@ -210,13 +211,13 @@ __global__ void k_any_col(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restric
     const Cx2<Real> *src = in + plane * in_outer + c0;
     for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
         const int row = e >> logTC, c = e & (TC - 1);
-        a[e] = row < nin && c0 + c < ncols ? ws_c(src[row * in_row + c]) : czero<C>();
+        sm_st(a + e, row < nin && c0 + c < ncols ? ws_c(src[row * in_row + c]) : czero<C>());
     }
     const C *y = any_fft<FWD ? -1 : 1>(a, b, logTC, TC, s, tw, 1);
     Cx2<Real> *dst = out + plane * out_outer + c0;
     for (int e = threadIdx.x; e < nout * TC; e += blockDim.x) {
         const int row = e >> logTC, c = e & (TC - 1);
-        if (c0 + c < ncols) st_ws(dst + row * out_row + c, y[e]);
+        if (c0 + c < ncols) st_ws(dst + row * out_row + c, sm_ld(y + e));
     }
 }
 
@@ -245,7 +246,7 @@ __global__ void k_any_z(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict_
     const long long base = ((long long)bb * nz * Ly + ky) * Px + c0;
     for (int e = threadIdx.x; e < Lz * TC; e += blockDim.x) {
         const int row = e >> logTC, c = e & (TC - 1);
-        a[e] = row < nz && c0 + c < ncols ? ws_c(in[base + row * zs + c]) : czero<C>();
+        sm_st(a + e, row < nz && c0 + c < ncols ? ws_c(in[base + row * zs + c]) : czero<C>());
     }
     C *y = any_fft<-1>(a, b, logTC, TC, s, tw, 1);
     C *other = y == a ? b : a;
@@ -257,13 +258,14 @@ __global__ void k_any_z(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict_
         const int kx = c0 + c;
         if (kx >= ncols) continue;
         const int kz = row <= nz ? row : Lz - row;
+        if (!dbg_index_ok(kz, nz + 1) || !dbg_index_ok(kya, ny + 1)) continue;
         if constexpr (TAIL) {
             const float wgt = (kx == 0 || kx == nx) ? 1.f : 2.f;
-            const float en = wgt * cenergy(y[e]);
+            const float en = wgt * cenergy(sm_ld(y + e));
             etot += en;
             if (kx >= nx - nx / 8 || kya >= ny - ny / 8 || kz >= nz - nz / 8) eshell += en;
         }
-        y[e] = cscale(y[e], srow[kz * splane + c]);
+        sm_st(y + e, cscale(sm_ld(y + e), srow[kz * splane + c]));
     }
     if constexpr (TAIL) {
 #pragma unroll
@@ -279,7 +281,7 @@ __global__ void k_any_z(const Cx2<Real> *__restrict__ in, Cx2<Real> *__restrict_
     const C *z = any_fft<1>(y, other, logTC, TC, s, tw, 1);
     for (int e = threadIdx.x; e < nz * TC; e += blockDim.x) {
         const int row = e >> logTC, c = e & (TC - 1);
-        if (c0 + c < ncols) st_ws(out + base + row * zs + c, z[e]);
+        if (c0 + c < ncols) st_ws(out + base + row * zs + c, sm_ld(z + e));
     }
 }
 

@@ -163,11 +163,13 @@ template <int RB> __device__ __forceinline__ int zw_swz(int row, int g) {
 
 // Exchange slots by shared-memory address (layout re.x, re.y, im.x, im.y).
 __device__ __forceinline__ void zw_sts(uint32_t a, CV x) {
+    if (!dbg_smem_ok(a, 16)) return;
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x.re.x), "f"(x.re.y), "f"(x.im.x),
                  "f"(x.im.y)
                  : "memory");
 }
 __device__ __forceinline__ CV zw_lds(uint32_t a) {
+    if (!dbg_smem_ok(a, 16)) return czero<CV>();
     float4 f;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(f.x), "=f"(f.y), "=f"(f.z), "=f"(f.w)
@@ -223,7 +225,7 @@ template <int E1> __device__ __forceinline__ void zw_front(CV *v, const ZwLane &
     using M = ZwMap<E1>;
     zw_f1<E1>(v);
 #pragma unroll
-    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<-1>(v[j], T[(M::inK(j) ? z.tkb : z.tnb) + 32 * M::kappa0(j)]);
+    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<-1>(v[j], sm_ld(T + (M::inK(j) ? z.tkb : z.tnb) + 32 * M::kappa0(j)));
 #pragma unroll
     for (int j = 0; j < E1; ++j) {
         if (!M::inK(j)) continue;
@@ -287,7 +289,7 @@ template <int E1> __device__ __forceinline__ void zw_back(CV *v, const ZwLane &z
         v[M::partner(j)] = zw_shfl16(csub(a, b));
     }
 #pragma unroll
-    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<1>(v[j], T[(M::inK(j) ? z.tkb : z.tnb) + 32 * M::kappa0(j)]);
+    for (int j = 0; j < E1; ++j) v[j] = zw_twmul<1>(v[j], sm_ld(T + (M::inK(j) ? z.tkb : z.tnb) + 32 * M::kappa0(j)));
     zw_f1_adj<E1>(v);
 }
 
@@ -375,7 +377,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) {
 #pragma unroll
             for (int r = 0; r < H; ++r) {
-                const float4 f = *reinterpret_cast<const float4 *>(Bb + io + 32 * RB * r);
+                const float4 f = sm_ld(reinterpret_cast<const float4 *>(Bb + io + 32 * RB * r));
                 v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
                 if (r & 1) v[r] = zw_sign(v[r], zl.sg);
             }
@@ -419,8 +421,8 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             for (int k2 = 0; k2 < 16; ++k2) {
                 const int kz = k2 < 8 ? kb + 2 * E1 * k2 : L - kb - 2 * E1 * k2;
                 const unsigned char *sp = symg + (kz >> 7) * (Z::SYM_KZB * Z::TC * 4) + 4 * (kz & (Z::SYM_KZB - 1));
-                v[k2] = cscale2(v[k2], f2(*reinterpret_cast<const float *>(sp),
-                                          *reinterpret_cast<const float *>(sp + Z::SYM_KZB * 4)));
+                v[k2] = cscale2(v[k2], f2(sm_ld(reinterpret_cast<const float *>(sp)),
+                                          sm_ld(reinterpret_cast<const float *>(sp + Z::SYM_KZB * 4))));
             }
         }
         if (last_arrival(1) && t + (int)gridDim.x < ntiles) issue_in(t + gridDim.x);
@@ -435,7 +437,7 @@ k_z_warp(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             for (int r = 0; r < H; ++r) {
                 CV x = v[r];
                 if (r & 1) x = zw_sign(x, zl.sg);
-                *reinterpret_cast<float4 *>(xo + io + 32 * RB * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+                sm_st(reinterpret_cast<float4 *>(xo + io + 32 * RB * r), make_float4(x.re.x, x.im.x, x.re.y, x.im.y));
             }
         }
         fence_proxy_async();
@@ -489,7 +491,7 @@ template <int E1, int RB>
 __device__ __forceinline__ void yw_fwd_front(CV *v, const unsigned char *inb, int io, const ZwLane &zl, const float2 *T) {
 #pragma unroll
     for (int r = 0; r < E1 / 2; ++r) {
-        const float4 f = *reinterpret_cast<const float4 *>(inb + io + 32 * RB * r);
+        const float4 f = sm_ld(reinterpret_cast<const float4 *>(inb + io + 32 * RB * r));
         v[r] = {f2(f.x, f.z), f2(f.y, f.w)};
         if (r & 1) v[r] = zw_sign(v[r], zl.sg);
     }
@@ -505,8 +507,8 @@ __device__ __forceinline__ void yw_fwd_back(CV *v, const ZwLane &zl, unsigned ch
     if (zl.rd) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2)
-            *reinterpret_cast<float4 *>(xb + zw_swz<RB>(kb + 2 * E1 * k2, g)) =
-                make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y);
+            sm_st(reinterpret_cast<float4 *>(xb + zw_swz<RB>(kb + 2 * E1 * k2, g)),
+                  make_float4(v[k2].re.x, v[k2].im.x, v[k2].re.y, v[k2].im.y));
     }
 }
 // y inverse of warp g's column pair: the 2N spectrum rows from xb, the N kept rows back to xb
@@ -517,7 +519,7 @@ __device__ __forceinline__ void yw_inv(CV *v, const ZwLane &zl, unsigned char *x
     if (zl.rd) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
-            const float4 f = *reinterpret_cast<const float4 *>(xb + zw_swz<RB>(kb + 2 * E1 * k2, g));
+            const float4 f = sm_ld(reinterpret_cast<const float4 *>(xb + zw_swz<RB>(kb + 2 * E1 * k2, g)));
             v[k2] = {f2(f.x, f.z), f2(f.y, f.w)};
         }
         dft<16, 1>(v);
@@ -530,7 +532,7 @@ __device__ __forceinline__ void yw_inv(CV *v, const ZwLane &zl, unsigned char *x
     for (int r = 0; r < E1 / 2; ++r) {
         CV x = v[r];
         if (r & 1) x = zw_sign(x, zl.sg);
-        *reinterpret_cast<float4 *>(xb + io + 32 * RB * r) = make_float4(x.re.x, x.im.x, x.re.y, x.im.y);
+        sm_st(reinterpret_cast<float4 *>(xb + io + 32 * RB * r), make_float4(x.re.x, x.im.x, x.re.y, x.im.y));
     }
 }
 
@@ -1106,9 +1108,11 @@ __host__ __device__ constexpr int w512_kappa(int j) { return j < 16 ? 2 * j : 2 
 __device__ __forceinline__ int sw64(int z, int c) { return z * 64 + ((((c >> 1) ^ (z >> 1)) & 3) << 4) + ((c & 1) << 3); }
 
 __device__ __forceinline__ void sts2(uint32_t a, CF x) {
+    if (!dbg_smem_ok(a, 8)) return;
     asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x.re), "f"(x.im) : "memory");
 }
 __device__ __forceinline__ CF lds2(uint32_t a) {
+    if (!dbg_smem_ok(a, 8)) return czero<CF>();
     float2 f;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(f.x), "=f"(f.y) : "r"(a) : "memory");
     return {f.x, f.y};
@@ -1116,17 +1120,21 @@ __device__ __forceinline__ CF lds2(uint32_t a) {
 
 // Shared 32-bit access by address.
 __device__ __forceinline__ void sts1(uint32_t a, float x) {
+    if (!dbg_smem_ok(a, 4)) return;
     asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(x) : "memory");
 }
 __device__ __forceinline__ float lds1(uint32_t a) {
+    if (!dbg_smem_ok(a, 4)) return 0.f;
     float f;
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(f) : "r"(a) : "memory");
     return f;
 }
 __device__ __forceinline__ void sts2f(uint32_t a, float2 x) {
+    if (!dbg_smem_ok(a, 8)) return;
     asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x.x), "f"(x.y) : "memory");
 }
 __device__ __forceinline__ float2 lds2f(uint32_t a) {
+    if (!dbg_smem_ok(a, 8)) return make_float2(0.f, 0.f);
     float2 f;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(f.x), "=f"(f.y) : "r"(a) : "memory");
     return f;
@@ -1226,7 +1234,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
     const uint32_t ar = xw + 128 * q + 8 * (q & 15);   // reader (lane l = q): pair i at ar ^ 8 i
     // Symbol value at kz <= N for this lane's column.
     auto sym_at = [&](int kz) {
-        return *reinterpret_cast<const float *>(Bb + (kz >> 8) * (Z::SYM_BOX * Z::TC * 4) + 1024 * g + 4 * (kz & 255));
+        return sm_ld(reinterpret_cast<const float *>(Bb + (kz >> 8) * (Z::SYM_BOX * Z::TC * 4) + 1024 * g + 4 * (kz & 255)));
     };
     bool stored = false;
     uint32_t ph = 0;
@@ -1242,7 +1250,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid && !bad) {
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
-                const float2 f = *reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g));
+                const float2 f = sm_ld(reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g)));
                 const CF x = {f.x, f.y};
                 u[r] = cv_pair(x, w32mul<-1>(x, r));
             }
@@ -1251,7 +1259,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
         if (valid) {
             dft<16, -1>(u);  // u[m] = (A[2m], A[2m + 1])
 #pragma unroll
-            for (int m = 0; m < 16; ++m) u[m] = twmul<-1>(u[m], T4[m * 32 + q]);
+            for (int m = 0; m < 16; ++m) u[m] = twmul<-1>(u[m], sm_ld(T4 + m * 32 + q));
         }
         if (!bad) bad = !mbar_wait(bar + 2, ph, status);  // the previous tile's store has read XO
         if (valid) {
@@ -1325,7 +1333,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
                 u[m] = {f2(lds1(sa), lds1(sb)), f2(lds1(sa + 4096), lds1(sb + 4096))};
             }
 #pragma unroll
-            for (int m = 0; m < 16; ++m) u[m] = twmul<1>(u[m], T4[m * 32 + q]);
+            for (int m = 0; m < 16; ++m) u[m] = twmul<1>(u[m], sm_ld(T4 + m * 32 + q));
             dft<16, 1>(u);  // u[r] = (a_r, b_r)
         }
         // Every warp's exchange reads are done: XO takes the output tile.
@@ -1334,7 +1342,7 @@ k_z_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
                 const CF z = cadd(cv_lo(u[r]), w32mul<1>(cv_hi(u[r]), r));  // adjoint of F1, row q + 32 r
-                *reinterpret_cast<float2 *>(xo + sw64(q + 32 * r, g)) = make_float2(z.re, z.im);
+                sm_st(reinterpret_cast<float2 *>(xo + sw64(q + 32 * r, g)), make_float2(z.re, z.im));
             }
         }
         fence_proxy_async();
@@ -1440,7 +1448,7 @@ k_y_w512(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtens
             if (valid && !bad) {
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
-                    const float2 f = *reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g));
+                    const float2 f = sm_ld(reinterpret_cast<const float2 *>(Bb + sw64(q + 32 * r, g)));
                     v[r] = {f.x, f.y};
                 }
             }

@@ -124,3 +124,22 @@ def test_product_path_has_no_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_release_build_has_no_debug_flags(lib):
+    """The bounds-check word exists only in the debug build: the release library answers
+    POISSON_ERR_UNSUPPORTED with the flags zeroed, and a null pointer is an argument error
+    (no device work in either case)."""
+    flags = ctypes.c_uint(7)
+    assert lib.poisson_debug_flags(ctypes.byref(flags), None) == -4
+    assert flags.value == 0
+    assert lib.poisson_debug_flags(None, None) == -1
+    assert lib.poisson_debug_selftest(None) == -4
+
+
+def test_debug_build_is_selected_by_the_environment(monkeypatch):
+    """POISSON_DEBUG=1 points the binding at libgspoisson_debug.so (and nothing else)."""
+    monkeypatch.setenv("POISSON_DEBUG", "1")
+    assert _lib.debug_requested()
+    monkeypatch.setenv("POISSON_DEBUG", "0")
+    assert not _lib.debug_requested()
