@@ -445,11 +445,11 @@ struct Stages<C, L, E, D, NS, Radices<R, Rs...>> {
             }
         } else {
             sync();  // every read of sm before this stage is done
-            S::template scatter<false>(v, q, [&](int row, C x) { sm[at(row)] = x; });
+            S::template scatter<false>(v, q, [&](int row, C x) { sm_st(sm + at(row), x); });
             sync();
             constexpr RunOpt next{false, false, O.to_regs, O.prune_out, O.sync_last};
             Stages<C, L, E, D, NS * R, Radices<Rs...>>::template run_with<next>(
-                v, q, sm, tw, twstride, [&](int row) { return sm[at(row)]; }, st, at, sync);
+                v, q, sm, tw, twstride, [&](int row) { return sm_ld(sm + at(row)); }, st, at, sync);
         }
     }
 

@@ -101,22 +101,22 @@ template <typename Real, int L, int KIND> struct TmaLayout {
 
 template <typename C> __device__ __forceinline__ C ld_sm_cc(const unsigned char *p);
 template <> __device__ __forceinline__ CV ld_sm_cc<CV>(const unsigned char *p) {
-    const float4 f = *reinterpret_cast<const float4 *>(p);
+    const float4 f = sm_ld(reinterpret_cast<const float4 *>(p));
     return {make_float2(f.x, f.z), make_float2(f.y, f.w)};
 }
 template <> __device__ __forceinline__ CD ld_sm_cc<CD>(const unsigned char *p) {
-    const double2 f = *reinterpret_cast<const double2 *>(p);
+    const double2 f = sm_ld(reinterpret_cast<const double2 *>(p));
     return {f.x, f.y};
 }
 template <> __device__ __forceinline__ CDF ld_sm_cc<CDF>(const unsigned char *p) {
-    const float4 f = *reinterpret_cast<const float4 *>(p);
+    const float4 f = sm_ld(reinterpret_cast<const float4 *>(p));
     return {DF(f.x, f.y), DF(f.z, f.w)};
 }
 __device__ __forceinline__ CV scale_sym_sm(CV x, const float *s) {
-    return cscale2(x, *reinterpret_cast<const float2 *>(s));
+    return cscale2(x, sm_ld(reinterpret_cast<const float2 *>(s)));
 }
-__device__ __forceinline__ CD scale_sym_sm(CD x, const double *s) { return cscale(x, *s); }
-__device__ __forceinline__ CDF scale_sym_sm(CDF x, const DF *s) { return cscale(x, *s); }
+__device__ __forceinline__ CD scale_sym_sm(CD x, const double *s) { return cscale(x, sm_ld(s)); }
+__device__ __forceinline__ CDF scale_sym_sm(CDF x, const DF *s) { return cscale(x, sm_ld(s)); }
 
 // Blocks per SM requested from the compiler: a register budget of 64 per thread for E <= 8
 // values per thread, 128 otherwise.
@@ -540,7 +540,7 @@ k_z_split_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ C
             const int j = qh + PH * b;
 #pragma unroll
             for (int r = 0; r < R0; ++r)
-                if ((2 * r < R0) == (h != 0)) xb[(j + r * (N / R0)) * NG + g] = v[b * R0 + r];
+                if ((2 * r < R0) == (h != 0)) sm_st(xb + (j + r * (N / R0)) * NG + g, v[b * R0 + r]);
         }
         __syncthreads();
         Cx2<Real> *dst = out + ((long long)bb * N * L + ky) * Px + col;
