@@ -53,13 +53,15 @@ struct CV {
 // two-sum of the leading parts (the operands ordered by magnitude, then Dekker's fast
 // two-sum), which yields the exact rounding error of that FP32 addition, and add it and
 // both lo parts in FP32 without renormalising: the result's lo may exceed ulp(hi) / 2 by
-// the few units a chain of sums collects (a product renormalises).  Products use the exact
-// product of an FP32 multiplication that the fused multiply-add gives (fma(a, b, -ab) = the
-// error of ab), the cross terms hi x lo, and a fast two-sum that renormalises (hi, lo).
+// the few units a chain of operations collects.  Products use the exact product of an FP32
+// multiplication that the fused multiply-add gives (fma(a, b, -ab) = the error of ab) and
+// the cross terms hi x lo; a lone product renormalises (hi, lo) with a fast two-sum, the
+// fused a b + c d of the complex products (df_sum_prod) leaves it unnormalised as well.
 // The error of a sum is at most about 2^-47 (|a| + |b|) for operands whose lo holds a few
 // units of ulp(hi), of a product about 2^-47 |a| |b| (the lo x lo term is dropped): the
-// norm-wise error model of an FFT in FP64.  Leaving sums unnormalised took the FP64 plan's
-// solve at N = 256 from 2.43 to 2.10 ms, within the same 1e-12 bar against the oracle.  The _rn
+// norm-wise error model of an FFT in FP64.  Leaving sums and the fused products
+// unnormalised took the FP64 plan's solve at N = 256 from 2.43 to 2.05 ms, within the same
+// 1e-12 bar against the oracle.  The _rn
 // intrinsics keep the compiler from contracting or reassociating the error terms.
 struct DF {
     float hi, lo;
@@ -98,9 +100,9 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
 }
 
 // a b + c d in one pass: the two leading products and their exact errors (FMA), one
-// two-sum of the products, the cross terms hi x lo accumulated in FP32, one renormalisation:
-// 16 FP32 operations and 3 selects instead of 22 and 6 for two products and a sum, with the
-// same error bound (the lo x lo terms dropped, about 2^-47 (|ab| + |cd|)).
+// two-sum of the products, the cross terms hi x lo accumulated in FP32, no renormalisation:
+// 13 FP32 operations and 3 selects, with the error bound of two products and a sum (the
+// lo x lo terms dropped, about 2^-47 (|ab| + |cd|)).
 __device__ __forceinline__ DF df_sum_prod(DF a, DF b, DF c, DF d) {
     const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
     const float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
@@ -111,7 +113,7 @@ __device__ __forceinline__ DF df_sum_prod(DF a, DF b, DF c, DF d) {
     t = __fmaf_rn(a.lo, b.hi, t);
     t = __fmaf_rn(c.hi, d.lo, t);
     t = __fmaf_rn(c.lo, d.hi, t);
-    return df_fast_two_sum(s, t);
+    return DF(s, t);  // left unnormalised, as a sum's result
 }
 
 struct CDF {
