@@ -45,8 +45,8 @@ KERNEL_NAMES = ["k_x_forward", "k_col<fwd>", "k_z_symbol", "k_col<inv>", "k_x_in
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; a
 # source change makes the figure stale and it is reported as null.
-NCU_TRAFFIC = {("7610356bafaa458a", "k_z_warp", 256): 358238208 + 236680192,
-               ("7610356bafaa458a", "k_z_w512", 512): 3127258880 + 2137626112}
+NCU_TRAFFIC = {("6acf6ecbe1e2131e", "k_z_warp", 256): 358141440 + 236751872,
+               ("6acf6ecbe1e2131e", "k_z_w512", 512): 3114766848 + 2138680576}
 
 
 def kernel_source_hash():
