@@ -43,3 +43,17 @@ def test_pass_table_fused_drops_w1():
     assert fused[0][3] == b[0] + b[1] - 2 * w1
     assert fused[2][3] == b[3] + b[4] - 2 * w1
     assert fused[1][3] == b[2]
+
+
+def test_traffic_table_is_current_and_plausible():
+    """Each DRAM traffic figure bench.py reports was taken on the kernel sources as they are
+    (its key carries their hash; a stale figure would be reported as null, so a committed
+    one must match), and lies between the z pass's algorithmic bytes and those plus the
+    symbol octant read twice (the excess ncu showed at N = 512)."""
+    import bench
+    h = bench.kernel_source_hash()
+    assert bench.NCU_TRAFFIC, "no traffic figure"
+    for (key_hash, kernel, N), traffic in bench.NCU_TRAFFIC.items():
+        assert key_hash == h, (kernel, N)
+        alg = bench.pass_bytes(N, 4)[2]
+        assert alg <= traffic <= alg + 2 * bench.symbol_bytes(N, 4), (kernel, N, traffic)
